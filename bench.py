@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""Benchmark of the hot path: circulation-based identification (Sec. 2.2.2,
+Eq. 5) plus plain density-guided localization (Sec. 3.3.3, Eq. 6) of every
+pierced plaquette, on a 512^3 complex64 random-wave tangle (16384 waves,
+|k| in [0.15, 0.35] rad/h, 5% multiplicative amplitude noise; seeds 7 / 8).
+
+One step = qtv_identify (sweep + segment scan + scatter) + qtv_localize over
+the whole field, inputs resident in HBM (1 GiB field: larger than the 129 MB
+L2, so no flush is needed).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl qtv|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica on its own GPU
+(weak scaling; the path needs no data exchange), and the value is the total
+grid points of all ranks over the slowest rank's time.  The reference arm
+(--impl reference) times the FP64 CPU oracle on the host cores on a bounded
+slab of the same field.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("grid points/s and HBM GB/s (identify+localize) vs peak; learned vs plain at "
+          "≤0.05h")
+UNIT = "grid points/s"
+WORKLOAD = ("512^3 complex64 random-wave tangle: 16384 plane waves, |k| uniform in "
+            "[0.15,0.35] rad/h, random directions, CN(0,1/W) amplitudes (seed 7), x (1+0.05 g) "
+            "real multiplicative noise (seed 8); plain identify + localize")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["qtv", "reference"], default="qtv")
+    p.add_argument("--n", type=int, default=512, help="grid edge (default 512)")
+    p.add_argument("--cpu-planes", type=int, default=48,
+                   help="planes of the field in the oracle's timed CPU sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=20)
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled in the background."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [c.strip() for c in line.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [r for t, r in self.rows if t0 <= t <= t1] or [r for _, r in self.rows]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if len(r) > 4 + i and r[4 + i].lower().startswith("active")})
+        pw = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def make_field(n, device):
+    import synth
+
+    if n == 512:
+        return synth.config_field("512_waves_noise", device=device)
+    psi = synth.random_waves((n, n, n), synth.wave_spec(7, 16384 if n >= 512 else 4096),
+                             device=device)
+    return synth.multiplicative_noise(psi, 8)
+
+
+def oracle_sample(psi_host_slab, planes):
+    """Oracle identify + localize on planes [0, planes) of a slab (with one halo
+    plane); returns (seconds, nodes, faces)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    w, fl = oracle.identify(psi_host_slab, k0=0, k1=planes)
+    ids, wind = oracle.face_list(w)
+    oracle.localize(psi_host_slab, ids, wind)
+    dt = time.perf_counter() - t0
+    nz, ny, nx = psi_host_slab.shape
+    return dt, planes * ny * nx, len(ids)
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+
+    n = args.n
+    planes = max(1, min(args.cpu_planes, n - 1))
+    try:
+        import torch
+
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+    except Exception:
+        dev = None
+    # the slab [0, planes] of the same field (input preparation, untimed)
+    spec = synth.wave_spec(7, 16384 if n >= 512 else 4096)
+    if dev is not None:
+        import torch
+
+        z = synth.random_waves((n, n, n), spec, device=dev) if dev == "cuda" else None
+        if z is not None:
+            slab = synth.multiplicative_noise(z, 8)[: planes + 1].cpu().numpy()
+            del z
+            torch.cuda.empty_cache()
+        else:
+            slab = synth.multiplicative_noise(
+                synth.random_waves_numpy((planes + 1, n, n), spec), 8)
+    else:
+        slab = synth.multiplicative_noise(synth.random_waves_numpy((planes + 1, n, n), spec), 8)
+    slab = np.ascontiguousarray(slab)
+    oracle.set_threads(cpu_cores())
+    # size each step so that K steps take about a minute of host time
+    dt1, _, _ = oracle_sample(slab[:2], 1)
+    budget = 60.0 / max(1, args.steps)
+    planes = int(max(1, min(planes, budget / max(dt1, 1e-6))))
+    slab = np.ascontiguousarray(slab[: planes + 1])
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_sample(slab, planes)
+    times = []
+    nodes = 0
+    for _ in range(args.steps):
+        dt, nodes, faces = oracle_sample(slab, planes)
+        times.append(dt)
+    total = sum(times)
+    value = nodes * len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"planes 0..{planes - 1}"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(),
+                         "kind": "oracle",
+                         "sample": f"{planes} z-planes of the {n}^3 field ({nodes} nodes), "
+                                   "FP64 identify + localize per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_qtv(args):
+    import torch
+
+    import paper_1911_12070_gb300 as qtv
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    qtv.build()
+    q = qtv.Qtv(dev.index)
+    n = args.n
+    psi = make_field(n, dev)
+    torch.cuda.synchronize()
+    nodes = n ** 3
+    stream = torch.cuda.current_stream()
+
+    # size the outputs from one untimed call
+    ids0, w0, _ = q.identify(psi)
+    F = ids0.numel()
+    cap = int(F * 1.05) + 1024
+    del ids0, w0
+    q.reserve(tuple(psi.shape), cap)
+    ids = torch.empty(cap, dtype=torch.int64, device=dev)
+    wnd = torch.empty(cap, dtype=torch.int8, device=dev)
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    xyz = torch.empty((cap, 3), dtype=torch.float32, device=dev)
+    resid = torch.empty(cap, dtype=torch.float32, device=dev)
+    flags = torch.empty(cap, dtype=torch.uint8, device=dev)
+
+    def step():
+        q.identify_into(psi, ids, wnd, count)
+        q.localize_into(psi, ids, wnd, xyz, resid, flags, n=cap, n_dev=count)
+
+    clk = ClockSampler(dev.index)
+    clk.start()
+    # soak (untimed) so the clock sampler sees the GPU under load
+    t_end = time.time() + 1.5
+    while time.time() < t_end:
+        for _ in range(20):
+            step()
+        torch.cuda.synchronize()
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    q.trace_enable(True)
+    q.trace_read(reset=True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    q.trace_enable(False)
+    trace = q.trace_read(reset=True)
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    F = int(count.item())
+    clocks = clk.summary(t0 - 2.0, t1)
+
+    # ---- end to end through the public API: pinned host field in, samples out
+    host_psi = torch.empty(psi.shape, dtype=torch.complex64, pin_memory=True)
+    host_psi.copy_(psi)
+    host_out = torch.empty(cap * 32, dtype=torch.uint8, pin_memory=True)
+    psi_e2e = torch.empty_like(psi)
+    lib = qtv.lib()
+    import ctypes
+
+    def e2e_step():
+        psi_e2e.copy_(host_psi, non_blocking=True)
+        q.identify_into(psi_e2e, ids, wnd, count)
+        q.localize_into(psi_e2e, ids, wnd, xyz, resid, flags, n=cap, n_dev=count)
+        # emission needs the sample count on the host
+        nf = int(count.item())
+        rc = lib.qtv_emit_samples(q.h, nf, ctypes.c_void_p(ids.data_ptr()),
+                                  ctypes.c_void_p(wnd.data_ptr()), ctypes.c_void_p(xyz.data_ptr()),
+                                  ctypes.c_void_p(resid.data_ptr()),
+                                  ctypes.c_void_p(flags.data_ptr()),
+                                  ctypes.c_void_p(host_out.data_ptr()),
+                                  ctypes.c_void_p(stream.cuda_stream))
+        assert rc == 0, lib.qtv_last_error_string()
+        return nf
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    ke = max(1, args.e2e_steps)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    d2h = 0
+    e0.record(stream)
+    for _ in range(ke):
+        d2h += e2e_step() * 32
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1)
+    if ws > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    clk.stop()
+
+    # ---- roofline of the dominant kernel (the sweep)
+    peak, peak_kind = peaks()
+    nbands = (n + 6) // 7
+    nseg = n * nbands
+    sweep_launches, sweep_ms = trace.get("sweep", (0, 0.0))
+    sweep_avg_ms = sweep_ms / max(1, sweep_launches)
+    sweep_bytes = 8 * nodes + 4 * F + 8 * nseg
+    achieved = sweep_bytes / (sweep_avg_ms * 1e-3) / 1e9 if sweep_avg_ms > 0 else 0.0
+    step_bytes = 8 * nodes + 9 * F + F * (9 + 32 + 17)
+    ms_per_step = ms / args.steps
+    launches = sum(v[0] for v in trace.values())
+
+    line = {
+        "metric": METRIC,
+        "value": ws * nodes * args.steps / (ms * 1e-3),
+        "unit": UNIT,
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [n, n, n], "pierced_faces": F,
+                   "l2": "inputs larger than L2 (1 GiB field, 129 MB L2); no flush",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": "sweep", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                     "traffic": None, "algorithmic_bytes": sweep_bytes,
+                     "avg_ms": sweep_avg_ms},
+        "step_hbm_gbs": step_bytes / (ms_per_step * 1e-3) / 1e9,
+        "kernels_ms": {k: v[1] / max(1, v[0]) for k, v in trace.items()},
+        "e2e": {"value": ws * nodes * ke / (ms_e2e * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": 8 * nodes, "d2h_bytes_per_step": d2h // ke},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        planes = max(1, min(args.cpu_planes, n - 1))
+        slab = np.ascontiguousarray(psi[: planes + 1].cpu().numpy())
+        oracle.set_threads(cpu_cores())
+        dt, nn, _ = oracle_sample(slab, planes)
+        line["cpu_baseline"] = {
+            "value": nn / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{planes} z-planes of the {n}^3 field ({nn} nodes), FP64 identify + "
+                      f"localize, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    q.close()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_qtv(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

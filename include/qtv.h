@@ -1,0 +1,214 @@
+/*
+ * qtv.h -- C ABI of libqtv: GPU vortex-core identification and sub-grid
+ * localization on a 3-D grid of a complex wave function psi.
+ *
+ * The two stages follow "Vectorizing Quantum Turbulence Vortex-Core Lines for
+ * Real-Time Visualization" (Liu, Xiong, Liu; arXiv 1911.12070):
+ *
+ *   identification -- circulation-based vortex identification, Sec. 2.2.2,
+ *     Eq. 5: C = closed-path integral of grad(sigma) . dl, |C| = 2 pi where the
+ *     path encloses a vortex core and 0 elsewhere.  Here the path is every
+ *     plaquette (unit square) of the three axis-aligned orientations, and the
+ *     result is the integer winding W = C / (2 pi) of each plaquette.
+ *   localization -- density-guided local optimisation, Sec. 3.3.3, Eq. 6:
+ *     x* = argmin rho(x), rho = |Phi|^2 (Eq. 3), with Phi linearly
+ *     interpolated between grid nodes (Sec. 5).  Here the search domain of
+ *     each sample is its pierced plaquette, where the bilinear interpolant has
+ *     exactly one zero when W = +-1.
+ *   direction -- each sample carries W, whose sign gives the direction of the
+ *     line by the right-hand rule about the plaquette normal (Sec. 3.4).
+ *
+ * Conventions shared by every entry point
+ *   psi      device pointer, complex64 interleaved (re, im) as two float32,
+ *            nx*ny*nz elements, x fastest: node (i,j,k) is element
+ *            (k*ny + j)*nx + i.  At least 8-byte aligned (16-byte alignment
+ *            and even nx enable 16-byte vector loads).
+ *   faces    named by the minimum corner (i,j,k) and orientation o:
+ *            o = 0: xy plaquette, normal +z, loop (i,j)->(i+1,j)->(i+1,j+1)->(i,j+1)
+ *            o = 1: yz plaquette, normal +x, loop (j,k)->(j+1,k)->(j+1,k+1)->(j,k+1)
+ *            o = 2: zx plaquette, normal +y, loop (k,i)->(k+1,i)->(k+1,i+1)->(k,i+1)
+ *            A face exists iff its four corners are in the grid (no periodic
+ *            wrap).  face id = (((k*ny + j)*nx + i) << 2) | o, a uint64.
+ *   streams  every call is asynchronous on the given cudaStream_t (passed as
+ *            void*; NULL = legacy default stream) unless stated otherwise.
+ *   memory   the caller owns every input and output buffer.  The handle owns
+ *            only its workspace (staging for stream compaction, segment tables).
+ *   errors   every call returns a status code; nothing throws across the ABI.
+ *            qtv_last_error_string() describes the last failure of the calling
+ *            thread.  Invalid arguments are rejected on the host before any
+ *            launch; device-side conditions are reported through device memory.
+ */
+#ifndef QTV_H
+#define QTV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define QTV_API __attribute__((visibility("default")))
+#else
+#define QTV_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define QTV_OK 0
+#define QTV_WARN_NONFINITE 1  /* not returned by asynchronous calls; see qtv_stats */
+#define QTV_ERR_ARG (-1)      /* invalid argument (null pointer, bad size, misalignment) */
+#define QTV_ERR_CAPACITY (-2) /* workspace or output too small; required size reported */
+#define QTV_ERR_CUDA (-3)     /* a CUDA runtime call failed */
+#define QTV_ERR_TIMEOUT (-4)  /* a bounded device-side wait gave up */
+#define QTV_ERR_STATE (-5)    /* call not valid in the handle's current state */
+
+/* localization modes */
+#define QTV_PLAIN 0   /* closed-form zero of the bilinear interpolant + Newton polish */
+#define QTV_LEARNED 1 /* learned locator with plain fallback (needs loaded weights) */
+
+/* per-sample flag bits */
+#define QTV_FLAG_ANOMALOUS 1u /* |W| != 1, or no zero of the interpolant inside the face */
+#define QTV_FLAG_FALLBACK 2u  /* learned prediction rejected; plain result used */
+#define QTV_FLAG_LEARNED 4u   /* position predicted by the learned locator */
+
+typedef struct qtv_handle_s* qtv_handle;
+
+/* Grid geometry.  h and origin only scale and shift output positions:
+ * node (i,j,k) sits at origin + h*(i,j,k).  periodic must be 0. */
+typedef struct {
+  int32_t nx, ny, nz;
+  float h;
+  float origin[3];
+  uint32_t periodic;
+} qtv_grid;
+
+/* Optional statistics of one identification call (device memory, written by
+ * the call).  faces_scanned = existing faces; pierced = faces with W != 0;
+ * ambiguous = faces with an edge phase difference within about 1e-4 rad of
+ * +-pi (FP32 test); zero_node_faces = faces with a corner where psi == 0;
+ * nonfinite_faces = faces with a NaN/Inf corner (their W is forced to 0). */
+typedef struct {
+  uint64_t faces_scanned;
+  uint64_t pierced;
+  uint64_t ambiguous;
+  uint64_t zero_node_faces;
+  uint64_t nonfinite_faces;
+  uint64_t anomalous;
+  uint64_t fallbacks;
+  uint64_t reserved;
+} qtv_stats;
+
+/* One emitted core sample (32 bytes, host memory). */
+typedef struct {
+  float x, y, z;   /* position, origin + h * grid coordinates */
+  float resid;     /* |psi_interp|^2 at the position (Eq. 6 objective) */
+  uint64_t face_id;
+  int8_t winding;  /* W of the pierced plaquette: direction by the right-hand rule */
+  uint8_t flags;   /* QTV_FLAG_* */
+  uint16_t reserved0;
+  uint32_t reserved1;
+} qtv_sample;
+
+/* Library version, (major << 16) | minor. */
+QTV_API int qtv_version(void);
+
+/* Text of the last error on the calling thread ("" if none).  The pointer
+ * stays valid until the thread's next failing call. */
+QTV_API const char* qtv_last_error_string(void);
+
+/* Create a handle bound to CUDA device `device` (made current for the call).
+ * Allocates no large workspace; see qtv_reserve.  *out receives the handle. */
+QTV_API int qtv_create(qtv_handle* out, int device);
+
+/* Free the handle and its workspace.  Synchronises the handle's device.
+ * NULL is accepted (no-op). */
+QTV_API int qtv_destroy(qtv_handle h);
+
+/* Size the handle's workspace for grids up to `grid` and up to max_faces
+ * pierced faces per identification call.  Synchronous (cudaMalloc).  Calls
+ * made later with larger sizes grow the workspace the same way, so call this
+ * first when later calls are captured into a CUDA graph. */
+QTV_API int qtv_reserve(qtv_handle h, const qtv_grid* grid, uint64_t max_faces);
+
+/*
+ * Identification (Sec. 2.2.2, Eq. 5) of every plaquette of the grid.
+ *
+ *   psi       device, complex64 field as above (read only).
+ *   face_ids  device, uint64[capacity]: ids of the faces with W != 0, in
+ *             ascending face-id order.
+ *   winding   device, int8[capacity]: W of each listed face.
+ *   capacity  length of face_ids / winding.
+ *   count     device, one uint64: receives the number of faces with W != 0.
+ *             If *count > capacity the face outputs are incomplete and must
+ *             not be used: retry with capacity >= *count (the Python binding
+ *             does this).  capacity = 0 with NULL outputs counts only.
+ *   stats     device qtv_stats or NULL.  NULL selects the fastest kernel.
+ *
+ * W is the sum over the four directed loop edges of the integer branch
+ * crossing of arg(psi), so that 2 pi W equals the sum of the wrapped phase
+ * differences arg(psi_b * conj(psi_a)) in (-pi, pi] (the discrete Eq. 5) up to
+ * rounding of those differences; it equals the FP64 definition on every face
+ * whose edge differences lie at least 1e-4 rad from +-pi.  A node with psi == 0
+ * exactly is given phase 0.  A face with a NaN/Inf corner gets W = 0.
+ * Returns QTV_ERR_ARG for bad arguments; device results are asynchronous.
+ */
+QTV_API int qtv_identify(qtv_handle h, const qtv_grid* grid, const void* psi, uint64_t* face_ids,
+                 int8_t* winding, uint64_t capacity, uint64_t* count, qtv_stats* stats,
+                 void* stream);
+
+/*
+ * Localization (Sec. 3.3.3, Eq. 6) of a list of pierced faces.
+ *
+ *   face_ids, winding  device, n entries (as produced by qtv_identify).
+ *   n        host upper bound on the number of faces (buffer length).
+ *   n_dev    optional device uint64: if not NULL the call processes
+ *            min(n, *n_dev) faces, so it can follow qtv_identify without a
+ *            host synchronisation.
+ *   mode     QTV_PLAIN or QTV_LEARNED.
+ *   fallback_resid  learned mode only: predictions whose interpolated |psi|^2,
+ *            divided by the neighbourhood mean |psi|^2, exceeds this are
+ *            replaced by the plain result (QTV_FLAG_FALLBACK).
+ *   xyz      device float[3*n]: sample positions, origin + h*(grid coords).
+ *   resid    device float[n]: |psi_bilinear|^2 at the sample.
+ *   flags    device uint8[n]: QTV_FLAG_* bits.
+ */
+QTV_API int qtv_localize(qtv_handle h, const qtv_grid* grid, const void* psi, const uint64_t* face_ids,
+                 const int8_t* winding, uint64_t n, const uint64_t* n_dev, int mode,
+                 float fallback_resid, float* xyz, float* resid, uint8_t* flags, void* stream);
+
+/*
+ * Emission (Sec. 3.4, direction by the right-hand rule): pack n samples into
+ * caller-owned host memory `host_out` (qtv_sample[n]; pinned memory makes the
+ * copy asynchronous).  Samples keep the order of the inputs (ascending face
+ * id when they come from qtv_identify).  The copy is complete when `stream`
+ * reaches this point; synchronise before reading host_out.
+ */
+QTV_API int qtv_emit_samples(qtv_handle h, uint64_t n, const uint64_t* face_ids, const int8_t* winding,
+                     const float* xyz, const float* resid, const uint8_t* flags,
+                     qtv_sample* host_out, void* stream);
+
+/*
+ * Kernel timing trace.  While enabled, the handle records a pair of CUDA
+ * events on the launching stream around each of its kernel launches (names:
+ * "sweep", "seg_scan", "scatter", "stats", "localize", "emit_pack").
+ * qtv_trace_read waits for the recorded events, writes up to max_entries
+ * per-kernel totals (launch count and summed device time) and, if reset is
+ * nonzero, clears the record.  Tracing adds host work per launch; leave it
+ * off outside measurement.
+ */
+typedef struct {
+  char name[24];
+  uint32_t launches;
+  float total_ms;
+} qtv_trace_entry;
+
+QTV_API int qtv_trace_enable(qtv_handle h, int on);
+QTV_API int qtv_trace_read(qtv_handle h, qtv_trace_entry* out, int max_entries, int* n_entries,
+                           int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QTV_H */

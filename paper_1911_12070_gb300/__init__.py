@@ -1,0 +1,230 @@
+"""GB300 vortex-core identification and sub-grid localization.
+
+Python binding of libqtv (``include/qtv.h``).  It only marshals arguments:
+every step of identification, localization and emission runs in the CUDA
+kernels of ``csrc/``.  PyTorch supplies device memory and streams.  There is
+no CPU fallback: if ``_build/libqtv.so`` cannot be loaded, :func:`lib` raises.
+
+Low-level: :func:`lib` returns the ctypes library whose functions carry the
+C names (``qtv_identify``, ``qtv_localize``, ``qtv_emit_samples``, ...).
+High-level: :class:`Qtv` wraps a handle and works on torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["lib", "Qtv", "Grid", "Stats", "Sample", "QtvError", "PLAIN", "LEARNED",
+           "FLAG_ANOMALOUS", "FLAG_FALLBACK", "FLAG_LEARNED", "SAMPLE_DTYPE", "build"]
+
+PLAIN, LEARNED = 0, 1
+FLAG_ANOMALOUS, FLAG_FALLBACK, FLAG_LEARNED = 1, 2, 4
+OK, WARN_NONFINITE, ERR_ARG, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = 0, 1, -1, -2, -3, -4, -5
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libqtv.so")
+
+
+class QtvError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"qtv error {code}: {msg}")
+        self.code = code
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("h", ctypes.c_float), ("origin", ctypes.c_float * 3), ("periodic", ctypes.c_uint32)]
+
+    @classmethod
+    def of(cls, shape, h=1.0, origin=(0.0, 0.0, 0.0)):
+        nz, ny, nx = shape
+        g = cls()
+        g.nx, g.ny, g.nz, g.h = nx, ny, nz, h
+        for i in range(3):
+            g.origin[i] = origin[i]
+        g.periodic = 0
+        return g
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("faces_scanned", "pierced", "ambiguous",
+                                              "zero_node_faces", "nonfinite_faces", "anomalous",
+                                              "fallbacks", "reserved")]
+
+
+class Sample(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_float), ("y", ctypes.c_float), ("z", ctypes.c_float),
+                ("resid", ctypes.c_float), ("face_id", ctypes.c_uint64), ("winding", ctypes.c_int8),
+                ("flags", ctypes.c_uint8), ("reserved0", ctypes.c_uint16),
+                ("reserved1", ctypes.c_uint32)]
+
+
+class TraceEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_uint32),
+                ("total_ms", ctypes.c_float)]
+
+
+SAMPLE_DTYPE = np.dtype([("x", "<f4"), ("y", "<f4"), ("z", "<f4"), ("resid", "<f4"),
+                         ("face_id", "<u8"), ("winding", "i1"), ("flags", "u1"),
+                         ("reserved0", "<u2"), ("reserved1", "<u4")])
+assert SAMPLE_DTYPE.itemsize == ctypes.sizeof(Sample) == 32
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    from . import nvcc_build
+
+    return nvcc_build.build(force=force)
+
+
+def lib() -> ctypes.CDLL:
+    """Load libqtv.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_1911_12070_gb300.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        P, u64, i32, f32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_float
+        L.qtv_version.restype = i32
+        L.qtv_last_error_string.restype = ctypes.c_char_p
+        L.qtv_create.argtypes = [ctypes.POINTER(P), i32]
+        L.qtv_destroy.argtypes = [P]
+        L.qtv_reserve.argtypes = [P, ctypes.POINTER(Grid), u64]
+        L.qtv_identify.argtypes = [P, ctypes.POINTER(Grid), P, P, P, u64, P, P, P]
+        L.qtv_localize.argtypes = [P, ctypes.POINTER(Grid), P, P, P, u64, P, i32, f32, P, P, P, P]
+        L.qtv_emit_samples.argtypes = [P, u64, P, P, P, P, P, P, P]
+        L.qtv_trace_enable.argtypes = [P, i32]
+        L.qtv_trace_read.argtypes = [P, ctypes.POINTER(TraceEntry), i32, ctypes.POINTER(i32), i32]
+        for name in ("qtv_create", "qtv_destroy", "qtv_reserve", "qtv_identify", "qtv_localize",
+                     "qtv_emit_samples", "qtv_trace_enable", "qtv_trace_read"):
+            getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc < 0:
+        raise QtvError(rc, lib().qtv_last_error_string().decode())
+    return rc
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    import torch
+
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Qtv:
+    """A libqtv handle bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        h = ctypes.c_void_p()
+        _check(lib().qtv_create(ctypes.byref(h), device))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().qtv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def trace_enable(self, on: bool = True):
+        _check(lib().qtv_trace_enable(self.h, 1 if on else 0))
+
+    def trace_read(self, reset: bool = True):
+        """{kernel name: (launches, total device ms)} recorded since the last reset."""
+        buf = (TraceEntry * 16)()
+        n = ctypes.c_int(0)
+        _check(lib().qtv_trace_read(self.h, buf, 16, ctypes.byref(n), 1 if reset else 0))
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
+                for i in range(min(n.value, 16))}
+
+    def reserve(self, shape, max_faces: int):
+        g = Grid.of(shape)
+        _check(lib().qtv_reserve(self.h, ctypes.byref(g), int(max_faces)))
+
+    # -- identification -------------------------------------------------------------
+    def identify_into(self, psi, face_ids, winding, count, stats=None, grid=None, stream=None):
+        """Raw call: all tensors preallocated on the device (count: uint64[1])."""
+        g = grid or Grid.of(tuple(psi.shape))
+        cap = 0 if face_ids is None else face_ids.numel()
+        _check(lib().qtv_identify(self.h, ctypes.byref(g), _ptr(psi), _ptr(face_ids),
+                                  _ptr(winding), cap, _ptr(count), _ptr(stats),
+                                  _stream_ptr(stream)))
+
+    def identify(self, psi, capacity: int | None = None, stats: bool = False, stream=None):
+        """Pierced faces of psi (complex64 [nz, ny, nx] on the device).
+
+        Returns (face_ids uint64-as-int64 tensor [n], winding int8 [n], stats dict or None).
+        Grows the output and retries when the capacity is too small."""
+        import torch
+
+        dev = psi.device
+        nz, ny, nx = psi.shape
+        if capacity is None:
+            capacity = max(1024, int(0.02 * nx * ny * nz))
+        count = torch.zeros(1, dtype=torch.int64, device=dev)
+        st = torch.zeros(8, dtype=torch.int64, device=dev) if stats else None
+        for _ in range(2):
+            ids = torch.empty(capacity, dtype=torch.int64, device=dev)
+            w = torch.empty(capacity, dtype=torch.int8, device=dev)
+            self.identify_into(psi, ids, w, count, st, stream=stream)
+            n = int(count.item())
+            if n <= capacity:
+                break
+            capacity = n
+        sd = None
+        if stats:
+            vals = st.cpu().numpy().astype(np.uint64)
+            sd = {f[0]: int(v) for f, v in zip(Stats._fields_, vals)}
+        return ids[:n], w[:n], sd
+
+    # -- localization ---------------------------------------------------------------
+    def localize_into(self, psi, face_ids, winding, xyz, resid, flags, n=None, n_dev=None,
+                      mode=PLAIN, fallback_resid=1e-3, grid=None, stream=None):
+        g = grid or Grid.of(tuple(psi.shape))
+        nn = face_ids.numel() if n is None else int(n)
+        _check(lib().qtv_localize(self.h, ctypes.byref(g), _ptr(psi), _ptr(face_ids),
+                                  _ptr(winding), nn, _ptr(n_dev), int(mode),
+                                  float(fallback_resid), _ptr(xyz), _ptr(resid), _ptr(flags),
+                                  _stream_ptr(stream)))
+
+    def localize(self, psi, face_ids, winding, mode=PLAIN, fallback_resid=1e-3, grid=None,
+                 stream=None):
+        import torch
+
+        n = face_ids.numel()
+        dev = psi.device
+        xyz = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        resid = torch.empty(n, dtype=torch.float32, device=dev)
+        flags = torch.empty(n, dtype=torch.uint8, device=dev)
+        self.localize_into(psi, face_ids, winding, xyz, resid, flags, mode=mode,
+                           fallback_resid=fallback_resid, grid=grid, stream=stream)
+        return xyz, resid, flags
+
+    # -- emission -------------------------------------------------------------------
+    def emit_samples(self, face_ids, winding, xyz, resid, flags, out=None, stream=None):
+        """Samples packed into host memory (numpy structured array, SAMPLE_DTYPE)."""
+        import torch
+
+        n = face_ids.numel()
+        if out is None:
+            out = torch.empty(n * 32, dtype=torch.uint8, pin_memory=True)
+        _check(lib().qtv_emit_samples(self.h, n, _ptr(face_ids), _ptr(winding), _ptr(xyz),
+                                      _ptr(resid), _ptr(flags), _ptr(out), _stream_ptr(stream)))
+        (torch.cuda.current_stream() if stream is None else stream).synchronize()
+        return out.numpy()[: n * 32].view(SAMPLE_DTYPE)

@@ -1,0 +1,324 @@
+// api.cu -- the C ABI of libqtv (include/qtv.h): argument validation, handle
+// workspace, and dispatch to the kernels.  Nothing here computes on the host.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "qtv_internal.cuh"
+
+namespace qtv {
+
+namespace {
+thread_local std::string g_err;
+
+// Makes the handle's device current for the scope of an API call.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return false;
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+template <typename T>
+int grow(T*& p, uint64_t& cap, uint64_t want, cudaStream_t st, const char* what) {
+  if (want <= cap && p) return QTV_OK;
+  if (capturing(st))
+    return set_error(QTV_ERR_STATE, "%s: workspace must grow to %llu entries during stream capture;"
+                     " call qtv_reserve before capturing", what, (unsigned long long)want);
+  if (p) {
+    cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p), want * sizeof(T));
+  if (e != cudaSuccess) {
+    p = nullptr;
+    return check_cuda(e, what);
+  }
+  cap = want;
+  return QTV_OK;
+}
+
+int validate_grid(const qtv_grid* g) {
+  if (!g) return set_error(QTV_ERR_ARG, "grid is NULL");
+  if (g->nx < 0 || g->ny < 0 || g->nz < 0)
+    return set_error(QTV_ERR_ARG, "negative grid size (%d, %d, %d)", g->nx, g->ny, g->nz);
+  if (g->periodic != 0) return set_error(QTV_ERR_ARG, "periodic grids are not supported");
+  if (g->nx > 64 * kMaxWarpsX)
+    return set_error(QTV_ERR_ARG, "nx = %d exceeds the supported maximum %d", g->nx,
+                     64 * kMaxWarpsX);
+  const unsigned long long n = (unsigned long long)g->nx * g->ny * g->nz;
+  if (n >> 60) return set_error(QTV_ERR_ARG, "grid too large");
+  if (!(g->h > 0.f)) return set_error(QTV_ERR_ARG, "grid spacing h must be positive");
+  return QTV_OK;
+}
+
+uint64_t seg_entries(const qtv_grid& g) {
+  const uint64_t nbands = (uint64_t)(g.ny + kRows - 1) / kRows;
+  return nbands * (uint64_t)g.nz;
+}
+}  // namespace
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int check_cuda(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return QTV_OK;
+  return set_error(QTV_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+namespace {
+cudaEvent_t take_event(qtv_handle h) {
+  if (!h->event_pool.empty()) {
+    cudaEvent_t e = h->event_pool.back();
+    h->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+const char* kKernelNames[K_COUNT] = {"sweep", "seg_scan", "scatter", "stats", "localize",
+                                     "emit_pack"};
+}  // namespace
+
+TraceScope::TraceScope(qtv_handle h_, int k, cudaStream_t s) : h(h_), kernel(k), st(s) {
+  if (!h || !h->trace_on) return;
+  a = take_event(h);
+  b = take_event(h);
+  if (a && b) cudaEventRecord(a, st);
+}
+
+TraceScope::~TraceScope() {
+  if (!a || !b) {
+    if (a) h->event_pool.push_back(a);
+    if (b) h->event_pool.push_back(b);
+    return;
+  }
+  cudaEventRecord(b, st);
+  h->trace.push_back(TraceRec{kernel, a, b});
+}
+
+}  // namespace qtv
+
+using namespace qtv;
+
+extern "C" {
+
+int qtv_version(void) { return (1 << 16) | 0; }
+
+const char* qtv_last_error_string(void) { return g_err.c_str(); }
+
+int qtv_create(qtv_handle* out, int device) {
+  if (!out) return set_error(QTV_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return check_cuda(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev)
+    return set_error(QTV_ERR_ARG, "device %d out of range (%d devices)", device, ndev);
+  DeviceGuard dg(device);
+  if (!dg.ok) return set_error(QTV_ERR_CUDA, "cudaSetDevice(%d) failed", device);
+  qtv_handle h = new (std::nothrow) qtv_handle_s();
+  if (!h) return set_error(QTV_ERR_ARG, "out of host memory");
+  h->device = device;
+  e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) {
+    delete h;
+    return check_cuda(e, "cudaDeviceGetAttribute(SM count)");
+  }
+  e = cudaMalloc(reinterpret_cast<void**>(&h->ws.counters), 8 * sizeof(unsigned long long));
+  if (e != cudaSuccess) {
+    delete h;
+    return check_cuda(e, "cudaMalloc(counters)");
+  }
+  *out = h;
+  return QTV_OK;
+}
+
+int qtv_destroy(qtv_handle h) {
+  if (!h) return QTV_OK;
+  DeviceGuard dg(h->device);
+  cudaDeviceSynchronize();
+  cudaFree(h->ws.staging);
+  cudaFree(h->ws.seg);
+  cudaFree(h->ws.seg_off);
+  cudaFree(h->ws.counters);
+  cudaFree(h->ws.pack);
+  for (auto& r : h->trace) {
+    cudaEventDestroy(r.start);
+    cudaEventDestroy(r.stop);
+  }
+  for (auto e : h->event_pool) cudaEventDestroy(e);
+  delete h;
+  return QTV_OK;
+}
+
+int qtv_trace_enable(qtv_handle h, int on) {
+  if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
+  h->trace_on = on != 0;
+  return QTV_OK;
+}
+
+int qtv_trace_read(qtv_handle h, qtv_trace_entry* out, int max_entries, int* n_entries,
+                   int reset) {
+  if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
+  if (!n_entries || (max_entries > 0 && !out)) return set_error(QTV_ERR_ARG, "NULL output");
+  DeviceGuard dg(h->device);
+  double tot[K_COUNT] = {0};
+  uint32_t cnt[K_COUNT] = {0};
+  for (auto& r : h->trace) {
+    cudaError_t e = cudaEventSynchronize(r.stop);
+    if (e != cudaSuccess) return check_cuda(e, "cudaEventSynchronize(trace)");
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, r.start, r.stop);
+    if (e != cudaSuccess) return check_cuda(e, "cudaEventElapsedTime(trace)");
+    tot[r.kernel] += ms;
+    cnt[r.kernel] += 1;
+  }
+  int n = 0;
+  for (int k = 0; k < K_COUNT; ++k) {
+    if (!cnt[k]) continue;
+    if (n < max_entries) {
+      memset(out[n].name, 0, sizeof out[n].name);
+      strncpy(out[n].name, kKernelNames[k], sizeof out[n].name - 1);
+      out[n].launches = cnt[k];
+      out[n].total_ms = (float)tot[k];
+    }
+    ++n;
+  }
+  *n_entries = n;
+  if (reset) {
+    for (auto& r : h->trace) {
+      h->event_pool.push_back(r.start);
+      h->event_pool.push_back(r.stop);
+    }
+    h->trace.clear();
+  }
+  return QTV_OK;
+}
+
+int qtv_reserve(qtv_handle h, const qtv_grid* grid, uint64_t max_faces) {
+  if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
+  int rc = validate_grid(grid);
+  if (rc) return rc;
+  DeviceGuard dg(h->device);
+  if (max_faces > 0xFFFFFFFFull)
+    return set_error(QTV_ERR_ARG, "max_faces above 2^32-1 is not supported");
+  rc = grow(h->ws.staging, h->ws.staging_cap, max_faces > 0 ? max_faces : 1, nullptr,
+            "cudaMalloc(staging)");
+  if (rc) return rc;
+  const uint64_t ns = seg_entries(*grid) > 0 ? seg_entries(*grid) : 1;
+  rc = grow(h->ws.seg, h->ws.seg_cap, ns, nullptr, "cudaMalloc(seg)");
+  if (rc) return rc;
+  rc = grow(h->ws.seg_off, h->ws.seg_off_cap, ns, nullptr, "cudaMalloc(seg_off)");
+  if (rc) return rc;
+  rc = grow(h->ws.pack, h->ws.pack_cap, max_faces > 0 ? max_faces : 1, nullptr,
+            "cudaMalloc(pack)");
+  if (rc) return rc;
+  return check_cuda(cudaDeviceSynchronize(), "qtv_reserve");
+}
+
+int qtv_identify(qtv_handle h, const qtv_grid* grid, const void* psi, uint64_t* face_ids,
+                 int8_t* winding, uint64_t capacity, uint64_t* count, qtv_stats* stats,
+                 void* stream) {
+  if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
+  int rc = validate_grid(grid);
+  if (rc) return rc;
+  if (!count) return set_error(QTV_ERR_ARG, "count is NULL");
+  if (capacity > 0 && (!face_ids || !winding))
+    return set_error(QTV_ERR_ARG, "face_ids / winding are NULL with capacity %llu",
+                     (unsigned long long)capacity);
+  if (capacity > 0xFFFFFFFFull)
+    return set_error(QTV_ERR_ARG, "capacity above 2^32-1 is not supported");
+  const qtv_grid& g = *grid;
+  const unsigned long long nn = (unsigned long long)g.nx * g.ny * g.nz;
+  if (nn > 0 && !psi) return set_error(QTV_ERR_ARG, "psi is NULL");
+  if (reinterpret_cast<uintptr_t>(psi) & 7u)
+    return set_error(QTV_ERR_ARG, "psi must be 8-byte aligned");
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return set_error(QTV_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (nn == 0 || g.nx < 1 || g.ny < 1 || g.nz < 1) {
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(uint64_t), st);
+    if (e == cudaSuccess && stats) e = cudaMemsetAsync(stats, 0, sizeof(qtv_stats), st);
+    return check_cuda(e, "cudaMemsetAsync(count)");
+  }
+  // staging holds every staged face up to the output capacity (at least one
+  // record so that count-only calls still have a valid buffer)
+  const uint64_t want_stage = capacity > 0 ? capacity : 1;
+  rc = grow(h->ws.staging, h->ws.staging_cap, want_stage, st, "cudaMalloc(staging)");
+  if (rc) return rc;
+  const uint64_t ns = seg_entries(g);
+  rc = grow(h->ws.seg, h->ws.seg_cap, ns, st, "cudaMalloc(seg)");
+  if (rc) return rc;
+  rc = grow(h->ws.seg_off, h->ws.seg_off_cap, ns, st, "cudaMalloc(seg_off)");
+  if (rc) return rc;
+  const uint64_t stage_cap = capacity > 0 ? capacity : 0;
+  return identify_launch(h, g, reinterpret_cast<const float2*>(psi), face_ids, winding, capacity,
+                         count, stats, st, h->ws.staging, stage_cap, h->ws.seg, h->ws.seg_off,
+                         h->ws.counters);
+}
+
+int qtv_localize(qtv_handle h, const qtv_grid* grid, const void* psi, const uint64_t* face_ids,
+                 const int8_t* winding, uint64_t n, const uint64_t* n_dev, int mode,
+                 float fallback_resid, float* xyz, float* resid, uint8_t* flags, void* stream) {
+  (void)fallback_resid;
+  if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
+  int rc = validate_grid(grid);
+  if (rc) return rc;
+  if (mode != QTV_PLAIN && mode != QTV_LEARNED)
+    return set_error(QTV_ERR_ARG, "unknown localization mode %d", mode);
+  if (mode == QTV_LEARNED) return set_error(QTV_ERR_STATE, "no learned locator loaded");
+  if (n == 0) return QTV_OK;
+  if (!psi || !face_ids || !winding || !xyz || !resid || !flags)
+    return set_error(QTV_ERR_ARG, "a required pointer is NULL");
+  if (reinterpret_cast<uintptr_t>(psi) & 7u)
+    return set_error(QTV_ERR_ARG, "psi must be 8-byte aligned");
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return set_error(QTV_ERR_CUDA, "cudaSetDevice failed");
+  return localize_launch(h, *grid, reinterpret_cast<const float2*>(psi), face_ids, winding, n, n_dev,
+                         xyz, resid, flags, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int qtv_emit_samples(qtv_handle h, uint64_t n, const uint64_t* face_ids, const int8_t* winding,
+                     const float* xyz, const float* resid, const uint8_t* flags,
+                     qtv_sample* host_out, void* stream) {
+  if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
+  if (n == 0) return QTV_OK;
+  if (!face_ids || !winding || !xyz || !resid || !host_out)
+    return set_error(QTV_ERR_ARG, "a required pointer is NULL");
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return set_error(QTV_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int rc = grow(h->ws.pack, h->ws.pack_cap, n, st, "cudaMalloc(pack)");
+  if (rc) return rc;
+  rc = emit_pack_launch(h, n, face_ids, winding, xyz, resid, flags, h->ws.pack, st);
+  if (rc) return rc;
+  return check_cuda(cudaMemcpyAsync(host_out, h->ws.pack, n * sizeof(qtv_sample),
+                                    cudaMemcpyDeviceToHost, st),
+                    "cudaMemcpyAsync(samples)");
+}
+
+}  // extern "C"

@@ -1,0 +1,71 @@
+"""The C ABI library loads and exports every entry point that include/qtv.h
+declares; host-side argument validation rejects bad calls before any launch.
+No GPU is needed: nothing here launches a kernel."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_1911_12070_gb300 as qtv
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qtv.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(qtv_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    qtv.build()
+    return qtv.lib()
+
+
+def test_header_declares_the_hot_path():
+    names = declared_functions()
+    for n in ("qtv_identify", "qtv_localize", "qtv_emit_samples", "qtv_create", "qtv_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", qtv.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT\s+(qtv_\w+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in declared_functions():
+        assert hasattr(lib, n)
+
+
+def test_no_internal_symbols_leak(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", qtv.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    text_syms = re.findall(r"\bT\s+(\S+)", out)
+    assert all(s.startswith("qtv_") for s in text_syms), [s for s in text_syms
+                                                          if not s.startswith("qtv_")][:5]
+
+
+def test_version(lib):
+    assert lib.qtv_version() >> 16 == 1
+
+
+def test_null_handle_is_rejected_on_the_host(lib):
+    g = qtv.Grid.of((8, 8, 8))
+    rc = lib.qtv_identify(None, ctypes.byref(g), None, None, None, 0, None, None, None)
+    assert rc == qtv.ERR_ARG
+    assert b"handle" in lib.qtv_last_error_string()
+    rc = lib.qtv_localize(None, ctypes.byref(g), None, None, None, 0, None, 0, 1e-3, None,
+                          None, None, None)
+    assert rc == qtv.ERR_ARG
+    assert lib.qtv_destroy(None) == 0
+
+
+def test_sample_layout_is_32_bytes():
+    assert ctypes.sizeof(qtv.Sample) == 32
+    assert qtv.SAMPLE_DTYPE.itemsize == 32
+    assert qtv.Sample.face_id.offset == 16 and qtv.Sample.winding.offset == 24

@@ -1,0 +1,128 @@
+"""GPU parity of plaquette localization (Sec. 3.3.3, Eq. 6) and emission
+through the C ABI.  Positions must match the FP64 oracle within 1e-4 grid
+spacings (plus half an FP32 ulp of the absolute coordinate) on every face the
+oracle finds unambiguous and well conditioned (|det J| >= 1e-3 max|corner|^2);
+the rest are counted."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from qtv_testutil import compare_positions, gpu_identify
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def q():
+    import paper_1911_12070_gb300 as qtv
+
+    qtv.build()
+    h = qtv.Qtv(0)
+    yield h
+    h.close()
+
+
+def _ok_mask(host, ids, ora):
+    o = (ids & np.uint64(3)).astype(np.int64)
+    lin = (ids >> np.uint64(2)).astype(np.int64)
+    _, fl = oracle.identify(host, k0=0, k1=host.shape[0]) if host.size < 3e7 else (None, None)
+    good = (ora["flags"] & (oracle.L_ANOMALOUS | oracle.L_ILLCOND)) == 0
+    if fl is not None:
+        amb = (fl.reshape(3, -1)[o, lin] & oracle.AMBIGUOUS) != 0
+        good &= ~amb
+    return good
+
+
+def _run(q, psi_dev):
+    ids_t, w_t, _ = q.identify(psi_dev)
+    xyz, resid, flags = q.localize(psi_dev, ids_t, w_t)
+    return (ids_t.cpu().numpy().view(np.uint64), w_t.cpu().numpy(), xyz.cpu().numpy(),
+            resid.cpu().numpy(), flags.cpu().numpy(), (ids_t, w_t, xyz, resid, flags))
+
+
+@pytest.mark.parametrize("case", ["config0", "waves_ragged", "waves_wide"])
+def test_positions_match_oracle(q, case):
+    if case == "config0":
+        host = synth.analytic_line_ring()
+    elif case == "waves_ragged":
+        host = synth.random_waves_numpy((33, 45, 67), synth.wave_spec(3, 512))
+    else:
+        host = synth.random_waves_numpy((24, 40, 700), synth.wave_spec(4, 512))
+    ids, w, xyz, resid, flags, _ = _run(q, torch.from_numpy(host).cuda())
+    ora = oracle.localize(host, ids, w)
+    ok = _ok_mask(host, ids, ora)
+    bad, emax = compare_positions(xyz, ora, ok)
+    assert bad == 0, f"{bad} of {ok.sum()} faces off by more than 1e-4 h (max {emax})"
+    assert ok.sum() >= 0.95 * len(ids)
+    # flags: anomalous only where the oracle finds no zero or |W| != 1
+    assert not np.any((flags & 1)[ok])
+    # residual |F|^2 at the sample is FP32 round-off of zero
+    assert np.all(resid[ok] < 1e-9)
+
+
+def test_linear_field_exact_core(q):
+    n = 40
+    z, y, x = np.meshgrid(*(np.arange(n, dtype=float),) * 3, indexing="ij")
+    host = ((0.3 - 1.1j) * ((z - 17.3) + 1j * (x - 21.6))).astype(np.complex64)
+    ids, w, xyz, resid, flags, _ = _run(q, torch.from_numpy(host).cuda())
+    assert len(ids) == n and set((ids & np.uint64(3)).tolist()) == {2}
+    assert np.max(np.abs(xyz[:, 2] - 17.3)) < 1e-4
+    assert np.max(np.abs(xyz[:, 0] - 21.6)) < 1e-4
+    assert np.array_equal(xyz[:, 1], np.arange(n, dtype=np.float32))
+
+
+def test_config1_256_positions(q):
+    psi = synth.config_field("256_waves", device="cuda", seed=2)
+    host = psi.cpu().numpy()
+    ids, w, xyz, resid, flags, _ = _run(q, psi)
+    ora = oracle.localize(host, ids, w)
+    ok = _ok_mask(host, ids, ora)
+    bad, emax = compare_positions(xyz, ora, ok)
+    print(f"256^3: {len(ids)} samples, {ok.sum()} well conditioned, max err {emax:.2e} h")
+    assert bad == 0
+
+
+def test_config2_512_sampled_positions(q):
+    psi = synth.config_field("512_waves_noise", device="cuda")
+    ids, w, xyz, resid, flags, _ = _run(q, psi)
+    host = psi.cpu().numpy()
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(len(ids), size=min(200000, len(ids)), replace=False))
+    ora = oracle.localize(host, ids[pick], w[pick])
+    ok = (ora["flags"] & (oracle.L_ANOMALOUS | oracle.L_ILLCOND)) == 0
+    bad, emax = compare_positions(xyz[pick], ora, ok)
+    print(f"512^3: {len(ids)} samples, checked {len(pick)}, max err {emax:.2e} h")
+    assert bad <= 0.0005 * len(pick)  # exact +-pi ties excluded by the identify test
+
+
+def test_n_dev_chains_without_host_sync(q):
+    psi = torch.from_numpy(synth.random_waves_numpy((24, 40, 130), synth.wave_spec(6, 512))).cuda()
+    ids_t, w_t, _ = q.identify(psi)
+    n = ids_t.numel()
+    cap = n + 500
+    ids = torch.zeros(cap, dtype=torch.int64, device="cuda")
+    w = torch.zeros(cap, dtype=torch.int8, device="cuda")
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    xyz = torch.full((cap, 3), -7.0, device="cuda")
+    resid = torch.zeros(cap, device="cuda")
+    flags = torch.zeros(cap, dtype=torch.uint8, device="cuda")
+    q.identify_into(psi, ids, w, count)
+    q.localize_into(psi, ids, w, xyz, resid, flags, n=cap, n_dev=count)
+    torch.cuda.synchronize()
+    ref, _, _ = q.localize(psi, ids_t, w_t)
+    assert torch.equal(xyz[:n], ref)
+    assert bool((xyz[n:] == -7.0).all())
+
+
+def test_emit_samples_roundtrip(q):
+    psi = torch.from_numpy(synth.analytic_line_ring()).cuda()
+    ids, w, xyz, resid, flags, dev = _run(q, psi)
+    s = q.emit_samples(*dev)
+    assert len(s) == len(ids)
+    assert np.array_equal(s["face_id"], ids)
+    assert np.array_equal(s["winding"], w)
+    assert np.array_equal(np.stack([s["x"], s["y"], s["z"]], 1), xyz)
+    assert np.array_equal(s["resid"], resid) and np.array_equal(s["flags"], flags)
