@@ -131,7 +131,8 @@ __device__ bool solve_face(const C2 P[4], float& uo, float& vo, float& f2o) {
   return found;
 }
 
-__global__ void localize_kernel(const float2* __restrict__ psi, int nx, int ny, float h, float ox,
+__global__ void localize_kernel(const float2* __restrict__ psi, int nx, int ny, int nz, float h,
+                                float ox,
                                 float oy, float oz, const uint64_t* __restrict__ face_ids,
                                 const int8_t* __restrict__ winding, unsigned long long n,
                                 const uint64_t* __restrict__ n_dev, float* __restrict__ xyz,
@@ -151,9 +152,17 @@ __global__ void localize_kernel(const float2* __restrict__ psi, int nx, int ny, 
     const long long k = (long long)(lin / ((unsigned long long)nx * ny));
     const long long sx = 1, sy = nx, sz = (long long)nx * ny;
     long long du, dv;  // strides of the face axes u, v
-    if (o == 0) { du = sx; dv = sy; }
-    else if (o == 1) { du = sy; dv = sz; }
-    else { du = sz; dv = sx; }
+    bool exists;
+    if (o == 0) { du = sx; dv = sy; exists = i + 1 < nx && j + 1 < ny; }
+    else if (o == 1) { du = sy; dv = sz; exists = j + 1 < ny && k + 1 < nz; }
+    else { du = sz; dv = sx; exists = k + 1 < nz && i + 1 < nx; }
+    if (o == 3 || !exists) {
+      // not a face of this grid: flag it and touch no node
+      xyz[3 * f + 0] = xyz[3 * f + 1] = xyz[3 * f + 2] = __int_as_float(0x7fc00000);
+      resid[f] = __int_as_float(0x7fc00000);
+      flags[f] = QTV_FLAG_ANOMALOUS;
+      continue;
+    }
     const long long base = (long long)lin;
     C2 P[4];
     const float2 p0 = __ldg(psi + base), p1 = __ldg(psi + base + du);
@@ -208,7 +217,8 @@ int localize_launch(qtv_handle h, const qtv_grid& g, const float2* psi, const ui
   TraceScope ts(h, K_LOCALIZE, st);
   unsigned long long blocks = (n + 255) / 256;
   if (blocks > 65535ull * 4) blocks = 65535ull * 4;
-  localize_kernel<<<(unsigned)blocks, 256, 0, st>>>(psi, g.nx, g.ny, g.h, g.origin[0], g.origin[1],
+  localize_kernel<<<(unsigned)blocks, 256, 0, st>>>(psi, g.nx, g.ny, g.nz, g.h, g.origin[0],
+                                                    g.origin[1],
                                                     g.origin[2], face_ids, winding, n, n_dev, xyz,
                                                     resid, flags);
   return check_cuda(cudaGetLastError(), "localize_kernel launch");
