@@ -156,7 +156,7 @@ __global__ void localize_kernel(const float2* __restrict__ psi, int nx, int ny, 
     if (o == 0) { du = sx; dv = sy; exists = i + 1 < nx && j + 1 < ny; }
     else if (o == 1) { du = sy; dv = sz; exists = j + 1 < ny && k + 1 < nz; }
     else { du = sz; dv = sx; exists = k + 1 < nz && i + 1 < nx; }
-    if (o == 3 || !exists) {
+    if (o == 3 || !exists || k >= nz) {
       // not a face of this grid: flag it and touch no node
       xyz[3 * f + 0] = xyz[3 * f + 1] = xyz[3 * f + 2] = __int_as_float(0x7fc00000);
       resid[f] = __int_as_float(0x7fc00000);
