@@ -52,6 +52,8 @@ def parse():
                    help="planes of the field in the oracle's timed CPU sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=20)
+    p.add_argument("--soak", type=float, default=1.5,
+                   help="seconds of untimed load before warm-up (clock sampling)")
     return p.parse_args()
 
 
@@ -257,7 +259,7 @@ def run_qtv(args):
     clk = ClockSampler(dev.index)
     clk.start()
     # soak (untimed) so the clock sampler sees the GPU under load
-    t_end = time.time() + 1.5
+    t_end = time.time() + args.soak
     while time.time() < t_end:
         for _ in range(20):
             step()
