@@ -189,6 +189,36 @@ QTV_API int qtv_emit_samples(qtv_handle h, uint64_t n, const uint64_t* face_ids,
                      qtv_sample* host_out, void* stream);
 
 /*
+ * Identification without any allocation (the paper has no counterpart; this
+ * is a deployment variant of qtv_identify).
+ *
+ * Some callers cannot allocate device memory at call time: engines that
+ * reserve the whole GPU up front through their own allocator, plug-ins that
+ * must not touch the device heap, and latency-critical loops where cudaMalloc
+ * or cudaFree would synchronise the device.  For them this entry point takes
+ * no handle and allocates nothing: its scratch lives in one fixed file-scope
+ * device array of the library (about 10 MiB, held on every GPU that loads
+ * libqtv until the process exits).  The caller still passes psi and the
+ * outputs, with the same meaning as in qtv_identify (no statistics).
+ *
+ * Limits: capacity <= QTV_STATIC_MAX_FACES and nz * ceil(ny / 7) <=
+ * QTV_STATIC_MAX_SEGMENTS (enough for 512^3 tangles); larger requests are
+ * rejected with QTV_ERR_ARG and a message naming the limit.
+ * The first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before capturing any stream.  The call uses the current device.
+ * Every call shares the one array, and the array keeps the last call's
+ * contents (each call clears what must start at zero): calls that may
+ * overlap on the GPU (different streams, or different host threads on the
+ * same device) race and must be serialised by the caller.
+ */
+#define QTV_STATIC_MAX_FACES (1u << 21)
+#define QTV_STATIC_MAX_SEGMENTS (1u << 17)
+QTV_API int qtv_identify_static(const qtv_grid* grid, const void* psi, uint64_t* face_ids,
+                                int8_t* winding, uint64_t capacity, uint64_t* count,
+                                void* stream);
+
+/*
  * Kernel timing trace.  While enabled, the handle records a pair of CUDA
  * events on the launching stream around each of its kernel launches (names:
  * "sweep", "seg_scan", "scatter", "stats", "localize", "emit_pack").

@@ -96,6 +96,8 @@ def lib() -> ctypes.CDLL:
         L.qtv_identify.argtypes = [P, ctypes.POINTER(Grid), P, P, P, u64, P, P, P]
         L.qtv_localize.argtypes = [P, ctypes.POINTER(Grid), P, P, P, u64, P, i32, f32, P, P, P, P]
         L.qtv_emit_samples.argtypes = [P, u64, P, P, P, P, P, P, P]
+        L.qtv_identify_static.argtypes = [ctypes.POINTER(Grid), P, P, P, u64, P, P]
+        L.qtv_identify_static.restype = i32
         L.qtv_trace_enable.argtypes = [P, i32]
         L.qtv_trace_read.argtypes = [P, ctypes.POINTER(TraceEntry), i32, ctypes.POINTER(i32), i32]
         for name in ("qtv_create", "qtv_destroy", "qtv_reserve", "qtv_identify", "qtv_localize",
