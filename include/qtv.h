@@ -63,6 +63,10 @@ extern "C" {
 #define QTV_ERR_TIMEOUT (-4)  /* a bounded device-side wait gave up */
 #define QTV_ERR_STATE (-5)    /* call not valid in the handle's current state */
 
+/* value of *count after a call whose bounded device-side wait gave up
+ * (the outputs are then unusable; the binding raises QTV_ERR_TIMEOUT) */
+#define QTV_COUNT_TIMEOUT 0xFFFFFFFFFFFFFFFFull
+
 /* localization modes */
 #define QTV_PLAIN 0   /* closed-form zero of the bilinear interpolant + Newton polish */
 #define QTV_LEARNED 1 /* learned locator with plain fallback (needs loaded weights) */
@@ -197,13 +201,14 @@ QTV_API int qtv_emit_samples(qtv_handle h, uint64_t n, const uint64_t* face_ids,
  * must not touch the device heap, and latency-critical loops where cudaMalloc
  * or cudaFree would synchronise the device.  For them this entry point takes
  * no handle and allocates nothing: its scratch lives in one fixed file-scope
- * device array of the library (about 10 MiB, held on every GPU that loads
+ * device array of the library (about 24 MiB, held on every GPU that loads
  * libqtv until the process exits).  The caller still passes psi and the
  * outputs, with the same meaning as in qtv_identify (no statistics).
  *
- * Limits: capacity <= QTV_STATIC_MAX_FACES and nz * ceil(ny / 7) <=
- * QTV_STATIC_MAX_SEGMENTS (enough for 512^3 tangles); larger requests are
- * rejected with QTV_ERR_ARG and a message naming the limit.
+ * Limits: capacity <= QTV_STATIC_MAX_FACES, nz * ceil(ny / 7) <=
+ * QTV_STATIC_MAX_SEGMENTS and nz * ceil(ny / 7) * ceil(nx / 64) <=
+ * QTV_STATIC_MAX_WARP_SEGMENTS (enough for 512^3 tangles); larger requests
+ * are rejected with QTV_ERR_ARG and a message naming the limit.
  * The first call on a device resolves the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before capturing any stream.  The call uses the current device.
@@ -214,6 +219,7 @@ QTV_API int qtv_emit_samples(qtv_handle h, uint64_t n, const uint64_t* face_ids,
  */
 #define QTV_STATIC_MAX_FACES (1u << 21)
 #define QTV_STATIC_MAX_SEGMENTS (1u << 17)
+#define QTV_STATIC_MAX_WARP_SEGMENTS (1u << 19)
 QTV_API int qtv_identify_static(const qtv_grid* grid, const void* psi, uint64_t* face_ids,
                                 int8_t* winding, uint64_t capacity, uint64_t* count,
                                 void* stream);

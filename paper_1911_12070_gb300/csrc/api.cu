@@ -67,9 +67,38 @@ int validate_grid(const qtv_grid* g) {
   return QTV_OK;
 }
 
-uint64_t seg_entries(const qtv_grid& g) {
-  const uint64_t nbands = (uint64_t)(g.ny + kRows - 1) / kRows;
-  return nbands * (uint64_t)g.nz;
+// Grow the handle workspace to what one identification call needs.
+int grow_identify(qtv_handle h, const qtv_grid& g, uint64_t capacity, const void* psi,
+                  cudaStream_t st) {
+  IdentNeeds n;
+  int rc = identify_needs(h->num_sms, g, capacity, psi, 0, &n);
+  if (rc) return rc;
+  if (n.staging > 0xFFFFFFFFull)
+    return set_error(QTV_ERR_ARG, "staging above 2^32 records is not supported");
+  rc = grow(h->ws.staging, h->ws.staging_cap, n.staging > 0 ? n.staging : 1, st,
+            "cudaMalloc(staging)");
+  if (!rc && n.seg) rc = grow(h->ws.seg, h->ws.seg_cap, n.seg, st, "cudaMalloc(seg)");
+  if (!rc && n.table) rc = grow(h->ws.table, h->ws.table_cap, n.table, st, "cudaMalloc(table)");
+  if (!rc && n.seg_off)
+    rc = grow(h->ws.seg_off, h->ws.seg_off_cap, n.seg_off, st, "cudaMalloc(seg_off)");
+  if (!rc && n.tiles) rc = grow(h->ws.tiles, h->ws.tiles_cap, n.tiles, st, "cudaMalloc(tiles)");
+  return rc;
+}
+
+IdentScratch scratch_of(qtv_handle h) {
+  IdentScratch sc;
+  sc.staging = h->ws.staging;
+  sc.staging_cap = h->ws.staging_cap;
+  sc.seg = h->ws.seg;
+  sc.seg_cap = h->ws.seg_cap;
+  sc.table = h->ws.table;
+  sc.table_cap = h->ws.table_cap;
+  sc.seg_off = h->ws.seg_off;
+  sc.seg_off_cap = h->ws.seg_off_cap;
+  sc.tiles = h->ws.tiles;
+  sc.tiles_cap = h->ws.tiles_cap;
+  sc.counters = h->ws.counters;
+  return sc;
 }
 }  // namespace
 
@@ -166,6 +195,8 @@ int qtv_destroy(qtv_handle h) {
   cudaFree(h->ws.seg_off);
   cudaFree(h->ws.counters);
   cudaFree(h->ws.pack);
+  cudaFree(h->ws.table);
+  cudaFree(h->ws.tiles);
   for (auto& r : h->trace) {
     cudaEventDestroy(r.start);
     cudaEventDestroy(r.stop);
@@ -226,13 +257,8 @@ int qtv_reserve(qtv_handle h, const qtv_grid* grid, uint64_t max_faces) {
   DeviceGuard dg(h->device);
   if (max_faces > 0xFFFFFFFFull)
     return set_error(QTV_ERR_ARG, "max_faces above 2^32-1 is not supported");
-  rc = grow(h->ws.staging, h->ws.staging_cap, max_faces > 0 ? max_faces : 1, nullptr,
-            "cudaMalloc(staging)");
-  if (rc) return rc;
-  const uint64_t ns = seg_entries(*grid) > 0 ? seg_entries(*grid) : 1;
-  rc = grow(h->ws.seg, h->ws.seg_cap, ns, nullptr, "cudaMalloc(seg)");
-  if (rc) return rc;
-  rc = grow(h->ws.seg_off, h->ws.seg_off_cap, ns, nullptr, "cudaMalloc(seg_off)");
+  // psi alignment decides the kernel; reserve for the staged sweep's layout
+  rc = grow_identify(h, *grid, max_faces, reinterpret_cast<const void*>(256), nullptr);
   if (rc) return rc;
   rc = grow(h->ws.pack, h->ws.pack_cap, max_faces > 0 ? max_faces : 1, nullptr,
             "cudaMalloc(pack)");
@@ -265,20 +291,10 @@ int qtv_identify(qtv_handle h, const qtv_grid* grid, const void* psi, uint64_t* 
     if (e == cudaSuccess && stats) e = cudaMemsetAsync(stats, 0, sizeof(qtv_stats), st);
     return check_cuda(e, "cudaMemsetAsync(count)");
   }
-  // staging holds every staged face up to the output capacity (at least one
-  // record so that count-only calls still have a valid buffer)
-  const uint64_t want_stage = capacity > 0 ? capacity : 1;
-  rc = grow(h->ws.staging, h->ws.staging_cap, want_stage, st, "cudaMalloc(staging)");
+  rc = grow_identify(h, g, capacity, psi, st);
   if (rc) return rc;
-  const uint64_t ns = seg_entries(g);
-  rc = grow(h->ws.seg, h->ws.seg_cap, ns, st, "cudaMalloc(seg)");
-  if (rc) return rc;
-  rc = grow(h->ws.seg_off, h->ws.seg_off_cap, ns, st, "cudaMalloc(seg_off)");
-  if (rc) return rc;
-  const uint64_t stage_cap = capacity > 0 ? capacity : 0;
   return identify_launch(h, g, reinterpret_cast<const float2*>(psi), face_ids, winding, capacity,
-                         count, stats, st, h->ws.staging, stage_cap, h->ws.seg, h->ws.seg_off,
-                         h->ws.counters);
+                         count, stats, st, scratch_of(h), 0);
 }
 
 int qtv_localize(qtv_handle h, const qtv_grid* grid, const void* psi, const uint64_t* face_ids,

@@ -425,7 +425,8 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(SweepArgs a) {
 __global__ void __launch_bounds__(1024) seg_scan_kernel(const uint2* __restrict__ seg, long long nseg,
                                                         unsigned long long* __restrict__ seg_off,
                                                         uint64_t* __restrict__ count,
-                                                        qtv_stats* stats, unsigned long long scanned) {
+                                                        qtv_stats* stats, unsigned long long scanned,
+                                                        const unsigned long long* status) {
   __shared__ unsigned long long warp_tot[32];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const long long per = (nseg + blockDim.x - 1) / blockDim.x;
@@ -450,7 +451,8 @@ __global__ void __launch_bounds__(1024) seg_scan_kernel(const uint2* __restrict_
     }
     warp_tot[lane] = iv - v;
     if (lane == 31) {
-      *count = iv;
+      // a bounded wait that gave up in the sweep makes the result unusable
+      *count = (*status & 0xffffffffull) ? QTV_COUNT_TIMEOUT : iv;
       if (stats) {
         stats->pierced = iv;
         stats->faces_scanned = scanned;
@@ -581,10 +583,47 @@ LaunchShape sweep_shape(int nw, bool vec) {
 
 }  // namespace
 
+int identify_needs(int num_sms, const qtv_grid& g, uint64_t capacity, const void* psi,
+                   uint64_t max_warps, IdentNeeds* n) {
+  *n = IdentNeeds();
+  const uint64_t nbands = (uint64_t)(g.ny + R - 1) / R;
+  const uint64_t nseg = nbands * (uint64_t)g.nz;
+  if (sweep_bulk_supported(g.nx, g.ny, g.nz, psi)) {
+    BulkNeeds b;
+    const int rc = bulk_needs(num_sms, g, capacity, max_warps, &b);
+    if (rc) return rc;
+    n->staging = b.recs;
+    n->table = b.table;
+    n->seg_off = b.seg_off;
+    n->tiles = b.tiles;
+  } else {
+    n->staging = capacity > 0 ? capacity : 1;
+    n->seg = nseg;
+    n->seg_off = nseg;
+  }
+  return QTV_OK;
+}
+
 int identify_launch(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* face_ids,
                     int8_t* winding, uint64_t capacity, uint64_t* count, qtv_stats* stats,
-                    cudaStream_t st, uint32_t* staging, uint64_t staging_cap, uint2* seg,
-                    unsigned long long* seg_off, unsigned long long* counters) {
+                    cudaStream_t st, const IdentScratch& sc, uint64_t max_warps) {
+  if (sweep_bulk_supported(g.nx, g.ny, g.nz, psi)) {
+    const int rc = bulk_identify(h, g, psi, face_ids, winding, capacity, count, stats, st, sc,
+                                 max_warps);
+    if (rc) return rc;
+    if (stats) {
+      TraceScope ts(h, K_STATS, st);
+      stats_kernel<<<h->num_sms * 8, 256, 0, st>>>(psi, g.nx, g.ny, g.nz, stats);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return check_cuda(e, "stats_kernel launch");
+    }
+    return QTV_OK;
+  }
+  uint32_t* staging = sc.staging;
+  const uint64_t staging_cap = capacity;
+  uint2* seg = sc.seg;
+  unsigned long long* seg_off = sc.seg_off;
+  unsigned long long* counters = sc.counters;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int nw = (nx + 63) / 64;
   const int nbands = (ny + R - 1) / R;
@@ -621,20 +660,22 @@ int identify_launch(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t
   a.staging_top = counters;
   a.seg = seg;
   a.stats = stats;
-  const int grid = (int)(nitems < resident ? nitems : resident);
   {
-    TraceScope ts(h, K_SWEEP, st);
-    sweep_fn(nw, vec)<<<grid, shp.threads, 0, st>>>(a);
+    const int grid = (int)(nitems < resident ? nitems : resident);
+    {
+      TraceScope ts(h, K_SWEEP, st);
+      sweep_fn(nw, vec)<<<grid, shp.threads, 0, st>>>(a);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return check_cuda(e, "sweep_kernel launch");
   }
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return check_cuda(e, "sweep_kernel launch");
 
   const unsigned long long scanned =
       (unsigned long long)(nx - 1) * (ny - 1) * nz + (unsigned long long)nx * (ny - 1) * (nz - 1) +
       (unsigned long long)(nx - 1) * ny * (nz - 1);
   {
     TraceScope ts(h, K_SEG_SCAN, st);
-    seg_scan_kernel<<<1, 1024, 0, st>>>(seg, nseg, seg_off, count, stats, scanned);
+    seg_scan_kernel<<<1, 1024, 0, st>>>(seg, nseg, seg_off, count, stats, scanned, counters + 2);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return check_cuda(e, "seg_scan_kernel launch");

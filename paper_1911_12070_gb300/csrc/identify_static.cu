@@ -11,11 +11,22 @@
 namespace qtv {
 namespace {
 
-constexpr unsigned long long kStagingBytes = (unsigned long long)QTV_STATIC_MAX_FACES * 4ull;
+// Layout of the scratch array.  Staging holds one 32-bit record per pierced
+// face (or per lane and row with faces), plus the slack that per-warp record
+// chunks may leave unused: 2 chunks of 64 records for each of at most
+// kMaxWarps resident warps.
+constexpr unsigned long long kMaxWarps = 8192;
+constexpr unsigned long long kStagingRecs = (unsigned long long)QTV_STATIC_MAX_FACES + 2ull * 64 * kMaxWarps + 64;
+constexpr unsigned long long kTableEntries = (unsigned long long)QTV_STATIC_MAX_WARP_SEGMENTS;
+constexpr unsigned long long kTileEntries = 256;
+constexpr unsigned long long kStagingBytes = kStagingRecs * 4ull;
+constexpr unsigned long long kTableBytes = kTableEntries * 16ull;
 constexpr unsigned long long kSegBytes = (unsigned long long)QTV_STATIC_MAX_SEGMENTS * 8ull;
 constexpr unsigned long long kSegOffBytes = (unsigned long long)QTV_STATIC_MAX_SEGMENTS * 8ull;
+constexpr unsigned long long kTileBytes = kTileEntries * 8ull;
 constexpr unsigned long long kCounterBytes = 256ull;
-constexpr unsigned long long kStaticBytes = kStagingBytes + kSegBytes + kSegOffBytes + kCounterBytes;
+constexpr unsigned long long kStaticBytes =
+    kTableBytes + kSegBytes + kSegOffBytes + kTileBytes + kCounterBytes + kStagingBytes;
 
 // The scratch.  In host code this name is only a host-side stand-in: the
 // device address comes from cudaGetSymbolAddress below.
@@ -92,16 +103,41 @@ extern "C" int qtv_identify_static(const qtv_grid* grid, const void* psi, uint64
   if (rc) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (nn == 0) return check_cuda(cudaMemsetAsync(count, 0, sizeof(uint64_t), st), "cudaMemsetAsync");
-  uint32_t* staging = reinterpret_cast<uint32_t*>(base);
-  uint2* seg = reinterpret_cast<uint2*>(base + kStagingBytes);
-  unsigned long long* seg_off = reinterpret_cast<unsigned long long*>(base + kStagingBytes + kSegBytes);
-  unsigned long long* counters =
-      reinterpret_cast<unsigned long long*>(base + kStagingBytes + kSegBytes + kSegOffBytes);
+  IdentNeeds need;
+  rc = identify_needs(num_sms, g, capacity, psi, kMaxWarps, &need);
+  if (rc) return rc;
+  if (need.table > kTableEntries)
+    return set_error(QTV_ERR_ARG,
+                     "qtv_identify_static: grid needs %llu (plane, band, warp) table entries "
+                     "(nz * ceil(ny / 7) * ceil(nx / 64)), above the static scratch limit of %u "
+                     "(QTV_STATIC_MAX_WARP_SEGMENTS)",
+                     (unsigned long long)need.table, (unsigned)QTV_STATIC_MAX_WARP_SEGMENTS);
+  if (need.staging > kStagingRecs || need.seg > QTV_STATIC_MAX_SEGMENTS ||
+      need.seg_off > QTV_STATIC_MAX_SEGMENTS || need.tiles > kTileEntries)
+    return set_error(QTV_ERR_ARG, "qtv_identify_static: request exceeds the static scratch");
+  unsigned char* p = base;
+  IdentScratch sc;
+  sc.table = reinterpret_cast<uint4*>(p);
+  sc.table_cap = kTableEntries;
+  p += kTableBytes;
+  sc.seg = reinterpret_cast<uint2*>(p);
+  sc.seg_cap = QTV_STATIC_MAX_SEGMENTS;
+  p += kSegBytes;
+  sc.seg_off = reinterpret_cast<unsigned long long*>(p);
+  sc.seg_off_cap = QTV_STATIC_MAX_SEGMENTS;
+  p += kSegOffBytes;
+  sc.tiles = reinterpret_cast<unsigned long long*>(p);
+  sc.tiles_cap = kTileEntries;
+  p += kTileBytes;
+  sc.counters = reinterpret_cast<unsigned long long*>(p);
+  p += kCounterBytes;
+  sc.staging = reinterpret_cast<uint32_t*>(p);
+  sc.staging_cap = kStagingRecs;
   // identify_launch only reads the SM count and the (off) trace switch of its
   // handle argument; a stack handle carries them without any allocation.
   qtv_handle_s tmp;
   tmp.device = dev;
   tmp.num_sms = num_sms;
   return identify_launch(&tmp, g, reinterpret_cast<const float2*>(psi), face_ids, winding,
-                         capacity, count, nullptr, st, staging, capacity, seg, seg_off, counters);
+                         capacity, count, nullptr, st, sc, kMaxWarps);
 }

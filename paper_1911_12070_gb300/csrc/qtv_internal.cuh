@@ -25,6 +25,31 @@ struct Workspace {
   uint64_t seg_off_cap = 0;
   qtv_sample* pack = nullptr;         // emission staging (device)
   uint64_t pack_cap = 0;
+  uint4* table = nullptr;             // per (plane, band, warp) record table
+  uint64_t table_cap = 0;
+  unsigned long long* tiles = nullptr;  // look-back state of the segment scan
+  uint64_t tiles_cap = 0;
+};
+
+// Raw scratch pointers of one identification call (handle workspace or the
+// static array of qtv_identify_static).
+struct IdentScratch {
+  uint32_t* staging = nullptr;  // face records (register sweep) / lane-row records (staged sweep)
+  uint64_t staging_cap = 0;
+  uint2* seg = nullptr;         // register sweep: per (plane, band) {count, base}
+  uint64_t seg_cap = 0;
+  uint4* table = nullptr;       // staged sweep: per (plane, band, warp) entry
+  uint64_t table_cap = 0;
+  unsigned long long* seg_off = nullptr;
+  uint64_t seg_off_cap = 0;
+  unsigned long long* tiles = nullptr;
+  uint64_t tiles_cap = 0;
+  unsigned long long* counters = nullptr;  // 8 words
+};
+
+// Entries of each scratch array that one call needs.
+struct IdentNeeds {
+  uint64_t staging = 0, seg = 0, table = 0, seg_off = 0, tiles = 0;
 };
 
 }  // namespace qtv
@@ -81,10 +106,25 @@ struct SweepArgs {
 constexpr int kRows = 7;          // owned rows per band (plus one halo row)
 constexpr int kMaxWarpsX = 32;    // nx <= 64 * 32
 
+// max_warps bounds the resident warps of the staged sweep (0 = no bound); it
+// bounds the staging slack that per-warp record chunks can leave unused.
+int identify_needs(int num_sms, const qtv_grid& g, uint64_t capacity, const void* psi,
+                   uint64_t max_warps, IdentNeeds* n);
 int identify_launch(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* face_ids,
                     int8_t* winding, uint64_t capacity, uint64_t* count, qtv_stats* stats,
-                    cudaStream_t st, uint32_t* staging, uint64_t staging_cap, uint2* seg,
-                    unsigned long long* seg_off, unsigned long long* counters);
+                    cudaStream_t st, const IdentScratch& sc, uint64_t max_warps);
+
+// Bulk-copy staged sweep with per-warp compaction (sweep_bulk.cu): even
+// nx <= 1024, 16-byte aligned psi.
+struct BulkNeeds {
+  uint64_t recs = 0, table = 0, seg_off = 0, tiles = 0;
+};
+bool sweep_bulk_supported(int nx, int ny, int nz, const void* psi);
+int bulk_needs(int num_sms, const qtv_grid& g, uint64_t capacity, uint64_t max_warps,
+               BulkNeeds* n);
+int bulk_identify(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* face_ids,
+                  int8_t* winding, uint64_t capacity, uint64_t* count, qtv_stats* stats,
+                  cudaStream_t st, const IdentScratch& sc, uint64_t max_warps);
 
 // Localization launch (localize.cu)
 int localize_launch(qtv_handle h, const qtv_grid& g, const float2* psi, const uint64_t* face_ids,
