@@ -201,7 +201,7 @@ QTV_API int qtv_emit_samples(qtv_handle h, uint64_t n, const uint64_t* face_ids,
  * must not touch the device heap, and latency-critical loops where cudaMalloc
  * or cudaFree would synchronise the device.  For them this entry point takes
  * no handle and allocates nothing: its scratch lives in one fixed file-scope
- * device array of the library (about 24 MiB, held on every GPU that loads
+ * device array of the library (about 64 MiB, held on every GPU that loads
  * libqtv until the process exits).  The caller still passes psi and the
  * outputs, with the same meaning as in qtv_identify (no statistics).
  *

@@ -11,15 +11,15 @@
 namespace qtv {
 namespace {
 
-// Layout of the scratch array.  Staging holds one 32-bit record per pierced
-// face (or per lane and row with faces), plus the slack that per-warp record
-// chunks may leave unused: 2 chunks of 64 records for each of at most
-// kMaxWarps resident warps.
-constexpr unsigned long long kMaxWarps = 8192;
-constexpr unsigned long long kStagingRecs = (unsigned long long)QTV_STATIC_MAX_FACES + 2ull * 64 * kMaxWarps + 64;
+// Layout of the scratch array.  Staging holds up to one 24-byte record per
+// pierced face, plus the slack that per-warp record chunks may leave unused
+// (2 chunks of 32 records for each of at most kMaxWarps resident warps).
+constexpr unsigned long long kMaxWarps = 4096;
+constexpr unsigned long long kStagingWords =
+    6ull * ((unsigned long long)QTV_STATIC_MAX_FACES + 2ull * 32 * kMaxWarps + 32);
 constexpr unsigned long long kTableEntries = (unsigned long long)QTV_STATIC_MAX_WARP_SEGMENTS;
 constexpr unsigned long long kTileEntries = 256;
-constexpr unsigned long long kStagingBytes = kStagingRecs * 4ull;
+constexpr unsigned long long kStagingBytes = kStagingWords * 4ull;
 constexpr unsigned long long kTableBytes = kTableEntries * 16ull;
 constexpr unsigned long long kSegBytes = (unsigned long long)QTV_STATIC_MAX_SEGMENTS * 8ull;
 constexpr unsigned long long kSegOffBytes = (unsigned long long)QTV_STATIC_MAX_SEGMENTS * 8ull;
@@ -112,7 +112,7 @@ extern "C" int qtv_identify_static(const qtv_grid* grid, const void* psi, uint64
                      "(nz * ceil(ny / 7) * ceil(nx / 64)), above the static scratch limit of %u "
                      "(QTV_STATIC_MAX_WARP_SEGMENTS)",
                      (unsigned long long)need.table, (unsigned)QTV_STATIC_MAX_WARP_SEGMENTS);
-  if (need.staging > kStagingRecs || need.seg > QTV_STATIC_MAX_SEGMENTS ||
+  if (need.staging > kStagingWords || need.seg > QTV_STATIC_MAX_SEGMENTS ||
       need.seg_off > QTV_STATIC_MAX_SEGMENTS || need.tiles > kTileEntries)
     return set_error(QTV_ERR_ARG, "qtv_identify_static: request exceeds the static scratch");
   unsigned char* p = base;
@@ -132,7 +132,7 @@ extern "C" int qtv_identify_static(const qtv_grid* grid, const void* psi, uint64
   sc.counters = reinterpret_cast<unsigned long long*>(p);
   p += kCounterBytes;
   sc.staging = reinterpret_cast<uint32_t*>(p);
-  sc.staging_cap = kStagingRecs;
+  sc.staging_cap = kStagingWords;
   // identify_launch only reads the SM count and the (off) trace switch of its
   // handle argument; a stack handle carries them without any allocation.
   qtv_handle_s tmp;

@@ -8,35 +8,41 @@
 // per row (value + 1), so the four-term plaquette sums of all rows of a column
 // take three integer instructions.
 //
-// Staging.  Thread 0 copies the band rows of each plane into one slot of a
-// 3-deep ring in shared memory with cp.async.bulk (one copy per row; completion
-// counted in bytes on the slot's mbarrier).  Threads read their 16-byte pairs
-// and the x-neighbour column from shared memory, so global latency is covered
-// by the ring.  Waits are bounded (about 2^32 SM cycles); a timeout sets a
-// status bit that turns the reported count into QTV_COUNT_TIMEOUT.
+// Staging.  Each plane's band rows are copied into one slot of a 3-deep ring
+// in shared memory with cp.async.bulk (one copy per row, issued by lane 0 of
+// the warp that owns the row index modulo the warp count; completion counted
+// in bytes on the slot's mbarrier, which every warp arrives on once per fill).
+// Threads read their 16-byte pairs and the x-neighbour column from shared
+// memory.  Waits are bounded (about 2^32 SM cycles); a timeout sets a status
+// bit that turns the reported count into QTV_COUNT_TIMEOUT.
 //
-// Edge test.  The winding contribution of edge a -> b is r = s_b - s_a when
-// the edge crosses the negative real axis and 0 otherwise (s = Im < 0).  With
-// s_a != s_b that happens iff cross(a, b) = Re a Im b - Im a Re b has the sign
-// of s_b - s_a.  Its FP32 FMA evaluation fma(Re a, Im b, -RN(Im a Re b)) has
-// the exact sign in every case that matters: when Re a and Re b have equal
-// signs the two terms cannot cancel, and when they differ |d| > pi/2, so a
-// wrong sign needs |sin d| < 2^-24, an edge within 1e-7 rad of +-pi (an
-// ambiguous edge).  Only the "cross > 0" bit is formed; a zero cross product
-// (a node with psi == 0) needs both comparisons, so a warp whose planes hold a
-// zero or non-finite node takes an exact path with both comparisons and drops
-// the faces that touch non-finite nodes.
+// Edge test.  Phases follow the IEEE atan2 convention theta in [-pi, pi]
+// with the sign of a zero imaginary part deciding +pi or -pi, so a node is in
+// the lower half-plane (s = 1) iff the sign bit of Im psi is set.  The
+// branch-crossing integer of edge a -> b is r = s_b - s_a when the edge
+// crosses the branch cut (arg = +-pi) and 0 otherwise; with s_a != s_b this
+// happens iff the sign bit of cross(a, b) = Re a Im b - Im a Re b is clear
+// (s_a = 0) or set (s_a = 1).  The FP32 FMA evaluation
+// fma(Re a, Im b, -RN(Im a Re b)) gives that sign bit exactly in every case
+// that matters: when Re a and Re b have equal signs the two terms cannot
+// cancel (and signed-zero results follow IEEE rules that match the atan2
+// convention), and when they differ |d| > pi/2, so a wrong sign needs
+// |sin d| < 2^-24, an edge within 1e-7 rad of +-pi (an ambiguous edge).
+// Sign bits are gathered four bits per row with one funnel shift each.  A
+// node with psi == 0 has no phase; it is read as phase 0, which makes every
+// edge that touches it contribute 0.  Warps whose planes hold a zero or a
+// non-finite node (detected by a product of |Re| + |Im|) take a path that
+// masks those edges and drops the faces that touch non-finite nodes.
 //
-// Compaction.  Each warp, each plane, emits one 32-bit record per (lane, row)
-// that has a pierced face: the six (W+4)^4 nibbles of the lane's two columns
-// and three orientations, the lane and the row.  Record positions come from
-// per-row warp ballots, so no shuffle scan and no cross-warp step is needed;
-// records go to per-warp chunks of a staging buffer reserved with one global
-// atomic per chunk (prefetched), and a 16-byte table entry per (plane, band,
-// warp) says where they are and how many faces they hold.  A finalize pass
-// scans the face totals in (plane, band) order (single pass, decoupled
-// look-back) and expands the records of each segment in (row, warp, lane)
-// order, which is ascending face-id order.
+// Compaction.  Each warp, each plane, emits one 24-byte record per lane that
+// has a pierced face: the six packed (W+4)^4 fields of its two columns and
+// three orientations (rows 0..6) plus the lane index.  Record positions come
+// from one warp ballot; records go to per-warp chunks of a staging buffer
+// reserved with one global atomic per chunk (prefetched), and a 16-byte table
+// entry per (plane, band, warp) says where they are and how many faces they
+// hold.  A finalize pass scans the face totals in (plane, band) order (single
+// pass, decoupled look-back) and expands the records of each segment row by
+// row, in (warp, lane) order, which is ascending face-id order.
 //
 // Schedule.  Work units are (plane, band) pairs ordered (z block, band, plane)
 // and cut into one contiguous range per CTA, so all CTAs get the same number
@@ -53,8 +59,9 @@ constexpr int RH = R + 1;
 constexpr int kStages = 3;
 constexpr uint32_t kOnes = 0x11111111u;
 constexpr uint32_t kFours = 0x44444444u;
-constexpr uint32_t kOwned = 0x0FFFFFFFu;
 constexpr uint32_t kOwnedBits = 0x01111111u;  // bit 0 of the fields of rows 0..6
+constexpr uint32_t kBit3 = 0x88888888u;
+constexpr int kRecWords = 6;                   // 32-bit words per staged record
 
 __device__ __forceinline__ uint32_t nz_fields(uint32_t d) {
   uint32_t t = d | (d >> 2);
@@ -124,95 +131,102 @@ __device__ __forceinline__ float cross_f(float ar, float ai, float br, float bi)
   return fmaf(ar, bi, -(ai * br));
 }
 
-// s-bits (Im < 0) of one column over the RH rows, one bit per 4-bit field
+// acc' = (acc << 4) | top nibble of x: the sign bit of x lands in bit 3 of a
+// new lowest field.  Push rows from the highest to the lowest.
+__device__ __forceinline__ uint32_t push_sign(uint32_t acc, float x) {
+  return __funnelshift_l(__float_as_uint(x), acc, 4);
+}
+// keep bit 3 of each field and move it to bit 0
+__device__ __forceinline__ uint32_t fields_of(uint32_t acc) { return (acc & kBit3) >> 3; }
+
+// sign bits of Im psi of one column over the RH rows (bit 0 of field r)
 __device__ __forceinline__ uint32_t sbits_col(const float4* v, int p) {
-  uint32_t s = 0;
+  uint32_t acc = 0;
 #pragma unroll
-  for (int r = 0; r < RH; ++r)
-    if ((p ? v[r].w : v[r].y) < 0.f) s |= 1u << (4 * r);
-  return s;
+  for (int r = RH - 1; r >= 0; --r) acc = push_sign(acc, p ? v[r].w : v[r].y);
+  return fields_of(acc);
 }
 __device__ __forceinline__ uint32_t sbits_nb(const float2* v) {
-  uint32_t s = 0;
+  uint32_t acc = 0;
+#pragma unroll
+  for (int r = RH - 1; r >= 0; --r) acc = push_sign(acc, v[r].y);
+  return fields_of(acc);
+}
+// psi == 0 (both parts +-0) bits of a column
+__device__ __forceinline__ uint32_t zbits_col(const float4* v, int p) {
+  uint32_t z = 0;
+#pragma unroll
+  for (int r = 0; r < RH; ++r) {
+    const uint32_t b = (__float_as_uint(p ? v[r].z : v[r].x) | __float_as_uint(p ? v[r].w : v[r].y)) << 1;
+    if (b == 0u) z |= 1u << (4 * r);
+  }
+  return z;
+}
+__device__ __forceinline__ uint32_t zbits_nb(const float2* v) {
+  uint32_t z = 0;
 #pragma unroll
   for (int r = 0; r < RH; ++r)
-    if (v[r].y < 0.f) s |= 1u << (4 * r);
-  return s;
+    if (((__float_as_uint(v[r].x) | __float_as_uint(v[r].y)) << 1) == 0u) z |= 1u << (4 * r);
+  return z;
 }
 
-// packed edge values (value + 1 per field) from tail/head s-bits and the
-// cross-sign bits
-__device__ __forceinline__ uint32_t pack_fast(uint32_t SA, uint32_t SB, uint32_t CP) {
-  return kOnes + (~SA & SB & CP) - (SA & ~SB & ~CP);
-}
-__device__ __forceinline__ uint32_t pack_exact(uint32_t SA, uint32_t SB, uint32_t CP, uint32_t CN) {
-  return kOnes + (~SA & SB & CP) - (SA & ~SB & CN);
+// packed edge values (value + 1 per field) from tail/head s-bits, the
+// cross-negative bits N and the edges E that touch a zero node
+__device__ __forceinline__ uint32_t pack_edges(uint32_t SA, uint32_t SB, uint32_t N, uint32_t E) {
+  return kOnes + (~SA & SB & ~N & ~E) - (SA & ~SB & N & ~E);
 }
 
 struct SmallSmem {
   uint2 xbits[2][kMaxWarpsX];  // {rz_k, ry_k+1} fields of column x0 of each warp
 };
 
-constexpr uint32_t kChunk = 64;    // records per staging chunk
-constexpr uint32_t kLowWater = 24; // prefetch the next chunk below this
+constexpr uint32_t kChunk = 32;     // records per staging chunk
+constexpr uint32_t kLowWater = 12;  // prefetch the next chunk below this
 
-// Edge fields of one step.  In: plane k (cur, s-bits Sk0/Sk1) and plane k+1
-// (nxt, nb column nbv).  EXACT selects both comparisons (zero nodes).
-template <bool EXACT>
-__device__ __forceinline__ void step_edges(const float4* cur, const float4* nxt, const float2* nbv,
-                                           uint32_t Sk0, uint32_t Sk1, uint32_t& S0n,
-                                           uint32_t& S1n, uint32_t& SNn, uint32_t& RZ0,
+// Edge fields of one step.  In: plane k (C, s-bits Sk0/Sk1, zero bits Zk*) and
+// plane k+1 (N, neighbour column nbv).  ZERO masks edges at zero nodes.
+template <bool ZERO>
+__device__ __forceinline__ void step_edges(const float4* C, const float4* N, const float2* nbv,
+                                           uint32_t Sk0, uint32_t Sk1, uint32_t Zk0,
+                                           uint32_t Zk1, uint32_t& S0n, uint32_t& S1n,
+                                           uint32_t& Z0n, uint32_t& Z1n, uint32_t& RZ0,
                                            uint32_t& RZ1, uint32_t& RX0n, uint32_t& RX1n,
                                            uint32_t& RY0n, uint32_t& RY1n) {
-  S0n = sbits_col(nxt, 0);
-  S1n = sbits_col(nxt, 1);
-  SNn = sbits_nb(nbv);
-  uint32_t pz0 = 0, pz1 = 0, px0 = 0, px1 = 0, py0 = 0, py1 = 0;
-  uint32_t nz0 = 0, nz1 = 0, nx0 = 0, nx1 = 0, ny0 = 0, ny1 = 0;
+  S0n = sbits_col(N, 0);
+  S1n = sbits_col(N, 1);
+  const uint32_t SNn = sbits_nb(nbv);
+  uint32_t az0 = 0, az1 = 0, ax0 = 0, ax1 = 0, ay0 = 0, ay1 = 0;
 #pragma unroll
-  for (int r = 0; r < RH; ++r) {
-    const uint32_t bit = 1u << (4 * r);
-    const float cz0 = cross_f(cur[r].x, cur[r].y, nxt[r].x, nxt[r].y);
-    const float cz1 = cross_f(cur[r].z, cur[r].w, nxt[r].z, nxt[r].w);
-    const float cx0 = cross_f(nxt[r].x, nxt[r].y, nxt[r].z, nxt[r].w);
-    const float cx1 = cross_f(nxt[r].z, nxt[r].w, nbv[r].x, nbv[r].y);
-    if (cz0 > 0.f) pz0 |= bit;
-    if (cz1 > 0.f) pz1 |= bit;
-    if (cx0 > 0.f) px0 |= bit;
-    if (cx1 > 0.f) px1 |= bit;
-    if (EXACT) {
-      if (cz0 < 0.f) nz0 |= bit;
-      if (cz1 < 0.f) nz1 |= bit;
-      if (cx0 < 0.f) nx0 |= bit;
-      if (cx1 < 0.f) nx1 |= bit;
-    }
+  for (int r = RH - 1; r >= 0; --r) {
+    az0 = push_sign(az0, cross_f(C[r].x, C[r].y, N[r].x, N[r].y));
+    az1 = push_sign(az1, cross_f(C[r].z, C[r].w, N[r].z, N[r].w));
+    ax0 = push_sign(ax0, cross_f(N[r].x, N[r].y, N[r].z, N[r].w));
+    ax1 = push_sign(ax1, cross_f(N[r].z, N[r].w, nbv[r].x, nbv[r].y));
     if (r < R) {
-      const float cy0 = cross_f(nxt[r].x, nxt[r].y, nxt[r + 1].x, nxt[r + 1].y);
-      const float cy1 = cross_f(nxt[r].z, nxt[r].w, nxt[r + 1].z, nxt[r + 1].w);
-      if (cy0 > 0.f) py0 |= bit;
-      if (cy1 > 0.f) py1 |= bit;
-      if (EXACT) {
-        if (cy0 < 0.f) ny0 |= bit;
-        if (cy1 < 0.f) ny1 |= bit;
-      }
+      ay0 = push_sign(ay0, cross_f(N[r].x, N[r].y, N[r + 1].x, N[r + 1].y));
+      ay1 = push_sign(ay1, cross_f(N[r].z, N[r].w, N[r + 1].z, N[r + 1].w));
     }
   }
-  const uint32_t SY0 = S0n & kOwnedBits, SY1 = S1n & kOwnedBits;
-  if (EXACT) {
-    RZ0 = pack_exact(Sk0, S0n, pz0, nz0);
-    RZ1 = pack_exact(Sk1, S1n, pz1, nz1);
-    RX0n = pack_exact(S0n, S1n, px0, nx0);
-    RX1n = pack_exact(S1n, SNn, px1, nx1);
-    RY0n = pack_exact(SY0, S0n >> 4, py0, ny0);
-    RY1n = pack_exact(SY1, S1n >> 4, py1, ny1);
-  } else {
-    RZ0 = pack_fast(Sk0, S0n, pz0);
-    RZ1 = pack_fast(Sk1, S1n, pz1);
-    RX0n = pack_fast(S0n, S1n, px0);
-    RX1n = pack_fast(S1n, SNn, px1);
-    RY0n = pack_fast(SY0, S0n >> 4, py0);
-    RY1n = pack_fast(SY1, S1n >> 4, py1);
+  uint32_t Ez0 = 0, Ez1 = 0, Ex0 = 0, Ex1 = 0, Ey0 = 0, Ey1 = 0;
+  Z0n = 0;
+  Z1n = 0;
+  if (ZERO) {
+    Z0n = zbits_col(N, 0);
+    Z1n = zbits_col(N, 1);
+    const uint32_t ZN = zbits_nb(nbv);
+    Ez0 = Zk0 | Z0n;
+    Ez1 = Zk1 | Z1n;
+    Ex0 = Z0n | Z1n;
+    Ex1 = Z1n | ZN;
+    Ey0 = Z0n | (Z0n >> 4);
+    Ey1 = Z1n | (Z1n >> 4);
   }
+  RZ0 = pack_edges(Sk0, S0n, fields_of(az0), Ez0);
+  RZ1 = pack_edges(Sk1, S1n, fields_of(az1), Ez1);
+  RX0n = pack_edges(S0n, S1n, fields_of(ax0), Ex0);
+  RX1n = pack_edges(S1n, SNn, fields_of(ax1), Ex1);
+  RY0n = pack_edges(S0n & kOwnedBits, S0n >> 4, fields_of(ay0), Ey0);
+  RY1n = pack_edges(S1n & kOwnedBits, S1n >> 4, fields_of(ay1), Ey1);
 }
 
 // non-finite bits of a column (one bit per field)
@@ -233,12 +247,23 @@ __device__ __forceinline__ uint32_t badbits_nb(const float2* v) {
   return b;
 }
 
+// product of |Re| + |Im| over the 3 columns of one plane: 0 when a node is
+// zero, non-finite when a node is; also 0 / infinite on FP32 under- and
+// overflow, which merely selects the masking path
+__device__ __forceinline__ bool plane_special(const float4* v, const float2* nbv) {
+  float prod = 1.f;
+#pragma unroll
+  for (int r = 0; r < RH; ++r)
+    prod *= (fabsf(v[r].x) + fabsf(v[r].y)) * (fabsf(v[r].z) + fabsf(v[r].w)) *
+            (fabsf(nbv[r].x) + fabsf(nbv[r].y));
+  return !(prod > 0.f && prod <= 3.402823466e38f);
+}
 
 struct V3Args {
   const float2* psi;
   int nx, ny, nz, nbands, hblock;
-  uint32_t* recs;
-  unsigned long long recs_cap;
+  uint32_t* recs;                // kRecWords words per record
+  unsigned long long recs_cap;   // records
   unsigned long long* counters;  // [0] chunk top, [1] status bits, [2] scan ticket
   uint4* table;                  // [(k * nbands + band) * NW + w]
 };
@@ -284,15 +309,15 @@ __global__ void __launch_bounds__(MAXT, MINB) sweep_bulk_kernel(V3Args a) {
   const uint32_t lt = (1u << lane) - 1u;
 
   // columns [nx, W) of every slot row are never copied: fill them with 1 (a
-  // finite, nonzero value, so that padding never sends a warp down the exact
-  // path; faces that touch padding do not exist and are masked anyway)
+  // finite, nonzero value, so that padding never selects the masking path;
+  // faces that touch padding do not exist and are masked anyway)
   {
     const int pad = W - nx;
     for (int idx = tid; idx < kStages * RH * pad; idx += blockDim.x)
       ring[(size_t)(idx / pad) * W + nx + idx % pad] = make_float2(1.f, 0.f);
   }
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) mbar_init(&mbar[s], 1);
+    for (int s = 0; s < kStages; ++s) mbar_init(&mbar[s], (uint32_t)NW);
     fence_mbar_init();
   }
   __syncthreads();
@@ -328,14 +353,18 @@ __global__ void __launch_bounds__(MAXT, MINB) sweep_bulk_kernel(V3Args a) {
       __syncthreads();
     }
 
-    auto issue = [&](int m) {  // copy plane m of the band into the next slot
-      if (tid == 0) {
-        uint64_t* bar = &mbar[fill % kStages];
-        float2* dst = ring + (size_t)(fill % kStages) * RH * W;
-        fence_proxy_async();
-        mbar_arrive_expect_tx(bar, row_bytes * (uint32_t)nrows);
+    // every warp arrives once per fill, lane 0 copying the rows r == w (mod NW)
+    auto issue = [&](int m) {
+      if (lane == 0) {
+        const int s = fill % kStages;
+        uint64_t* bar = &mbar[s];
+        float2* dst = ring + (size_t)s * RH * W;
         const float2* src = a.psi + (size_t)m * plane + (size_t)j0 * nx;
-        for (int r = 0; r < nrows; ++r)
+        uint32_t mine = 0;
+        for (int r = w; r < nrows; r += NW) ++mine;
+        fence_proxy_async();
+        mbar_arrive_expect_tx(bar, row_bytes * mine);
+        for (int r = w; r < nrows; r += NW)
           bulk_g2s(dst + (size_t)r * W, src + (size_t)r * nx, row_bytes, bar);
       }
       ++fill;
@@ -361,9 +390,9 @@ __global__ void __launch_bounds__(MAXT, MINB) sweep_bulk_kernel(V3Args a) {
     // ---- prologue: plane kb
     for (int i = 0; i < min(kStages, nplanes); ++i) issue(kb + i);
     float4 bufA[RH], bufB[RH];
-    uint32_t Sk0, Sk1, RX0, RX1, RY0, RY1, RYN;
+    uint32_t Sk0, Sk1, Zk0 = 0, Zk1 = 0, RX0, RX1, RY0, RY1, RYN;
     bool bad_k;
-    uint32_t Bk0 = 0, Bk1 = 0, BkN = 0;  // non-finite bits of plane k (exact path only)
+    uint32_t Bk0 = 0, Bk1 = 0, BkN = 0;  // non-finite bits of plane k (masking path only)
     {
       const float2* sp = acquire();
       float2 nbv[RH];
@@ -372,58 +401,45 @@ __global__ void __launch_bounds__(MAXT, MINB) sweep_bulk_kernel(V3Args a) {
         bufA[r] = *reinterpret_cast<const float4*>(sp + (size_t)r * W + x0);
         nbv[r] = nbin ? sp[(size_t)r * W + x0 + 2] : make_float2(1.f, 0.f);
       }
-      float prod = 1.f;
-#pragma unroll
-      for (int r = 0; r < RH; ++r)
-        prod *= (fabsf(bufA[r].x) + fabsf(bufA[r].y)) * (fabsf(bufA[r].z) + fabsf(bufA[r].w)) *
-                (fabsf(nbv[r].x) + fabsf(nbv[r].y));
-      bad_k = __any_sync(0xffffffffu, !(prod > 0.f && prod <= 3.402823466e38f));
+      bad_k = __any_sync(0xffffffffu, plane_special(bufA, nbv));
       Sk0 = sbits_col(bufA, 0);
       Sk1 = sbits_col(bufA, 1);
       const uint32_t SN = sbits_nb(nbv);
-      uint32_t px0 = 0, px1 = 0, py0 = 0, py1 = 0, pyn = 0, qx0 = 0, qx1 = 0, qy0 = 0, qy1 = 0,
-               qyn = 0;
+      uint32_t ax0 = 0, ax1 = 0, ay0 = 0, ay1 = 0, ayn = 0;
 #pragma unroll
-      for (int r = 0; r < RH; ++r) {
-        const uint32_t bit = 1u << (4 * r);
-        const float cx0 = cross_f(bufA[r].x, bufA[r].y, bufA[r].z, bufA[r].w);
-        const float cx1 = cross_f(bufA[r].z, bufA[r].w, nbv[r].x, nbv[r].y);
-        if (cx0 > 0.f) px0 |= bit;
-        if (cx1 > 0.f) px1 |= bit;
-        if (cx0 < 0.f) qx0 |= bit;
-        if (cx1 < 0.f) qx1 |= bit;
+      for (int r = RH - 1; r >= 0; --r) {
+        ax0 = push_sign(ax0, cross_f(bufA[r].x, bufA[r].y, bufA[r].z, bufA[r].w));
+        ax1 = push_sign(ax1, cross_f(bufA[r].z, bufA[r].w, nbv[r].x, nbv[r].y));
         if (r < R) {
-          const float cy0 = cross_f(bufA[r].x, bufA[r].y, bufA[r + 1].x, bufA[r + 1].y);
-          const float cy1 = cross_f(bufA[r].z, bufA[r].w, bufA[r + 1].z, bufA[r + 1].w);
-          const float cyn = cross_f(nbv[r].x, nbv[r].y, nbv[r + 1].x, nbv[r + 1].y);
-          if (cy0 > 0.f) py0 |= bit;
-          if (cy1 > 0.f) py1 |= bit;
-          if (cyn > 0.f) pyn |= bit;
-          if (cy0 < 0.f) qy0 |= bit;
-          if (cy1 < 0.f) qy1 |= bit;
-          if (cyn < 0.f) qyn |= bit;
+          ay0 = push_sign(ay0, cross_f(bufA[r].x, bufA[r].y, bufA[r + 1].x, bufA[r + 1].y));
+          ay1 = push_sign(ay1, cross_f(bufA[r].z, bufA[r].w, bufA[r + 1].z, bufA[r + 1].w));
+          ayn = push_sign(ayn, cross_f(nbv[r].x, nbv[r].y, nbv[r + 1].x, nbv[r + 1].y));
         }
       }
-      RX0 = pack_exact(Sk0, Sk1, px0, qx0);
-      RX1 = pack_exact(Sk1, SN, px1, qx1);
-      RY0 = pack_exact(Sk0 & kOwnedBits, Sk0 >> 4, py0, qy0);
-      RY1 = pack_exact(Sk1 & kOwnedBits, Sk1 >> 4, py1, qy1);
-      RYN = pack_exact(SN & kOwnedBits, SN >> 4, pyn, qyn);
+      uint32_t ZN = 0;
       if (bad_k) {
+        Zk0 = zbits_col(bufA, 0);
+        Zk1 = zbits_col(bufA, 1);
+        ZN = zbits_nb(nbv);
         Bk0 = badbits_col(bufA, 0);
         Bk1 = badbits_col(bufA, 1);
         BkN = badbits_nb(nbv);
       }
+      RX0 = pack_edges(Sk0, Sk1, fields_of(ax0), Zk0 | Zk1);
+      RX1 = pack_edges(Sk1, SN, fields_of(ax1), Zk1 | ZN);
+      RY0 = pack_edges(Sk0 & kOwnedBits, Sk0 >> 4, fields_of(ay0), Zk0 | (Zk0 >> 4));
+      RY1 = pack_edges(Sk1 & kOwnedBits, Sk1 >> 4, fields_of(ay1), Zk1 | (Zk1 >> 4));
+      RYN = pack_edges(SN & kOwnedBits, SN >> 4, fields_of(ayn), ZN | (ZN >> 4));
     }
     __syncthreads();  // slot of plane kb fully read
     if (kb + kStages <= klast) issue(kb + kStages);
 
-    // one z step: plane k = kb + t in C, plane k + 1 loaded into N
-    auto step = [&](float4(&C)[RH], float4(&N)[RH], int t) {
+    // one z step: plane k = kb + t in C, plane k + 1 loaded into Nn
+    auto step = [&](float4(&C)[RH], float4(&Nn)[RH], int t) {
       const int k = kb + t;
       const bool has_up = k + 1 < nz;
-      uint32_t S0n = 0, S1n = 0, SNn = 0, RZ0 = kOnes, RZ1 = kOnes, RX0n = kOnes, RX1n = kOnes,
-               RY0n = kOnes, RY1n = kOnes;
+      uint32_t S0n = 0, S1n = 0, Z0n = 0, Z1n = 0, RZ0 = kOnes, RZ1 = kOnes, RX0n = kOnes,
+               RX1n = kOnes, RY0n = kOnes, RY1n = kOnes;
       uint32_t Bn0 = 0, Bn1 = 0, BnN = 0;
       bool bad_k1 = false;
       if (has_up) {
@@ -431,22 +447,19 @@ __global__ void __launch_bounds__(MAXT, MINB) sweep_bulk_kernel(V3Args a) {
         float2 nbv[RH];
 #pragma unroll
         for (int r = 0; r < RH; ++r) {
-          N[r] = *reinterpret_cast<const float4*>(sp + (size_t)r * W + x0);
+          Nn[r] = *reinterpret_cast<const float4*>(sp + (size_t)r * W + x0);
           nbv[r] = nbin ? sp[(size_t)r * W + x0 + 2] : make_float2(1.f, 0.f);
         }
-        float prod = 1.f;
-#pragma unroll
-        for (int r = 0; r < RH; ++r)
-          prod *= (fabsf(N[r].x) + fabsf(N[r].y)) * (fabsf(N[r].z) + fabsf(N[r].w)) *
-                  (fabsf(nbv[r].x) + fabsf(nbv[r].y));
-        bad_k1 = __any_sync(0xffffffffu, !(prod > 0.f && prod <= 3.402823466e38f));
+        bad_k1 = __any_sync(0xffffffffu, plane_special(Nn, nbv));
         if (bad_k || bad_k1) {
-          step_edges<true>(C, N, nbv, Sk0, Sk1, S0n, S1n, SNn, RZ0, RZ1, RX0n, RX1n, RY0n, RY1n);
-          Bn0 = badbits_col(N, 0);
-          Bn1 = badbits_col(N, 1);
+          step_edges<true>(C, Nn, nbv, Sk0, Sk1, Zk0, Zk1, S0n, S1n, Z0n, Z1n, RZ0, RZ1, RX0n,
+                           RX1n, RY0n, RY1n);
+          Bn0 = badbits_col(Nn, 0);
+          Bn1 = badbits_col(Nn, 1);
           BnN = badbits_nb(nbv);
         } else {
-          step_edges<false>(C, N, nbv, Sk0, Sk1, S0n, S1n, SNn, RZ0, RZ1, RX0n, RX1n, RY0n, RY1n);
+          step_edges<false>(C, Nn, nbv, Sk0, Sk1, 0u, 0u, S0n, S1n, Z0n, Z1n, RZ0, RZ1, RX0n,
+                            RX1n, RY0n, RY1n);
         }
       }
       if (lane == 0) sm.xbits[t & 1][w] = make_uint2(RZ0, RY0n);
@@ -487,82 +500,71 @@ __global__ void __launch_bounds__(MAXT, MINB) sweep_bulk_kernel(V3Args a) {
 #pragma unroll
         for (int s = 0; s < 6; ++s) keep[s] &= ~((bb[s] & kOnes) * 0xFu);
       }
-      uint32_t cnt = 0, anyf = 0;
+      uint32_t cnt = 0, anyw = 0;
 #pragma unroll
       for (int s = 0; s < 6; ++s) {
         d[s] = (d[s] ^ kFours) & keep[s];
-        const uint32_t nzb = nz_fields(d[s]);
-        cnt += nzb;
-        anyf |= nzb;
+        cnt += nz_fields(d[s]);
+        anyw |= d[s];
       }
-      // ---- per-warp compaction: one record per (lane, row) with faces
+      // ---- per-warp compaction: one record per lane with faces
       const uint32_t bsum = (cnt & 0x0F0F0F0Fu) + ((cnt >> 4) & 0x0F0F0F0Fu);
       const uint32_t faces_w = __reduce_add_sync(0xffffffffu, (bsum * 0x01010101u) >> 24);
-      {
-        uint32_t bal[R], pre[R];
-        uint32_t T = 0, rc_lo = 0, rc_hi = 0;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          bal[r] = __ballot_sync(0xffffffffu, (anyf >> (4 * r)) & 1u);
-          pre[r] = T;
-          const uint32_t c = __popc(bal[r]);
-          T += c;
-          if (r < 5) rc_lo |= c << (6 * r);
-          else rc_hi |= c << (6 * (r - 5));
-        }
-        uint32_t base1 = cb, base2 = 0, n1 = T;
-        if (T > cl) {
-          const uint32_t need = T - cl;
-          uint32_t nbase, ncap;
-          if (have_next && need <= kChunk) {
-            nbase = __shfl_sync(0xffffffffu, nb_l0, 0);
-            ncap = kChunk;
-            have_next = false;
-          } else {
-            ncap = need > kChunk ? need : kChunk;
-            uint32_t x = 0;
-            if (lane == 0) {
-              const unsigned long long got = atomicAdd(a.counters, (unsigned long long)ncap);
-              x = (uint32_t)got;
-              if (got + ncap > a.recs_cap) overflow = true;
-            }
-            nbase = __shfl_sync(0xffffffffu, x, 0);
-          }
-          n1 = cl;
-          base2 = nbase;
-          cb = nbase + need;
-          cl = ncap - need;
+      const uint32_t bal = __ballot_sync(0xffffffffu, anyw != 0u);
+      const uint32_t T = __popc(bal);
+      uint32_t base1 = cb, base2 = 0, n1 = T;
+      if (T > cl) {
+        const uint32_t need = T - cl;
+        uint32_t nbase, ncap;
+        if (have_next && need <= kChunk) {
+          nbase = __shfl_sync(0xffffffffu, nb_l0, 0);
+          ncap = kChunk;
+          have_next = false;
         } else {
-          cb += T;
-          cl -= T;
-        }
-        if (cl < kLowWater && !have_next) {
+          ncap = need > kChunk ? need : kChunk;
+          uint32_t x = 0;
           if (lane == 0) {
-            const unsigned long long got = atomicAdd(a.counters, (unsigned long long)kChunk);
-            nb_l0 = (uint32_t)got;
-            if (got + kChunk > a.recs_cap) overflow = true;
+            const unsigned long long got = atomicAdd(a.counters, (unsigned long long)ncap);
+            x = (uint32_t)got;
+            if (got + ncap > a.recs_cap) overflow = true;
           }
-          have_next = true;
+          nbase = __shfl_sync(0xffffffffu, x, 0);
         }
-        if (lane == 0)
-          a.table[((size_t)k * a.nbands + band) * NW + w] =
-              make_uint4(base1, base2, rc_lo, rc_hi | (n1 << 12) | (faces_w << 20));
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          if ((anyf >> (4 * r)) & 1u) {
-            const uint32_t q = pre[r] + __popc(bal[r] & lt);
-            const unsigned long long addr =
-                q < n1 ? (unsigned long long)base1 + q : (unsigned long long)base2 + (q - n1);
-            uint32_t rec = ((uint32_t)r << 29) | ((uint32_t)lane << 24);
-#pragma unroll
-            for (int s = 0; s < 6; ++s) rec |= ((d[s] >> (4 * r)) & 0xFu) << (4 * s);
-            if (addr < a.recs_cap) a.recs[addr] = rec;
-          }
+        n1 = cl;
+        base2 = nbase;
+        cb = nbase + need;
+        cl = ncap - need;
+      } else {
+        cb += T;
+        cl -= T;
+      }
+      if (cl < kLowWater && !have_next) {
+        if (lane == 0) {
+          const unsigned long long got = atomicAdd(a.counters, (unsigned long long)kChunk);
+          nb_l0 = (uint32_t)got;
+          if (got + kChunk > a.recs_cap) overflow = true;
+        }
+        have_next = true;
+      }
+      if (lane == 0)
+        a.table[((size_t)k * a.nbands + band) * NW + w] =
+            make_uint4(base1, base2, T | (n1 << 6) | (faces_w << 12), 0u);
+      if (anyw) {
+        const uint32_t q = __popc(bal & lt);
+        const unsigned long long idx =
+            q < n1 ? (unsigned long long)base1 + q : (unsigned long long)base2 + (q - n1);
+        if (idx < a.recs_cap) {
+          uint2* p = reinterpret_cast<uint2*>(a.recs + idx * kRecWords);
+          p[0] = make_uint2(d[0] | ((uint32_t)lane << 28), d[1] | ((uint32_t)(lane >> 4) << 28));
+          p[1] = make_uint2(d[2], d[3]);
+          p[2] = make_uint2(d[4], d[5]);
         }
       }
       // plane k + 1 becomes plane k
       Sk0 = S0n;
       Sk1 = S1n;
+      Zk0 = Z0n;
+      Zk1 = Z1n;
       RX0 = RX0n;
       RX1 = RX1n;
       RY0 = RY0n;
@@ -572,7 +574,6 @@ __global__ void __launch_bounds__(MAXT, MINB) sweep_bulk_kernel(V3Args a) {
       Bk0 = Bn0;
       Bk1 = Bn1;
       BkN = BnN;
-      (void)SNn;
     };
 
     for (int t = 0; t < nsteps; t += 2) {
@@ -620,7 +621,7 @@ __global__ void __launch_bounds__(kScanThreads) v3_scan_kernel(
     const long long s = s0 + i;
     uint32_t f = 0;
     if (s < nseg)
-      for (int q = 0; q < NW; ++q) f += __ldg(&table[s * NW + q].w) >> 20;
+      for (int q = 0; q < NW; ++q) f += (__ldg(&table[s * NW + q].z) >> 12) & 0xFFFu;
     v[i] = f;
     local += f;
   }
@@ -691,8 +692,9 @@ __global__ void __launch_bounds__(kScanThreads) v3_scan_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// Finalize 2: one warp per (plane, band) segment expands its records, in
-// (row, warp, lane) order, into face ids and windings at their final offsets.
+// Finalize 2: one warp per (plane, band) segment expands its records into face
+// ids and windings at their final offsets, row by row, records in (warp,
+// lane) order within a row.
 // ---------------------------------------------------------------------------
 constexpr int kExpandWarps = 8;
 
@@ -701,83 +703,78 @@ __global__ void __launch_bounds__(32 * kExpandWarps) v3_expand_kernel(
     const uint32_t* __restrict__ recs, unsigned long long recs_cap,
     const unsigned long long* __restrict__ seg_off, uint64_t* __restrict__ face_ids,
     int8_t* __restrict__ winding, unsigned long long capacity) {
-  __shared__ uint32_t s_start[kExpandWarps][R][kMaxWarpsX];
-  __shared__ uint32_t s_wpre[kExpandWarps][R][kMaxWarpsX];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long nwarps = (long long)gridDim.x * kExpandWarps;
   for (long long s = (long long)blockIdx.x * kExpandWarps + wib; s < nseg; s += nwarps) {
     uint4 e = make_uint4(0u, 0u, 0u, 0u);
     if (lane < NW) e = table[s * NW + lane];
-    const uint32_t base1 = e.x, base2 = e.y, n1 = (e.w >> 12) & 0xFFu;
-    uint32_t rowstart[R];
-    uint32_t run = 0, wp = 0;
+    const uint32_t n = e.z & 63u, n1 = (e.z >> 6) & 63u;
+    uint32_t incl = n;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const uint32_t n = r < 5 ? (e.z >> (6 * r)) & 63u : (e.w >> (6 * (r - 5))) & 63u;
-      uint32_t incl = n;
-#pragma unroll
-      for (int dd = 1; dd < 32; dd <<= 1) {
-        const uint32_t x = __shfl_up_sync(0xffffffffu, incl, dd);
-        if (lane >= dd) incl += x;
-      }
-      rowstart[r] = run;
-      if (lane < NW) {
-        s_start[wib][r][lane] = run + incl - n;
-        s_wpre[wib][r][lane] = wp;
-      }
-      wp += n;
-      run += __shfl_sync(0xffffffffu, incl, 31);
+    for (int dd = 1; dd < 32; dd <<= 1) {
+      const uint32_t x = __shfl_up_sync(0xffffffffu, incl, dd);
+      if (lane >= dd) incl += x;
     }
-    __syncwarp();
-    const uint32_t rtot = run;
+    const uint32_t start = incl - n;  // first flattened record of warp `lane`
+    const uint32_t rtot = __shfl_sync(0xffffffffu, incl, 31);
     if (rtot == 0) continue;
     const unsigned long long fbase = seg_off[s];
     const long long k = s / nbands;
-    const int band = (int)(s % nbands);
-    const long long j0 = (long long)band * R;
+    const long long j0 = (long long)(s % nbands) * R;
     unsigned long long fo = 0;
-    for (uint32_t g0 = 0; g0 < rtot; g0 += 32) {
-      const uint32_t g = g0 + lane;
-      const bool valid = g < rtot;
-      int r = 0;
+    for (int r = 0; r < R; ++r) {
+      for (uint32_t g0 = 0; g0 < rtot; g0 += 32) {
+        const uint32_t g = g0 + lane;
+        const bool valid = g < rtot;
+        // warp of flattened record g: last ww with start(ww) <= g
+        int ww = 0;
+        for (int q = 1; q < NW; ++q)
+          if (__shfl_sync(0xffffffffu, start, q) <= g) ww = q;
+        const uint32_t qi = g - __shfl_sync(0xffffffffu, start, ww);
+        const uint32_t b1 = __shfl_sync(0xffffffffu, e.x, ww);
+        const uint32_t b2 = __shfl_sync(0xffffffffu, e.y, ww);
+        const uint32_t m1 = __shfl_sync(0xffffffffu, n1, ww);
+        const unsigned long long idx =
+            qi < m1 ? (unsigned long long)b1 + qi : (unsigned long long)b2 + (qi - m1);
+        uint32_t dw[kRecWords] = {0u, 0u, 0u, 0u, 0u, 0u};
+        if (valid && idx < recs_cap) {
+          const uint2* p = reinterpret_cast<const uint2*>(recs + idx * kRecWords);
+          const uint2 q0 = p[0], q1 = p[1], q2 = p[2];
+          dw[0] = q0.x;
+          dw[1] = q0.y;
+          dw[2] = q1.x;
+          dw[3] = q1.y;
+          dw[4] = q2.x;
+          dw[5] = q2.y;
+        }
+        const uint32_t rl = (dw[0] >> 28) | ((dw[1] >> 28) << 4);
+        uint32_t nf = 0;
 #pragma unroll
-      for (int rr = 1; rr < R; ++rr)
-        if (rowstart[rr] <= g) r = rr;
-      int ww = 0;
-      for (int q = 1; q < NW; ++q)
-        if (s_start[wib][r][q] <= g) ww = q;
-      const uint32_t widx = g - s_start[wib][r][ww] + s_wpre[wib][r][ww];
-      const uint32_t b1 = __shfl_sync(0xffffffffu, base1, ww);
-      const uint32_t b2 = __shfl_sync(0xffffffffu, base2, ww);
-      const uint32_t m1 = __shfl_sync(0xffffffffu, n1, ww);
-      const unsigned long long addr =
-          widx < m1 ? (unsigned long long)b1 + widx : (unsigned long long)b2 + (widx - m1);
-      const uint32_t rec = (valid && addr < recs_cap) ? recs[addr] : 0u;
-      const uint32_t nf = __popc(nz_fields(rec & 0x00FFFFFFu));
-      uint32_t incl = nf;
+        for (int sl = 0; sl < 6; ++sl) nf += ((dw[sl] >> (4 * r)) & 0xFu) ? 1u : 0u;
+        uint32_t inc = nf;
 #pragma unroll
-      for (int dd = 1; dd < 32; dd <<= 1) {
-        const uint32_t x = __shfl_up_sync(0xffffffffu, incl, dd);
-        if (lane >= dd) incl += x;
-      }
-      unsigned long long pos = fbase + fo + (incl - nf);
-      if (nf) {
-        const uint32_t rrow = rec >> 29, rl = (rec >> 24) & 31u;
-        const unsigned long long lin0 =
-            ((unsigned long long)k * ny + (unsigned long long)(j0 + rrow)) * nx + 64u * ww + 2u * rl;
+        for (int dd = 1; dd < 32; dd <<= 1) {
+          const uint32_t x = __shfl_up_sync(0xffffffffu, inc, dd);
+          if (lane >= dd) inc += x;
+        }
+        unsigned long long pos = fbase + fo + (inc - nf);
+        if (nf) {
+          const unsigned long long lin0 =
+              ((unsigned long long)k * ny + (unsigned long long)(j0 + r)) * nx + 64u * ww + 2u * rl;
 #pragma unroll
-        for (int sl = 0; sl < 6; ++sl) {
-          const uint32_t nib = (rec >> (4 * sl)) & 0xFu;
-          if (nib) {
-            if (pos < capacity) {
-              face_ids[pos] = ((lin0 + (unsigned long long)(sl / 3)) << 2) | (unsigned)(sl % 3);
-              winding[pos] = (int8_t)((int)(nib ^ 4u) - 4);
+          for (int sl = 0; sl < 6; ++sl) {
+            const uint32_t nib = (dw[sl] >> (4 * r)) & 0xFu;
+            if (nib) {
+              if (pos < capacity) {
+                face_ids[pos] = ((lin0 + (unsigned long long)(sl / 3)) << 2) | (unsigned)(sl % 3);
+                winding[pos] = (int8_t)((int)(nib ^ 4u) - 4);
+              }
+              ++pos;
             }
-            ++pos;
           }
         }
+        fo += __shfl_sync(0xffffffffu, inc, 31);
       }
-      fo += __shfl_sync(0xffffffffu, incl, 31);
     }
   }
 }
@@ -834,6 +831,8 @@ int bulk_plan(int num_sms, const qtv_grid& g, uint64_t capacity, uint64_t max_wa
   p->hblock = (int)((g.nz + zblocks - 1) / zblocks);
   p->nseg = (long long)g.nz * nbands;
   p->ntiles = (p->nseg + kScanTile - 1) / kScanTile;
+  // records (kRecWords words each): at most one per pierced face, plus two
+  // partly used chunks per warp
   p->recs_need = capacity + 2ull * kChunk * (unsigned long long)grid * nw + kChunk;
   p->table_need = (unsigned long long)p->nseg * nw;
   return QTV_OK;
@@ -852,7 +851,7 @@ int bulk_needs(int num_sms, const qtv_grid& g, uint64_t capacity, uint64_t max_w
   BulkPlan p;
   const int rc = bulk_plan(num_sms, g, capacity, max_warps, &p);
   if (rc) return rc;
-  n->recs = p.recs_need;
+  n->recs = p.recs_need * kRecWords;  // staging words
   n->table = p.table_need;
   n->seg_off = (unsigned long long)p.nseg;
   n->tiles = (unsigned long long)p.ntiles;
@@ -865,7 +864,7 @@ int bulk_identify(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* 
   BulkPlan p;
   int rc = bulk_plan(h->num_sms, g, capacity, max_warps, &p);
   if (rc) return rc;
-  if (sc.staging_cap < p.recs_need || sc.table_cap < p.table_need ||
+  if (sc.staging_cap < p.recs_need * kRecWords || sc.table_cap < p.table_need ||
       sc.seg_off_cap < (uint64_t)p.nseg || sc.tiles_cap < (uint64_t)p.ntiles)
     return set_error(QTV_ERR_CAPACITY, "identification scratch too small for this grid");
   cudaError_t e = cudaMemsetAsync(sc.counters, 0, 4 * sizeof(unsigned long long), st);
