@@ -341,10 +341,15 @@ def run_qtv(args):
     # ---- roofline of the dominant kernel (the sweep)
     peak, peak_kind = peaks()
     nbands = (n + 6) // 7
+    nwarps_x = (n + 63) // 64
     nseg = n * nbands
     sweep_launches, sweep_ms = trace.get("sweep", (0, 0.0))
     sweep_avg_ms = sweep_ms / max(1, sweep_launches)
-    sweep_bytes = 8 * nodes + 4 * F + 8 * nseg
+    # psi read once + one 16-byte table entry per (plane, band, warp) + one
+    # 4-byte face total per (plane, band); the staged records (24 B per lane
+    # and plane with faces, < 0.3 B/node) are left out, so this is a lower
+    # bound of the sweep's traffic
+    sweep_bytes = 8 * nodes + 16 * nseg * nwarps_x + 4 * nseg
     achieved = sweep_bytes / (sweep_avg_ms * 1e-3) / 1e9 if sweep_avg_ms > 0 else 0.0
     step_bytes = 8 * nodes + 9 * F + F * (9 + 32 + 17)
     ms_per_step = ms / args.steps

@@ -593,6 +593,7 @@ int identify_needs(int num_sms, const qtv_grid& g, uint64_t capacity, const void
     const int rc = bulk_needs(num_sms, g, capacity, max_warps, &b);
     if (rc) return rc;
     n->staging = b.recs;
+    n->seg = b.segf;
     n->table = b.table;
     n->seg_off = b.seg_off;
     n->tiles = b.tiles;

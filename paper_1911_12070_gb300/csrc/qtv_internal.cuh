@@ -36,7 +36,8 @@ struct Workspace {
 struct IdentScratch {
   uint32_t* staging = nullptr;  // face records (register sweep) / lane-row records (staged sweep)
   uint64_t staging_cap = 0;
-  uint2* seg = nullptr;         // register sweep: per (plane, band) {count, base}
+  uint2* seg = nullptr;         // per (plane, band): {count, base} (register sweep) or
+                                // two u32 face totals per entry (staged sweep)
   uint64_t seg_cap = 0;
   uint4* table = nullptr;       // staged sweep: per (plane, band, warp) entry
   uint64_t table_cap = 0;
@@ -117,7 +118,7 @@ int identify_launch(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t
 // Bulk-copy staged sweep with per-warp compaction (sweep_bulk.cu): even
 // nx <= 1024, 16-byte aligned psi.
 struct BulkNeeds {
-  uint64_t recs = 0, table = 0, seg_off = 0, tiles = 0;
+  uint64_t recs = 0, table = 0, seg_off = 0, tiles = 0, segf = 0;
 };
 bool sweep_bulk_supported(int nx, int ny, int nz, const void* psi);
 int bulk_needs(int num_sms, const qtv_grid& g, uint64_t capacity, uint64_t max_warps,

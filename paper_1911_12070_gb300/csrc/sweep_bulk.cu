@@ -266,6 +266,7 @@ struct V3Args {
   unsigned long long recs_cap;   // records
   unsigned long long* counters;  // [0] chunk top, [1] status bits, [2] scan ticket
   uint4* table;                  // [(k * nbands + band) * NW + w]
+  unsigned int* segf;            // [k * nbands + band]: pierced faces (zeroed before)
 };
 
 // unit u of the (z block, band, plane) order -> band, plane, end of its z block
@@ -546,9 +547,11 @@ __global__ void __launch_bounds__(MAXT, MINB) sweep_bulk_kernel(V3Args a) {
         }
         have_next = true;
       }
-      if (lane == 0)
+      if (lane == 0) {
         a.table[((size_t)k * a.nbands + band) * NW + w] =
             make_uint4(base1, base2, T | (n1 << 6) | (faces_w << 12), 0u);
+        if (faces_w) atomicAdd(&a.segf[(size_t)k * a.nbands + band], faces_w);
+      }
       if (anyw) {
         const uint32_t q = __popc(bal & lt);
         const unsigned long long idx =
@@ -603,7 +606,7 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
 }
 
 __global__ void __launch_bounds__(kScanThreads) v3_scan_kernel(
-    const uint4* __restrict__ table, int NW, long long nseg, unsigned long long* __restrict__ seg_off,
+    const unsigned int* __restrict__ segf, long long nseg, unsigned long long* __restrict__ seg_off,
     uint64_t* count, unsigned long long* counters, unsigned long long* tiles, long long ntiles,
     qtv_stats* stats, unsigned long long scanned) {
   __shared__ unsigned long long s_warp[kScanThreads / 32];
@@ -619,9 +622,7 @@ __global__ void __launch_bounds__(kScanThreads) v3_scan_kernel(
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     const long long s = s0 + i;
-    uint32_t f = 0;
-    if (s < nseg)
-      for (int q = 0; q < NW; ++q) f += (__ldg(&table[s * NW + q].z) >> 12) & 0xFFFu;
+    const uint32_t f = s < nseg ? __ldg(&segf[s]) : 0u;
     v[i] = f;
     local += f;
   }
@@ -693,10 +694,18 @@ __global__ void __launch_bounds__(kScanThreads) v3_scan_kernel(
 
 // ---------------------------------------------------------------------------
 // Finalize 2: one warp per (plane, band) segment expands its records into face
-// ids and windings at their final offsets, row by row, records in (warp,
-// lane) order within a row.
+// ids and windings at their final offsets: row by row, and within a row in
+// flattened record order (warp, lane), which is ascending x.
 // ---------------------------------------------------------------------------
 constexpr int kExpandWarps = 8;
+
+// fields 0..6 of the packed count of pierced faces per row in a record
+__device__ __forceinline__ uint32_t rec_row_counts(const uint32_t* dw) {
+  uint32_t c = 0;
+#pragma unroll
+  for (int sl = 0; sl < kRecWords; ++sl) c += nz_fields(dw[sl] & 0x0FFFFFFFu);
+  return c;
+}
 
 __global__ void __launch_bounds__(32 * kExpandWarps) v3_expand_kernel(
     const uint4* __restrict__ table, int NW, long long nseg, int nbands, int nx, int ny,
@@ -715,66 +724,131 @@ __global__ void __launch_bounds__(32 * kExpandWarps) v3_expand_kernel(
       const uint32_t x = __shfl_up_sync(0xffffffffu, incl, dd);
       if (lane >= dd) incl += x;
     }
-    const uint32_t start = incl - n;  // first flattened record of warp `lane`
+    const uint32_t start = lane < NW ? incl - n : 0xFFFFFFFFu;
     const uint32_t rtot = __shfl_sync(0xffffffffu, incl, 31);
     if (rtot == 0) continue;
     const unsigned long long fbase = seg_off[s];
     const long long k = s / nbands;
     const long long j0 = (long long)(s % nbands) * R;
-    unsigned long long fo = 0;
-    for (int r = 0; r < R; ++r) {
-      for (uint32_t g0 = 0; g0 < rtot; g0 += 32) {
-        const uint32_t g = g0 + lane;
-        const bool valid = g < rtot;
-        // warp of flattened record g: last ww with start(ww) <= g
-        int ww = 0;
-        for (int q = 1; q < NW; ++q)
-          if (__shfl_sync(0xffffffffu, start, q) <= g) ww = q;
-        const uint32_t qi = g - __shfl_sync(0xffffffffu, start, ww);
-        const uint32_t b1 = __shfl_sync(0xffffffffu, e.x, ww);
-        const uint32_t b2 = __shfl_sync(0xffffffffu, e.y, ww);
-        const uint32_t m1 = __shfl_sync(0xffffffffu, n1, ww);
-        const unsigned long long idx =
-            qi < m1 ? (unsigned long long)b1 + qi : (unsigned long long)b2 + (qi - m1);
-        uint32_t dw[kRecWords] = {0u, 0u, 0u, 0u, 0u, 0u};
-        if (valid && idx < recs_cap) {
-          const uint2* p = reinterpret_cast<const uint2*>(recs + idx * kRecWords);
-          const uint2 q0 = p[0], q1 = p[1], q2 = p[2];
-          dw[0] = q0.x;
-          dw[1] = q0.y;
-          dw[2] = q1.x;
-          dw[3] = q1.y;
-          dw[4] = q2.x;
-          dw[5] = q2.y;
+    const uint32_t nchunks = (rtot + 31) / 32;
+
+    // record of flattened index g = g0 + lane (zeros past the end)
+    auto load = [&](uint32_t g0, uint32_t* dw, int& ww) {
+      const uint32_t g = g0 + lane;
+      int lo = 0;
+#pragma unroll
+      for (int stp = 8; stp >= 1; stp >>= 1) {
+        const int cand = lo + stp;
+        const uint32_t sv = __shfl_sync(0xffffffffu, start, cand & 31);
+        if (cand < NW && sv <= g) lo = cand;
+      }
+      ww = lo;
+      const uint32_t qi = g - __shfl_sync(0xffffffffu, start, lo);
+      const uint32_t b1 = __shfl_sync(0xffffffffu, e.x, lo);
+      const uint32_t b2 = __shfl_sync(0xffffffffu, e.y, lo);
+      const uint32_t m1 = __shfl_sync(0xffffffffu, n1, lo);
+      const unsigned long long idx =
+          qi < m1 ? (unsigned long long)b1 + qi : (unsigned long long)b2 + (qi - m1);
+#pragma unroll
+      for (int sl = 0; sl < kRecWords; ++sl) dw[sl] = 0u;
+      if (g < rtot && idx < recs_cap) {
+        const uint2* p = reinterpret_cast<const uint2*>(recs + idx * kRecWords);
+        const uint2 q0 = p[0], q1 = p[1], q2 = p[2];
+        dw[0] = q0.x;
+        dw[1] = q0.y;
+        dw[2] = q1.x;
+        dw[3] = q1.y;
+        dw[4] = q2.x;
+        dw[5] = q2.y;
+      }
+    };
+    // per-row exclusive counts within the chunk (bytes: even rows, odd rows)
+    auto scan_rows = [&](uint32_t cnt, uint32_t& exe, uint32_t& exo, uint32_t& te, uint32_t& to) {
+      const uint32_t ce = cnt & 0x0F0F0F0Fu, co = (cnt >> 4) & 0x0F0F0F0Fu;
+      uint32_t ie = ce, io = co;
+#pragma unroll
+      for (int dd = 1; dd < 32; dd <<= 1) {
+        const uint32_t xe = __shfl_up_sync(0xffffffffu, ie, dd);
+        const uint32_t xo = __shfl_up_sync(0xffffffffu, io, dd);
+        if (lane >= dd) {
+          ie += xe;
+          io += xo;
         }
+      }
+      exe = ie - ce;
+      exo = io - co;
+      te = __shfl_sync(0xffffffffu, ie, 31);
+      to = __shfl_sync(0xffffffffu, io, 31);
+    };
+    auto field8 = [](uint32_t ev, uint32_t od, int r) -> uint32_t {
+      return ((r & 1) ? (od >> (8 * (r >> 1))) : (ev >> (8 * (r >> 1)))) & 0xFFu;
+    };
+
+    // pass 1 (several chunks only): per-row totals of the segment
+    uint32_t rowtot[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) rowtot[r] = 0;
+    uint32_t dw[kRecWords];
+    int ww = 0;
+    uint32_t cnt = 0, exe = 0, exo = 0, te = 0, to = 0;
+    if (nchunks == 1) {
+      load(0, dw, ww);
+      cnt = rec_row_counts(dw);
+      scan_rows(cnt, exe, exo, te, to);
+#pragma unroll
+      for (int r = 0; r < R; ++r) rowtot[r] = field8(te, to, r);
+    } else {
+      for (uint32_t c = 0; c < nchunks; ++c) {
+        uint32_t tdw[kRecWords];
+        int tww;
+        load(c * 32, tdw, tww);
+        uint32_t a0, a1, t0, t1;
+        scan_rows(rec_row_counts(tdw), a0, a1, t0, t1);
+#pragma unroll
+        for (int r = 0; r < R; ++r) rowtot[r] += field8(t0, t1, r);
+      }
+    }
+    uint32_t rowbase[R];
+    {
+      uint32_t acc = 0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        rowbase[r] = acc;
+        acc += rowtot[r];
+      }
+    }
+    // pass 2: write
+    for (uint32_t c = 0; c < nchunks; ++c) {
+      if (nchunks > 1) {
+        load(c * 32, dw, ww);
+        cnt = rec_row_counts(dw);
+        scan_rows(cnt, exe, exo, te, to);
+      }
+      if (cnt) {
         const uint32_t rl = (dw[0] >> 28) | ((dw[1] >> 28) << 4);
-        uint32_t nf = 0;
 #pragma unroll
-        for (int sl = 0; sl < 6; ++sl) nf += ((dw[sl] >> (4 * r)) & 0xFu) ? 1u : 0u;
-        uint32_t inc = nf;
+        for (int r = 0; r < R; ++r) {
+          if ((cnt >> (4 * r)) & 0xFu) {
+            unsigned long long pos = fbase + rowbase[r] + field8(exe, exo, r);
+            const unsigned long long lin0 = ((unsigned long long)k * ny + (unsigned long long)(j0 + r)) *
+                                                (unsigned long long)nx +
+                                            64u * (unsigned)ww + 2u * rl;
 #pragma unroll
-        for (int dd = 1; dd < 32; dd <<= 1) {
-          const uint32_t x = __shfl_up_sync(0xffffffffu, inc, dd);
-          if (lane >= dd) inc += x;
-        }
-        unsigned long long pos = fbase + fo + (inc - nf);
-        if (nf) {
-          const unsigned long long lin0 =
-              ((unsigned long long)k * ny + (unsigned long long)(j0 + r)) * nx + 64u * ww + 2u * rl;
-#pragma unroll
-          for (int sl = 0; sl < 6; ++sl) {
-            const uint32_t nib = (dw[sl] >> (4 * r)) & 0xFu;
-            if (nib) {
-              if (pos < capacity) {
-                face_ids[pos] = ((lin0 + (unsigned long long)(sl / 3)) << 2) | (unsigned)(sl % 3);
-                winding[pos] = (int8_t)((int)(nib ^ 4u) - 4);
+            for (int sl = 0; sl < 6; ++sl) {
+              const uint32_t nib = (dw[sl] >> (4 * r)) & 0xFu;
+              if (nib) {
+                if (pos < capacity) {
+                  face_ids[pos] = ((lin0 + (unsigned long long)(sl / 3)) << 2) | (unsigned)(sl % 3);
+                  winding[pos] = (int8_t)((int)(nib ^ 4u) - 4);
+                }
+                ++pos;
               }
-              ++pos;
             }
           }
         }
-        fo += __shfl_sync(0xffffffffu, inc, 31);
       }
+#pragma unroll
+      for (int r = 0; r < R; ++r) rowbase[r] += field8(te, to, r);
     }
   }
 }
@@ -855,6 +929,7 @@ int bulk_needs(int num_sms, const qtv_grid& g, uint64_t capacity, uint64_t max_w
   n->table = p.table_need;
   n->seg_off = (unsigned long long)p.nseg;
   n->tiles = (unsigned long long)p.ntiles;
+  n->segf = (unsigned long long)(p.nseg + 1) / 2;  // uint2 entries holding nseg u32
   return QTV_OK;
 }
 
@@ -865,10 +940,12 @@ int bulk_identify(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* 
   int rc = bulk_plan(h->num_sms, g, capacity, max_warps, &p);
   if (rc) return rc;
   if (sc.staging_cap < p.recs_need * kRecWords || sc.table_cap < p.table_need ||
+      sc.seg_cap * 2 < (uint64_t)p.nseg ||
       sc.seg_off_cap < (uint64_t)p.nseg || sc.tiles_cap < (uint64_t)p.ntiles)
     return set_error(QTV_ERR_CAPACITY, "identification scratch too small for this grid");
   cudaError_t e = cudaMemsetAsync(sc.counters, 0, 4 * sizeof(unsigned long long), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(sc.tiles, 0, p.ntiles * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sc.seg, 0, p.nseg * sizeof(unsigned int), st);
   if (e == cudaSuccess && stats) e = cudaMemsetAsync(stats, 0, sizeof(qtv_stats), st);
   if (e != cudaSuccess) return check_cuda(e, "cudaMemsetAsync(identify scratch)");
   V3Args a;
@@ -882,6 +959,7 @@ int bulk_identify(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* 
   a.recs_cap = p.recs_need;
   a.counters = sc.counters;
   a.table = sc.table;
+  a.segf = reinterpret_cast<unsigned int*>(sc.seg);
   {
     TraceScope ts(h, K_SWEEP, st);
     bulk_fn(p.nw)<<<p.grid, p.nw * 32, p.smem, st>>>(a);
@@ -894,7 +972,7 @@ int bulk_identify(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* 
   {
     TraceScope ts(h, K_SEG_SCAN, st);
     v3_scan_kernel<<<(unsigned)p.ntiles, kScanThreads, 0, st>>>(
-        sc.table, p.nw, p.nseg, sc.seg_off, count, sc.counters, sc.tiles, p.ntiles, stats, scanned);
+        reinterpret_cast<const unsigned int*>(sc.seg), p.nseg, sc.seg_off, count, sc.counters, sc.tiles, p.ntiles, stats, scanned);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return check_cuda(e, "v3_scan_kernel launch");
