@@ -4,8 +4,9 @@ Eq. 5) plus plain density-guided localization (Sec. 3.3.3, Eq. 6) of every
 pierced plaquette, on a 512^3 complex64 random-wave tangle (16384 waves,
 |k| in [0.15, 0.35] rad/h, 5% multiplicative amplitude noise; seeds 7 / 8).
 
-One step = qtv_identify (sweep + segment scan + scatter) + qtv_localize over
-the whole field, inputs resident in HBM (1 GiB field: larger than the 129 MB
+One step = qtv_identify_localize over the whole field (identification sweep,
+segment scan, and the pass that writes every pierced face and localizes it),
+inputs resident in HBM (1 GiB field: larger than the 129 MB
 L2, so no flush is needed).  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl qtv|reference]
@@ -253,8 +254,8 @@ def run_qtv(args):
     flags = torch.empty(cap, dtype=torch.uint8, device=dev)
 
     def step():
-        q.identify_into(psi, ids, wnd, count)
-        q.localize_into(psi, ids, wnd, xyz, resid, flags, n=cap, n_dev=count)
+        # identification + plain localization, fused (qtv_identify_localize)
+        q.identify_localize_into(psi, ids, wnd, count, xyz, resid, flags)
 
     clk = ClockSampler(dev.index)
     clk.start()
@@ -304,8 +305,7 @@ def run_qtv(args):
 
     def e2e_step():
         psi_e2e.copy_(host_psi, non_blocking=True)
-        q.identify_into(psi_e2e, ids, wnd, count)
-        q.localize_into(psi_e2e, ids, wnd, xyz, resid, flags, n=cap, n_dev=count)
+        q.identify_localize_into(psi_e2e, ids, wnd, count, xyz, resid, flags)
         # emission needs the sample count on the host
         nf = int(count.item())
         rc = lib.qtv_emit_samples(q.h, nf, ctypes.c_void_p(ids.data_ptr()),

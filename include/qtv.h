@@ -182,6 +182,18 @@ QTV_API int qtv_localize(qtv_handle h, const qtv_grid* grid, const void* psi, co
                  float fallback_resid, float* xyz, float* resid, uint8_t* flags, void* stream);
 
 /*
+ * Identification and plain localization in one call: the result of
+ * qtv_identify followed by qtv_localize(QTV_PLAIN) on its faces, with the
+ * localization fused into the pass that writes the faces out (one pass over
+ * the face list instead of two).  Outputs as in those calls, each with
+ * `capacity` entries; *count as in qtv_identify.
+ */
+QTV_API int qtv_identify_localize(qtv_handle h, const qtv_grid* grid, const void* psi,
+                                  uint64_t* face_ids, int8_t* winding, uint64_t capacity,
+                                  uint64_t* count, float* xyz, float* resid, uint8_t* flags,
+                                  qtv_stats* stats, void* stream);
+
+/*
  * Emission (Sec. 3.4, direction by the right-hand rule): pack n samples into
  * caller-owned host memory `host_out` (qtv_sample[n]; pinned memory makes the
  * copy asynchronous).  Samples keep the order of the inputs (ascending face

@@ -96,6 +96,9 @@ def lib() -> ctypes.CDLL:
         L.qtv_identify.argtypes = [P, ctypes.POINTER(Grid), P, P, P, u64, P, P, P]
         L.qtv_localize.argtypes = [P, ctypes.POINTER(Grid), P, P, P, u64, P, i32, f32, P, P, P, P]
         L.qtv_emit_samples.argtypes = [P, u64, P, P, P, P, P, P, P]
+        L.qtv_identify_localize.argtypes = [P, ctypes.POINTER(Grid), P, P, P, u64, P, P, P, P, P,
+                                             P]
+        L.qtv_identify_localize.restype = i32
         L.qtv_identify_static.argtypes = [ctypes.POINTER(Grid), P, P, P, u64, P, P]
         L.qtv_identify_static.restype = i32
         L.qtv_trace_enable.argtypes = [P, i32]
@@ -186,6 +189,8 @@ class Qtv:
             w = torch.empty(capacity, dtype=torch.int8, device=dev)
             self.identify_into(psi, ids, w, count, st, stream=stream)
             n = int(count.item())
+            if n < 0:  # QTV_COUNT_TIMEOUT read as int64
+                raise QtvError(ERR_TIMEOUT, "a bounded device wait gave up")
             if n <= capacity:
                 break
             capacity = n
@@ -194,6 +199,40 @@ class Qtv:
             vals = st.cpu().numpy().astype(np.uint64)
             sd = {f[0]: int(v) for f, v in zip(Stats._fields_, vals)}
         return ids[:n], w[:n], sd
+
+    def identify_localize_into(self, psi, face_ids, winding, count, xyz, resid, flags,
+                               stats=None, grid=None, stream=None):
+        """Raw fused call: identification + plain localization, preallocated outputs."""
+        g = grid or Grid.of(tuple(psi.shape))
+        cap = 0 if face_ids is None else face_ids.numel()
+        _check(lib().qtv_identify_localize(self.h, ctypes.byref(g), _ptr(psi), _ptr(face_ids),
+                                           _ptr(winding), cap, _ptr(count), _ptr(xyz),
+                                           _ptr(resid), _ptr(flags), _ptr(stats),
+                                           _stream_ptr(stream)))
+
+    def identify_localize(self, psi, capacity: int | None = None, stream=None):
+        """(face_ids, winding, xyz, resid, flags) of psi in one fused call."""
+        import torch
+
+        dev = psi.device
+        nz, ny, nx = psi.shape
+        if capacity is None:
+            capacity = max(1024, int(0.02 * nx * ny * nz))
+        count = torch.zeros(1, dtype=torch.int64, device=dev)
+        for _ in range(2):
+            ids = torch.empty(capacity, dtype=torch.int64, device=dev)
+            w = torch.empty(capacity, dtype=torch.int8, device=dev)
+            xyz = torch.empty((capacity, 3), dtype=torch.float32, device=dev)
+            resid = torch.empty(capacity, dtype=torch.float32, device=dev)
+            flags = torch.empty(capacity, dtype=torch.uint8, device=dev)
+            self.identify_localize_into(psi, ids, w, count, xyz, resid, flags, stream=stream)
+            n = int(count.item())
+            if n < 0:  # QTV_COUNT_TIMEOUT read as int64
+                raise QtvError(ERR_TIMEOUT, "a bounded device wait gave up")
+            if n <= capacity:
+                break
+            capacity = n
+        return ids[:n], w[:n], xyz[:n], resid[:n], flags[:n]
 
     # -- localization ---------------------------------------------------------------
     def localize_into(self, psi, face_ids, winding, xyz, resid, flags, n=None, n_dev=None,

@@ -297,6 +297,39 @@ int qtv_identify(qtv_handle h, const qtv_grid* grid, const void* psi, uint64_t* 
                          count, stats, st, scratch_of(h), 0);
 }
 
+int qtv_identify_localize(qtv_handle h, const qtv_grid* grid, const void* psi,
+                          uint64_t* face_ids, int8_t* winding, uint64_t capacity, uint64_t* count,
+                          float* xyz, float* resid, uint8_t* flags, qtv_stats* stats,
+                          void* stream) {
+  if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
+  int rc = validate_grid(grid);
+  if (rc) return rc;
+  if (!count) return set_error(QTV_ERR_ARG, "count is NULL");
+  if (capacity > 0 && (!face_ids || !winding || !xyz || !resid || !flags))
+    return set_error(QTV_ERR_ARG, "an output is NULL with capacity %llu",
+                     (unsigned long long)capacity);
+  if (capacity > 0xFFFFFFFFull)
+    return set_error(QTV_ERR_ARG, "capacity above 2^32-1 is not supported");
+  const qtv_grid& g = *grid;
+  const unsigned long long nn = (unsigned long long)g.nx * g.ny * g.nz;
+  if (nn > 0 && !psi) return set_error(QTV_ERR_ARG, "psi is NULL");
+  if (reinterpret_cast<uintptr_t>(psi) & 7u)
+    return set_error(QTV_ERR_ARG, "psi must be 8-byte aligned");
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return set_error(QTV_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (nn == 0 || g.nx < 1 || g.ny < 1 || g.nz < 1) {
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(uint64_t), st);
+    if (e == cudaSuccess && stats) e = cudaMemsetAsync(stats, 0, sizeof(qtv_stats), st);
+    return check_cuda(e, "cudaMemsetAsync(count)");
+  }
+  rc = grow_identify(h, g, capacity, psi, st);
+  if (rc) return rc;
+  return identify_launch(h, g, reinterpret_cast<const float2*>(psi), face_ids, winding, capacity,
+                         count, stats, st, scratch_of(h), 0, capacity > 0 ? xyz : nullptr, resid,
+                         flags);
+}
+
 int qtv_localize(qtv_handle h, const qtv_grid* grid, const void* psi, const uint64_t* face_ids,
                  const int8_t* winding, uint64_t n, const uint64_t* n_dev, int mode,
                  float fallback_resid, float* xyz, float* resid, uint8_t* flags, void* stream) {

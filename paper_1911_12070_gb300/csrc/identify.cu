@@ -607,10 +607,11 @@ int identify_needs(int num_sms, const qtv_grid& g, uint64_t capacity, const void
 
 int identify_launch(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* face_ids,
                     int8_t* winding, uint64_t capacity, uint64_t* count, qtv_stats* stats,
-                    cudaStream_t st, const IdentScratch& sc, uint64_t max_warps) {
+                    cudaStream_t st, const IdentScratch& sc, uint64_t max_warps, float* xyz,
+                    float* resid, uint8_t* flags) {
   if (sweep_bulk_supported(g.nx, g.ny, g.nz, psi)) {
     const int rc = bulk_identify(h, g, psi, face_ids, winding, capacity, count, stats, st, sc,
-                                 max_warps);
+                                 max_warps, xyz, resid, flags);
     if (rc) return rc;
     if (stats) {
       TraceScope ts(h, K_STATS, st);
@@ -691,6 +692,11 @@ int identify_launch(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t
                                                 staging_cap, face_ids, winding, capacity);
     e = cudaGetLastError();
     if (e != cudaSuccess) return check_cuda(e, "scatter_kernel launch");
+  }
+  if (xyz && capacity > 0) {
+    const int rc = localize_launch(h, g, psi, face_ids, winding, capacity, count, xyz, resid, flags,
+                                   st);
+    if (rc) return rc;
   }
   if (stats) {
     TraceScope ts(h, K_STATS, st);

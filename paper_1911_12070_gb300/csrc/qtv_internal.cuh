@@ -113,7 +113,8 @@ int identify_needs(int num_sms, const qtv_grid& g, uint64_t capacity, const void
                    uint64_t max_warps, IdentNeeds* n);
 int identify_launch(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* face_ids,
                     int8_t* winding, uint64_t capacity, uint64_t* count, qtv_stats* stats,
-                    cudaStream_t st, const IdentScratch& sc, uint64_t max_warps);
+                    cudaStream_t st, const IdentScratch& sc, uint64_t max_warps,
+                    float* xyz = nullptr, float* resid = nullptr, uint8_t* flags = nullptr);
 
 // Bulk-copy staged sweep with per-warp compaction (sweep_bulk.cu): even
 // nx <= 1024, 16-byte aligned psi.
@@ -125,7 +126,8 @@ int bulk_needs(int num_sms, const qtv_grid& g, uint64_t capacity, uint64_t max_w
                BulkNeeds* n);
 int bulk_identify(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* face_ids,
                   int8_t* winding, uint64_t capacity, uint64_t* count, qtv_stats* stats,
-                  cudaStream_t st, const IdentScratch& sc, uint64_t max_warps);
+                  cudaStream_t st, const IdentScratch& sc, uint64_t max_warps,
+                  float* xyz = nullptr, float* resid = nullptr, uint8_t* flags = nullptr);
 
 // Localization launch (localize.cu)
 int localize_launch(qtv_handle h, const qtv_grid& g, const float2* psi, const uint64_t* face_ids,

@@ -49,7 +49,7 @@
 // of planes, and CTAs that hold neighbouring bands march the same z block at
 // the same time (the halo row of a band is the first row of the next one and
 // is then served by L2).
-#include "qtv_internal.cuh"
+#include "localize_impl.cuh"
 
 namespace qtv {
 namespace {
@@ -707,11 +707,23 @@ __device__ __forceinline__ uint32_t rec_row_counts(const uint32_t* dw) {
   return c;
 }
 
-__global__ void __launch_bounds__(32 * kExpandWarps) v3_expand_kernel(
+// Optional fused localization (LOC): each face written is also localized
+// (Sec. 3.3.3, Eq. 6) straight away, while its id is in registers.
+struct LocOut {
+  const float2* psi;
+  int nz;
+  float h, ox, oy, oz;
+  float* xyz;
+  float* resid;
+  uint8_t* flags;
+};
+
+template <bool LOC>
+__global__ void __launch_bounds__(32 * kExpandWarps, LOC ? 3 : 4) v3_expand_kernel(
     const uint4* __restrict__ table, int NW, long long nseg, int nbands, int nx, int ny,
     const uint32_t* __restrict__ recs, unsigned long long recs_cap,
     const unsigned long long* __restrict__ seg_off, uint64_t* __restrict__ face_ids,
-    int8_t* __restrict__ winding, unsigned long long capacity) {
+    int8_t* __restrict__ winding, unsigned long long capacity, LocOut lo) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long nwarps = (long long)gridDim.x * kExpandWarps;
   for (long long s = (long long)blockIdx.x * kExpandWarps + wib; s < nseg; s += nwarps) {
@@ -838,8 +850,22 @@ __global__ void __launch_bounds__(32 * kExpandWarps) v3_expand_kernel(
               const uint32_t nib = (dw[sl] >> (4 * r)) & 0xFu;
               if (nib) {
                 if (pos < capacity) {
-                  face_ids[pos] = ((lin0 + (unsigned long long)(sl / 3)) << 2) | (unsigned)(sl % 3);
-                  winding[pos] = (int8_t)((int)(nib ^ 4u) - 4);
+                  const unsigned long long fid =
+                      ((lin0 + (unsigned long long)(sl / 3)) << 2) | (unsigned)(sl % 3);
+                  const int wv = (int)(nib ^ 4u) - 4;
+                  face_ids[pos] = fid;
+                  winding[pos] = (int8_t)wv;
+                  if (LOC) {
+                    float pxyz[3], rr;
+                    uint8_t fl;
+                    loc::localize_face(lo.psi, nx, ny, lo.nz, lo.h, lo.ox, lo.oy, lo.oz, fid, wv,
+                                       pxyz, &rr, &fl);
+                    lo.xyz[3 * pos + 0] = pxyz[0];
+                    lo.xyz[3 * pos + 1] = pxyz[1];
+                    lo.xyz[3 * pos + 2] = pxyz[2];
+                    lo.resid[pos] = rr;
+                    lo.flags[pos] = fl;
+                  }
                 }
                 ++pos;
               }
@@ -935,7 +961,8 @@ int bulk_needs(int num_sms, const qtv_grid& g, uint64_t capacity, uint64_t max_w
 
 int bulk_identify(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* face_ids,
                   int8_t* winding, uint64_t capacity, uint64_t* count, qtv_stats* stats,
-                  cudaStream_t st, const IdentScratch& sc, uint64_t max_warps) {
+                  cudaStream_t st, const IdentScratch& sc, uint64_t max_warps, float* xyz,
+                  float* resid, uint8_t* flags) {
   BulkPlan p;
   int rc = bulk_plan(h->num_sms, g, capacity, max_warps, &p);
   if (rc) return rc;
@@ -978,12 +1005,20 @@ int bulk_identify(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* 
   if (e != cudaSuccess) return check_cuda(e, "v3_scan_kernel launch");
   if (capacity > 0) {
     long long blocks = (p.nseg + kExpandWarps - 1) / kExpandWarps;
-    const long long maxb = (long long)h->num_sms * 16;
+    const long long maxb = (long long)h->num_sms * 4;
     if (blocks > maxb) blocks = maxb;
-    TraceScope ts(h, K_SCATTER, st);
-    v3_expand_kernel<<<(unsigned)blocks, 32 * kExpandWarps, 0, st>>>(
-        sc.table, p.nw, p.nseg, a.nbands, g.nx, g.ny, sc.staging, p.recs_need, sc.seg_off, face_ids,
-        winding, capacity);
+    LocOut lo{psi, g.nz, g.h, g.origin[0], g.origin[1], g.origin[2], xyz, resid, flags};
+    if (xyz) {
+      TraceScope ts(h, K_SCATTER, st);
+      v3_expand_kernel<true><<<(unsigned)blocks, 32 * kExpandWarps, 0, st>>>(
+          sc.table, p.nw, p.nseg, a.nbands, g.nx, g.ny, sc.staging, p.recs_need, sc.seg_off,
+          face_ids, winding, capacity, lo);
+    } else {
+      TraceScope ts(h, K_SCATTER, st);
+      v3_expand_kernel<false><<<(unsigned)blocks, 32 * kExpandWarps, 0, st>>>(
+          sc.table, p.nw, p.nseg, a.nbands, g.nx, g.ny, sc.staging, p.recs_need, sc.seg_off,
+          face_ids, winding, capacity, lo);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return check_cuda(e, "v3_expand_kernel launch");
   }

@@ -134,3 +134,14 @@ def test_emit_samples_roundtrip(q):
     assert np.array_equal(s["winding"], w)
     assert np.array_equal(np.stack([s["x"], s["y"], s["z"]], 1), xyz)
     assert np.array_equal(s["resid"], resid) and np.array_equal(s["flags"], flags)
+
+
+@pytest.mark.parametrize("shape", [(24, 40, 130), (33, 45, 67), (40, 64, 512)])
+def test_fused_identify_localize_equals_separate_calls(q, shape):
+    psi = torch.from_numpy(synth.random_waves_numpy(shape, synth.wave_spec(7, 512))).cuda()
+    ids, w, xyz, resid, flags = q.identify_localize(psi)
+    ids2, w2, _ = q.identify(psi)
+    xyz2, resid2, flags2 = q.localize(psi, ids2, w2)
+    assert torch.equal(ids, ids2) and torch.equal(w, w2)
+    assert torch.equal(xyz, xyz2) and torch.equal(flags, flags2)
+    assert torch.equal(resid, resid2)
