@@ -850,22 +850,8 @@ __global__ void __launch_bounds__(32 * kExpandWarps, LOC ? 3 : 4) v3_expand_kern
               const uint32_t nib = (dw[sl] >> (4 * r)) & 0xFu;
               if (nib) {
                 if (pos < capacity) {
-                  const unsigned long long fid =
-                      ((lin0 + (unsigned long long)(sl / 3)) << 2) | (unsigned)(sl % 3);
-                  const int wv = (int)(nib ^ 4u) - 4;
-                  face_ids[pos] = fid;
-                  winding[pos] = (int8_t)wv;
-                  if (LOC) {
-                    float pxyz[3], rr;
-                    uint8_t fl;
-                    loc::localize_face(lo.psi, nx, ny, lo.nz, lo.h, lo.ox, lo.oy, lo.oz, fid, wv,
-                                       pxyz, &rr, &fl);
-                    lo.xyz[3 * pos + 0] = pxyz[0];
-                    lo.xyz[3 * pos + 1] = pxyz[1];
-                    lo.xyz[3 * pos + 2] = pxyz[2];
-                    lo.resid[pos] = rr;
-                    lo.flags[pos] = fl;
-                  }
+                  face_ids[pos] = ((lin0 + (unsigned long long)(sl / 3)) << 2) | (unsigned)(sl % 3);
+                  winding[pos] = (int8_t)((int)(nib ^ 4u) - 4);
                 }
                 ++pos;
               }
@@ -875,6 +861,23 @@ __global__ void __launch_bounds__(32 * kExpandWarps, LOC ? 3 : 4) v3_expand_kern
       }
 #pragma unroll
       for (int r = 0; r < R; ++r) rowbase[r] += field8(te, to, r);
+    }
+    if (LOC) {
+      // the segment's faces are [fbase, fbase + nf): localize them one per lane
+      __syncwarp();
+      const unsigned long long nf = rowbase[R - 1];
+      const unsigned long long fend = fbase + nf < capacity ? fbase + nf : capacity;
+      for (unsigned long long f = fbase + lane; f < fend; f += 32) {
+        float pxyz[3], rr;
+        uint8_t fl;
+        loc::localize_face(lo.psi, nx, ny, lo.nz, lo.h, lo.ox, lo.oy, lo.oz, face_ids[f],
+                           winding[f], pxyz, &rr, &fl);
+        lo.xyz[3 * f + 0] = pxyz[0];
+        lo.xyz[3 * f + 1] = pxyz[1];
+        lo.xyz[3 * f + 2] = pxyz[2];
+        lo.resid[f] = rr;
+        lo.flags[f] = fl;
+      }
     }
   }
 }
