@@ -183,10 +183,9 @@ QTV_API int qtv_localize(qtv_handle h, const qtv_grid* grid, const void* psi, co
 
 /*
  * Identification and plain localization in one call: the result of
- * qtv_identify followed by qtv_localize(QTV_PLAIN) on its faces, with the
- * localization fused into the pass that writes the faces out (one pass over
- * the face list instead of two).  Outputs as in those calls, each with
- * `capacity` entries; *count as in qtv_identify.
+ * qtv_identify followed by qtv_localize(QTV_PLAIN, n_dev = count) on its
+ * faces, enqueued together without a host synchronisation.  Outputs as in
+ * those calls, each with `capacity` entries; *count as in qtv_identify.
  */
 QTV_API int qtv_identify_localize(qtv_handle h, const qtv_grid* grid, const void* psi,
                                   uint64_t* face_ids, int8_t* winding, uint64_t capacity,

@@ -49,7 +49,7 @@
 // of planes, and CTAs that hold neighbouring bands march the same z block at
 // the same time (the halo row of a band is the first row of the next one and
 // is then served by L2).
-#include "localize_impl.cuh"
+#include "qtv_internal.cuh"
 
 namespace qtv {
 namespace {
@@ -707,28 +707,28 @@ __device__ __forceinline__ uint32_t rec_row_counts(const uint32_t* dw) {
   return c;
 }
 
-// Optional fused localization (LOC): each face written is also localized
-// (Sec. 3.3.3, Eq. 6) straight away, while its id is in registers.
-struct LocOut {
-  const float2* psi;
-  int nz;
-  float h, ox, oy, oz;
-  float* xyz;
-  float* resid;
-  uint8_t* flags;
-};
-
-template <bool LOC>
-__global__ void __launch_bounds__(32 * kExpandWarps, LOC ? 3 : 4) v3_expand_kernel(
+__global__ void __launch_bounds__(32 * kExpandWarps, 6) v3_expand_kernel(
     const uint4* __restrict__ table, int NW, long long nseg, int nbands, int nx, int ny,
     const uint32_t* __restrict__ recs, unsigned long long recs_cap,
     const unsigned long long* __restrict__ seg_off, uint64_t* __restrict__ face_ids,
-    int8_t* __restrict__ winding, unsigned long long capacity, LocOut lo) {
+    int8_t* __restrict__ winding, unsigned long long capacity) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long nwarps = (long long)gridDim.x * kExpandWarps;
-  for (long long s = (long long)blockIdx.x * kExpandWarps + wib; s < nseg; s += nwarps) {
-    uint4 e = make_uint4(0u, 0u, 0u, 0u);
-    if (lane < NW) e = table[s * NW + lane];
+  long long s = (long long)blockIdx.x * kExpandWarps + wib;
+  // the next segment's table entries and offset are loaded one segment ahead
+  uint4 e_next = make_uint4(0u, 0u, 0u, 0u);
+  unsigned long long fb_next = 0;
+  if (s < nseg) {
+    if (lane < NW) e_next = table[s * NW + lane];
+    fb_next = seg_off[s];
+  }
+  for (; s < nseg; s += nwarps) {
+    const uint4 e = e_next;
+    const unsigned long long fbase = fb_next;
+    if (s + nwarps < nseg) {
+      if (lane < NW) e_next = table[(s + nwarps) * NW + lane];
+      fb_next = seg_off[s + nwarps];
+    }
     const uint32_t n = e.z & 63u, n1 = (e.z >> 6) & 63u;
     uint32_t incl = n;
 #pragma unroll
@@ -739,7 +739,6 @@ __global__ void __launch_bounds__(32 * kExpandWarps, LOC ? 3 : 4) v3_expand_kern
     const uint32_t start = lane < NW ? incl - n : 0xFFFFFFFFu;
     const uint32_t rtot = __shfl_sync(0xffffffffu, incl, 31);
     if (rtot == 0) continue;
-    const unsigned long long fbase = seg_off[s];
     const long long k = s / nbands;
     const long long j0 = (long long)(s % nbands) * R;
     const uint32_t nchunks = (rtot + 31) / 32;
@@ -861,23 +860,6 @@ __global__ void __launch_bounds__(32 * kExpandWarps, LOC ? 3 : 4) v3_expand_kern
       }
 #pragma unroll
       for (int r = 0; r < R; ++r) rowbase[r] += field8(te, to, r);
-    }
-    if (LOC) {
-      // the segment's faces are [fbase, fbase + nf): localize them one per lane
-      __syncwarp();
-      const unsigned long long nf = rowbase[R - 1];
-      const unsigned long long fend = fbase + nf < capacity ? fbase + nf : capacity;
-      for (unsigned long long f = fbase + lane; f < fend; f += 32) {
-        float pxyz[3], rr;
-        uint8_t fl;
-        loc::localize_face(lo.psi, nx, ny, lo.nz, lo.h, lo.ox, lo.oy, lo.oz, face_ids[f],
-                           winding[f], pxyz, &rr, &fl);
-        lo.xyz[3 * f + 0] = pxyz[0];
-        lo.xyz[3 * f + 1] = pxyz[1];
-        lo.xyz[3 * f + 2] = pxyz[2];
-        lo.resid[f] = rr;
-        lo.flags[f] = fl;
-      }
     }
   }
 }
@@ -1008,23 +990,17 @@ int bulk_identify(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* 
   if (e != cudaSuccess) return check_cuda(e, "v3_scan_kernel launch");
   if (capacity > 0) {
     long long blocks = (p.nseg + kExpandWarps - 1) / kExpandWarps;
-    const long long maxb = (long long)h->num_sms * 4;
+    const long long maxb = (long long)h->num_sms * 6;
     if (blocks > maxb) blocks = maxb;
-    LocOut lo{psi, g.nz, g.h, g.origin[0], g.origin[1], g.origin[2], xyz, resid, flags};
-    if (xyz) {
-      TraceScope ts(h, K_SCATTER, st);
-      v3_expand_kernel<true><<<(unsigned)blocks, 32 * kExpandWarps, 0, st>>>(
-          sc.table, p.nw, p.nseg, a.nbands, g.nx, g.ny, sc.staging, p.recs_need, sc.seg_off,
-          face_ids, winding, capacity, lo);
-    } else {
-      TraceScope ts(h, K_SCATTER, st);
-      v3_expand_kernel<false><<<(unsigned)blocks, 32 * kExpandWarps, 0, st>>>(
-          sc.table, p.nw, p.nseg, a.nbands, g.nx, g.ny, sc.staging, p.recs_need, sc.seg_off,
-          face_ids, winding, capacity, lo);
-    }
+    TraceScope ts(h, K_SCATTER, st);
+    v3_expand_kernel<<<(unsigned)blocks, 32 * kExpandWarps, 0, st>>>(
+        sc.table, p.nw, p.nseg, a.nbands, g.nx, g.ny, sc.staging, p.recs_need, sc.seg_off, face_ids,
+        winding, capacity);
     e = cudaGetLastError();
     if (e != cudaSuccess) return check_cuda(e, "v3_expand_kernel launch");
   }
+  if (xyz && capacity > 0)
+    return localize_launch(h, g, psi, face_ids, winding, capacity, count, xyz, resid, flags, st);
   return QTV_OK;
 }
 
