@@ -707,11 +707,12 @@ __device__ __forceinline__ uint32_t rec_row_counts(const uint32_t* dw) {
   return c;
 }
 
-__global__ void __launch_bounds__(32 * kExpandWarps, 6) v3_expand_kernel(
+__global__ void __launch_bounds__(32 * kExpandWarps, 4) v3_expand_kernel(
     const uint4* __restrict__ table, int NW, long long nseg, int nbands, int nx, int ny,
     const uint32_t* __restrict__ recs, unsigned long long recs_cap,
     const unsigned long long* __restrict__ seg_off, uint64_t* __restrict__ face_ids,
     int8_t* __restrict__ winding, unsigned long long capacity) {
+  __shared__ uint32_t s_rowbase[kExpandWarps][R];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long nwarps = (long long)gridDim.x * kExpandWarps;
   long long s = (long long)blockIdx.x * kExpandWarps + wib;
@@ -835,26 +836,34 @@ __global__ void __launch_bounds__(32 * kExpandWarps, 6) v3_expand_kernel(
         cnt = rec_row_counts(dw);
         scan_rows(cnt, exe, exo, te, to);
       }
+      // write this lane's faces: rows with faces, then slots with faces
       if (cnt) {
         const uint32_t rl = (dw[0] >> 28) | ((dw[1] >> 28) << 4);
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          if ((cnt >> (4 * r)) & 0xFu) {
-            unsigned long long pos = fbase + rowbase[r] + field8(exe, exo, r);
-            const unsigned long long lin0 = ((unsigned long long)k * ny + (unsigned long long)(j0 + r)) *
-                                                (unsigned long long)nx +
-                                            64u * (unsigned)ww + 2u * rl;
+        for (int r = 0; r < R; ++r) s_rowbase[wib][r] = rowbase[r];
+        uint32_t rm = nz_fields((dw[0] | dw[1]) & 0x0FFFFFFFu | dw[2] | dw[3] | dw[4] | dw[5]);
+        while (rm) {
+          const int f = __ffs(rm) - 1;
+          const int r = f >> 2;
+          rm &= rm - 1u;
+          uint32_t rn = 0;
 #pragma unroll
-            for (int sl = 0; sl < 6; ++sl) {
-              const uint32_t nib = (dw[sl] >> (4 * r)) & 0xFu;
-              if (nib) {
-                if (pos < capacity) {
-                  face_ids[pos] = ((lin0 + (unsigned long long)(sl / 3)) << 2) | (unsigned)(sl % 3);
-                  winding[pos] = (int8_t)((int)(nib ^ 4u) - 4);
-                }
-                ++pos;
-              }
+          for (int sl = 0; sl < 6; ++sl) rn |= ((dw[sl] >> f) & 0xFu) << (4 * sl);
+          unsigned long long pos = fbase + s_rowbase[wib][r] + field8(exe, exo, r);
+          const unsigned long long lin0 =
+              ((unsigned long long)k * ny + (unsigned long long)(j0 + r)) * (unsigned long long)nx +
+              64u * (unsigned)ww + 2u * rl;
+          uint32_t nzm = nz_fields(rn);
+          while (nzm) {
+            const int g = __ffs(nzm) - 1;
+            nzm &= nzm - 1u;
+            const int sl = g >> 2;
+            const uint32_t nib = (rn >> g) & 0xFu;
+            if (pos < capacity) {
+              face_ids[pos] = ((lin0 + (unsigned long long)(sl >= 3)) << 2) | (unsigned)(sl % 3);
+              winding[pos] = (int8_t)((int)(nib ^ 4u) - 4);
             }
+            ++pos;
           }
         }
       }
@@ -990,7 +999,7 @@ int bulk_identify(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* 
   if (e != cudaSuccess) return check_cuda(e, "v3_scan_kernel launch");
   if (capacity > 0) {
     long long blocks = (p.nseg + kExpandWarps - 1) / kExpandWarps;
-    const long long maxb = (long long)h->num_sms * 6;
+    const long long maxb = (long long)h->num_sms * 4;
     if (blocks > maxb) blocks = maxb;
     TraceScope ts(h, K_SCATTER, st);
     v3_expand_kernel<<<(unsigned)blocks, 32 * kExpandWarps, 0, st>>>(
