@@ -236,6 +236,49 @@ QTV_API int qtv_identify_static(const qtv_grid* grid, const void* psi, uint64_t*
                                 void* stream);
 
 /*
+ * Learned locator (the paper has no counterpart: it is trained on positions
+ * made by the plain localization, Sec. 3.3.3 / Eq. 6, which stays its fallback
+ * and the judge of its error).  A 128-256-256-3 MLP (ReLU) maps the encoded
+ * 4x4x4 neighbourhood of a pierced face to its face coordinates (u, v, n);
+ * dense layers use BF16 tensor cores with FP32 accumulation.
+ *
+ * Encoding (qtv_locator_encode): block node (a, b, c) in 0..3 is grid node
+ * min_corner + (a-1) e_u + (b-1) e_v + (c-1) e_n in the face frame
+ * (u, v, n) = (x, y, z), (y, z, x), (z, x, y) for xy, yz, zx faces; psi is
+ * conjugated for W = -1 and divided by the RMS of |psi| over the block.
+ * x is BF16 [n][128] with index ((c*4 + b)*4 + a)*2 + {0: Re, 1: Im};
+ * ok[f] = 0 for faces whose block leaves the grid; rms[f] = the RMS.
+ *
+ * Parameters: QTV_LOCATOR_PARAMS FP32 values: W1 [256][128], b1 [256],
+ * W2 [256][256], b2 [256], W3 [3][256], b3 [3] (weights as [out][in]).
+ * Adam state: first then second moments, 2 * QTV_LOCATOR_PARAMS values.
+ * Training: loss = mean over the batch of |y - target|^2; one Adam step
+ * (beta 0.9 / 0.999, eps 1e-8) per qtv_locator_train_step; batch sizes are
+ * positive multiples of 64.  x, targets, y, grads and loss are device memory.
+ * Inference is qtv_localize(mode = QTV_LEARNED): predictions outside the face
+ * or with |psi_bilinear(u, v)|^2 / rms^2 > fallback_resid are replaced by the
+ * plain result (QTV_FLAG_FALLBACK); accepted ones carry QTV_FLAG_LEARNED.
+ * Checkpoints (qtv_locator_save / _load) hold the step count, parameters and
+ * Adam moments with an FNV-1a checksum; loading resumes training exactly.
+ */
+#define QTV_LOCATOR_PARAMS 99587
+QTV_API int qtv_locator_init(qtv_handle h, uint64_t seed);
+QTV_API int qtv_locator_get(qtv_handle h, float* params, float* adam, uint64_t* step);
+QTV_API int qtv_locator_set(qtv_handle h, const float* params, const float* adam, uint64_t step);
+QTV_API int qtv_locator_encode(qtv_handle h, const qtv_grid* grid, const void* psi,
+                               const uint64_t* face_ids, const int8_t* winding, uint64_t n,
+                               const uint64_t* n_dev, uint16_t* x, uint8_t* ok, float* rms,
+                               void* stream);
+QTV_API int qtv_locator_forward(qtv_handle h, const uint16_t* x, uint64_t n, float* y,
+                                void* stream);
+QTV_API int qtv_locator_gradients(qtv_handle h, const uint16_t* x, const float* targets,
+                                  uint64_t n, float* grads, float* loss, void* stream);
+QTV_API int qtv_locator_train_step(qtv_handle h, const uint16_t* x, const float* targets,
+                                   uint64_t n, float lr, float* loss, void* stream);
+QTV_API int qtv_locator_save(qtv_handle h, const char* path);
+QTV_API int qtv_locator_load(qtv_handle h, const char* path);
+
+/*
  * Kernel timing trace.  While enabled, the handle records a pair of CUDA
  * events on the launching stream around each of its kernel launches (names:
  * "sweep", "seg_scan", "scatter", "stats", "localize", "emit_pack").

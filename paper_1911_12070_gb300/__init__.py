@@ -16,6 +16,8 @@ import os
 
 import numpy as np
 
+LOCATOR_PARAMS = 99587
+
 __all__ = ["lib", "Qtv", "Grid", "Stats", "Sample", "QtvError", "PLAIN", "LEARNED",
            "FLAG_ANOMALOUS", "FLAG_FALLBACK", "FLAG_LEARNED", "SAMPLE_DTYPE", "build"]
 
@@ -101,6 +103,19 @@ def lib() -> ctypes.CDLL:
         L.qtv_identify_localize.restype = i32
         L.qtv_identify_static.argtypes = [ctypes.POINTER(Grid), P, P, P, u64, P, P]
         L.qtv_identify_static.restype = i32
+        L.qtv_locator_init.argtypes = [P, u64]
+        L.qtv_locator_get.argtypes = [P, P, P, ctypes.POINTER(u64)]
+        L.qtv_locator_set.argtypes = [P, P, P, u64]
+        L.qtv_locator_encode.argtypes = [P, ctypes.POINTER(Grid), P, P, P, u64, P, P, P, P, P]
+        L.qtv_locator_forward.argtypes = [P, P, u64, P, P]
+        L.qtv_locator_gradients.argtypes = [P, P, P, u64, P, P, P]
+        L.qtv_locator_train_step.argtypes = [P, P, P, u64, f32, P, P]
+        L.qtv_locator_save.argtypes = [P, ctypes.c_char_p]
+        L.qtv_locator_load.argtypes = [P, ctypes.c_char_p]
+        for name in ("qtv_locator_init", "qtv_locator_get", "qtv_locator_set", "qtv_locator_encode",
+                     "qtv_locator_forward", "qtv_locator_gradients", "qtv_locator_train_step",
+                     "qtv_locator_save", "qtv_locator_load"):
+            getattr(L, name).restype = i32
         L.qtv_trace_enable.argtypes = [P, i32]
         L.qtv_trace_read.argtypes = [P, ctypes.POINTER(TraceEntry), i32, ctypes.POINTER(i32), i32]
         for name in ("qtv_create", "qtv_destroy", "qtv_reserve", "qtv_identify", "qtv_localize",
@@ -256,6 +271,74 @@ class Qtv:
         self.localize_into(psi, face_ids, winding, xyz, resid, flags, mode=mode,
                            fallback_resid=fallback_resid, grid=grid, stream=stream)
         return xyz, resid, flags
+
+    # -- learned locator ------------------------------------------------------------
+    def locator_init(self, seed: int = 0):
+        _check(lib().qtv_locator_init(self.h, int(seed)))
+
+    def locator_get(self):
+        """(params float32 [P], adam float32 [2P], step) copied to the host."""
+        p = np.zeros(LOCATOR_PARAMS, np.float32)
+        a = np.zeros(2 * LOCATOR_PARAMS, np.float32)
+        st = ctypes.c_uint64(0)
+        _check(lib().qtv_locator_get(self.h, p.ctypes.data, a.ctypes.data, ctypes.byref(st)))
+        return p, a, int(st.value)
+
+    def locator_set(self, params, adam=None, step: int = 0):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        a = None if adam is None else np.ascontiguousarray(adam, dtype=np.float32)
+        _check(lib().qtv_locator_set(self.h, p.ctypes.data, None if a is None else a.ctypes.data,
+                                     int(step)))
+
+    def locator_encode(self, psi, face_ids, winding, grid=None, stream=None):
+        """(x uint16-as-int16 [n,128] BF16 bits, ok uint8 [n], rms float32 [n])."""
+        import torch
+
+        n = face_ids.numel()
+        dev = psi.device
+        x = torch.empty((n, 128), dtype=torch.int16, device=dev)
+        ok = torch.empty(n, dtype=torch.uint8, device=dev)
+        rms = torch.empty(n, dtype=torch.float32, device=dev)
+        g = grid or Grid.of(tuple(psi.shape))
+        _check(lib().qtv_locator_encode(self.h, ctypes.byref(g), _ptr(psi), _ptr(face_ids),
+                                        _ptr(winding), n, None, _ptr(x), _ptr(ok), _ptr(rms),
+                                        _stream_ptr(stream)))
+        return x, ok, rms
+
+    def locator_forward(self, x, stream=None):
+        import torch
+
+        n = x.shape[0]
+        y = torch.empty((n, 3), dtype=torch.float32, device=x.device)
+        _check(lib().qtv_locator_forward(self.h, _ptr(x), n, _ptr(y), _stream_ptr(stream)))
+        return y
+
+    def locator_gradients(self, x, targets, stream=None):
+        """(grads float32 [P], loss) for one batch (rows a multiple of 64)."""
+        import torch
+
+        n = x.shape[0]
+        g = torch.empty(LOCATOR_PARAMS, dtype=torch.float32, device=x.device)
+        loss = torch.zeros(1, dtype=torch.float32, device=x.device)
+        _check(lib().qtv_locator_gradients(self.h, _ptr(x), _ptr(targets), n, _ptr(g), _ptr(loss),
+                                           _stream_ptr(stream)))
+        return g, loss
+
+    def locator_train_step(self, x, targets, lr: float, loss=None, stream=None):
+        """One Adam step on a batch; loss (device float[1]) receives the batch loss."""
+        import torch
+
+        if loss is None:
+            loss = torch.zeros(1, dtype=torch.float32, device=x.device)
+        _check(lib().qtv_locator_train_step(self.h, _ptr(x), _ptr(targets), x.shape[0], float(lr),
+                                            _ptr(loss), _stream_ptr(stream)))
+        return loss
+
+    def locator_save(self, path: str):
+        _check(lib().qtv_locator_save(self.h, path.encode()))
+
+    def locator_load(self, path: str):
+        _check(lib().qtv_locator_load(self.h, path.encode()))
 
     # -- emission -------------------------------------------------------------------
     def emit_samples(self, face_ids, winding, xyz, resid, flags, out=None, stream=None):

@@ -197,6 +197,7 @@ int qtv_destroy(qtv_handle h) {
   cudaFree(h->ws.pack);
   cudaFree(h->ws.table);
   cudaFree(h->ws.tiles);
+  locator_free(h->loc);
   for (auto& r : h->trace) {
     cudaEventDestroy(r.start);
     cudaEventDestroy(r.stop);
@@ -333,13 +334,11 @@ int qtv_identify_localize(qtv_handle h, const qtv_grid* grid, const void* psi,
 int qtv_localize(qtv_handle h, const qtv_grid* grid, const void* psi, const uint64_t* face_ids,
                  const int8_t* winding, uint64_t n, const uint64_t* n_dev, int mode,
                  float fallback_resid, float* xyz, float* resid, uint8_t* flags, void* stream) {
-  (void)fallback_resid;
   if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
   int rc = validate_grid(grid);
   if (rc) return rc;
   if (mode != QTV_PLAIN && mode != QTV_LEARNED)
     return set_error(QTV_ERR_ARG, "unknown localization mode %d", mode);
-  if (mode == QTV_LEARNED) return set_error(QTV_ERR_STATE, "no learned locator loaded");
   if (n == 0) return QTV_OK;
   if (!psi || !face_ids || !winding || !xyz || !resid || !flags)
     return set_error(QTV_ERR_ARG, "a required pointer is NULL");
@@ -347,6 +346,10 @@ int qtv_localize(qtv_handle h, const qtv_grid* grid, const void* psi, const uint
     return set_error(QTV_ERR_ARG, "psi must be 8-byte aligned");
   DeviceGuard dg(h->device);
   if (!dg.ok) return set_error(QTV_ERR_CUDA, "cudaSetDevice failed");
+  if (mode == QTV_LEARNED)
+    return locator_localize(h, *grid, reinterpret_cast<const float2*>(psi), face_ids, winding, n,
+                            n_dev, fallback_resid, xyz, resid, flags,
+                            reinterpret_cast<cudaStream_t>(stream));
   return localize_launch(h, *grid, reinterpret_cast<const float2*>(psi), face_ids, winding, n, n_dev,
                          xyz, resid, flags, reinterpret_cast<cudaStream_t>(stream));
 }

@@ -58,6 +58,8 @@ struct IdentNeeds {
 #include <vector>
 
 namespace qtv {
+struct Locator;  // learned locator state (locator.cu)
+void locator_free(Locator* L);
 enum KernelId { K_SWEEP = 0, K_SEG_SCAN, K_SCATTER, K_STATS, K_LOCALIZE, K_EMIT_PACK, K_COUNT };
 struct TraceRec {
   int kernel;
@@ -72,6 +74,7 @@ struct qtv_handle_s {
   bool trace_on = false;
   std::vector<qtv::TraceRec> trace;      // recorded, not yet read
   std::vector<cudaEvent_t> event_pool;   // free events
+  qtv::Locator* loc = nullptr;           // learned locator (weights, Adam state, buffers)
 };
 
 namespace qtv {
@@ -133,6 +136,11 @@ int bulk_identify(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* 
 int localize_launch(qtv_handle h, const qtv_grid& g, const float2* psi, const uint64_t* face_ids,
                     const int8_t* winding, uint64_t n, const uint64_t* n_dev, float* xyz,
                     float* resid, uint8_t* flags, cudaStream_t st);
+
+// Learned localization with plain fallback (locator.cu)
+int locator_localize(qtv_handle h, const qtv_grid& g, const float2* psi, const uint64_t* face_ids,
+                     const int8_t* winding, uint64_t n, const uint64_t* n_dev, float thresh,
+                     float* xyz, float* resid, uint8_t* flags, cudaStream_t st);
 
 // Emission pack (localize.cu)
 int emit_pack_launch(qtv_handle h, uint64_t n, const uint64_t* face_ids, const int8_t* winding, const float* xyz,

@@ -1,0 +1,238 @@
+"""GPU parity and behaviour of the learned locator (no counterpart in the
+paper; trained on the plain localization of Sec. 3.3.3, Eq. 6).
+
+* the encoding kernel equals the FP64 oracle encoding to BF16 rounding;
+* the forward pass, the gradients of all six parameter tensors and the Adam
+  update equal the FP64 oracle within BF16 tolerances (cosine > 0.999 and
+  relative error < 2e-2 for the gradients);
+* a checkpoint resumes training bit for bit;
+* trained on noisy neighbourhoods with labels from the plain solve of the clean
+  field, the network's positions are within 0.05 h RMS of those labels on a
+  held-out field, and are compared with what the plain method gives on the
+  noisy field (the gain);
+* learned localization falls back to the plain result exactly where it must.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import mlp
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def q():
+    import paper_1911_12070_gb300 as qtv
+
+    qtv.build()
+    h = qtv.Qtv(0)
+    yield h
+    h.close()
+
+
+def bf16_to_f64(t):
+    b = t.cpu().numpy().view(np.uint16).astype(np.uint32) << 16
+    return b.view(np.float32).astype(np.float64)
+
+
+def round_bf16(a):
+    a32 = np.asarray(a, np.float32)
+    bits = a32.view(np.uint32).astype(np.uint64)
+    bits = (bits + 0x7FFF + ((bits >> 16) & 1)) >> 16
+    return (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def params_to_dict(p):
+    p = np.asarray(p, np.float64)
+    o = 0
+    d = {}
+    for l, (fi, fo) in enumerate(zip(mlp.SIZES[:-1], mlp.SIZES[1:]), start=1):
+        d[f"W{l}"] = p[o:o + fi * fo].reshape(fo, fi)
+        o += fi * fo
+        d[f"b{l}"] = p[o:o + fo].copy()
+        o += fo
+    assert o == p.size
+    return d
+
+
+def dict_to_params(d):
+    return np.concatenate([np.concatenate([d[f"W{l}"].reshape(-1), d[f"b{l}"]]) for l in (1, 2, 3)])
+
+
+@pytest.fixture(scope="module")
+def small_faces(q):
+    host = synth.random_waves_numpy((24, 40, 130), synth.wave_spec(12, 512))
+    psi = torch.from_numpy(host).cuda()
+    ids, w, _ = q.identify(psi)
+    return host, psi, ids, w
+
+
+def test_encoding_matches_oracle(q, small_faces):
+    host, psi, ids, w = small_faces
+    x, ok, rms = q.locator_encode(psi, ids, w)
+    xo, oko, rmso = mlp.encode(host, ids.cpu().numpy().view(np.uint64), w.cpu().numpy())
+    okg = ok.cpu().numpy().astype(bool)
+    assert np.array_equal(okg, oko)
+    assert okg.sum() > 100 and (~okg).sum() > 0
+    xg = bf16_to_f64(x)[okg]
+    ref = xo[okg]
+    assert np.all(np.abs(xg - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-30)
+    assert np.allclose(rms.cpu().numpy()[okg], rmso[okg], rtol=1e-5)
+
+
+def _batch(q, small_faces, n=128):
+    host, psi, ids, w = small_faces
+    x, ok, _ = q.locator_encode(psi, ids, w)
+    xb = x[ok.bool()][:n].contiguous()
+    assert xb.shape[0] == n
+    rng = np.random.default_rng(1)
+    t = torch.from_numpy(rng.uniform(0, 1, (n, 3)).astype(np.float32)).cuda()
+    return xb, t
+
+
+def _oracle_with_bf16_weights(q):
+    p, _, _ = q.locator_get()
+    d = params_to_dict(p)
+    # the tensor cores see BF16 copies of W1 and W2
+    d["W1"] = round_bf16(d["W1"])
+    d["W2"] = round_bf16(d["W2"])
+    return p, d
+
+
+def test_forward_matches_oracle(q, small_faces):
+    q.locator_init(7)
+    xb, _ = _batch(q, small_faces)
+    y = q.locator_forward(xb).cpu().numpy().astype(np.float64)
+    _, d = _oracle_with_bf16_weights(q)
+    yo, _ = mlp.forward(d, bf16_to_f64(xb))
+    scale = np.sqrt(np.mean(yo ** 2))
+    assert np.max(np.abs(y - yo)) < 2e-2 * scale
+
+
+def test_gradients_match_oracle(q, small_faces):
+    q.locator_init(11)
+    xb, t = _batch(q, small_faces)
+    g, loss = q.locator_gradients(xb, t)
+    gg = params_to_dict(g.cpu().numpy())
+    _, d = _oracle_with_bf16_weights(q)
+    lo, go = mlp.loss_and_grads(d, bf16_to_f64(xb), t.cpu().numpy().astype(np.float64))
+    assert abs(float(loss.item()) - lo) < 1e-2 * lo
+    for key in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        a, b = gg[key].reshape(-1), go[key].reshape(-1)
+        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert cos > 0.999 and rel < 2e-2, (key, cos, rel)
+
+
+def test_adam_step_matches_oracle(q, small_faces):
+    q.locator_init(13)
+    xb, t = _batch(q, small_faces)
+    p0, _, s0 = q.locator_get()
+    g, _ = q.locator_gradients(xb, t)
+    q.locator_train_step(xb, t, lr=1e-3)
+    torch.cuda.synchronize()
+    p1, adam, s1 = q.locator_get()
+    assert s1 == s0 + 1
+    d = params_to_dict(p0)
+    gd = params_to_dict(g.cpu().numpy())
+    m = {k: np.zeros_like(v) for k, v in d.items()}
+    v = {k: np.zeros_like(v) for k, v in d.items()}
+    mlp.adam_step(d, gd, m, v, t=1, lr=1e-3)
+    ref = dict_to_params(d)
+    assert np.max(np.abs(p1 - ref)) < 1e-6
+    assert np.allclose(adam[:len(p1)], dict_to_params(m), rtol=1e-5, atol=1e-12)
+
+
+def test_checkpoint_resumes_bit_exactly(q, small_faces):
+    import paper_1911_12070_gb300 as qtv
+
+    xb, t = _batch(q, small_faces)
+    q.locator_init(17)
+    for _ in range(5):
+        q.locator_train_step(xb, t, lr=1e-3)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "loc.qtv")
+        q.locator_save(path)
+        for _ in range(3):
+            q.locator_train_step(xb, t, lr=1e-3)
+        pa, aa, sa = q.locator_get()
+        q2 = qtv.Qtv(0)
+        q2.locator_load(path)
+        for _ in range(3):
+            q2.locator_train_step(xb, t, lr=1e-3)
+        pb, ab, sb = q2.locator_get()
+        q2.close()
+        # a corrupted file is rejected
+        raw = bytearray(open(path, "rb").read())
+        raw[100] ^= 0xFF
+        open(path, "wb").write(bytes(raw))
+        with pytest.raises(qtv.QtvError):
+            q.locator_load(path)
+    assert sa == sb == 8
+    assert np.array_equal(pa, pb) and np.array_equal(aa, ab)
+
+
+@pytest.fixture(scope="module")
+def trained(q):
+    from paper_1911_12070_gb300 import learned
+
+    ex = [learned.make_examples(q, *learned.field_pair(s, 256, 4096, 0.05, "cuda"))
+          for s in (101, 102, 103, 104)]
+    x = torch.cat([e["x"] for e in ex])
+    t = torch.cat([e["t"] for e in ex])
+    q.locator_init(1)
+    losses = learned.train(q, x, t, steps=2400, batch=4096, lr=2e-3)
+    clean, noisy = learned.field_pair(120, 256, 4096, 0.05, "cuda")
+    test = learned.make_examples(q, clean, noisy)
+    return losses, test, clean, noisy
+
+
+def test_training_reduces_loss_and_meets_accuracy(q, trained):
+    from paper_1911_12070_gb300 import learned
+
+    losses, test, clean, noisy = trained
+    assert losses[-50:].mean() < 0.1 * losses[:10].mean()
+    y = q.locator_forward(test["x"])
+    rms_learned = learned.rms_h(y[:, :2], test["t"][:, :2])
+    print(f"held-out: {len(test['t'])} faces, learned RMS {rms_learned:.4f} h")
+    assert rms_learned <= 0.05
+
+
+def test_gain_over_plain_on_noisy_field(q, trained):
+    """What the network adds: on the 5%-noise field the plain zero moves with
+    the noise; the network sees 64 nodes and is compared with the same clean
+    labels."""
+    from paper_1911_12070_gb300 import learned
+
+    _, test, clean, noisy = trained
+    y = q.locator_forward(test["x"])
+    rms_learned = learned.rms_h(y[:, :2], test["t"][:, :2])
+    xyz_n, _, _ = q.localize(noisy, test["ids"], test["w"])
+    uv_plain_noisy = learned.face_uv(test["ids"], xyz_n, tuple(noisy.shape))
+    rms_plain = learned.rms_h(uv_plain_noisy, test["t"][:, :2])
+    print(f"noisy field vs clean cores: plain {rms_plain:.4f} h, learned {rms_learned:.4f} h")
+    assert rms_learned < rms_plain
+
+
+def test_learned_localize_fallback_is_plain(q, trained):
+    import paper_1911_12070_gb300 as qtv
+
+    _, test, clean, noisy = trained
+    ids, w = test["ids"], test["w"]
+    xyz_l, resid_l, flags_l = q.localize(clean, ids, w, mode=qtv.LEARNED, fallback_resid=1e-3)
+    xyz_p, resid_p, flags_p = q.localize(clean, ids, w)
+    fl = flags_l.cpu().numpy()
+    learned_mask = (fl & qtv.FLAG_LEARNED) != 0
+    fb = (fl & qtv.FLAG_FALLBACK) != 0
+    assert np.all(learned_mask ^ fb)
+    assert torch.equal(xyz_l[torch.from_numpy(fb).cuda()], xyz_p[torch.from_numpy(fb).cuda()])
+    d = torch.linalg.norm(xyz_l - xyz_p, dim=1).cpu().numpy()
+    print(f"learned accepted {learned_mask.mean():.3f}, RMS vs plain {np.sqrt(np.mean(d**2)):.4f} h")
+    assert np.sqrt(np.mean(d ** 2)) <= 0.05
