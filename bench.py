@@ -49,12 +49,16 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["qtv", "reference"], default="qtv")
     p.add_argument("--n", type=int, default=512, help="grid edge (default 512)")
-    p.add_argument("--cpu-planes", type=int, default=48,
+    p.add_argument("--cpu-seconds", type=float, default=12.0,
+                   help="host seconds of the oracle's timed CPU sample")
+    p.add_argument("--cpu-planes", type=int, default=96,
                    help="planes of the field in the oracle's timed CPU sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--soak", type=float, default=1.5,
                    help="seconds of untimed load before warm-up (clock sampling)")
+    p.add_argument("--no-learned", action="store_true",
+                   help="skip training the learned locator and its report against plain")
     return p.parse_args()
 
 
@@ -127,6 +131,62 @@ def make_field(n, device):
     psi = synth.random_waves((n, n, n), synth.wave_spec(7, 16384 if n >= 512 else 4096),
                              device=device)
     return synth.multiplicative_noise(psi, 8)
+
+
+def learned_report(q, psi, ids, wnd, F, stream, reps=20):
+    """Trains the learned locator (12 seeds of 256^3, about 2e6 faces, the
+    library's own training kernels), then times learned and plain localization
+    of the F faces of the bench field and measures the learned positions
+    against the plain ones (the plain solve is the judge)."""
+    import torch
+
+    import paper_1911_12070_gb300 as qtv
+    from paper_1911_12070_gb300 import learned
+
+    torch.cuda.synchronize()
+    t0 = time.time()
+    losses = learned.fit(q)
+    torch.cuda.synchronize()
+    fit_s = time.time() - t0
+    fid, w = ids[:F], wnd[:F]
+    dev = psi.device
+    outs = {}
+    ms = {}
+    for mode in (qtv.PLAIN, qtv.LEARNED):
+        o = (torch.empty((F, 3), dtype=torch.float32, device=dev),
+             torch.empty(F, dtype=torch.float32, device=dev),
+             torch.empty(F, dtype=torch.uint8, device=dev))
+        outs[mode] = o
+        for _ in range(3):
+            q.localize_into(psi, fid, w, *o, mode=mode, fallback_resid=1e-3)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            q.localize_into(psi, fid, w, *o, mode=mode, fallback_resid=1e-3)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms[mode] = e0.elapsed_time(e1) / reps
+    xyz_p, _, fl_p = outs[qtv.PLAIN]
+    xyz_l, _, fl_l = outs[qtv.LEARNED]
+    good = (fl_p & qtv.FLAG_ANOMALOUS) == 0
+    accepted = (fl_l & qtv.FLAG_LEARNED) != 0
+    d2 = torch.sum((xyz_l - xyz_p) ** 2, 1)
+    rms_all = float(torch.sqrt(torch.mean(d2[good])))
+    rms_acc = float(torch.sqrt(torch.mean(d2[good & accepted])))
+    flop = 2 * (128 * 256 + 256 * 256 + 256 * 3) * F
+    return {
+        "faces": F,
+        "train": {"faces": "12 random-wave fields 256^3 (4096 waves, seeds 101-112), 5% noise "
+                           "inputs, clean plain labels", "steps": int(len(losses)),
+                  "seconds": fit_s, "final_loss": float(np.mean(losses[-50:]))},
+        "plain_ms": ms[qtv.PLAIN], "learned_ms": ms[qtv.LEARNED],
+        "learned_mlp_tflops": flop / (ms[qtv.LEARNED] * 1e-3) / 1e12,
+        "accepted_frac": float(accepted.float().mean()),
+        "rms_vs_plain_h": rms_all, "rms_vs_plain_accepted_h": rms_acc,
+        "fallback_resid": 1e-3,
+    }
 
 
 def oracle_sample(psi_host_slab, planes):
@@ -383,17 +443,26 @@ def run_qtv(args):
         "clocks": clocks,
     }
 
+    if rank == 0 and not args.no_learned:
+        line["learned"] = learned_report(q, psi, ids, wnd, F, stream)
+
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
 
         planes = max(1, min(args.cpu_planes, n - 1))
         slab = np.ascontiguousarray(psi[: planes + 1].cpu().numpy())
         oracle.set_threads(cpu_cores())
-        dt, nn, _ = oracle_sample(slab, planes)
+        # repeat the slab until about args.cpu_seconds of host work
+        dt, nn, reps = 0.0, 0, 0
+        while reps < 1 or dt < args.cpu_seconds:
+            d, m, _ = oracle_sample(slab, planes)
+            dt += d
+            nn += m
+            reps += 1
         line["cpu_baseline"] = {
             "value": nn / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"{planes} z-planes of the {n}^3 field ({nn} nodes), FP64 identify + "
-                      f"localize, {dt:.1f} s"}
+            "sample": f"{planes} z-planes of the {n}^3 field ({nn // reps} nodes), FP64 identify "
+                      f"+ localize, {reps} passes, {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     q.close()

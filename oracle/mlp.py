@@ -10,8 +10,10 @@ written from the definitions:
   faces; node (a, b, c) of the block is grid node
   min_corner + (a - 1) e_u + (b - 1) e_v + (c - 1) e_n, so the face spans
   a, b in {1, 2} at c = 1.  psi is conjugated when W = -1 (the zero of the
-  interpolant does not move and the winding becomes +1) and divided by the
-  RMS of |psi| over the block.  Input vector index ((c * 4 + b) * 4 + a) * 2 +
+  interpolant does not move and the winding becomes +1), multiplied by
+  conj(P0)/|P0| with P0 the value at the face's minimum corner (block node
+  (1, 1, 1); a constant phase does not move the zero either) and divided by
+  the RMS of |psi| over the block.  Input vector index ((c * 4 + b) * 4 + a) * 2 +
   {0: Re, 1: Im}.  Faces whose block leaves the grid are not encoded.
 * network -- y = W3 relu(W2 relu(W1 x + b1) + b2) + b3, sizes 128-256-256-3;
   W_l has shape (out, in).
@@ -116,6 +118,9 @@ def encode(psi: np.ndarray, face_ids: np.ndarray, winding: np.ndarray):
             continue
         if int(winding[f]) == -1:
             vals = np.conj(vals)
+        p0 = vals[1, 1, 1]
+        if abs(p0) > 0:
+            vals = vals * (np.conj(p0) / abs(p0))
         r = np.sqrt(np.mean(np.abs(vals) ** 2))
         if not r > 0:
             continue

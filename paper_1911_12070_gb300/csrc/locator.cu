@@ -80,6 +80,21 @@ __global__ void encode_kernel(const float2* __restrict__ psi, int nx, int ny, in
       if (conjg) v.y = -v.y;
       val[h] = v;
     }
+    // rotate by conj(P0)/|P0|, P0 = block node (1, 1, 1) = q 21, held by lane 21
+    {
+      const float p0r = __shfl_sync(0xffffffffu, val[0].x, 21);
+      const float p0i = __shfl_sync(0xffffffffu, val[0].y, 21);
+      const float m0 = sqrtf(p0r * p0r + p0i * p0i);
+      if (m0 > 0.f) {
+        const float cr = p0r / m0, ci = -p0i / m0;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const float re = val[hh].x * cr - val[hh].y * ci;
+          const float im = val[hh].x * ci + val[hh].y * cr;
+          val[hh] = make_float2(re, im);
+        }
+      }
+    }
     float s2 = val[0].x * val[0].x + val[0].y * val[0].y + val[1].x * val[1].x + val[1].y * val[1].y;
 #pragma unroll
     for (int d = 16; d; d >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, d);
@@ -310,37 +325,42 @@ __global__ void out_back_kernel(const float* __restrict__ dy, const float* __res
   }
 }
 
-// dW3[o][k] = sum_m dY[m][o] A2[m][k]; db3[o] = sum_m dY[m][o] (one block per k chunk)
+constexpr int kRowChunk = 64;  // rows per block of the reductions below
+
+// dW3[o][k] += sum_m dY[m][o] A2[m][k] and db3[o] += sum_m dY[m][o] over one
+// chunk of rows per block (thread k = 0..kH, k == kH the bias); G zeroed first
 __global__ void out_wgrad_kernel(const float* __restrict__ dy, const uint16_t* __restrict__ A2,
                                  unsigned long long n, float* __restrict__ G) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;  // 0..kH (kH = b3 row)
-  if (k > kH) return;
+  const int k = threadIdx.x;
+  const unsigned long long m0 = (unsigned long long)blockIdx.x * kRowChunk;
+  const unsigned long long m1 = m0 + kRowChunk < n ? m0 + kRowChunk : n;
   float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-  for (unsigned long long m = 0; m < n; ++m) {
+  for (unsigned long long m = m0; m < m1; ++m) {
     const float a = k < kH ? bf2f(A2[m * kH + k]) : 1.f;
     s0 = fmaf(dy[3 * m], a, s0);
     s1 = fmaf(dy[3 * m + 1], a, s1);
     s2 = fmaf(dy[3 * m + 2], a, s2);
   }
   if (k < kH) {
-    G[kOffW3 + k] = s0;
-    G[kOffW3 + kH + k] = s1;
-    G[kOffW3 + 2 * kH + k] = s2;
-  } else {
-    G[kOffB3] = s0;
-    G[kOffB3 + 1] = s1;
-    G[kOffB3 + 2] = s2;
+    atomicAdd(&G[kOffW3 + k], s0);
+    atomicAdd(&G[kOffW3 + kH + k], s1);
+    atomicAdd(&G[kOffW3 + 2 * kH + k], s2);
+  } else if (k == kH) {
+    atomicAdd(&G[kOffB3], s0);
+    atomicAdd(&G[kOffB3 + 1], s1);
+    atomicAdd(&G[kOffB3 + 2], s2);
   }
 }
 
-// column sums of a BF16 [n x kH] matrix (bias gradients)
+// out[k] += column sums of a BF16 [n x kH] matrix over one chunk of rows
 __global__ void colsum_kernel(const uint16_t* __restrict__ D, unsigned long long n,
                               float* __restrict__ out) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= kH) return;
+  const int k = threadIdx.x;
+  const unsigned long long m0 = (unsigned long long)blockIdx.x * kRowChunk;
+  const unsigned long long m1 = m0 + kRowChunk < n ? m0 + kRowChunk : n;
   float s = 0.f;
-  for (unsigned long long m = 0; m < n; ++m) s += bf2f(D[m * kH + k]);
-  out[k] = s;
+  for (unsigned long long m = m0; m < m1; ++m) s += bf2f(D[m * kH + k]);
+  atomicAdd(&out[k], s);
 }
 
 // Adam (Kingma & Ba), bias-corrected; refreshes the BF16 copies of W1, W2
@@ -573,8 +593,13 @@ static int forward_backward(Locator* L, const uint16_t* X, const float* T, unsig
   if (rc) return rc;
   out_layer_kernel<<<blocks_for(n, 256, 1024), 256, 0, st>>>(L->A2, L->P, n, L->Y, T, L->DY, loss);
   out_back_kernel<<<blocks_for(n * kH, 256, 4096), 256, 0, st>>>(L->DY, L->P, L->A2, n, L->D2);
-  out_wgrad_kernel<<<(kH + 1 + 127) / 128, 128, 0, st>>>(L->DY, L->A2, n, L->G);
-  colsum_kernel<<<(kH + 127) / 128, 128, 0, st>>>(L->D2, n, L->G + kOffB2);
+  const unsigned chunks = (unsigned)((n + kRowChunk - 1) / kRowChunk);
+  cudaError_t e = cudaMemsetAsync(L->G + kOffB1, 0, kH * sizeof(float), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L->G + kOffB2, 0, kH * sizeof(float), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L->G + kOffW3, 0, (kOut * kH + kOut) * sizeof(float), st);
+  if (e != cudaSuccess) return check_cuda(e, "memset(grads)");
+  out_wgrad_kernel<<<chunks, kH + 32, 0, st>>>(L->DY, L->A2, n, L->G);
+  colsum_kernel<<<chunks, kH, 0, st>>>(L->D2, n, L->G + kOffB2);
   // dW2[n][k] = sum_m dH2[m][n] A1[m][k]
   rc = gemm<true, true, EPI_STORE_F32>(kH, kH, (int)n, L->D2, kH, L->A1, kH, L->G + kOffW2, kH,
                                        nullptr, nullptr, st);
@@ -583,7 +608,7 @@ static int forward_backward(Locator* L, const uint16_t* X, const float* T, unsig
   rc = gemm<false, true, EPI_RELU_MASK_BF16>((int)n, kH, kH, L->D2, kH, L->w2b, kH, L->D1, kH,
                                              nullptr, L->A1, st);
   if (rc) return rc;
-  colsum_kernel<<<(kH + 127) / 128, 128, 0, st>>>(L->D1, n, L->G + kOffB1);
+  colsum_kernel<<<chunks, kH, 0, st>>>(L->D1, n, L->G + kOffB1);
   // dW1[n][k] = sum_m dH1[m][n] X[m][k]
   rc = gemm<true, true, EPI_STORE_F32>(kH, kIn, (int)n, L->D1, kH, X, kIn, L->G + kOffW1, kIn,
                                        nullptr, nullptr, st);

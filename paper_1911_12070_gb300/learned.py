@@ -88,6 +88,23 @@ def train(q: Qtv, x, t, steps: int, batch: int = 4096, lr: float = 2e-3, seed: i
     return loss_buf.cpu().numpy()
 
 
+TRAIN_SEEDS = tuple(range(101, 113))
+
+
+def fit(q: Qtv, seeds=TRAIN_SEEDS, n: int = 256, waves: int = 4096, noise: float = 0.05,
+        steps: int = 20000, batch: int = 4096, lr: float = 2e-3, init_seed: int = 1):
+    """Trains the handle's locator from scratch on the random-wave fields of the
+    given seeds (12 seeds of 256^3 give about 2.0e6 faces); returns the losses."""
+    import torch
+
+    ex = [make_examples(q, *field_pair(s, n, waves, noise, "cuda")) for s in seeds]
+    x = torch.cat([e["x"] for e in ex])
+    t = torch.cat([e["t"] for e in ex])
+    del ex
+    q.locator_init(init_seed)
+    return train(q, x, t, steps=steps, batch=batch, lr=lr)
+
+
 def rms_h(a, b):
     """Root mean square distance (rows of a, b) as a float."""
     import torch

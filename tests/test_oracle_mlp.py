@@ -69,10 +69,24 @@ def test_encoding_normalisation_and_face_position():
     assert ok[0]
     assert abs(np.sum(x[0] ** 2) / 64 - 1.0) < 1e-12
     z = (x[0, 0::2] + 1j * x[0, 1::2]).reshape(4, 4, 4) * rms[0]  # [c][b][a]
+    # the minimum corner is rotated onto the positive real axis
+    ph = np.conj(psi[k, j, i]) / abs(psi[k, j, i])
+    assert abs(z[1, 1, 1].imag) < 1e-12 and z[1, 1, 1].real > 0
     # face corners of an xy face at block (a, b) in {1,2}, c = 1
-    assert np.allclose(z[1, 1, 1], psi[k, j, i]) and np.allclose(z[1, 1, 2], psi[k, j, i + 1])
-    assert np.allclose(z[1, 2, 2], psi[k, j + 1, i + 1]) and np.allclose(z[1, 2, 1], psi[k, j + 1, i])
-    assert np.allclose(z[0, 0, 0], psi[k - 1, j - 1, i - 1])
+    assert np.allclose(z[1, 1, 1], psi[k, j, i] * ph) and np.allclose(z[1, 1, 2], psi[k, j, i + 1] * ph)
+    assert np.allclose(z[1, 2, 2], psi[k, j + 1, i + 1] * ph)
+    assert np.allclose(z[1, 2, 1], psi[k, j + 1, i] * ph)
+    assert np.allclose(z[0, 0, 0], psi[k - 1, j - 1, i - 1] * ph)
+
+
+def test_encoding_is_phase_invariant():
+    psi = _field(6)
+    nz, ny, nx = psi.shape
+    fid = np.array([(((4 * ny + 5) * nx + 6) << 2) | 2], np.uint64)
+    w = np.array([1], np.int8)
+    x0, _, _ = mlp.encode(psi, fid, w)
+    x1, _, _ = mlp.encode((psi * np.complex64(np.exp(1j * 2.1))).astype(np.complex64), fid, w)
+    assert np.allclose(x0, x1, atol=1e-6)
 
 
 def test_encoding_of_negative_winding_is_conjugate():
