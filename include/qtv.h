@@ -245,7 +245,9 @@ QTV_API int qtv_identify_static(const qtv_grid* grid, const void* psi, uint64_t*
  * Encoding (qtv_locator_encode): block node (a, b, c) in 0..3 is grid node
  * min_corner + (a-1) e_u + (b-1) e_v + (c-1) e_n in the face frame
  * (u, v, n) = (x, y, z), (y, z, x), (z, x, y) for xy, yz, zx faces; psi is
- * conjugated for W = -1 and divided by the RMS of |psi| over the block.
+ * conjugated for W = -1, multiplied by conj(P0)/|P0| with P0 the value at
+ * the face's minimum corner (block node (1, 1, 1)), and divided by the RMS of
+ * |psi| over the block.
  * x is BF16 [n][128] with index ((c*4 + b)*4 + a)*2 + {0: Re, 1: Im};
  * ok[f] = 0 for faces whose block leaves the grid; rms[f] = the RMS.
  *
@@ -279,9 +281,61 @@ QTV_API int qtv_locator_save(qtv_handle h, const char* path);
 QTV_API int qtv_locator_load(qtv_handle h, const char* path);
 
 /*
+ * Batches of snapshots.  Identification (Sec. 2.2.2, Eq. 5) and localization
+ * (Sec. 3.3.3, Eq. 6) of up to QTV_BATCH_MAX snapshots of different grid
+ * sizes in one pass: one persistent sweep launch whose CTAs take contiguous
+ * ranges of the (plane, band, x tile) units of all snapshots, then one scan,
+ * one expand and one localization launch over the concatenated face list.
+ * The sequence is captured into a CUDA graph on the first qtv_batch_run and
+ * replayed by later calls with the same outputs and mode.
+ *
+ * qtv_batch_plan: grids[i] / psis[i] (device, complex64, x fastest, 16-byte
+ * aligned, even nx <= 1024, periodic = 0) must stay valid and unchanged in
+ * place until the next plan or qtv_destroy (new data may be written into the
+ * same buffers between runs).  The call runs a counting pass, then picks the
+ * sweep shape (warps per x tile, resident CTAs per SM, z-block height) by
+ * timing candidates on these fields, unless tune_cache names a text file that
+ * holds a shape for this device and these grid sizes; a newly timed shape is
+ * appended to that file (tune_cache may be NULL).  Each line of the file is
+ * "qtv-tune-v1 <key> <warps per tile> <CTAs per SM, 0 = max> <z-block
+ * factor> <ms>"; the last line whose key matches wins, and the key "*"
+ * matches every batch (a pinned shape).  Synchronizes `stream`.
+ *
+ * qtv_batch_run: face_ids / winding [capacity] receive the faces of all
+ * snapshots, snapshot i in [offsets[i], offsets[i+1]) in ascending face-id
+ * order (face ids are snapshot-local); offsets (device, n + 1 entries)
+ * receives the slice starts and the total in offsets[n]
+ * (QTV_COUNT_TIMEOUT when a bounded wait gave up).  A total above capacity
+ * means outputs were truncated: grow and run again.  xyz [capacity][3],
+ * resid and flags (all NULL to skip localization) receive the positions
+ * (mode QTV_PLAIN or QTV_LEARNED, as qtv_localize).  Asynchronous on stream.
+ */
+#define QTV_BATCH_MAX 32
+typedef struct {
+  uint64_t nodes;         /* grid nodes of all snapshots */
+  uint64_t faces;         /* pierced faces found by the counting pass */
+  int32_t warps_per_tile; /* chosen shape: tile width 64 * warps_per_tile columns */
+  int32_t tile_columns;
+  int32_t ctas_per_sm;
+  float zscale;           /* factor on the z-block height */
+  int32_t grid;           /* CTAs of the sweep launch */
+  int32_t source;         /* 1: tune cache, 2: timed now */
+  int32_t candidates;     /* shapes timed (source 2) */
+  float tuned_ms;         /* sweep time of the chosen shape */
+} qtv_batch_info;
+
+QTV_API int qtv_batch_plan(qtv_handle h, int n, const qtv_grid* grids, const void* const* psis,
+                           const char* tune_cache, void* stream);
+QTV_API int qtv_batch_info_get(qtv_handle h, qtv_batch_info* out);
+QTV_API int qtv_batch_run(qtv_handle h, uint64_t* face_ids, int8_t* winding, uint64_t capacity,
+                          uint64_t* offsets, float* xyz, float* resid, uint8_t* flags, int mode,
+                          float fallback_resid, void* stream);
+
+/*
  * Kernel timing trace.  While enabled, the handle records a pair of CUDA
  * events on the launching stream around each of its kernel launches (names:
- * "sweep", "seg_scan", "scatter", "stats", "localize", "emit_pack").
+ * "sweep", "seg_scan", "scatter", "stats", "localize", "emit_pack", and
+ * "batch" for one replay of a batch graph).
  * qtv_trace_read waits for the recorded events, writes up to max_entries
  * per-kernel totals (launch count and summed device time) and, if reset is
  * nonzero, clears the record.  Tracing adds host work per launch; leave it

@@ -68,6 +68,17 @@ class TraceEntry(ctypes.Structure):
                 ("total_ms", ctypes.c_float)]
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("nodes", ctypes.c_uint64), ("faces", ctypes.c_uint64),
+                ("warps_per_tile", ctypes.c_int32), ("tile_columns", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("zscale", ctypes.c_float),
+                ("grid", ctypes.c_int32), ("source", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("tuned_ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 SAMPLE_DTYPE = np.dtype([("x", "<f4"), ("y", "<f4"), ("z", "<f4"), ("resid", "<f4"),
                          ("face_id", "<u8"), ("winding", "i1"), ("flags", "u1"),
                          ("reserved0", "<u2"), ("reserved1", "<u4")])
@@ -115,6 +126,12 @@ def lib() -> ctypes.CDLL:
         for name in ("qtv_locator_init", "qtv_locator_get", "qtv_locator_set", "qtv_locator_encode",
                      "qtv_locator_forward", "qtv_locator_gradients", "qtv_locator_train_step",
                      "qtv_locator_save", "qtv_locator_load"):
+            getattr(L, name).restype = i32
+        L.qtv_batch_plan.argtypes = [P, i32, ctypes.POINTER(Grid), ctypes.POINTER(P),
+                                     ctypes.c_char_p, P]
+        L.qtv_batch_info_get.argtypes = [P, ctypes.POINTER(BatchInfo)]
+        L.qtv_batch_run.argtypes = [P, P, P, u64, P, P, P, P, i32, f32, P]
+        for name in ("qtv_batch_plan", "qtv_batch_info_get", "qtv_batch_run"):
             getattr(L, name).restype = i32
         L.qtv_trace_enable.argtypes = [P, i32]
         L.qtv_trace_read.argtypes = [P, ctypes.POINTER(TraceEntry), i32, ctypes.POINTER(i32), i32]
@@ -271,6 +288,67 @@ class Qtv:
         self.localize_into(psi, face_ids, winding, xyz, resid, flags, mode=mode,
                            fallback_resid=fallback_resid, grid=grid, stream=stream)
         return xyz, resid, flags
+
+    # -- batches of snapshots ---------------------------------------------------------
+    def batch_plan(self, psis, tune_cache=None, grids=None, stream=None):
+        """Plans one pass over the snapshots psis (list of complex64 [nz, ny, nx]
+        device tensors, kept alive by the handle); returns the plan's info."""
+        n = len(psis)
+        gs = (Grid * n)(*[grids[i] if grids else Grid.of(tuple(p.shape)) for i, p in enumerate(psis)])
+        ps = (ctypes.c_void_p * n)(*[p.data_ptr() for p in psis])
+        path = None if tune_cache is None else str(tune_cache).encode()
+        self._batch_psis = list(psis)
+        _check(lib().qtv_batch_plan(self.h, n, gs, ps, path, _stream_ptr(stream)))
+        return self.batch_info()
+
+    def batch_info(self):
+        info = BatchInfo()
+        _check(lib().qtv_batch_info_get(self.h, ctypes.byref(info)))
+        return info.as_dict()
+
+    def batch_run_into(self, face_ids, winding, offsets, xyz=None, resid=None, flags=None,
+                       mode=PLAIN, fallback_resid=1e-3, stream=None):
+        """Raw call: preallocated device outputs; offsets int64 [n + 1]."""
+        cap = 0 if face_ids is None else face_ids.numel()
+        _check(lib().qtv_batch_run(self.h, _ptr(face_ids), _ptr(winding), cap, _ptr(offsets),
+                                   _ptr(xyz), _ptr(resid), _ptr(flags), int(mode),
+                                   float(fallback_resid), _stream_ptr(stream)))
+
+    def batch_run(self, capacity=None, localize=True, mode=PLAIN, fallback_resid=1e-3,
+                  stream=None):
+        """Runs the planned batch; returns one dict per snapshot with ids, w and
+        (localize) xyz, resid, flags, views into shared output tensors."""
+        import torch
+
+        psis = self._batch_psis
+        dev = psis[0].device
+        if capacity is None:
+            capacity = int(self.batch_info()["faces"] * 1.02) + 1024
+        n = len(psis)
+        while True:
+            ids = torch.empty(capacity, dtype=torch.int64, device=dev)
+            w = torch.empty(capacity, dtype=torch.int8, device=dev)
+            off = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+            xyz = resid = fl = None
+            if localize:
+                xyz = torch.empty((capacity, 3), dtype=torch.float32, device=dev)
+                resid = torch.empty(capacity, dtype=torch.float32, device=dev)
+                fl = torch.empty(capacity, dtype=torch.uint8, device=dev)
+            self.batch_run_into(ids, w, off, xyz, resid, fl, mode, fallback_resid, stream)
+            o = off.cpu().numpy().view(np.uint64)
+            if o[n] == 0xFFFFFFFFFFFFFFFF:
+                raise QtvError(-4, "batch: a bounded device wait gave up")
+            if int(o[n]) <= capacity:
+                break
+            capacity = int(o[n]) + 1024
+        out = []
+        for i in range(n):
+            a, b = int(o[i]), int(o[i + 1])
+            d = {"ids": ids[a:b], "w": w[a:b]}
+            if localize:
+                d.update(xyz=xyz[a:b], resid=resid[a:b], flags=fl[a:b])
+            out.append(d)
+        return out
 
     # -- learned locator ------------------------------------------------------------
     def locator_init(self, seed: int = 0):

@@ -14,18 +14,7 @@ namespace {
 thread_local std::string g_err;
 
 // Makes the handle's device current for the scope of an API call.
-struct DeviceGuard {
-  int prev = -1;
-  bool ok = true;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
+
 
 bool capturing(cudaStream_t st) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -129,7 +118,7 @@ cudaEvent_t take_event(qtv_handle h) {
   return e;
 }
 const char* kKernelNames[K_COUNT] = {"sweep", "seg_scan", "scatter", "stats", "localize",
-                                     "emit_pack"};
+                                     "emit_pack", "batch"};
 }  // namespace
 
 TraceScope::TraceScope(qtv_handle h_, int k, cudaStream_t s) : h(h_), kernel(k), st(s) {
@@ -198,6 +187,7 @@ int qtv_destroy(qtv_handle h) {
   cudaFree(h->ws.table);
   cudaFree(h->ws.tiles);
   locator_free(h->loc);
+  batch_free(h->batch);
   for (auto& r : h->trace) {
     cudaEventDestroy(r.start);
     cudaEventDestroy(r.stop);
@@ -347,7 +337,8 @@ int qtv_localize(qtv_handle h, const qtv_grid* grid, const void* psi, const uint
   DeviceGuard dg(h->device);
   if (!dg.ok) return set_error(QTV_ERR_CUDA, "cudaSetDevice failed");
   if (mode == QTV_LEARNED)
-    return locator_localize(h, *grid, reinterpret_cast<const float2*>(psi), face_ids, winding, n,
+    return locator_localize(h, single_geo(*grid, reinterpret_cast<const float2*>(psi)), face_ids,
+                            winding, n,
                             n_dev, fallback_resid, xyz, resid, flags,
                             reinterpret_cast<cudaStream_t>(stream));
   return localize_launch(h, *grid, reinterpret_cast<const float2*>(psi), face_ids, winding, n, n_dev,

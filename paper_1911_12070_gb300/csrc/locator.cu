@@ -42,17 +42,24 @@ __device__ __forceinline__ float bf2f(uint16_t b) {
 // ---------------------------------------------------------------------------
 // encoding: one warp per face, two block nodes per lane
 // ---------------------------------------------------------------------------
-__global__ void encode_kernel(const float2* __restrict__ psi, int nx, int ny, int nz,
+// faces f in [f0, min(f0 + m, nn)) with nn = min(n, *n_dev); outputs at row f - f0
+__global__ void encode_kernel(const __grid_constant__ FaceGeo geo, unsigned long long f0,
+                              unsigned long long m, unsigned long long n,
+                              const uint64_t* __restrict__ n_dev,
                               const uint64_t* __restrict__ face_ids,
-                              const int8_t* __restrict__ winding, unsigned long long n,
-                              const uint64_t* __restrict__ n_dev, uint16_t* __restrict__ x,
-                              uint8_t* __restrict__ ok, float* __restrict__ rms) {
+                              const int8_t* __restrict__ winding, uint16_t* __restrict__ xo,
+                              uint8_t* __restrict__ oko, float* __restrict__ rmso) {
   unsigned long long nn = n;
   if (n_dev) nn = *n_dev < n ? *n_dev : n;
+  if (f0 + m < nn) nn = f0 + m;
   const int lane = threadIdx.x & 31;
   const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-  for (unsigned long long f = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (unsigned long long f = f0 + (((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
        f < nn; f += warps) {
+    const GridGeo& G = geo.g[geo_snapshot(geo, f)];
+    const float2* __restrict__ psi = G.psi;
+    const int nx = G.nx, ny = G.ny, nz = G.nz;
+    uint16_t* x = xo + (f - f0) * kIn;
     const uint64_t id = face_ids[f];
     const int o = (int)(id & 3u);
     const unsigned long long lin = id >> 2;
@@ -106,11 +113,11 @@ __global__ void encode_kernel(const float2* __restrict__ psi, int nx, int ny, in
     for (int h = 0; h < 2; ++h) {
       const int q = lane + 32 * h;
       const uint32_t pk = (uint32_t)f2bf(val[h].x * inv) | ((uint32_t)f2bf(val[h].y * inv) << 16);
-      reinterpret_cast<uint32_t*>(x + f * kIn)[q] = pk;
+      reinterpret_cast<uint32_t*>(x)[q] = pk;
     }
     if (lane == 0) {
-      ok[f] = good ? 1 : 0;
-      rms[f] = good ? r : 0.f;
+      oko[f - f0] = good ? 1 : 0;
+      rmso[f - f0] = good ? r : 0.f;
     }
   }
 }
@@ -417,22 +424,30 @@ __global__ void init_kernel(float* __restrict__ P, unsigned long long seed) {
 }
 
 // learned head: prediction -> position, residual test, plain fallback
-__global__ void head_kernel(const float2* __restrict__ psi, int nx, int ny, int nz, float h,
-                            float ox, float oy, float oz, const uint64_t* __restrict__ face_ids,
-                            const int8_t* __restrict__ winding, unsigned long long n,
-                            const uint64_t* __restrict__ n_dev, const float* __restrict__ y,
-                            const uint8_t* __restrict__ ok, const float* __restrict__ rms,
+// faces f in [f0, min(f0 + m, nn)); network rows at f - f0
+__global__ void head_kernel(const __grid_constant__ FaceGeo geo, unsigned long long f0,
+                            unsigned long long m, unsigned long long n,
+                            const uint64_t* __restrict__ n_dev,
+                            const uint64_t* __restrict__ face_ids,
+                            const int8_t* __restrict__ winding, const float* __restrict__ yo,
+                            const uint8_t* __restrict__ oko, const float* __restrict__ rmso,
                             float thresh, float* __restrict__ xyz, float* __restrict__ resid,
                             uint8_t* __restrict__ flags, unsigned long long* __restrict__ nfall) {
   unsigned long long nn = n;
   if (n_dev) nn = *n_dev < n ? *n_dev : n;
+  if (f0 + m < nn) nn = f0 + m;
   unsigned int fallbacks = 0;
-  for (unsigned long long f = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; f < nn;
-       f += (unsigned long long)gridDim.x * blockDim.x) {
+  for (unsigned long long f = f0 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+       f < nn; f += (unsigned long long)gridDim.x * blockDim.x) {
+    const GridGeo& G = geo.g[geo_snapshot(geo, f)];
+    const float2* __restrict__ psi = G.psi;
+    const int nx = G.nx, ny = G.ny, nz = G.nz;
+    const float h = G.h, ox = G.ox, oy = G.oy, oz = G.oz;
+    const unsigned long long row = f - f0;
     const uint64_t id = face_ids[f];
     const int wv = winding[f];
-    bool use = ok[f] != 0 && (wv == 1 || wv == -1);
-    const float u = y[3 * f], v = y[3 * f + 1];
+    bool use = oko[row] != 0 && (wv == 1 || wv == -1);
+    const float u = yo[3 * row], v = yo[3 * row + 1];
     float r2 = 0.f;
     if (use) use = u >= -0.01f && u <= 1.01f && v >= -0.01f && v <= 1.01f;
     const int o = (int)(id & 3u);
@@ -449,7 +464,7 @@ __global__ void head_kernel(const float2* __restrict__ psi, int nx, int ny, int 
       const float fr = w0 * p0.x + w1 * p1.x + w2 * p2.x + w3 * p3.x;
       const float fi = w0 * p0.y + w1 * p1.y + w2 * p2.y + w3 * p3.y;
       r2 = fr * fr + fi * fi;
-      const float nr = rms[f];
+      const float nr = rmso[row];
       use = r2 <= thresh * nr * nr;
     }
     if (use) {
@@ -498,8 +513,9 @@ struct Locator {
   uint16_t* w2b = nullptr; // BF16 W2 [256][256]
   unsigned long long step = 0;
   bool ready = false;
-  // activations for up to `cap` rows
+  // activations for up to `cap` rows; rows_gen counts their reallocations
   unsigned long long cap = 0;
+  unsigned long long rows_gen = 0;
   uint16_t *A1 = nullptr, *A2 = nullptr, *D1 = nullptr, *D2 = nullptr, *X = nullptr;
   float *Y = nullptr, *DY = nullptr, *rms = nullptr;
   uint8_t* ok = nullptr;
@@ -575,6 +591,7 @@ static int locator_rows(qtv_handle h, unsigned long long n, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMalloc(&L->ok, n);
   if (e != cudaSuccess) return check_cuda(e, "cudaMalloc(locator rows)");
   L->cap = n;
+  ++L->rows_gen;
   return QTV_OK;
 }
 
@@ -616,24 +633,37 @@ static int forward_backward(Locator* L, const uint16_t* X, const float* T, unsig
   return check_cuda(cudaGetLastError(), "locator backward");
 }
 
-int locator_localize(qtv_handle h, const qtv_grid& g, const float2* psi, const uint64_t* face_ids,
+constexpr unsigned long long kLocChunk = 1ull << 20;  // faces per learned chunk
+
+int locator_prepare(qtv_handle h, uint64_t n, uint64_t* generation) {
+  Locator* L = h->loc;
+  if (!L || !L->ready) return set_error(QTV_ERR_STATE, "no learned locator loaded");
+  const int rc = locator_rows(h, n < kLocChunk ? n : kLocChunk, nullptr);
+  if (generation) *generation = L->rows_gen;
+  return rc;
+}
+
+int locator_localize(qtv_handle h, const FaceGeo& geo, const uint64_t* face_ids,
                      const int8_t* winding, uint64_t n, const uint64_t* n_dev, float thresh,
                      float* xyz, float* resid, uint8_t* flags, cudaStream_t st) {
   Locator* L = h->loc;
   if (!L || !L->ready) return set_error(QTV_ERR_STATE, "no learned locator loaded");
-  int rc = locator_rows(h, n, st);
+  const unsigned long long chunk = n < kLocChunk ? n : kLocChunk;
+  int rc = locator_rows(h, chunk, st);
   if (rc) return rc;
   TraceScope ts(h, K_LOCALIZE, st);
-  encode_kernel<<<blocks_for(n * 32, 256, 65535), 256, 0, st>>>(psi, g.nx, g.ny, g.nz, face_ids,
-                                                                winding, n, n_dev, L->X, L->ok,
-                                                                L->rms);
-  rc = forward_hidden(L, L->X, n, st);
-  if (rc) return rc;
-  out_layer_kernel<<<blocks_for(n, 256, 4096), 256, 0, st>>>(L->A2, L->P, n, L->Y, nullptr, nullptr,
-                                                              nullptr);
-  head_kernel<<<blocks_for(n, 256, 65535), 256, 0, st>>>(
-      psi, g.nx, g.ny, g.nz, g.h, g.origin[0], g.origin[1], g.origin[2], face_ids, winding, n, n_dev,
-      L->Y, L->ok, L->rms, thresh, xyz, resid, flags, nullptr);
+  for (unsigned long long f0 = 0; f0 < n; f0 += chunk) {
+    const unsigned long long m = n - f0 < chunk ? n - f0 : chunk;
+    encode_kernel<<<blocks_for(m * 32, 256, 65535), 256, 0, st>>>(geo, f0, m, n, n_dev, face_ids,
+                                                                  winding, L->X, L->ok, L->rms);
+    rc = forward_hidden(L, L->X, m, st);
+    if (rc) return rc;
+    out_layer_kernel<<<blocks_for(m, 256, 4096), 256, 0, st>>>(L->A2, L->P, m, L->Y, nullptr,
+                                                                nullptr, nullptr);
+    head_kernel<<<blocks_for(m, 256, 65535), 256, 0, st>>>(geo, f0, m, n, n_dev, face_ids, winding,
+                                                           L->Y, L->ok, L->rms, thresh, xyz, resid,
+                                                           flags, nullptr);
+  }
   return check_cuda(cudaGetLastError(), "learned localize");
 }
 
@@ -700,8 +730,8 @@ int qtv_locator_encode(qtv_handle h, const qtv_grid* grid, const void* psi, cons
     return set_error(QTV_ERR_ARG, "a required pointer is NULL");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   encode_kernel<<<blocks_for(n * 32, 256, 65535), 256, 0, st>>>(
-      reinterpret_cast<const float2*>(psi), grid->nx, grid->ny, grid->nz, face_ids, winding, n,
-      n_dev, x, ok, rms);
+      single_geo(*grid, reinterpret_cast<const float2*>(psi)), 0ull, n, n, n_dev, face_ids,
+      winding, x, ok, rms);
   return check_cuda(cudaGetLastError(), "encode_kernel launch");
 }
 

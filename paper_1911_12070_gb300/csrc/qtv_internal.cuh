@@ -14,6 +14,20 @@ namespace qtv {
 int set_error(int code, const char* fmt, ...);
 int check_cuda(cudaError_t e, const char* what);
 
+// Makes a device current for a scope and restores the caller's device.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
 // Workspace owned by a handle.
 struct Workspace {
   uint32_t* staging = nullptr;        // staged face records of the sweep
@@ -60,7 +74,11 @@ struct IdentNeeds {
 namespace qtv {
 struct Locator;  // learned locator state (locator.cu)
 void locator_free(Locator* L);
-enum KernelId { K_SWEEP = 0, K_SEG_SCAN, K_SCATTER, K_STATS, K_LOCALIZE, K_EMIT_PACK, K_COUNT };
+enum KernelId {
+  K_SWEEP = 0, K_SEG_SCAN, K_SCATTER, K_STATS, K_LOCALIZE, K_EMIT_PACK, K_BATCH, K_COUNT
+};
+struct BatchPlan;  // batched snapshots (batch.cu)
+void batch_free(BatchPlan* b);
 struct TraceRec {
   int kernel;
   cudaEvent_t start, stop;
@@ -75,6 +93,7 @@ struct qtv_handle_s {
   std::vector<qtv::TraceRec> trace;      // recorded, not yet read
   std::vector<cudaEvent_t> event_pool;   // free events
   qtv::Locator* loc = nullptr;           // learned locator (weights, Adam state, buffers)
+  qtv::BatchPlan* batch = nullptr;       // batch plan, scratch and captured graph
 };
 
 namespace qtv {
@@ -124,6 +143,101 @@ int identify_launch(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t
 struct BulkNeeds {
   uint64_t recs = 0, table = 0, seg_off = 0, tiles = 0, segf = 0;
 };
+
+// One snapshot of a sweep.  Its work units are (plane, band, x tile) triples
+// in (z block, band, tile, plane) order; units, segments ((plane, band)
+// pairs) and table entries ((plane, band, tile, warp)) of all snapshots are
+// numbered consecutively.
+struct SnapDesc {
+  const float2* psi = nullptr;
+  int nx = 0, ny = 0, nz = 0;
+  int nbands = 0;   // ceil(ny / kRows)
+  int ntx = 1;      // x tiles per row
+  int st = 0;       // x stride of the tiles (even); tile t stages columns
+                    // [t st, t st + st + 2), the last one [t st, nx)
+  int hblock = 1;   // planes per z block
+  int pad_ = 0;
+  long long unit0 = 0, seg0 = 0, tab0 = 0;  // first unit / segment / table entry
+};
+constexpr int kMaxSnaps = QTV_BATCH_MAX;
+
+// Kernel parameters of the sweep and the expand pass (passed by value).
+struct BulkParams {
+  SnapDesc s[kMaxSnaps];
+  int nsnap = 0;
+  int nwt = 0;      // warps per tile (tile width 64 nwt columns)
+  long long units = 0, nseg = 0;
+  uint32_t* recs = nullptr;
+  unsigned long long recs_cap = 0;   // records
+  unsigned long long* counters = nullptr;  // [0] chunk top, [1] status bits, [2] scan ticket
+  uint4* table = nullptr;
+  unsigned int* segf = nullptr;      // pierced faces per segment (zeroed before)
+};
+
+// Tunable shape of a sweep: warps per tile (0: one tile as wide as the widest
+// row), resident CTAs per SM (0: as many as fit) and a factor on the z-block
+// height.
+struct TileConfig {
+  int nwt = 0;
+  int ctas_per_sm = 0;
+  float zscale = 1.f;
+};
+
+struct BulkLayout {
+  BulkParams p;
+  int grid = 0, threads = 0, expand_blocks = 1;
+  size_t smem = 0;
+  long long ntiles = 0;  // scan tiles
+  unsigned long long recs_need = 0, table_need = 0;
+};
+
+// Geometry of the faces of one call: one grid, or the concatenated face lists
+// of several snapshots (snapshot s owns faces [offsets[s], offsets[s + 1]);
+// offsets is device memory and is read only when n > 1).
+struct GridGeo {
+  const float2* psi = nullptr;
+  int nx = 0, ny = 0, nz = 0;
+  float h = 1.f, ox = 0.f, oy = 0.f, oz = 0.f;
+};
+struct FaceGeo {
+  GridGeo g[kMaxSnaps];
+  int n = 0;
+  const uint64_t* offsets = nullptr;
+};
+inline FaceGeo single_geo(const qtv_grid& g, const float2* psi) {
+  FaceGeo f;
+  f.n = 1;
+  f.g[0].psi = psi;
+  f.g[0].nx = g.nx;
+  f.g[0].ny = g.ny;
+  f.g[0].nz = g.nz;
+  f.g[0].h = g.h;
+  f.g[0].ox = g.origin[0];
+  f.g[0].oy = g.origin[1];
+  f.g[0].oz = g.origin[2];
+  return f;
+}
+#ifdef __CUDACC__
+// snapshot of face f: the largest s with offsets[s] <= f
+__device__ __forceinline__ int geo_snapshot(const FaceGeo& G, unsigned long long f) {
+  if (G.n <= 1) return 0;
+  int lo = 0, hi = G.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(G.offsets + mid) <= f) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+#endif
+
+int bulk_variant_occupancy(int nw, int* ctas_per_sm, size_t* smem);
+int bulk_layout(int num_sms, int nsnap, const qtv_grid* grids, const float2* const* psis,
+                const TileConfig& tc, uint64_t capacity, uint64_t max_warps, BulkLayout* L);
+int bulk_launch(qtv_handle h, BulkLayout& L, const IdentScratch& sc, uint64_t* face_ids,
+                int8_t* winding, uint64_t capacity, uint64_t* count, uint64_t* offsets,
+                qtv_stats* stats, unsigned long long scanned, cudaStream_t st, bool expand_always);
+int bulk_sweep_only(BulkLayout& L, const IdentScratch& sc, cudaStream_t st);
 bool sweep_bulk_supported(int nx, int ny, int nz, const void* psi);
 int bulk_needs(int num_sms, const qtv_grid& g, uint64_t capacity, uint64_t max_warps,
                BulkNeeds* n);
@@ -137,10 +251,16 @@ int localize_launch(qtv_handle h, const qtv_grid& g, const float2* psi, const ui
                     const int8_t* winding, uint64_t n, const uint64_t* n_dev, float* xyz,
                     float* resid, uint8_t* flags, cudaStream_t st);
 
-// Learned localization with plain fallback (locator.cu)
-int locator_localize(qtv_handle h, const qtv_grid& g, const float2* psi, const uint64_t* face_ids,
+// Learned localization with plain fallback (locator.cu); n faces (at most
+// *n_dev when n_dev is given) processed in chunks of locator rows
+int locator_localize(qtv_handle h, const FaceGeo& geo, const uint64_t* face_ids,
                      const int8_t* winding, uint64_t n, const uint64_t* n_dev, float thresh,
                      float* xyz, float* resid, uint8_t* flags, cudaStream_t st);
+// Allocates the locator's row buffers for the chunk that n faces use (outside
+// stream capture) and reports how often they have been reallocated (a graph
+// that captured them is stale once this changes); QTV_ERR_STATE when no
+// locator is loaded.
+int locator_prepare(qtv_handle h, uint64_t n, uint64_t* generation);
 
 // Emission pack (localize.cu)
 int emit_pack_launch(qtv_handle h, uint64_t n, const uint64_t* face_ids, const int8_t* winding, const float* xyz,

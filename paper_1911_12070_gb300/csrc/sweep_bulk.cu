@@ -49,6 +49,8 @@
 // of planes, and CTAs that hold neighbouring bands march the same z block at
 // the same time (the halo row of a band is the first row of the next one and
 // is then served by L2).
+#include <algorithm>
+
 #include "qtv_internal.cuh"
 
 namespace qtv {
@@ -259,21 +261,12 @@ __device__ __forceinline__ bool plane_special(const float4* v, const float2* nbv
   return !(prod > 0.f && prod <= 3.402823466e38f);
 }
 
-struct V3Args {
-  const float2* psi;
-  int nx, ny, nz, nbands, hblock;
-  uint32_t* recs;                // kRecWords words per record
-  unsigned long long recs_cap;   // records
-  unsigned long long* counters;  // [0] chunk top, [1] status bits, [2] scan ticket
-  uint4* table;                  // [(k * nbands + band) * NW + w]
-  unsigned int* segf;            // [k * nbands + band]: pierced faces (zeroed before)
-};
-
-// unit u of the (z block, band, plane) order -> band, plane, end of its z block
-__device__ __forceinline__ void unit_pos(long long u, int nbands, int nz, int H, int& band, int& k,
-                                         int& kend) {
+// unit u of one snapshot's (z block, band, tile, plane) order -> column
+// (band * ntx + tile), plane, end of its z block
+__device__ __forceinline__ void unit_pos(long long u, long long cols, int nz, int H, long long& col,
+                                         int& k, int& kend) {
   const long long full = nz / H;
-  const long long per_full = (long long)nbands * H;
+  const long long per_full = cols * H;
   long long zb, rem;
   int h;
   if (u < full * per_full) {
@@ -285,38 +278,26 @@ __device__ __forceinline__ void unit_pos(long long u, int nbands, int nz, int H,
     rem = u - full * per_full;
     h = nz - (int)full * H;
   }
-  band = (int)(rem / h);
+  col = rem / h;
   k = (int)zb * H + (int)(rem % h);
   kend = (int)zb * H + h;
 }
 
 template <int MAXT, int MINB>
-__global__ void __launch_bounds__(MAXT, MINB) sweep_bulk_kernel(V3Args a) {
+__global__ void __launch_bounds__(MAXT, MINB) sweep_bulk_kernel(const __grid_constant__ BulkParams a) {
   extern __shared__ __align__(128) unsigned char dsm[];
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int w = tid >> 5;
   const int NW = blockDim.x >> 5;
-  const int W = NW * 64;  // row pitch of a ring slot, in elements
+  const int W = NW * 64;  // row pitch of a ring slot (the tile width), in elements
   float2* ring = reinterpret_cast<float2*>(dsm);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(dsm + (size_t)kStages * RH * W * sizeof(float2));
   SmallSmem& sm = *reinterpret_cast<SmallSmem*>(mbar + kStages);
-  const int nx = a.nx, ny = a.ny, nz = a.nz;
-  const int x0 = 64 * w + 2 * lane;
-  const bool c0 = x0 < nx, c1 = x0 + 1 < nx, c2 = x0 + 2 < nx;
+  const int x0 = 64 * w + 2 * lane;  // tile-local column of this lane's pair
   const bool nbin = x0 + 2 < W;
-  const size_t plane = (size_t)nx * ny;
-  const uint32_t row_bytes = (uint32_t)nx * 8u;
   const uint32_t lt = (1u << lane) - 1u;
 
-  // columns [nx, W) of every slot row are never copied: fill them with 1 (a
-  // finite, nonzero value, so that padding never selects the masking path;
-  // faces that touch padding do not exist and are masked anyway)
-  {
-    const int pad = W - nx;
-    for (int idx = tid; idx < kStages * RH * pad; idx += blockDim.x)
-      ring[(size_t)(idx / pad) * W + nx + idx % pad] = make_float2(1.f, 0.f);
-  }
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&mbar[s], (uint32_t)NW);
     fence_mbar_init();
@@ -329,14 +310,24 @@ __global__ void __launch_bounds__(MAXT, MINB) sweep_bulk_kernel(V3Args a) {
   uint32_t cb = 0, cl = 0, nb_l0 = 0;
   bool have_next = false;
   bool overflow = false;
+  // columns [valid_w, W) of every row and rows [valid_r, RH) of every column
+  // of every ring slot hold the padding value 1 (finite and nonzero, so that
+  // padding never selects the masking path; faces that touch it are masked)
+  int valid_w = W, valid_r = RH;
 
-  const long long U = (long long)a.nbands * nz;
+  const long long U = a.units;
   long long u = U * blockIdx.x / gridDim.x;
   const long long uend = U * (blockIdx.x + 1) / gridDim.x;
 
   while (u < uend) {
-    int band, kb, kblk;
-    unit_pos(u, a.nbands, nz, a.hblock, band, kb, kblk);
+    int si = 0;
+    while (si + 1 < a.nsnap && a.s[si + 1].unit0 <= u) ++si;
+    const SnapDesc& sd = a.s[si];
+    const int nx = sd.nx, ny = sd.ny, nz = sd.nz, ntx = sd.ntx;
+    long long col;
+    int kb, kblk;
+    unit_pos(u - sd.unit0, (long long)sd.nbands * ntx, nz, sd.hblock, col, kb, kblk);
+    const int band = (int)(col / ntx), tile = (int)(col % ntx);
     const int ke = (int)min((long long)kblk, (long long)kb + (uend - u));
     u += ke - kb;
     const int j0 = band * R;
@@ -344,23 +335,42 @@ __global__ void __launch_bounds__(MAXT, MINB) sweep_bulk_kernel(V3Args a) {
     const int klast = min(ke, nz - 1);
     const int nplanes = klast - kb + 1;
     const int nsteps = ke - kb;
+    // tile: staged columns [xt0, xt0 + tw); this CTA owns the faces of the
+    // lanes with x0 < own_end (the last pair of a non-final tile only feeds
+    // its left neighbour and is owned by the next tile)
+    const int xt0 = tile * sd.st;
+    const bool last_tile = tile == ntx - 1;
+    const int tw = last_tile ? nx - xt0 : sd.st + 2;
+    const int own_end = last_tile ? tw : sd.st;
+    const uint32_t row_bytes = (uint32_t)tw * 8u;
+    const size_t plane = (size_t)nx * ny;
 
-    if (nrows < RH) {  // rows beyond the grid are never copied: fill with 1
-      const int per = (RH - nrows) * W;
-      for (int idx = tid; idx < kStages * per; idx += blockDim.x) {
-        const int s = idx / per, rem = idx % per;
-        ring[((size_t)s * RH + nrows + rem / W) * W + rem % W] = make_float2(1.f, 0.f);
+    if (tw < valid_w || nrows < valid_r) {
+      const int cw = valid_w - tw;
+      if (cw > 0)
+        for (int idx = tid; idx < kStages * RH * cw; idx += blockDim.x)
+          ring[(size_t)(idx / cw) * W + tw + idx % cw] = make_float2(1.f, 0.f);
+      const int rr = valid_r - nrows;
+      if (rr > 0) {
+        const int per = rr * W;
+        for (int idx = tid; idx < kStages * per; idx += blockDim.x) {
+          const int sl = idx / per, rem = idx % per;
+          ring[((size_t)sl * RH + nrows + rem / W) * W + rem % W] = make_float2(1.f, 0.f);
+        }
       }
+      fence_proxy_async();  // later bulk copies may land in rows written here
       __syncthreads();
     }
+    valid_w = tw;
+    valid_r = nrows;
 
     // every warp arrives once per fill, lane 0 copying the rows r == w (mod NW)
     auto issue = [&](int m) {
       if (lane == 0) {
-        const int s = fill % kStages;
-        uint64_t* bar = &mbar[s];
-        float2* dst = ring + (size_t)s * RH * W;
-        const float2* src = a.psi + (size_t)m * plane + (size_t)j0 * nx;
+        const int sl = fill % kStages;
+        uint64_t* bar = &mbar[sl];
+        float2* dst = ring + (size_t)sl * RH * W;
+        const float2* src = sd.psi + (size_t)m * plane + (size_t)j0 * nx + xt0;
         uint32_t mine = 0;
         for (int r = w; r < nrows; r += NW) ++mine;
         fence_proxy_async();
@@ -371,10 +381,10 @@ __global__ void __launch_bounds__(MAXT, MINB) sweep_bulk_kernel(V3Args a) {
       ++fill;
     };
     auto acquire = [&]() -> const float2* {
-      const int s = use % kStages;
-      if (!mbar_wait(&mbar[s], (use / kStages) & 1u)) timeout = true;
+      const int sl = use % kStages;
+      if (!mbar_wait(&mbar[sl], (use / kStages) & 1u)) timeout = true;
       ++use;
-      return ring + (size_t)s * RH * W;
+      return ring + (size_t)sl * RH * W;
     };
 
     // row validity and slot existence (bit 0 of each field)
@@ -384,9 +394,16 @@ __global__ void __launch_bounds__(MAXT, MINB) sweep_bulk_kernel(V3Args a) {
       if (j0 + r < ny) rowv |= 1u << (4 * r);
       if (j0 + r + 1 < ny) rowv1 |= 1u << (4 * r);
     }
+    const bool own = x0 < own_end;
+    const bool c0 = own && x0 < tw, c1 = own && x0 + 1 < tw, c2 = own && x0 + 2 < tw;
     const uint32_t ex_xy0 = c1 ? rowv1 : 0u, ex_xy1 = c2 ? rowv1 : 0u;
     const uint32_t ex_yz0 = c0 ? rowv1 : 0u, ex_yz1 = c1 ? rowv1 : 0u;
     const uint32_t ex_zx0 = c1 ? rowv : 0u, ex_zx1 = c2 ? rowv : 0u;
+    // table entry of (plane k, band, tile, warp w) = tbase + k * tstride
+    const unsigned long long tstride = (unsigned long long)sd.nbands * ntx * NW;
+    const unsigned long long tbase =
+        (unsigned long long)sd.tab0 + ((unsigned long long)band * ntx + tile) * NW + w;
+    unsigned int* const segf = a.segf + sd.seg0 + band;
 
     // ---- prologue: plane kb
     for (int i = 0; i < min(kStages, nplanes); ++i) issue(kb + i);
@@ -499,14 +516,14 @@ __global__ void __launch_bounds__(MAXT, MINB) sweep_bulk_kernel(V3Args a) {
         const uint32_t bzx1 = Bk1 | BkN | Bn1 | BnN;
         const uint32_t bb[6] = {bxy0, byz0, bzx0, bxy1, byz1, bzx1};
 #pragma unroll
-        for (int s = 0; s < 6; ++s) keep[s] &= ~((bb[s] & kOnes) * 0xFu);
+        for (int q = 0; q < 6; ++q) keep[q] &= ~((bb[q] & kOnes) * 0xFu);
       }
       uint32_t cnt = 0, anyw = 0;
 #pragma unroll
-      for (int s = 0; s < 6; ++s) {
-        d[s] = (d[s] ^ kFours) & keep[s];
-        cnt += nz_fields(d[s]);
-        anyw |= d[s];
+      for (int q = 0; q < 6; ++q) {
+        d[q] = (d[q] ^ kFours) & keep[q];
+        cnt += nz_fields(d[q]);
+        anyw |= d[q];
       }
       // ---- per-warp compaction: one record per lane with faces
       const uint32_t bsum = (cnt & 0x0F0F0F0Fu) + ((cnt >> 4) & 0x0F0F0F0Fu);
@@ -548,9 +565,9 @@ __global__ void __launch_bounds__(MAXT, MINB) sweep_bulk_kernel(V3Args a) {
         have_next = true;
       }
       if (lane == 0) {
-        a.table[((size_t)k * a.nbands + band) * NW + w] =
+        a.table[tbase + (unsigned long long)k * tstride] =
             make_uint4(base1, base2, T | (n1 << 6) | (faces_w << 12), 0u);
-        if (faces_w) atomicAdd(&a.segf[(size_t)k * a.nbands + band], faces_w);
+        if (faces_w) atomicAdd(&segf[(size_t)k * sd.nbands], faces_w);
       }
       if (anyw) {
         const uint32_t q = __popc(bal & lt);
@@ -590,8 +607,9 @@ __global__ void __launch_bounds__(MAXT, MINB) sweep_bulk_kernel(V3Args a) {
 }
 
 // ---------------------------------------------------------------------------
-// Finalize 1: exclusive scan of the per-segment face totals in (plane, band)
-// order, single pass with decoupled look-back over tiles taken by ticket.
+// Finalize 1: exclusive scan of the per-segment face totals in (snapshot,
+// plane, band) order, single pass with decoupled look-back over tiles taken by
+// ticket.
 // ---------------------------------------------------------------------------
 constexpr int kScanThreads = 512;
 constexpr int kScanItems = 8;
@@ -693,9 +711,10 @@ __global__ void __launch_bounds__(kScanThreads) v3_scan_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// Finalize 2: one warp per (plane, band) segment expands its records into face
-// ids and windings at their final offsets: row by row, and within a row in
-// flattened record order (warp, lane), which is ascending x.
+// Finalize 2: one warp per (snapshot, plane, band) segment expands its
+// records into face ids and windings at their final offsets: row by row, and
+// within a row in flattened record order (tile, warp, lane), which is
+// ascending x.
 // ---------------------------------------------------------------------------
 constexpr int kExpandWarps = 8;
 
@@ -708,26 +727,48 @@ __device__ __forceinline__ uint32_t rec_row_counts(const uint32_t* dw) {
 }
 
 __global__ void __launch_bounds__(32 * kExpandWarps, 4) v3_expand_kernel(
-    const uint4* __restrict__ table, int NW, long long nseg, int nbands, int nx, int ny,
-    const uint32_t* __restrict__ recs, unsigned long long recs_cap,
-    const unsigned long long* __restrict__ seg_off, uint64_t* __restrict__ face_ids,
-    int8_t* __restrict__ winding, unsigned long long capacity) {
+    const __grid_constant__ BulkParams a, const unsigned long long* __restrict__ seg_off,
+    uint64_t* __restrict__ face_ids, int8_t* __restrict__ winding, unsigned long long capacity,
+    uint64_t* __restrict__ offsets) {
   __shared__ uint32_t s_rowbase[kExpandWarps][R];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const uint4* __restrict__ table = a.table;
+  const uint32_t* __restrict__ recs = a.recs;
+  const unsigned long long recs_cap = a.recs_cap;
+  const long long nseg = a.nseg;
+  if (offsets && blockIdx.x == 0 && threadIdx.x < (unsigned)a.nsnap)
+    offsets[threadIdx.x] = a.s[threadIdx.x].seg0 < nseg ? seg_off[a.s[threadIdx.x].seg0] : 0ull;
+  if (capacity == 0) return;
   const long long nwarps = (long long)gridDim.x * kExpandWarps;
   long long s = (long long)blockIdx.x * kExpandWarps + wib;
+  // snapshot of segment s and its per-segment table geometry
+  auto locate = [&](long long sg, int& si, long long& local, int& NWs) {
+    si = 0;
+    while (si + 1 < a.nsnap && a.s[si + 1].seg0 <= sg) ++si;
+    local = sg - a.s[si].seg0;
+    NWs = a.s[si].ntx * a.nwt;
+  };
   // the next segment's table entries and offset are loaded one segment ahead
   uint4 e_next = make_uint4(0u, 0u, 0u, 0u);
   unsigned long long fb_next = 0;
   if (s < nseg) {
-    if (lane < NW) e_next = table[s * NW + lane];
+    int si, NWs;
+    long long local;
+    locate(s, si, local, NWs);
+    if (lane < NWs) e_next = table[a.s[si].tab0 + local * NWs + lane];
     fb_next = seg_off[s];
   }
   for (; s < nseg; s += nwarps) {
     const uint4 e = e_next;
     const unsigned long long fbase = fb_next;
+    int si, NW;
+    long long local;
+    locate(s, si, local, NW);
     if (s + nwarps < nseg) {
-      if (lane < NW) e_next = table[(s + nwarps) * NW + lane];
+      int si2, NW2;
+      long long local2;
+      locate(s + nwarps, si2, local2, NW2);
+      if (lane < NW2) e_next = table[a.s[si2].tab0 + local2 * NW2 + lane];
       fb_next = seg_off[s + nwarps];
     }
     const uint32_t n = e.z & 63u, n1 = (e.z >> 6) & 63u;
@@ -740,8 +781,12 @@ __global__ void __launch_bounds__(32 * kExpandWarps, 4) v3_expand_kernel(
     const uint32_t start = lane < NW ? incl - n : 0xFFFFFFFFu;
     const uint32_t rtot = __shfl_sync(0xffffffffu, incl, 31);
     if (rtot == 0) continue;
-    const long long k = s / nbands;
-    const long long j0 = (long long)(s % nbands) * R;
+    const SnapDesc& sd = a.s[si];
+    const int nbands = sd.nbands;
+    const unsigned long long nx = (unsigned)sd.nx, ny = (unsigned)sd.ny;
+    const long long k = local / nbands;
+    const long long j0 = (local % nbands) * R;
+    const int nwt = a.nwt;  // warps per tile
     const uint32_t nchunks = (rtot + 31) / 32;
 
     // record of flattened index g = g0 + lane (zeros past the end)
@@ -749,7 +794,7 @@ __global__ void __launch_bounds__(32 * kExpandWarps, 4) v3_expand_kernel(
       const uint32_t g = g0 + lane;
       int lo = 0;
 #pragma unroll
-      for (int stp = 8; stp >= 1; stp >>= 1) {
+      for (int stp = 16; stp >= 1; stp >>= 1) {
         const int cand = lo + stp;
         const uint32_t sv = __shfl_sync(0xffffffffu, start, cand & 31);
         if (cand < NW && sv <= g) lo = cand;
@@ -841,6 +886,11 @@ __global__ void __launch_bounds__(32 * kExpandWarps, 4) v3_expand_kernel(
         const uint32_t rl = (dw[0] >> 28) | ((dw[1] >> 28) << 4);
 #pragma unroll
         for (int r = 0; r < R; ++r) s_rowbase[wib][r] = rowbase[r];
+        // first column of warp ww: tile ww / nwt at x = tile * st, warp
+        // ww % nwt of the tile at 64 columns each
+        const unsigned tw_i = (unsigned)ww / (unsigned)nwt;
+        const unsigned long long xw =
+            (unsigned long long)tw_i * (unsigned)sd.st + 64u * ((unsigned)ww - tw_i * (unsigned)nwt);
         uint32_t rm = nz_fields((dw[0] | dw[1]) & 0x0FFFFFFFu | dw[2] | dw[3] | dw[4] | dw[5]);
         while (rm) {
           const int f = __ffs(rm) - 1;
@@ -851,8 +901,7 @@ __global__ void __launch_bounds__(32 * kExpandWarps, 4) v3_expand_kernel(
           for (int sl = 0; sl < 6; ++sl) rn |= ((dw[sl] >> f) & 0xFu) << (4 * sl);
           unsigned long long pos = fbase + s_rowbase[wib][r] + field8(exe, exo, r);
           const unsigned long long lin0 =
-              ((unsigned long long)k * ny + (unsigned long long)(j0 + r)) * (unsigned long long)nx +
-              64u * (unsigned)ww + 2u * rl;
+              ((unsigned long long)k * ny + (unsigned long long)(j0 + r)) * nx + xw + 2u * rl;
           uint32_t nzm = nz_fields(rn);
           while (nzm) {
             const int g = __ffs(nzm) - 1;
@@ -873,83 +922,215 @@ __global__ void __launch_bounds__(32 * kExpandWarps, 4) v3_expand_kernel(
   }
 }
 
-using BulkFn = void (*)(V3Args);
+using BulkFn = void (*)(BulkParams);
 
 BulkFn bulk_fn(int nw) {
+  if (nw <= 2) return sweep_bulk_kernel<64, 8>;
   if (nw <= 4) return sweep_bulk_kernel<128, 4>;
   if (nw <= 8) return sweep_bulk_kernel<256, 2>;
   return sweep_bulk_kernel<512, 1>;
 }
 
-struct BulkPlan {
-  int grid = 0, nw = 0, hblock = 1;
-  size_t smem = 0;
-  long long nseg = 0, ntiles = 0;
-  unsigned long long recs_need = 0, table_need = 0;
-};
+int bulk_fn_index(int nw) { return nw <= 2 ? 0 : (nw <= 4 ? 1 : (nw <= 8 ? 2 : 3)); }
 
-size_t bulk_smem_bytes(int nx) {
-  const int nw = (nx + 63) / 64;
+size_t bulk_smem_for_warps(int nw) {
   return (size_t)kStages * RH * nw * 64 * sizeof(float2) + kStages * sizeof(uint64_t) +
          sizeof(SmallSmem);
 }
 
-int bulk_plan(int num_sms, const qtv_grid& g, uint64_t capacity, uint64_t max_warps,
-              BulkPlan* p) {
-  const int nw = (g.nx + 63) / 64;
-  const int nbands = (g.ny + R - 1) / R;
+}  // namespace
+
+// Sets the shared-memory opt-in of a sweep variant once; returns its maximum
+// resident CTAs per SM.
+int bulk_variant_occupancy(int nw, int* ctas_per_sm, size_t* smem) {
+  static bool attr_set[4] = {false, false, false, false};
+  const int which = bulk_fn_index(nw);
   BulkFn fn = bulk_fn(nw);
-  static bool attr_set[3] = {false, false, false};
-  const int which = nw <= 4 ? 0 : (nw <= 8 ? 1 : 2);
   if (!attr_set[which]) {
     cudaError_t e =
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return check_cuda(e, "cudaFuncSetAttribute(sweep_bulk)");
     attr_set[which] = true;
   }
-  p->smem = bulk_smem_bytes(g.nx);
+  *smem = bulk_smem_for_warps(nw);
   int bps = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, nw * 32, p->smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, nw * 32, *smem);
   if (e != cudaSuccess) return check_cuda(e, "occupancy(sweep_bulk)");
-  if (bps < 1) return set_error(QTV_ERR_ARG, "sweep_bulk: no resident CTA for nx = %d", g.nx);
-  const long long units = (long long)nbands * g.nz;
-  long long grid = (long long)bps * num_sms;
-  if (max_warps > 0 && grid * nw > (long long)max_warps) grid = (long long)max_warps / nw;
-  if (grid > units) grid = units;
-  if (grid < 1) grid = 1;
-  long long zblocks = (grid + nbands / 2) / nbands;
-  if (zblocks < 1) zblocks = 1;
-  if (zblocks > g.nz) zblocks = g.nz;
-  p->grid = (int)grid;
-  p->nw = nw;
-  p->hblock = (int)((g.nz + zblocks - 1) / zblocks);
-  p->nseg = (long long)g.nz * nbands;
-  p->ntiles = (p->nseg + kScanTile - 1) / kScanTile;
-  // records (kRecWords words each): at most one per pierced face, plus two
-  // partly used chunks per warp
-  p->recs_need = capacity + 2ull * kChunk * (unsigned long long)grid * nw + kChunk;
-  p->table_need = (unsigned long long)p->nseg * nw;
+  if (bps < 1) return set_error(QTV_ERR_ARG, "sweep_bulk: no resident CTA with %d warps", nw);
+  *ctas_per_sm = bps;
   return QTV_OK;
 }
-
-}  // namespace
 
 bool sweep_bulk_supported(int nx, int ny, int nz, const void* psi) {
   if (nx < 2 || ny < 1 || nz < 1 || (nx & 1) || nx > 1024) return false;
   if (reinterpret_cast<uintptr_t>(psi) & 15u) return false;
-  return bulk_smem_bytes(nx) <= 227u * 1024u;
+  return bulk_smem_for_warps((nx + 63) / 64) <= 227u * 1024u;
+}
+
+int bulk_layout(int num_sms, int nsnap, const qtv_grid* grids, const float2* const* psis,
+                const TileConfig& tc, uint64_t capacity, uint64_t max_warps, BulkLayout* L) {
+  if (nsnap < 1 || nsnap > kMaxSnaps)
+    return set_error(QTV_ERR_ARG, "%d snapshots (1 to %d supported)", nsnap, kMaxSnaps);
+  int nwt = tc.nwt;
+  if (nwt <= 0) {  // one tile per row, as wide as the widest snapshot needs
+    nwt = 1;
+    for (int i = 0; i < nsnap; ++i) nwt = std::max(nwt, (grids[i].nx + 63) / 64);
+  }
+  if (nwt < 1 || nwt > 16)
+    return set_error(QTV_ERR_ARG, "tile of %d warps (1 to 16 supported)", nwt);
+  const int TX = 64 * nwt;
+  BulkParams& p = L->p;
+  p = BulkParams();
+  p.nsnap = nsnap;
+  p.nwt = nwt;
+  long long units = 0, nseg = 0, tab = 0;
+  for (int i = 0; i < nsnap; ++i) {
+    const qtv_grid& g = grids[i];
+    if (!sweep_bulk_supported(g.nx, g.ny, g.nz, psis[i]))
+      return set_error(QTV_ERR_ARG, "snapshot %d (%d x %d x %d): the staged sweep needs even nx "
+                       "<= 1024 and a 16-byte aligned field", i, g.nx, g.ny, g.nz);
+    SnapDesc& d = p.s[i];
+    d.psi = psis[i];
+    d.nx = g.nx;
+    d.ny = g.ny;
+    d.nz = g.nz;
+    d.nbands = (g.ny + R - 1) / R;
+    if (g.nx <= TX) {
+      d.ntx = 1;
+      d.st = 0;
+    } else {
+      // tiles stage st + 2 <= TX columns at stride st (even), the last one the rest
+      d.ntx = (g.nx - 2 + (TX - 2) - 1) / (TX - 2);
+      const int per = (g.nx - 2 + d.ntx - 1) / d.ntx;
+      d.st = (per + 1) & ~1;
+      if (d.st + 2 > TX || g.nx - (d.ntx - 1) * d.st > TX || g.nx - (d.ntx - 1) * d.st < 2)
+        return set_error(QTV_ERR_ARG, "no tiling of nx = %d into %d-column tiles", g.nx, TX);
+    }
+    if (d.ntx * nwt > 32)
+      return set_error(QTV_ERR_ARG, "snapshot %d: %d tiles of %d warps exceed 32 warps per row",
+                       i, d.ntx, nwt);
+    d.unit0 = units;
+    d.seg0 = nseg;
+    d.tab0 = tab;
+    const long long cols = (long long)d.nbands * d.ntx;
+    units += cols * g.nz;
+    nseg += (long long)d.nbands * g.nz;
+    tab += (long long)d.nbands * g.nz * d.ntx * nwt;
+  }
+  p.units = units;
+  p.nseg = nseg;
+  int bps = 0;
+  size_t smem = 0;
+  int rc = bulk_variant_occupancy(nwt, &bps, &smem);
+  if (rc) return rc;
+  if (tc.ctas_per_sm > 0 && tc.ctas_per_sm < bps) bps = tc.ctas_per_sm;
+  long long grid = (long long)bps * num_sms;
+  if (max_warps > 0 && grid * nwt > (long long)max_warps) grid = (long long)max_warps / nwt;
+  if (grid > units) grid = units;
+  if (grid < 1) grid = 1;
+  // z blocks: the CTAs that a snapshot gets (in proportion to its units) are
+  // spread over its (band, tile) columns
+  for (int i = 0; i < nsnap; ++i) {
+    SnapDesc& d = p.s[i];
+    const long long cols = (long long)d.nbands * d.ntx;
+    const double share = (double)grid * (double)(cols * d.nz) / (double)units;
+    long long zblocks = (long long)(share / (double)cols + 0.5);
+    if (zblocks < 1) zblocks = 1;
+    if (zblocks > d.nz) zblocks = d.nz;
+    long long H = (d.nz + zblocks - 1) / zblocks;
+    H = (long long)((double)H * (tc.zscale > 0.f ? tc.zscale : 1.f) + 0.5);
+    if (H < 1) H = 1;
+    if (H > d.nz) H = d.nz;
+    d.hblock = (int)H;
+  }
+  L->grid = (int)grid;
+  L->threads = nwt * 32;
+  L->smem = smem;
+  L->ntiles = (nseg + kScanTile - 1) / kScanTile;
+  // records (kRecWords words each): at most one per pierced face, plus two
+  // partly used chunks per warp
+  L->recs_need = capacity + 2ull * kChunk * (unsigned long long)grid * nwt + kChunk;
+  L->table_need = (unsigned long long)tab;
+  L->expand_blocks = (int)std::min<long long>((nseg + kExpandWarps - 1) / kExpandWarps,
+                                              (long long)num_sms * 4);
+  return QTV_OK;
+}
+
+// The launches of one layout: scratch zeroing, sweep, scan, expand.  count
+// receives the total; offsets (optional) receives the first face of each
+// snapshot (nsnap entries).
+int bulk_launch(qtv_handle h, BulkLayout& L, const IdentScratch& sc, uint64_t* face_ids,
+                int8_t* winding, uint64_t capacity, uint64_t* count, uint64_t* offsets,
+                qtv_stats* stats, unsigned long long scanned, cudaStream_t st, bool expand_always) {
+  BulkParams& p = L.p;
+  if (sc.staging_cap < L.recs_need * kRecWords || sc.table_cap < L.table_need ||
+      sc.seg_cap * 2 < (uint64_t)p.nseg || sc.seg_off_cap < (uint64_t)p.nseg ||
+      sc.tiles_cap < (uint64_t)L.ntiles)
+    return set_error(QTV_ERR_CAPACITY, "identification scratch too small for this grid");
+  cudaError_t e = cudaMemsetAsync(sc.counters, 0, 4 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sc.tiles, 0, L.ntiles * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sc.seg, 0, p.nseg * sizeof(unsigned int), st);
+  if (e == cudaSuccess && stats) e = cudaMemsetAsync(stats, 0, sizeof(qtv_stats), st);
+  if (e != cudaSuccess) return check_cuda(e, "cudaMemsetAsync(identify scratch)");
+  p.recs = sc.staging;
+  p.recs_cap = L.recs_need;
+  p.counters = sc.counters;
+  p.table = sc.table;
+  p.segf = reinterpret_cast<unsigned int*>(sc.seg);
+  {
+    TraceScope ts(h, K_SWEEP, st);
+    bulk_fn(p.nwt)<<<L.grid, L.threads, L.smem, st>>>(p);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return check_cuda(e, "sweep_bulk_kernel launch");
+  {
+    TraceScope ts(h, K_SEG_SCAN, st);
+    v3_scan_kernel<<<(unsigned)L.ntiles, kScanThreads, 0, st>>>(
+        reinterpret_cast<const unsigned int*>(sc.seg), p.nseg, sc.seg_off, count, sc.counters,
+        sc.tiles, L.ntiles, stats, scanned);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return check_cuda(e, "v3_scan_kernel launch");
+  if (capacity > 0 || expand_always) {
+    TraceScope ts(h, K_SCATTER, st);
+    v3_expand_kernel<<<(unsigned)L.expand_blocks, 32 * kExpandWarps, 0, st>>>(
+        p, sc.seg_off, face_ids, winding, capacity, offsets);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return check_cuda(e, "v3_expand_kernel launch");
+  }
+  return QTV_OK;
+}
+
+// Sweep alone (autotuning): zeroing and the sweep kernel of one layout.
+int bulk_sweep_only(BulkLayout& L, const IdentScratch& sc, cudaStream_t st) {
+  BulkParams& p = L.p;
+  if (sc.staging_cap < L.recs_need * kRecWords || sc.table_cap < L.table_need ||
+      sc.seg_cap * 2 < (uint64_t)p.nseg)
+    return set_error(QTV_ERR_CAPACITY, "identification scratch too small for this layout");
+  cudaError_t e = cudaMemsetAsync(sc.counters, 0, 4 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sc.seg, 0, p.nseg * sizeof(unsigned int), st);
+  if (e != cudaSuccess) return check_cuda(e, "cudaMemsetAsync(sweep scratch)");
+  p.recs = sc.staging;
+  p.recs_cap = L.recs_need;
+  p.counters = sc.counters;
+  p.table = sc.table;
+  p.segf = reinterpret_cast<unsigned int*>(sc.seg);
+  bulk_fn(p.nwt)<<<L.grid, L.threads, L.smem, st>>>(p);
+  return check_cuda(cudaGetLastError(), "sweep_bulk_kernel launch");
 }
 
 int bulk_needs(int num_sms, const qtv_grid& g, uint64_t capacity, uint64_t max_warps,
                BulkNeeds* n) {
-  BulkPlan p;
-  const int rc = bulk_plan(num_sms, g, capacity, max_warps, &p);
+  BulkLayout L;
+  // alignment is checked by the caller; sizing needs only a 16-byte aligned stand-in
+  const float2* psi = reinterpret_cast<const float2*>(uintptr_t(256));
+  const int rc = bulk_layout(num_sms, 1, &g, &psi, TileConfig(), capacity, max_warps, &L);
   if (rc) return rc;
-  n->recs = p.recs_need * kRecWords;  // staging words
-  n->table = p.table_need;
-  n->seg_off = (unsigned long long)p.nseg;
-  n->tiles = (unsigned long long)p.ntiles;
-  n->segf = (unsigned long long)(p.nseg + 1) / 2;  // uint2 entries holding nseg u32
+  n->recs = L.recs_need * kRecWords;  // staging words
+  n->table = L.table_need;
+  n->seg_off = (unsigned long long)L.p.nseg;
+  n->tiles = (unsigned long long)L.ntiles;
+  n->segf = (unsigned long long)(L.p.nseg + 1) / 2;  // uint2 entries holding nseg u32
   return QTV_OK;
 }
 
@@ -957,57 +1138,15 @@ int bulk_identify(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* 
                   int8_t* winding, uint64_t capacity, uint64_t* count, qtv_stats* stats,
                   cudaStream_t st, const IdentScratch& sc, uint64_t max_warps, float* xyz,
                   float* resid, uint8_t* flags) {
-  BulkPlan p;
-  int rc = bulk_plan(h->num_sms, g, capacity, max_warps, &p);
+  BulkLayout L;
+  int rc = bulk_layout(h->num_sms, 1, &g, &psi, TileConfig(), capacity, max_warps, &L);
   if (rc) return rc;
-  if (sc.staging_cap < p.recs_need * kRecWords || sc.table_cap < p.table_need ||
-      sc.seg_cap * 2 < (uint64_t)p.nseg ||
-      sc.seg_off_cap < (uint64_t)p.nseg || sc.tiles_cap < (uint64_t)p.ntiles)
-    return set_error(QTV_ERR_CAPACITY, "identification scratch too small for this grid");
-  cudaError_t e = cudaMemsetAsync(sc.counters, 0, 4 * sizeof(unsigned long long), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(sc.tiles, 0, p.ntiles * sizeof(unsigned long long), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(sc.seg, 0, p.nseg * sizeof(unsigned int), st);
-  if (e == cudaSuccess && stats) e = cudaMemsetAsync(stats, 0, sizeof(qtv_stats), st);
-  if (e != cudaSuccess) return check_cuda(e, "cudaMemsetAsync(identify scratch)");
-  V3Args a;
-  a.psi = psi;
-  a.nx = g.nx;
-  a.ny = g.ny;
-  a.nz = g.nz;
-  a.nbands = (g.ny + R - 1) / R;
-  a.hblock = p.hblock;
-  a.recs = sc.staging;
-  a.recs_cap = p.recs_need;
-  a.counters = sc.counters;
-  a.table = sc.table;
-  a.segf = reinterpret_cast<unsigned int*>(sc.seg);
-  {
-    TraceScope ts(h, K_SWEEP, st);
-    bulk_fn(p.nw)<<<p.grid, p.nw * 32, p.smem, st>>>(a);
-  }
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return check_cuda(e, "sweep_bulk_kernel launch");
   const unsigned long long nx = g.nx, ny = g.ny, nz = g.nz;
   const unsigned long long scanned =
       (nx - 1) * (ny - 1) * nz + nx * (ny - 1) * (nz - 1) + (nx - 1) * ny * (nz - 1);
-  {
-    TraceScope ts(h, K_SEG_SCAN, st);
-    v3_scan_kernel<<<(unsigned)p.ntiles, kScanThreads, 0, st>>>(
-        reinterpret_cast<const unsigned int*>(sc.seg), p.nseg, sc.seg_off, count, sc.counters, sc.tiles, p.ntiles, stats, scanned);
-  }
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return check_cuda(e, "v3_scan_kernel launch");
-  if (capacity > 0) {
-    long long blocks = (p.nseg + kExpandWarps - 1) / kExpandWarps;
-    const long long maxb = (long long)h->num_sms * 4;
-    if (blocks > maxb) blocks = maxb;
-    TraceScope ts(h, K_SCATTER, st);
-    v3_expand_kernel<<<(unsigned)blocks, 32 * kExpandWarps, 0, st>>>(
-        sc.table, p.nw, p.nseg, a.nbands, g.nx, g.ny, sc.staging, p.recs_need, sc.seg_off, face_ids,
-        winding, capacity);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return check_cuda(e, "v3_expand_kernel launch");
-  }
+  rc = bulk_launch(h, L, sc, face_ids, winding, capacity, count, nullptr, stats, scanned, st,
+                   false);
+  if (rc) return rc;
   if (xyz && capacity > 0)
     return localize_launch(h, g, psi, face_ids, winding, capacity, count, xyz, resid, flags, st);
   return QTV_OK;

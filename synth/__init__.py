@@ -142,6 +142,19 @@ def multiplicative_noise(psi, seed: int, level: float = 0.05):
     return psi * torch.as_tensor(fac, device=psi.device)
 
 
+# the 16 snapshots of the uneven batch workload: (edge, waves), seeds 201..216
+BATCH16 = [(256, 4096)] * 8 + [(384, 4096)] * 4 + [(512, 16384)] * 3 + [(768, 16384)]
+
+
+def batch_fields(device="cuda", sizes=None, seed0: int = 201):
+    """Random-wave tangles of an uneven batch: one snapshot per (edge, waves)
+    entry of sizes (default BATCH16: 8 x 256^3, 4 x 384^3, 3 x 512^3,
+    1 x 768^3), seeds seed0, seed0 + 1, ... (torch)."""
+    sizes = BATCH16 if sizes is None else sizes
+    return [random_waves((n, n, n), wave_spec(seed0 + i, w), device=device)
+            for i, (n, w) in enumerate(sizes)]
+
+
 def config_field(name: str, device="cpu", seed: int | None = None):
     """Fields of the named workloads.
 
