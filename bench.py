@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--soak", type=float, default=1.5,
                    help="seconds of untimed load before warm-up (clock sampling)")
+    p.add_argument("--no-batch", action="store_true",
+                   help="skip the 16-snapshot batch against per-snapshot launches")
     p.add_argument("--no-learned", action="store_true",
                    help="skip training the learned locator and its report against plain")
     return p.parse_args()
@@ -187,6 +189,87 @@ def learned_report(q, psi, ids, wnd, F, stream, reps=20):
         "rms_vs_plain_h": rms_all, "rms_vs_plain_accepted_h": rms_acc,
         "fallback_resid": 1e-3,
     }
+
+
+def batch_report(q, stream, reps=10, learned=False):
+    """The uneven 16-snapshot workload (8 x 256^3, 4 x 384^3, 3 x 512^3,
+    1 x 768^3; seeds 201-216): one replay of the batch graph (persistent
+    sweep over all snapshots, one finalize and one localization pass) against
+    the same work as 16 separate qtv_identify_localize calls, identification
+    plus plain localization in both; the learned-localization replay is timed
+    too when a trained locator is loaded."""
+    import torch
+
+    import paper_1911_12070_gb300 as qtv
+    import synth
+
+    devs = synth.batch_fields("cuda")
+    nodes = sum(d.numel() for d in devs)
+    t0 = time.time()
+    info = q.batch_plan(devs)
+    plan_s = time.time() - t0
+    dev = devs[0].device
+    cap = int(info["faces"] * 1.02) + 1024
+    ids = torch.empty(cap, dtype=torch.int64, device=dev)
+    w = torch.empty(cap, dtype=torch.int8, device=dev)
+    off = torch.zeros(len(devs) + 1, dtype=torch.int64, device=dev)
+    xyz = torch.empty((cap, 3), dtype=torch.float32, device=dev)
+    resid = torch.empty(cap, dtype=torch.float32, device=dev)
+    fl = torch.empty(cap, dtype=torch.uint8, device=dev)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    graph_ms = timed(lambda: q.batch_run_into(ids, w, off, xyz, resid, fl))
+    faces = int(off[-1])
+    # the same work as one call per snapshot
+    o = off.cpu().numpy()
+    per = []
+    for i, d in enumerate(devs):
+        m = int(o[i + 1] - o[i]) + 1024
+        per.append((d, torch.empty(m, dtype=torch.int64, device=dev),
+                    torch.empty(m, dtype=torch.int8, device=dev),
+                    torch.zeros(1, dtype=torch.int64, device=dev),
+                    torch.empty((m, 3), dtype=torch.float32, device=dev),
+                    torch.empty(m, dtype=torch.float32, device=dev),
+                    torch.empty(m, dtype=torch.uint8, device=dev)))
+    q.reserve((768, 768, 768), max(int(o[i + 1] - o[i]) for i in range(len(devs))) + 1024)
+
+    def singles():
+        for d, a, b, c, x, r, f in per:
+            q.identify_localize_into(d, a, b, c, x, r, f)
+
+    single_ms = timed(singles)
+    out = {
+        "workload": "16 random-wave snapshots: 8 x 256^3, 4 x 384^3 (4096 waves), 3 x 512^3, "
+                    "1 x 768^3 (16384 waves); seeds 201-216; identify + plain localize",
+        "nodes": nodes, "faces": faces, "plan_seconds": plan_s,
+        "tuned": {k: info[k] for k in ("warps_per_tile", "tile_columns", "ctas_per_sm", "zscale",
+                                       "concurrent", "sweeps", "grid", "source", "candidates",
+                                       "tuned_ms")},
+        "graph_ms": graph_ms, "value": nodes / (graph_ms * 1e-3),
+        "per_snapshot_ms": single_ms, "per_snapshot_value": nodes / (single_ms * 1e-3),
+        "speedup_vs_per_snapshot": single_ms / graph_ms,
+        "unit": UNIT,
+        "hbm_gbs": (8 * nodes + 58 * faces) / (graph_ms * 1e-3) / 1e9,
+    }
+    if learned:
+        out["learned_graph_ms"] = timed(lambda: q.batch_run_into(
+            ids, w, off, xyz, resid, fl, mode=qtv.LEARNED, fallback_resid=1e-3))
+    del devs, per
+    q.batch_plan([torch.zeros((2, 2, 2), dtype=torch.complex64, device=dev)])  # release
+    torch.cuda.empty_cache()
+    return out
 
 
 def oracle_sample(psi_host_slab, planes):
@@ -445,6 +528,9 @@ def run_qtv(args):
 
     if rank == 0 and not args.no_learned:
         line["learned"] = learned_report(q, psi, ids, wnd, F, stream)
+
+    if rank == 0 and not args.no_batch:
+        line["batch"] = batch_report(q, stream, learned=not args.no_learned)
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle

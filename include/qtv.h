@@ -283,9 +283,11 @@ QTV_API int qtv_locator_load(qtv_handle h, const char* path);
 /*
  * Batches of snapshots.  Identification (Sec. 2.2.2, Eq. 5) and localization
  * (Sec. 3.3.3, Eq. 6) of up to QTV_BATCH_MAX snapshots of different grid
- * sizes in one pass: one persistent sweep launch whose CTAs take contiguous
- * ranges of the (plane, band, x tile) units of all snapshots, then one scan,
- * one expand and one localization launch over the concatenated face list.
+ * sizes in one pass: persistent sweep launches whose CTAs take contiguous
+ * ranges of the (plane, band, x tile) units of many snapshots (one launch for
+ * all snapshots at a common tile width, or one per group of snapshots of equal
+ * row width, serial or concurrent), then one scan, one expand and one
+ * localization launch over the concatenated face list.
  * The sequence is captured into a CUDA graph on the first qtv_batch_run and
  * replayed by later calls with the same outputs and mode.
  *
@@ -297,9 +299,10 @@ QTV_API int qtv_locator_load(qtv_handle h, const char* path);
  * timing candidates on these fields, unless tune_cache names a text file that
  * holds a shape for this device and these grid sizes; a newly timed shape is
  * appended to that file (tune_cache may be NULL).  Each line of the file is
- * "qtv-tune-v1 <key> <warps per tile> <CTAs per SM, 0 = max> <z-block
- * factor> <ms>"; the last line whose key matches wins, and the key "*"
- * matches every batch (a pinned shape).  Synchronizes `stream`.
+ * "qtv-tune-v2 <key> <warps per tile, 0 = per snapshot> <CTAs per SM, 0 =
+ * max> <z-block factor> <concurrent 0/1> <ms>"; the last line whose key
+ * matches wins, and the key "*" matches every batch (a pinned shape).
+ * Synchronizes `stream`.
  *
  * qtv_batch_run: face_ids / winding [capacity] receive the faces of all
  * snapshots, snapshot i in [offsets[i], offsets[i+1]) in ascending face-id
@@ -314,11 +317,14 @@ QTV_API int qtv_locator_load(qtv_handle h, const char* path);
 typedef struct {
   uint64_t nodes;         /* grid nodes of all snapshots */
   uint64_t faces;         /* pierced faces found by the counting pass */
-  int32_t warps_per_tile; /* chosen shape: tile width 64 * warps_per_tile columns */
-  int32_t tile_columns;
-  int32_t ctas_per_sm;
+  int32_t warps_per_tile; /* chosen shape: tiles of 64 * warps_per_tile columns for every
+                             snapshot, or 0: each snapshot one tile as wide as its row */
+  int32_t tile_columns;   /* 64 * warps_per_tile (0 when per snapshot) */
+  int32_t ctas_per_sm;    /* cap on resident CTAs per SM (0: as many as fit) */
   float zscale;           /* factor on the z-block height */
-  int32_t grid;           /* CTAs of the sweep launch */
+  int32_t concurrent;     /* 1: sweeps of the width groups run concurrently */
+  int32_t sweeps;         /* sweep launches (width groups) */
+  int32_t grid;           /* CTAs of all sweep launches */
   int32_t source;         /* 1: tune cache, 2: timed now */
   int32_t candidates;     /* shapes timed (source 2) */
   float tuned_ms;         /* sweep time of the chosen shape */

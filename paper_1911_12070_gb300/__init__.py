@@ -72,6 +72,7 @@ class BatchInfo(ctypes.Structure):
     _fields_ = [("nodes", ctypes.c_uint64), ("faces", ctypes.c_uint64),
                 ("warps_per_tile", ctypes.c_int32), ("tile_columns", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("zscale", ctypes.c_float),
+                ("concurrent", ctypes.c_int32), ("sweeps", ctypes.c_int32),
                 ("grid", ctypes.c_int32), ("source", ctypes.c_int32),
                 ("candidates", ctypes.c_int32), ("tuned_ms", ctypes.c_float)]
 

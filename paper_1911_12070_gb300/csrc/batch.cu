@@ -44,6 +44,7 @@ struct BatchPlan {
   uint64_t tiles_cap = 0;
   unsigned long long* counters = nullptr;
   uint64_t* count_buf = nullptr;  // [kMaxSnaps + 1] offsets of the counting pass
+  SweepBranches br{};  // streams and events of concurrent group sweeps
   // captured graph and what it was captured for
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -71,6 +72,11 @@ void batch_free(BatchPlan* b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->cap) cudaStreamDestroy(b->cap);
+  for (int i = 0; i < b->br.n; ++i) {
+    cudaStreamDestroy(b->br.streams[i]);
+    cudaEventDestroy(b->br.join[i]);
+  }
+  if (b->br.n) cudaEventDestroy(b->br.fork);
   cudaFree(b->staging);
   cudaFree(b->table);
   cudaFree(b->segf);
@@ -121,19 +127,21 @@ int grow(T** p, uint64_t* cap, uint64_t need, const char* what) {
   return QTV_OK;
 }
 
-int ensure_scratch(BatchPlan* b, const BulkLayout& L) {
+int ensure_scratch(BatchPlan* b, const BatchLayout& L) {
   int rc = grow(&b->staging, &b->staging_cap, L.recs_need * 6ull, "cudaMalloc(batch staging)");
   if (!rc) rc = grow(&b->table, &b->table_cap, L.table_need, "cudaMalloc(batch table)");
-  if (!rc && (uint64_t)L.p.nseg > b->seg_cap) {
+  // segment totals are addressed as pairs of u32 by the scratch descriptor
+  const uint64_t nseg = ((uint64_t)L.fin.nseg + 1) & ~1ull;
+  if (!rc && nseg > b->seg_cap) {
     cudaFree(b->segf);
     cudaFree(b->seg_off);
     b->segf = nullptr;
     b->seg_off = nullptr;
     b->seg_cap = 0;
-    cudaError_t e = cudaMalloc(&b->segf, L.p.nseg * sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMalloc(&b->seg_off, L.p.nseg * sizeof(unsigned long long));
+    cudaError_t e = cudaMalloc(&b->segf, nseg * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->seg_off, nseg * sizeof(unsigned long long));
     if (e != cudaSuccess) return check_cuda(e, "cudaMalloc(batch segments)");
-    b->seg_cap = L.p.nseg;
+    b->seg_cap = nseg;
   }
   if (!rc) rc = grow(&b->tiles, &b->tiles_cap, (uint64_t)L.ntiles, "cudaMalloc(batch tiles)");
   return rc;
@@ -188,7 +196,7 @@ std::string tune_key(const BatchPlan* b, int device, int num_sms) {
   return k;
 }
 
-constexpr const char* kTuneTag = "qtv-tune-v1";
+constexpr const char* kTuneTag = "qtv-tune-v2";
 
 bool tune_lookup(const char* path, const std::string& key, TileConfig* tc, float* ms) {
   if (!path || !*path) return false;
@@ -198,13 +206,15 @@ bool tune_lookup(const char* path, const std::string& key, TileConfig* tc, float
   bool found = false;
   while (fgets(line, sizeof line, f)) {
     char tag[32], k[3500];
-    int nwt = 0, ctas = 0;
+    int nwt = 0, ctas = 0, conc = 0;
     float zs = 0.f, t = 0.f;
-    if (sscanf(line, "%31s %3499s %d %d %f %f", tag, k, &nwt, &ctas, &zs, &t) != 6) continue;
+    if (sscanf(line, "%31s %3499s %d %d %f %d %f", tag, k, &nwt, &ctas, &zs, &conc, &t) != 7)
+      continue;
     if (strcmp(tag, kTuneTag) != 0 || (key != k && strcmp(k, "*") != 0)) continue;
     tc->nwt = nwt;
     tc->ctas_per_sm = ctas;
     tc->zscale = zs;
+    tc->concurrent = conc;
     *ms = t;
     found = true;  // the last matching line wins
   }
@@ -216,16 +226,32 @@ void tune_store(const char* path, const std::string& key, const TileConfig& tc, 
   if (!path || !*path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %s %d %d %.3f %.6f\n", kTuneTag, key.c_str(), tc.nwt, tc.ctas_per_sm, tc.zscale,
-          ms);
+  fprintf(f, "%s %s %d %d %.3f %d %.6f\n", kTuneTag, key.c_str(), tc.nwt, tc.ctas_per_sm,
+          tc.zscale, tc.concurrent, ms);
   fclose(f);
 }
 
-// Times the sweep of each candidate shape on the plan's fields; returns the
-// fastest (median of 3 timed launches after one warm-up).
+// Times the sweeps of each candidate shape on the plan's fields; returns the
+// fastest (median of 3 timed launches after one warm-up).  Candidates: one
+// tile width for all snapshots (64 to 1024 columns), or per-snapshot widths
+// with one sweep per width group (serial or concurrent), each with a few
+// occupancies and z-block heights.
 int autotune(qtv_handle h, BatchPlan* b, uint64_t faces, cudaStream_t st, TileConfig* best,
              float* best_ms, int* ncand) {
   std::vector<TileConfig> cands;
+  auto add = [&](int nwt, int ctas, float zs, int conc) {
+    TileConfig tc;
+    tc.nwt = nwt;
+    tc.ctas_per_sm = ctas;
+    tc.zscale = zs;
+    tc.concurrent = conc;
+    BatchLayout L;
+    if (batch_layout(h->num_sms, b->n, b->grids.data(), b->psis.data(), tc, faces, 0, &L) ==
+        QTV_OK) {
+      if (conc && !L.concurrent) return;  // one group: same as serial
+      cands.push_back(tc);
+    }
+  };
   for (int nwt : {2, 4, 8, 16}) {
     int bps = 0;
     size_t smem = 0;
@@ -234,17 +260,11 @@ int autotune(qtv_handle h, BatchPlan* b, uint64_t faces, cudaStream_t st, TileCo
     std::sort(occ.begin(), occ.end());
     occ.erase(std::unique(occ.begin(), occ.end()), occ.end());
     for (int c : occ)
-      for (float zs : {0.5f, 1.f, 2.f}) {
-        TileConfig tc;
-        tc.nwt = nwt;
-        tc.ctas_per_sm = c;
-        tc.zscale = zs;
-        BulkLayout L;
-        if (bulk_layout(h->num_sms, b->n, b->grids.data(), b->psis.data(), tc, faces, 0, &L))
-          continue;
-        cands.push_back(tc);
-      }
+      for (float zs : {0.5f, 1.f, 2.f}) add(nwt, c, zs, 0);
   }
+  for (int conc : {0, 1})
+    for (int c : {0, 2, 1})
+      for (float zs : {0.5f, 1.f, 2.f}) add(0, c, zs, conc);
   if (cands.empty()) return set_error(QTV_ERR_ARG, "no sweep shape fits this batch");
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return check_cuda(cudaGetLastError(), "event");
@@ -255,15 +275,15 @@ int autotune(qtv_handle h, BatchPlan* b, uint64_t faces, cudaStream_t st, TileCo
   int rc = QTV_OK;
   *best_ms = 1e30f;
   for (const TileConfig& tc : cands) {
-    BulkLayout L;
-    rc = bulk_layout(h->num_sms, b->n, b->grids.data(), b->psis.data(), tc, faces, 0, &L);
+    BatchLayout L;
+    rc = batch_layout(h->num_sms, b->n, b->grids.data(), b->psis.data(), tc, faces, 0, &L);
     if (!rc) rc = ensure_scratch(b, L);
     if (rc) break;
     IdentScratch sc = scratch_of(b);
     float t[3];
     for (int r = 0; r < 4 && !rc; ++r) {
       cudaEventRecord(e0, st);
-      rc = bulk_sweep_only(L, sc, st);
+      rc = batch_sweep_only(h, L, sc, st, &b->br);
       cudaEventRecord(e1, st);
       if (!rc) rc = check_cuda(cudaEventSynchronize(e1), "autotune sync");
       if (!rc && r > 0) cudaEventElapsedTime(&t[r - 1], e0, e1);
@@ -321,22 +341,39 @@ int qtv_batch_plan(qtv_handle h, int n, const qtv_grid* grids, const void* const
   if (e != cudaSuccess) return check_cuda(e, "qtv_batch_plan allocation");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
+  // branch streams for concurrent group sweeps: one per distinct row width
+  {
+    std::vector<int> widths;
+    for (int i = 0; i < n; ++i) {
+      const int w = (grids[i].nx + 63) / 64;
+      if (std::find(widths.begin(), widths.end(), w) == widths.end()) widths.push_back(w);
+    }
+    if (widths.size() > 1) {
+      e = cudaEventCreateWithFlags(&b->br.fork, cudaEventDisableTiming);
+      if (e != cudaSuccess) return check_cuda(e, "cudaEventCreate(fork)");
+      for (size_t i = 0; i < widths.size(); ++i) {
+        e = cudaStreamCreateWithFlags(&b->br.streams[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+          e = cudaEventCreateWithFlags(&b->br.join[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+          if (b->br.streams[i]) cudaStreamDestroy(b->br.streams[i]);
+          return check_cuda(e, "branch stream");
+        }
+        b->br.n = (int)i + 1;
+      }
+    }
+  }
   // counting pass with the default shape: the face total sizes the staging of
   // the candidates (face totals do not depend on the staging size)
-  BulkLayout L0;
-  int rc = bulk_layout(h->num_sms, n, b->grids.data(), b->psis.data(), TileConfig(), 0, 0, &L0);
-  if (rc) {
-    TileConfig t4;
-    t4.nwt = 4;
-    rc = bulk_layout(h->num_sms, n, b->grids.data(), b->psis.data(), t4, 0, 0, &L0);
-  }
+  BatchLayout L0;
+  int rc = batch_layout(h->num_sms, n, b->grids.data(), b->psis.data(), TileConfig(), 0, 0, &L0);
   if (rc) return rc;
   rc = ensure_scratch(b, L0);
   if (rc) return rc;
   const bool tr = h->trace_on;
   h->trace_on = false;
-  rc = bulk_launch(h, L0, scratch_of(b), nullptr, nullptr, 0, b->count_buf + n, b->count_buf,
-                   nullptr, 0, st, true);
+  rc = batch_launch(h, L0, scratch_of(b), nullptr, nullptr, 0, b->count_buf + n, b->count_buf,
+                    nullptr, 0, st, true, nullptr);
   h->trace_on = tr;
   if (rc) return rc;
   uint64_t total = 0;
@@ -355,8 +392,8 @@ int qtv_batch_plan(qtv_handle h, int n, const qtv_grid* grids, const void* const
   float ms = 0.f;
   TileConfig tc;
   if (tune_lookup(tune_cache, key, &tc, &ms)) {
-    BulkLayout Lc;
-    if (bulk_layout(h->num_sms, n, b->grids.data(), b->psis.data(), tc, total, 0, &Lc) ==
+    BatchLayout Lc;
+    if (batch_layout(h->num_sms, n, b->grids.data(), b->psis.data(), tc, total, 0, &Lc) ==
         QTV_OK) {
       b->tc = tc;
       b->info.source = 1;
@@ -376,11 +413,14 @@ int qtv_batch_plan(qtv_handle h, int n, const qtv_grid* grids, const void* const
   b->info.warps_per_tile = b->tc.nwt;
   b->info.ctas_per_sm = b->tc.ctas_per_sm;
   b->info.zscale = b->tc.zscale;
-  BulkLayout L;
-  rc = bulk_layout(h->num_sms, n, b->grids.data(), b->psis.data(), b->tc, total, 0, &L);
+  b->info.concurrent = b->tc.concurrent;
+  BatchLayout L;
+  rc = batch_layout(h->num_sms, n, b->grids.data(), b->psis.data(), b->tc, total, 0, &L);
   if (rc) return rc;
-  b->info.grid = L.grid;
-  b->info.tile_columns = 64 * L.p.nwt;
+  b->info.grid = 0;
+  for (const BulkLayout& g : L.groups) b->info.grid += g.grid;
+  b->info.sweeps = (int)L.groups.size();
+  b->info.tile_columns = 64 * b->tc.nwt;
   return QTV_OK;
 }
 
@@ -416,8 +456,8 @@ int qtv_batch_run(qtv_handle h, uint64_t* face_ids, int8_t* winding, uint64_t ca
     if (rc) return rc;
   }
   if (!b->have_graph || !(key == b->key)) {
-    BulkLayout L;
-    int rc = bulk_layout(h->num_sms, b->n, b->grids.data(), b->psis.data(), b->tc, capacity, 0, &L);
+    BatchLayout L;
+    int rc = batch_layout(h->num_sms, b->n, b->grids.data(), b->psis.data(), b->tc, capacity, 0, &L);
     if (!rc) rc = ensure_scratch(b, L);
     if (rc) return rc;
     if (b->exec) {
@@ -432,8 +472,8 @@ int qtv_batch_run(qtv_handle h, uint64_t* face_ids, int8_t* winding, uint64_t ca
       h->trace_on = tr;
       return check_cuda(e, "cudaStreamBeginCapture");
     }
-    rc = bulk_launch(h, L, scratch_of(b), face_ids, winding, capacity, offsets + b->n, offsets,
-                     nullptr, 0, b->cap, true);
+    rc = batch_launch(h, L, scratch_of(b), face_ids, winding, capacity, offsets + b->n, offsets,
+                      nullptr, 0, b->cap, true, &b->br);
     if (!rc && loc && capacity > 0) {
       const FaceGeo geo = geo_of(b, offsets);
       if (mode == QTV_LEARNED) {

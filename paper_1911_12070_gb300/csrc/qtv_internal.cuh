@@ -156,7 +156,7 @@ struct SnapDesc {
   int st = 0;       // x stride of the tiles (even); tile t stages columns
                     // [t st, t st + st + 2), the last one [t st, nx)
   int hblock = 1;   // planes per z block
-  int pad_ = 0;
+  int nwt = 1;      // warps per x tile (tile width 64 nwt columns)
   long long unit0 = 0, seg0 = 0, tab0 = 0;  // first unit / segment / table entry
 };
 constexpr int kMaxSnaps = QTV_BATCH_MAX;
@@ -165,7 +165,7 @@ constexpr int kMaxSnaps = QTV_BATCH_MAX;
 struct BulkParams {
   SnapDesc s[kMaxSnaps];
   int nsnap = 0;
-  int nwt = 0;      // warps per tile (tile width 64 nwt columns)
+  int nwt = 0;      // warps per tile of the sweep launch (its CTA width)
   long long units = 0, nseg = 0;
   uint32_t* recs = nullptr;
   unsigned long long recs_cap = 0;   // records
@@ -174,21 +174,45 @@ struct BulkParams {
   unsigned int* segf = nullptr;      // pierced faces per segment (zeroed before)
 };
 
-// Tunable shape of a sweep: warps per tile (0: one tile as wide as the widest
-// row), resident CTAs per SM (0: as many as fit) and a factor on the z-block
-// height.
+// Tunable shape of a sweep: warps per x tile for every snapshot (0: per
+// snapshot, one tile as wide as its row), resident CTAs per SM (0: as many as
+// fit), a factor on the z-block height, and whether the sweeps of snapshot
+// groups of different tile widths run concurrently (each on a share of the
+// GPU in proportion to its nodes) or one after the other.
 struct TileConfig {
   int nwt = 0;
   int ctas_per_sm = 0;
   float zscale = 1.f;
+  int concurrent = 0;
 };
 
+// One sweep launch: the snapshots of one group (same warps per tile), units
+// numbered within the group, segments and table entries numbered globally.
 struct BulkLayout {
   BulkParams p;
-  int grid = 0, threads = 0, expand_blocks = 1;
+  int grid = 0, threads = 0;
   size_t smem = 0;
+};
+
+// A whole pass: the sweep launches of all groups, and the parameters of the
+// expand pass over all snapshots in their given order.
+struct BatchLayout {
+  std::vector<BulkLayout> groups;
+  std::vector<int> group_of;
+  BulkParams fin;
+  bool concurrent = false;
+  int expand_blocks = 1;
   long long ntiles = 0;  // scan tiles
   unsigned long long recs_need = 0, table_need = 0;
+};
+
+// Streams and events for concurrent sweeps (fork from and join into the
+// launching stream).
+struct SweepBranches {
+  int n = 0;
+  cudaStream_t streams[kMaxSnaps];
+  cudaEvent_t fork;
+  cudaEvent_t join[kMaxSnaps];
 };
 
 // Geometry of the faces of one call: one grid, or the concatenated face lists
@@ -232,12 +256,14 @@ __device__ __forceinline__ int geo_snapshot(const FaceGeo& G, unsigned long long
 #endif
 
 int bulk_variant_occupancy(int nw, int* ctas_per_sm, size_t* smem);
-int bulk_layout(int num_sms, int nsnap, const qtv_grid* grids, const float2* const* psis,
-                const TileConfig& tc, uint64_t capacity, uint64_t max_warps, BulkLayout* L);
-int bulk_launch(qtv_handle h, BulkLayout& L, const IdentScratch& sc, uint64_t* face_ids,
-                int8_t* winding, uint64_t capacity, uint64_t* count, uint64_t* offsets,
-                qtv_stats* stats, unsigned long long scanned, cudaStream_t st, bool expand_always);
-int bulk_sweep_only(BulkLayout& L, const IdentScratch& sc, cudaStream_t st);
+int batch_layout(int num_sms, int nsnap, const qtv_grid* grids, const float2* const* psis,
+                 const TileConfig& tc, uint64_t capacity, uint64_t max_warps, BatchLayout* B);
+int batch_launch(qtv_handle h, BatchLayout& B, const IdentScratch& sc, uint64_t* face_ids,
+                 int8_t* winding, uint64_t capacity, uint64_t* count, uint64_t* offsets,
+                 qtv_stats* stats, unsigned long long scanned, cudaStream_t st, bool expand_always,
+                 const SweepBranches* br);
+int batch_sweep_only(qtv_handle h, BatchLayout& B, const IdentScratch& sc, cudaStream_t st,
+                     const SweepBranches* br);
 bool sweep_bulk_supported(int nx, int ny, int nz, const void* psi);
 int bulk_needs(int num_sms, const qtv_grid& g, uint64_t capacity, uint64_t max_warps,
                BulkNeeds* n);

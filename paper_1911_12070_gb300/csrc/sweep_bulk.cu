@@ -404,6 +404,7 @@ __global__ void __launch_bounds__(MAXT, MINB) sweep_bulk_kernel(const __grid_con
     const unsigned long long tbase =
         (unsigned long long)sd.tab0 + ((unsigned long long)band * ntx + tile) * NW + w;
     unsigned int* const segf = a.segf + sd.seg0 + band;
+    const unsigned sstride = (unsigned)sd.nbands;
 
     // ---- prologue: plane kb
     for (int i = 0; i < min(kStages, nplanes); ++i) issue(kb + i);
@@ -567,7 +568,7 @@ __global__ void __launch_bounds__(MAXT, MINB) sweep_bulk_kernel(const __grid_con
       if (lane == 0) {
         a.table[tbase + (unsigned long long)k * tstride] =
             make_uint4(base1, base2, T | (n1 << 6) | (faces_w << 12), 0u);
-        if (faces_w) atomicAdd(&segf[(size_t)k * sd.nbands], faces_w);
+        if (faces_w) atomicAdd(&segf[(size_t)k * sstride], faces_w);
       }
       if (anyw) {
         const uint32_t q = __popc(bal & lt);
@@ -746,7 +747,7 @@ __global__ void __launch_bounds__(32 * kExpandWarps, 4) v3_expand_kernel(
     si = 0;
     while (si + 1 < a.nsnap && a.s[si + 1].seg0 <= sg) ++si;
     local = sg - a.s[si].seg0;
-    NWs = a.s[si].ntx * a.nwt;
+    NWs = a.s[si].ntx * a.s[si].nwt;
   };
   // the next segment's table entries and offset are loaded one segment ahead
   uint4 e_next = make_uint4(0u, 0u, 0u, 0u);
@@ -786,7 +787,7 @@ __global__ void __launch_bounds__(32 * kExpandWarps, 4) v3_expand_kernel(
     const unsigned long long nx = (unsigned)sd.nx, ny = (unsigned)sd.ny;
     const long long k = local / nbands;
     const long long j0 = (local % nbands) * R;
-    const int nwt = a.nwt;  // warps per tile
+    const int nwt = sd.nwt;  // warps per tile of this snapshot
     const uint32_t nchunks = (rtot + 31) / 32;
 
     // record of flattened index g = g0 + lane (zeros past the end)
@@ -938,6 +939,27 @@ size_t bulk_smem_for_warps(int nw) {
          sizeof(SmallSmem);
 }
 
+// x tiles of a row of nx columns for tiles of nwt warps: one tile when it
+// fits, else ntx tiles at an even stride st, each staging st + 2 <= 64 nwt
+// columns (the last one the rest)
+int snap_tiles(int nx, int nwt, int* ntx, int* st) {
+  const int TX = 64 * nwt;
+  if (nx <= TX) {
+    *ntx = 1;
+    *st = 0;
+    return QTV_OK;
+  }
+  if (TX < 4) return set_error(QTV_ERR_ARG, "tile of %d columns too narrow", TX);
+  const int n = (nx - 2 + (TX - 2) - 1) / (TX - 2);
+  const int per = (nx - 2 + n - 1) / n;
+  const int s = (per + 1) & ~1;
+  if (s + 2 > TX || nx - (n - 1) * s > TX || nx - (n - 1) * s < 2)
+    return set_error(QTV_ERR_ARG, "no tiling of nx = %d into %d-column tiles", nx, TX);
+  *ntx = n;
+  *st = s;
+  return QTV_OK;
+}
+
 }  // namespace
 
 // Sets the shared-memory opt-in of a sweep variant once; returns its maximum
@@ -967,133 +989,198 @@ bool sweep_bulk_supported(int nx, int ny, int nz, const void* psi) {
   return bulk_smem_for_warps((nx + 63) / 64) <= 227u * 1024u;
 }
 
-int bulk_layout(int num_sms, int nsnap, const qtv_grid* grids, const float2* const* psis,
-                const TileConfig& tc, uint64_t capacity, uint64_t max_warps, BulkLayout* L) {
+int batch_layout(int num_sms, int nsnap, const qtv_grid* grids, const float2* const* psis,
+                 const TileConfig& tc, uint64_t capacity, uint64_t max_warps, BatchLayout* B) {
   if (nsnap < 1 || nsnap > kMaxSnaps)
     return set_error(QTV_ERR_ARG, "%d snapshots (1 to %d supported)", nsnap, kMaxSnaps);
-  int nwt = tc.nwt;
-  if (nwt <= 0) {  // one tile per row, as wide as the widest snapshot needs
-    nwt = 1;
-    for (int i = 0; i < nsnap; ++i) nwt = std::max(nwt, (grids[i].nx + 63) / 64);
-  }
-  if (nwt < 1 || nwt > 16)
-    return set_error(QTV_ERR_ARG, "tile of %d warps (1 to 16 supported)", nwt);
-  const int TX = 64 * nwt;
-  BulkParams& p = L->p;
-  p = BulkParams();
-  p.nsnap = nsnap;
-  p.nwt = nwt;
-  long long units = 0, nseg = 0, tab = 0;
+  if (tc.nwt < 0 || tc.nwt > 16)
+    return set_error(QTV_ERR_ARG, "tile of %d warps (1 to 16 supported)", tc.nwt);
+  BulkParams& fin = B->fin;
+  fin = BulkParams();
+  fin.nsnap = nsnap;
+  B->groups.clear();
+  B->group_of.assign(nsnap, 0);
+  long long nseg = 0, tab = 0;
   for (int i = 0; i < nsnap; ++i) {
     const qtv_grid& g = grids[i];
     if (!sweep_bulk_supported(g.nx, g.ny, g.nz, psis[i]))
       return set_error(QTV_ERR_ARG, "snapshot %d (%d x %d x %d): the staged sweep needs even nx "
                        "<= 1024 and a 16-byte aligned field", i, g.nx, g.ny, g.nz);
-    SnapDesc& d = p.s[i];
+    SnapDesc& d = fin.s[i];
     d.psi = psis[i];
     d.nx = g.nx;
     d.ny = g.ny;
     d.nz = g.nz;
     d.nbands = (g.ny + R - 1) / R;
-    if (g.nx <= TX) {
-      d.ntx = 1;
-      d.st = 0;
-    } else {
-      // tiles stage st + 2 <= TX columns at stride st (even), the last one the rest
-      d.ntx = (g.nx - 2 + (TX - 2) - 1) / (TX - 2);
-      const int per = (g.nx - 2 + d.ntx - 1) / d.ntx;
-      d.st = (per + 1) & ~1;
-      if (d.st + 2 > TX || g.nx - (d.ntx - 1) * d.st > TX || g.nx - (d.ntx - 1) * d.st < 2)
-        return set_error(QTV_ERR_ARG, "no tiling of nx = %d into %d-column tiles", g.nx, TX);
-    }
-    if (d.ntx * nwt > 32)
+    d.nwt = tc.nwt > 0 ? tc.nwt : (g.nx + 63) / 64;
+    int rc = snap_tiles(g.nx, d.nwt, &d.ntx, &d.st);
+    if (rc) return rc;
+    if (d.ntx * d.nwt > 32)
       return set_error(QTV_ERR_ARG, "snapshot %d: %d tiles of %d warps exceed 32 warps per row",
-                       i, d.ntx, nwt);
-    d.unit0 = units;
+                       i, d.ntx, d.nwt);
     d.seg0 = nseg;
     d.tab0 = tab;
-    const long long cols = (long long)d.nbands * d.ntx;
-    units += cols * g.nz;
     nseg += (long long)d.nbands * g.nz;
-    tab += (long long)d.nbands * g.nz * d.ntx * nwt;
+    tab += (long long)d.nbands * g.nz * d.ntx * d.nwt;
   }
-  p.units = units;
-  p.nseg = nseg;
-  int bps = 0;
-  size_t smem = 0;
-  int rc = bulk_variant_occupancy(nwt, &bps, &smem);
-  if (rc) return rc;
-  if (tc.ctas_per_sm > 0 && tc.ctas_per_sm < bps) bps = tc.ctas_per_sm;
-  long long grid = (long long)bps * num_sms;
-  if (max_warps > 0 && grid * nwt > (long long)max_warps) grid = (long long)max_warps / nwt;
-  if (grid > units) grid = units;
-  if (grid < 1) grid = 1;
-  // z blocks: the CTAs that a snapshot gets (in proportion to its units) are
-  // spread over its (band, tile) columns
+  fin.nseg = nseg;
+  // groups: snapshots with the same warps per tile, in order of appearance
+  std::vector<int> gw;
   for (int i = 0; i < nsnap; ++i) {
-    SnapDesc& d = p.s[i];
-    const long long cols = (long long)d.nbands * d.ntx;
-    const double share = (double)grid * (double)(cols * d.nz) / (double)units;
-    long long zblocks = (long long)(share / (double)cols + 0.5);
-    if (zblocks < 1) zblocks = 1;
-    if (zblocks > d.nz) zblocks = d.nz;
-    long long H = (d.nz + zblocks - 1) / zblocks;
-    H = (long long)((double)H * (tc.zscale > 0.f ? tc.zscale : 1.f) + 0.5);
-    if (H < 1) H = 1;
-    if (H > d.nz) H = d.nz;
-    d.hblock = (int)H;
+    int gi = 0;
+    while (gi < (int)gw.size() && gw[gi] != fin.s[i].nwt) ++gi;
+    if (gi == (int)gw.size()) gw.push_back(fin.s[i].nwt);
+    B->group_of[i] = gi;
   }
-  L->grid = (int)grid;
-  L->threads = nwt * 32;
-  L->smem = smem;
-  L->ntiles = (nseg + kScanTile - 1) / kScanTile;
+  double total_nodes = 0;
+  for (int i = 0; i < nsnap; ++i)
+    total_nodes += (double)grids[i].nx * grids[i].ny * grids[i].nz;
+  unsigned long long slack = kChunk;
+  B->groups.resize(gw.size());
+  for (size_t gi = 0; gi < gw.size(); ++gi) {
+    BulkLayout& L = B->groups[gi];
+    BulkParams& p = L.p;
+    p = BulkParams();
+    p.nwt = gw[gi];
+    long long units = 0;
+    double nodes = 0;
+    for (int i = 0; i < nsnap; ++i) {
+      if (B->group_of[i] != (int)gi) continue;
+      SnapDesc d = fin.s[i];
+      d.unit0 = units;
+      units += (long long)d.nbands * d.ntx * d.nz;
+      nodes += (double)d.nx * d.ny * d.nz;
+      p.s[p.nsnap++] = d;
+    }
+    p.units = units;
+    p.nseg = nseg;
+    int bps = 0;
+    size_t smem = 0;
+    int rc = bulk_variant_occupancy(p.nwt, &bps, &smem);
+    if (rc) return rc;
+    if (tc.ctas_per_sm > 0 && tc.ctas_per_sm < bps) bps = tc.ctas_per_sm;
+    long long grid = (long long)bps * num_sms;
+    // concurrent groups share the GPU in proportion to their nodes
+    if (tc.concurrent && gw.size() > 1)
+      grid = (long long)((double)grid * nodes / total_nodes + 0.5);
+    if (max_warps > 0 && grid * p.nwt > (long long)max_warps) grid = (long long)max_warps / p.nwt;
+    if (grid > units) grid = units;
+    if (grid < 1) grid = 1;
+    // z blocks: the CTAs that a snapshot gets (in proportion to its units)
+    // are spread over its (band, tile) columns
+    for (int j = 0; j < p.nsnap; ++j) {
+      SnapDesc& d = p.s[j];
+      const long long cols = (long long)d.nbands * d.ntx;
+      const double share = (double)grid * (double)(cols * d.nz) / (double)units;
+      long long zblocks = (long long)(share / (double)cols + 0.5);
+      if (zblocks < 1) zblocks = 1;
+      if (zblocks > d.nz) zblocks = d.nz;
+      long long H = (d.nz + zblocks - 1) / zblocks;
+      H = (long long)((double)H * (tc.zscale > 0.f ? tc.zscale : 1.f) + 0.5);
+      if (H < 1) H = 1;
+      if (H > d.nz) H = d.nz;
+      d.hblock = (int)H;
+    }
+    L.grid = (int)grid;
+    L.threads = p.nwt * 32;
+    L.smem = smem;
+    slack += 2ull * kChunk * (unsigned long long)grid * p.nwt;
+  }
+  B->concurrent = tc.concurrent && gw.size() > 1;
+  B->ntiles = (nseg + kScanTile - 1) / kScanTile;
   // records (kRecWords words each): at most one per pierced face, plus two
-  // partly used chunks per warp
-  L->recs_need = capacity + 2ull * kChunk * (unsigned long long)grid * nwt + kChunk;
-  L->table_need = (unsigned long long)tab;
-  L->expand_blocks = (int)std::min<long long>((nseg + kExpandWarps - 1) / kExpandWarps,
+  // partly used chunks per warp of every sweep
+  B->recs_need = capacity + slack;
+  B->table_need = (unsigned long long)tab;
+  B->expand_blocks = (int)std::min<long long>((nseg + kExpandWarps - 1) / kExpandWarps,
                                               (long long)num_sms * 4);
   return QTV_OK;
 }
 
-// The launches of one layout: scratch zeroing, sweep, scan, expand.  count
+namespace {
+
+int check_scratch(const BatchLayout& B, const IdentScratch& sc, bool scan) {
+  if (sc.staging_cap < B.recs_need * kRecWords || sc.table_cap < B.table_need ||
+      sc.seg_cap * 2 < (uint64_t)B.fin.nseg ||
+      (scan && (sc.seg_off_cap < (uint64_t)B.fin.nseg || sc.tiles_cap < (uint64_t)B.ntiles)))
+    return set_error(QTV_ERR_CAPACITY, "identification scratch too small for this layout");
+  return QTV_OK;
+}
+
+// The sweeps of all groups on st, or (concurrent) on the branch streams
+// forked from and joined back into st.
+int launch_sweeps(qtv_handle h, BatchLayout& B, const IdentScratch& sc, cudaStream_t st,
+                  const SweepBranches* br) {
+  const bool fork = B.concurrent && br && (int)B.groups.size() <= br->n;
+  cudaError_t e = cudaSuccess;
+  if (fork) {
+    e = cudaEventRecord(br->fork, st);
+    if (e != cudaSuccess) return check_cuda(e, "cudaEventRecord(fork)");
+  }
+  for (size_t gi = 0; gi < B.groups.size(); ++gi) {
+    BulkLayout& L = B.groups[gi];
+    BulkParams& p = L.p;
+    p.recs = sc.staging;
+    p.recs_cap = B.recs_need;
+    p.counters = sc.counters;
+    p.table = sc.table;
+    p.segf = reinterpret_cast<unsigned int*>(sc.seg);
+    cudaStream_t s = st;
+    if (fork) {
+      s = br->streams[gi];
+      e = cudaStreamWaitEvent(s, br->fork, 0);
+      if (e != cudaSuccess) return check_cuda(e, "cudaStreamWaitEvent(fork)");
+    }
+    {
+      TraceScope ts(h, K_SWEEP, s);
+      bulk_fn(p.nwt)<<<L.grid, L.threads, L.smem, s>>>(p);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return check_cuda(e, "sweep_bulk_kernel launch");
+    if (fork) {
+      e = cudaEventRecord(br->join[gi], s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, br->join[gi], 0);
+      if (e != cudaSuccess) return check_cuda(e, "sweep join");
+    }
+  }
+  return QTV_OK;
+}
+
+}  // namespace
+
+// The launches of one layout: scratch zeroing, sweeps, scan, expand.  count
 // receives the total; offsets (optional) receives the first face of each
 // snapshot (nsnap entries).
-int bulk_launch(qtv_handle h, BulkLayout& L, const IdentScratch& sc, uint64_t* face_ids,
-                int8_t* winding, uint64_t capacity, uint64_t* count, uint64_t* offsets,
-                qtv_stats* stats, unsigned long long scanned, cudaStream_t st, bool expand_always) {
-  BulkParams& p = L.p;
-  if (sc.staging_cap < L.recs_need * kRecWords || sc.table_cap < L.table_need ||
-      sc.seg_cap * 2 < (uint64_t)p.nseg || sc.seg_off_cap < (uint64_t)p.nseg ||
-      sc.tiles_cap < (uint64_t)L.ntiles)
-    return set_error(QTV_ERR_CAPACITY, "identification scratch too small for this grid");
+int batch_launch(qtv_handle h, BatchLayout& B, const IdentScratch& sc, uint64_t* face_ids,
+                 int8_t* winding, uint64_t capacity, uint64_t* count, uint64_t* offsets,
+                 qtv_stats* stats, unsigned long long scanned, cudaStream_t st, bool expand_always,
+                 const SweepBranches* br) {
+  int rc = check_scratch(B, sc, true);
+  if (rc) return rc;
   cudaError_t e = cudaMemsetAsync(sc.counters, 0, 4 * sizeof(unsigned long long), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(sc.tiles, 0, L.ntiles * sizeof(unsigned long long), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(sc.seg, 0, p.nseg * sizeof(unsigned int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sc.tiles, 0, B.ntiles * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sc.seg, 0, B.fin.nseg * sizeof(unsigned int), st);
   if (e == cudaSuccess && stats) e = cudaMemsetAsync(stats, 0, sizeof(qtv_stats), st);
   if (e != cudaSuccess) return check_cuda(e, "cudaMemsetAsync(identify scratch)");
-  p.recs = sc.staging;
-  p.recs_cap = L.recs_need;
-  p.counters = sc.counters;
-  p.table = sc.table;
-  p.segf = reinterpret_cast<unsigned int*>(sc.seg);
-  {
-    TraceScope ts(h, K_SWEEP, st);
-    bulk_fn(p.nwt)<<<L.grid, L.threads, L.smem, st>>>(p);
-  }
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return check_cuda(e, "sweep_bulk_kernel launch");
+  rc = launch_sweeps(h, B, sc, st, br);
+  if (rc) return rc;
   {
     TraceScope ts(h, K_SEG_SCAN, st);
-    v3_scan_kernel<<<(unsigned)L.ntiles, kScanThreads, 0, st>>>(
-        reinterpret_cast<const unsigned int*>(sc.seg), p.nseg, sc.seg_off, count, sc.counters,
-        sc.tiles, L.ntiles, stats, scanned);
+    v3_scan_kernel<<<(unsigned)B.ntiles, kScanThreads, 0, st>>>(
+        reinterpret_cast<const unsigned int*>(sc.seg), B.fin.nseg, sc.seg_off, count, sc.counters,
+        sc.tiles, B.ntiles, stats, scanned);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return check_cuda(e, "v3_scan_kernel launch");
   if (capacity > 0 || expand_always) {
+    BulkParams& p = B.fin;
+    p.recs = sc.staging;
+    p.recs_cap = B.recs_need;
+    p.counters = sc.counters;
+    p.table = sc.table;
+    p.segf = reinterpret_cast<unsigned int*>(sc.seg);
     TraceScope ts(h, K_SCATTER, st);
-    v3_expand_kernel<<<(unsigned)L.expand_blocks, 32 * kExpandWarps, 0, st>>>(
+    v3_expand_kernel<<<(unsigned)B.expand_blocks, 32 * kExpandWarps, 0, st>>>(
         p, sc.seg_off, face_ids, winding, capacity, offsets);
     e = cudaGetLastError();
     if (e != cudaSuccess) return check_cuda(e, "v3_expand_kernel launch");
@@ -1101,36 +1188,29 @@ int bulk_launch(qtv_handle h, BulkLayout& L, const IdentScratch& sc, uint64_t* f
   return QTV_OK;
 }
 
-// Sweep alone (autotuning): zeroing and the sweep kernel of one layout.
-int bulk_sweep_only(BulkLayout& L, const IdentScratch& sc, cudaStream_t st) {
-  BulkParams& p = L.p;
-  if (sc.staging_cap < L.recs_need * kRecWords || sc.table_cap < L.table_need ||
-      sc.seg_cap * 2 < (uint64_t)p.nseg)
-    return set_error(QTV_ERR_CAPACITY, "identification scratch too small for this layout");
+// Sweeps alone (autotuning): zeroing and the sweep launches of one layout.
+int batch_sweep_only(qtv_handle h, BatchLayout& B, const IdentScratch& sc, cudaStream_t st,
+                     const SweepBranches* br) {
+  int rc = check_scratch(B, sc, false);
+  if (rc) return rc;
   cudaError_t e = cudaMemsetAsync(sc.counters, 0, 4 * sizeof(unsigned long long), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(sc.seg, 0, p.nseg * sizeof(unsigned int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sc.seg, 0, B.fin.nseg * sizeof(unsigned int), st);
   if (e != cudaSuccess) return check_cuda(e, "cudaMemsetAsync(sweep scratch)");
-  p.recs = sc.staging;
-  p.recs_cap = L.recs_need;
-  p.counters = sc.counters;
-  p.table = sc.table;
-  p.segf = reinterpret_cast<unsigned int*>(sc.seg);
-  bulk_fn(p.nwt)<<<L.grid, L.threads, L.smem, st>>>(p);
-  return check_cuda(cudaGetLastError(), "sweep_bulk_kernel launch");
+  return launch_sweeps(h, B, sc, st, br);
 }
 
 int bulk_needs(int num_sms, const qtv_grid& g, uint64_t capacity, uint64_t max_warps,
                BulkNeeds* n) {
-  BulkLayout L;
+  BatchLayout B;
   // alignment is checked by the caller; sizing needs only a 16-byte aligned stand-in
   const float2* psi = reinterpret_cast<const float2*>(uintptr_t(256));
-  const int rc = bulk_layout(num_sms, 1, &g, &psi, TileConfig(), capacity, max_warps, &L);
+  const int rc = batch_layout(num_sms, 1, &g, &psi, TileConfig(), capacity, max_warps, &B);
   if (rc) return rc;
-  n->recs = L.recs_need * kRecWords;  // staging words
-  n->table = L.table_need;
-  n->seg_off = (unsigned long long)L.p.nseg;
-  n->tiles = (unsigned long long)L.ntiles;
-  n->segf = (unsigned long long)(L.p.nseg + 1) / 2;  // uint2 entries holding nseg u32
+  n->recs = B.recs_need * kRecWords;  // staging words
+  n->table = B.table_need;
+  n->seg_off = (unsigned long long)B.fin.nseg;
+  n->tiles = (unsigned long long)B.ntiles;
+  n->segf = (unsigned long long)(B.fin.nseg + 1) / 2;  // uint2 entries holding nseg u32
   return QTV_OK;
 }
 
@@ -1138,14 +1218,14 @@ int bulk_identify(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* 
                   int8_t* winding, uint64_t capacity, uint64_t* count, qtv_stats* stats,
                   cudaStream_t st, const IdentScratch& sc, uint64_t max_warps, float* xyz,
                   float* resid, uint8_t* flags) {
-  BulkLayout L;
-  int rc = bulk_layout(h->num_sms, 1, &g, &psi, TileConfig(), capacity, max_warps, &L);
+  BatchLayout B;
+  int rc = batch_layout(h->num_sms, 1, &g, &psi, TileConfig(), capacity, max_warps, &B);
   if (rc) return rc;
   const unsigned long long nx = g.nx, ny = g.ny, nz = g.nz;
   const unsigned long long scanned =
       (nx - 1) * (ny - 1) * nz + nx * (ny - 1) * (nz - 1) + (nx - 1) * ny * (nz - 1);
-  rc = bulk_launch(h, L, sc, face_ids, winding, capacity, count, nullptr, stats, scanned, st,
-                   false);
+  rc = batch_launch(h, B, sc, face_ids, winding, capacity, count, nullptr, stats, scanned, st,
+                    false, nullptr);
   if (rc) return rc;
   if (xyz && capacity > 0)
     return localize_launch(h, g, psi, face_ids, winding, capacity, count, xyz, resid, flags, st);

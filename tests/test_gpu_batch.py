@@ -4,8 +4,9 @@ launch, one finalize pass and one localization pass, replayed as a CUDA graph.
 
 * every snapshot's slice of the batch output equals the FP64 oracle bit for
   bit on unambiguous faces (windings) and within 1e-4 h (positions), for each
-  x-tile shape (64 to 1024 columns per tile, various CTAs per SM and z-block
-  heights), shapes pinned through a tune-cache line with the key "*";
+  sweep shape (one tile width of 64 to 1024 columns for all snapshots, or one
+  sweep per row-width group, serial or concurrent; various CTAs per SM and
+  z-block heights), shapes pinned through a tune-cache line with the key "*";
 * the slices equal the single-snapshot calls bit for bit (ids, windings, plain
   and learned positions and flags);
 * capacity overflow reports the total, replays are deterministic, and new data
@@ -49,9 +50,9 @@ def small_batch():
     return hosts, devs
 
 
-def _pin(path, nwt, ctas, zscale):
+def _pin(path, nwt, ctas, zscale, concurrent=0):
     with open(path, "w") as f:
-        f.write(f"qtv-tune-v1 * {nwt} {ctas} {zscale} 0.0\n")
+        f.write(f"qtv-tune-v2 * {nwt} {ctas} {zscale} {concurrent} 0.0\n")
 
 
 def _check_slices(hosts, out):
@@ -76,16 +77,20 @@ def _check_slices(hosts, out):
         assert nbad == 0, f"{nbad} positions off in a {host.shape} snapshot (max {emax})"
 
 
-@pytest.mark.parametrize("shape", [(1, 0, 1.0), (2, 0, 0.5), (4, 2, 1.0), (8, 1, 2.0),
-                                   (16, 0, 1.0), (4, 0, 3.0)])
+@pytest.mark.parametrize("shape", [(1, 0, 1.0, 0), (2, 0, 0.5, 0), (4, 2, 1.0, 0), (8, 1, 2.0, 0),
+                                   (16, 0, 1.0, 0), (4, 0, 3.0, 0), (0, 0, 1.0, 0),
+                                   (0, 0, 1.0, 1), (0, 1, 0.5, 1)])
 def test_small_batch_matches_oracle_for_each_tile_shape(q, small_batch, shape):
     hosts, devs = small_batch
-    nwt, ctas, zs = shape
+    nwt, ctas, zs, conc = shape
     with tempfile.TemporaryDirectory() as d:
         path = os.path.join(d, "tune.txt")
-        _pin(path, nwt, ctas, zs)
+        _pin(path, nwt, ctas, zs, conc)
         info = q.batch_plan(devs, tune_cache=path)
     assert info["source"] == 1 and info["warps_per_tile"] == nwt
+    assert info["concurrent"] == conc
+    # per-snapshot widths: one sweep per distinct row width in warps
+    assert info["sweeps"] == (1 if nwt else len({(s[2] + 63) // 64 for s in SMALL}))
     out = q.batch_run()
     _check_slices(hosts, out)
 
@@ -96,7 +101,7 @@ def test_batch_equals_single_calls(q, small_batch):
     hosts, devs = small_batch
     with tempfile.TemporaryDirectory() as d:
         path = os.path.join(d, "tune.txt")
-        _pin(path, 2, 0, 1.0)
+        _pin(path, 0, 0, 1.0, 1)
         q.batch_plan(devs, tune_cache=path)
     out = q.batch_run()
     q.locator_init(5)
@@ -172,10 +177,10 @@ def test_autotuner_stores_and_reuses_choice(q, small_batch):
         info = q.batch_plan(devs, tune_cache=path)
         assert info["source"] == 2 and info["candidates"] >= 6 and info["tuned_ms"] > 0
         lines = open(path).read().splitlines()
-        assert len(lines) == 1 and lines[0].startswith("qtv-tune-v1 ")
+        assert len(lines) == 1 and lines[0].startswith("qtv-tune-v2 ")
         info2 = q.batch_plan(devs, tune_cache=path)
         assert info2["source"] == 1
-        for k in ("warps_per_tile", "ctas_per_sm", "zscale"):
+        for k in ("warps_per_tile", "ctas_per_sm", "zscale", "concurrent"):
             assert info2[k] == info[k]
 
 
