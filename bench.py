@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--soak", type=float, default=1.5,
                    help="seconds of untimed load before warm-up (clock sampling)")
+    p.add_argument("--sweep-variant", type=int, default=-1,
+                   help="identification sweep: 0 nibble, 1 bit-sliced, -1 library default")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the 16-snapshot batch against per-snapshot launches")
     p.add_argument("--no-learned", action="store_true",
@@ -377,6 +379,7 @@ def run_qtv(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     qtv.build()
     q = qtv.Qtv(dev.index)
+    q.configure_sweep(variant=args.sweep_variant)
     n = args.n
     psi = make_field(n, dev)
     torch.cuda.synchronize()

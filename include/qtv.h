@@ -281,6 +281,18 @@ QTV_API int qtv_locator_save(qtv_handle h, const char* path);
 QTV_API int qtv_locator_load(qtv_handle h, const char* path);
 
 /*
+ * Shape of the identification sweep used by this handle's single-snapshot
+ * calls.  variant 0: nibble sweep (7-row bands, 64 columns per warp, warps
+ * per tile 1..16, 0 = one tile per row); variant 1: bit-sliced sweep (16-row
+ * bands, 31 columns per warp, warps per tile 2, 4 or 8, 0 = 4; stages 2 or 3
+ * shared-memory ring slots, 0 = 3; rows wider than 32 warps of tiles fall back
+ * to variant 0); -1: the library default.  ctas_per_sm caps resident CTAs per
+ * SM (0 = as many as fit).  Both variants give identical results.
+ */
+QTV_API int qtv_configure_sweep(qtv_handle h, int variant, int warps_per_tile, int stages,
+                                int ctas_per_sm);
+
+/*
  * Batches of snapshots.  Identification (Sec. 2.2.2, Eq. 5) and localization
  * (Sec. 3.3.3, Eq. 6) of up to QTV_BATCH_MAX snapshots of different grid
  * sizes in one pass: persistent sweep launches whose CTAs take contiguous
@@ -299,9 +311,10 @@ QTV_API int qtv_locator_load(qtv_handle h, const char* path);
  * timing candidates on these fields, unless tune_cache names a text file that
  * holds a shape for this device and these grid sizes; a newly timed shape is
  * appended to that file (tune_cache may be NULL).  Each line of the file is
- * "qtv-tune-v2 <key> <warps per tile, 0 = per snapshot> <CTAs per SM, 0 =
- * max> <z-block factor> <concurrent 0/1> <ms>"; the last line whose key
- * matches wins, and the key "*" matches every batch (a pinned shape).
+ * "qtv-tune-v3 <key> <variant> <warps per tile, 0 = per snapshot> <CTAs per
+ * SM, 0 = max> <z-block factor> <concurrent 0/1> <stages> <ms>" (variant and
+ * stages as for qtv_configure_sweep); the last line whose key matches wins,
+ * and the key "*" matches every batch (a pinned shape).
  * Synchronizes `stream`.
  *
  * qtv_batch_run: face_ids / winding [capacity] receive the faces of all
@@ -319,10 +332,13 @@ typedef struct {
   uint64_t faces;         /* pierced faces found by the counting pass */
   int32_t warps_per_tile; /* chosen shape: tiles of 64 * warps_per_tile columns for every
                              snapshot, or 0: each snapshot one tile as wide as its row */
-  int32_t tile_columns;   /* 64 * warps_per_tile (0 when per snapshot) */
+  int32_t tile_columns;   /* owned columns per tile: 64 * warps_per_tile (variant 0; 0 when
+                             per snapshot) or 31 * warps_per_tile (variant 1) */
   int32_t ctas_per_sm;    /* cap on resident CTAs per SM (0: as many as fit) */
   float zscale;           /* factor on the z-block height */
   int32_t concurrent;     /* 1: sweeps of the width groups run concurrently */
+  int32_t variant;        /* sweep variant (qtv_configure_sweep) */
+  int32_t stages;         /* ring stages of the bit-sliced sweep */
   int32_t sweeps;         /* sweep launches (width groups) */
   int32_t grid;           /* CTAs of all sweep launches */
   int32_t source;         /* 1: tune cache, 2: timed now */

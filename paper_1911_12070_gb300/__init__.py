@@ -72,7 +72,8 @@ class BatchInfo(ctypes.Structure):
     _fields_ = [("nodes", ctypes.c_uint64), ("faces", ctypes.c_uint64),
                 ("warps_per_tile", ctypes.c_int32), ("tile_columns", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("zscale", ctypes.c_float),
-                ("concurrent", ctypes.c_int32), ("sweeps", ctypes.c_int32),
+                ("concurrent", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("stages", ctypes.c_int32), ("sweeps", ctypes.c_int32),
                 ("grid", ctypes.c_int32), ("source", ctypes.c_int32),
                 ("candidates", ctypes.c_int32), ("tuned_ms", ctypes.c_float)]
 
@@ -128,6 +129,8 @@ def lib() -> ctypes.CDLL:
                      "qtv_locator_forward", "qtv_locator_gradients", "qtv_locator_train_step",
                      "qtv_locator_save", "qtv_locator_load"):
             getattr(L, name).restype = i32
+        L.qtv_configure_sweep.argtypes = [P, i32, i32, i32, i32]
+        L.qtv_configure_sweep.restype = i32
         L.qtv_batch_plan.argtypes = [P, i32, ctypes.POINTER(Grid), ctypes.POINTER(P),
                                      ctypes.c_char_p, P]
         L.qtv_batch_info_get.argtypes = [P, ctypes.POINTER(BatchInfo)]
@@ -190,6 +193,12 @@ class Qtv:
         _check(lib().qtv_trace_read(self.h, buf, 16, ctypes.byref(n), 1 if reset else 0))
         return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
                 for i in range(min(n.value, 16))}
+
+    def configure_sweep(self, variant: int = -1, warps_per_tile: int = 0, stages: int = 0,
+                        ctas_per_sm: int = 0):
+        """Sweep shape of this handle's single-snapshot calls (qtv_configure_sweep)."""
+        _check(lib().qtv_configure_sweep(self.h, int(variant), int(warps_per_tile), int(stages),
+                                         int(ctas_per_sm)))
 
     def reserve(self, shape, max_faces: int):
         g = Grid.of(shape)

@@ -60,7 +60,7 @@ int validate_grid(const qtv_grid* g) {
 int grow_identify(qtv_handle h, const qtv_grid& g, uint64_t capacity, const void* psi,
                   cudaStream_t st) {
   IdentNeeds n;
-  int rc = identify_needs(h->num_sms, g, capacity, psi, 0, &n);
+  int rc = identify_needs(h, h->num_sms, g, capacity, psi, 0, &n);
   if (rc) return rc;
   if (n.staging > 0xFFFFFFFFull)
     return set_error(QTV_ERR_ARG, "staging above 2^32 records is not supported");
@@ -194,6 +194,23 @@ int qtv_destroy(qtv_handle h) {
   }
   for (auto e : h->event_pool) cudaEventDestroy(e);
   delete h;
+  return QTV_OK;
+}
+
+int qtv_configure_sweep(qtv_handle h, int variant, int warps_per_tile, int stages,
+                        int ctas_per_sm) {
+  if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
+  if (variant < -1 || variant > 1) return set_error(QTV_ERR_ARG, "unknown sweep variant %d", variant);
+  if (warps_per_tile < 0 || warps_per_tile > 16 || stages < 0 || stages > 3 || ctas_per_sm < 0)
+    return set_error(QTV_ERR_ARG, "sweep shape out of range");
+  if (variant == 1 && warps_per_tile != 0 && warps_per_tile != 2 && warps_per_tile != 4 &&
+      warps_per_tile != 8)
+    return set_error(QTV_ERR_ARG, "bit-sliced sweep: %d warps per tile (2, 4 or 8)",
+                     warps_per_tile);
+  h->sweep_variant = variant;
+  h->sweep_nwt = warps_per_tile;
+  h->sweep_stages = stages;
+  h->sweep_ctas = ctas_per_sm;
   return QTV_OK;
 }
 

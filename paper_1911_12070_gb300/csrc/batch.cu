@@ -128,7 +128,8 @@ int grow(T** p, uint64_t* cap, uint64_t need, const char* what) {
 }
 
 int ensure_scratch(BatchPlan* b, const BatchLayout& L) {
-  int rc = grow(&b->staging, &b->staging_cap, L.recs_need * 6ull, "cudaMalloc(batch staging)");
+  int rc = grow(&b->staging, &b->staging_cap, L.recs_need * (uint64_t)L.rec_words,
+                "cudaMalloc(batch staging)");
   if (!rc) rc = grow(&b->table, &b->table_cap, L.table_need, "cudaMalloc(batch table)");
   // segment totals are addressed as pairs of u32 by the scratch descriptor
   const uint64_t nseg = ((uint64_t)L.fin.nseg + 1) & ~1ull;
@@ -196,7 +197,7 @@ std::string tune_key(const BatchPlan* b, int device, int num_sms) {
   return k;
 }
 
-constexpr const char* kTuneTag = "qtv-tune-v2";
+constexpr const char* kTuneTag = "qtv-tune-v3";
 
 bool tune_lookup(const char* path, const std::string& key, TileConfig* tc, float* ms) {
   if (!path || !*path) return false;
@@ -206,15 +207,18 @@ bool tune_lookup(const char* path, const std::string& key, TileConfig* tc, float
   bool found = false;
   while (fgets(line, sizeof line, f)) {
     char tag[32], k[3500];
-    int nwt = 0, ctas = 0, conc = 0;
+    int var = 0, nwt = 0, ctas = 0, conc = 0, stages = 3;
     float zs = 0.f, t = 0.f;
-    if (sscanf(line, "%31s %3499s %d %d %f %d %f", tag, k, &nwt, &ctas, &zs, &conc, &t) != 7)
+    if (sscanf(line, "%31s %3499s %d %d %d %f %d %d %f", tag, k, &var, &nwt, &ctas, &zs, &conc,
+               &stages, &t) != 9)
       continue;
     if (strcmp(tag, kTuneTag) != 0 || (key != k && strcmp(k, "*") != 0)) continue;
+    tc->variant = var;
     tc->nwt = nwt;
     tc->ctas_per_sm = ctas;
     tc->zscale = zs;
     tc->concurrent = conc;
+    tc->stages = stages;
     *ms = t;
     found = true;  // the last matching line wins
   }
@@ -226,8 +230,8 @@ void tune_store(const char* path, const std::string& key, const TileConfig& tc, 
   if (!path || !*path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %s %d %d %.3f %d %.6f\n", kTuneTag, key.c_str(), tc.nwt, tc.ctas_per_sm,
-          tc.zscale, tc.concurrent, ms);
+  fprintf(f, "%s %s %d %d %d %.3f %d %d %.6f\n", kTuneTag, key.c_str(), tc.variant, tc.nwt,
+          tc.ctas_per_sm, tc.zscale, tc.concurrent, tc.stages, ms);
   fclose(f);
 }
 
@@ -239,12 +243,14 @@ void tune_store(const char* path, const std::string& key, const TileConfig& tc, 
 int autotune(qtv_handle h, BatchPlan* b, uint64_t faces, cudaStream_t st, TileConfig* best,
              float* best_ms, int* ncand) {
   std::vector<TileConfig> cands;
-  auto add = [&](int nwt, int ctas, float zs, int conc) {
+  auto add = [&](int nwt, int ctas, float zs, int conc, int variant = 0, int stages = 3) {
     TileConfig tc;
     tc.nwt = nwt;
     tc.ctas_per_sm = ctas;
     tc.zscale = zs;
     tc.concurrent = conc;
+    tc.variant = variant;
+    tc.stages = stages;
     BatchLayout L;
     if (batch_layout(h->num_sms, b->n, b->grids.data(), b->psis.data(), tc, faces, 0, &L) ==
         QTV_OK) {
@@ -265,6 +271,17 @@ int autotune(qtv_handle h, BatchPlan* b, uint64_t faces, cudaStream_t st, TileCo
   for (int conc : {0, 1})
     for (int c : {0, 2, 1})
       for (float zs : {0.5f, 1.f, 2.f}) add(0, c, zs, conc);
+  // bit-sliced sweep: one tile width for all snapshots
+  for (int nwt : {2, 4, 8})
+    for (int stages : {2, 3}) {
+      int bps = 0;
+      size_t smem = 0;
+      if (bits_variant_occupancy(nwt, stages, &bps, &smem)) continue;
+      std::vector<int> occ = {bps, std::max(1, bps / 2)};
+      occ.erase(std::unique(occ.begin(), occ.end()), occ.end());
+      for (int c : occ)
+        for (float zs : {1.f, 2.f}) add(nwt, c, zs, 0, 1, stages);
+    }
   if (cands.empty()) return set_error(QTV_ERR_ARG, "no sweep shape fits this batch");
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return check_cuda(cudaGetLastError(), "event");
@@ -414,13 +431,15 @@ int qtv_batch_plan(qtv_handle h, int n, const qtv_grid* grids, const void* const
   b->info.ctas_per_sm = b->tc.ctas_per_sm;
   b->info.zscale = b->tc.zscale;
   b->info.concurrent = b->tc.concurrent;
+  b->info.variant = b->tc.variant;
+  b->info.stages = b->tc.stages;
   BatchLayout L;
   rc = batch_layout(h->num_sms, n, b->grids.data(), b->psis.data(), b->tc, total, 0, &L);
   if (rc) return rc;
   b->info.grid = 0;
   for (const BulkLayout& g : L.groups) b->info.grid += g.grid;
   b->info.sweeps = (int)L.groups.size();
-  b->info.tile_columns = 64 * b->tc.nwt;
+  b->info.tile_columns = b->tc.variant == 1 ? 31 * L.fin.s[0].nwt : 64 * b->tc.nwt;
   return QTV_OK;
 }
 

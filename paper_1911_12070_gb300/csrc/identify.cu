@@ -583,14 +583,14 @@ LaunchShape sweep_shape(int nw, bool vec) {
 
 }  // namespace
 
-int identify_needs(int num_sms, const qtv_grid& g, uint64_t capacity, const void* psi,
-                   uint64_t max_warps, IdentNeeds* n) {
+int identify_needs(qtv_handle h, int num_sms, const qtv_grid& g, uint64_t capacity,
+                   const void* psi, uint64_t max_warps, IdentNeeds* n) {
   *n = IdentNeeds();
   const uint64_t nbands = (uint64_t)(g.ny + R - 1) / R;
   const uint64_t nseg = nbands * (uint64_t)g.nz;
   if (sweep_bulk_supported(g.nx, g.ny, g.nz, psi)) {
     BulkNeeds b;
-    const int rc = bulk_needs(num_sms, g, capacity, max_warps, &b);
+    const int rc = bulk_needs(h, num_sms, g, capacity, max_warps, &b);
     if (rc) return rc;
     n->staging = b.recs;
     n->seg = b.segf;

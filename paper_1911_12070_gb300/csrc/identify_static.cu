@@ -104,7 +104,7 @@ extern "C" int qtv_identify_static(const qtv_grid* grid, const void* psi, uint64
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (nn == 0) return check_cuda(cudaMemsetAsync(count, 0, sizeof(uint64_t), st), "cudaMemsetAsync");
   IdentNeeds need;
-  rc = identify_needs(num_sms, g, capacity, psi, kMaxWarps, &need);
+  rc = identify_needs(nullptr, num_sms, g, capacity, psi, kMaxWarps, &need);
   if (rc) return rc;
   if (need.table > kTableEntries)
     return set_error(QTV_ERR_ARG,

@@ -94,6 +94,8 @@ struct qtv_handle_s {
   std::vector<cudaEvent_t> event_pool;   // free events
   qtv::Locator* loc = nullptr;           // learned locator (weights, Adam state, buffers)
   qtv::BatchPlan* batch = nullptr;       // batch plan, scratch and captured graph
+  // sweep shape of single-snapshot calls (qtv_configure_sweep); -1 / 0 = default
+  int sweep_variant = -1, sweep_nwt = 0, sweep_stages = 0, sweep_ctas = 0;
 };
 
 namespace qtv {
@@ -131,8 +133,8 @@ constexpr int kMaxWarpsX = 32;    // nx <= 64 * 32
 
 // max_warps bounds the resident warps of the staged sweep (0 = no bound); it
 // bounds the staging slack that per-warp record chunks can leave unused.
-int identify_needs(int num_sms, const qtv_grid& g, uint64_t capacity, const void* psi,
-                   uint64_t max_warps, IdentNeeds* n);
+int identify_needs(qtv_handle h, int num_sms, const qtv_grid& g, uint64_t capacity,
+                   const void* psi, uint64_t max_warps, IdentNeeds* n);
 int identify_launch(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* face_ids,
                     int8_t* winding, uint64_t capacity, uint64_t* count, qtv_stats* stats,
                     cudaStream_t st, const IdentScratch& sc, uint64_t max_warps,
@@ -179,11 +181,15 @@ struct BulkParams {
 // fit), a factor on the z-block height, and whether the sweeps of snapshot
 // groups of different tile widths run concurrently (each on a share of the
 // GPU in proportion to its nodes) or one after the other.
+// variant 0: nibble sweep (7-row bands, 64 columns per warp); variant 1:
+// bit-sliced sweep (16-row bands, 31 columns per warp, 2 or 3 ring stages).
 struct TileConfig {
   int nwt = 0;
   int ctas_per_sm = 0;
   float zscale = 1.f;
   int concurrent = 0;
+  int variant = 0;
+  int stages = 3;
 };
 
 // One sweep launch: the snapshots of one group (same warps per tile), units
@@ -200,6 +206,8 @@ struct BatchLayout {
   std::vector<BulkLayout> groups;
   std::vector<int> group_of;
   BulkParams fin;
+  int variant = 0, stages = 3;
+  int rec_words = 6;  // 32-bit words per staged record
   bool concurrent = false;
   int expand_blocks = 1;
   long long ntiles = 0;  // scan tiles
@@ -256,6 +264,13 @@ __device__ __forceinline__ int geo_snapshot(const FaceGeo& G, unsigned long long
 #endif
 
 int bulk_variant_occupancy(int nw, int* ctas_per_sm, size_t* smem);
+// bit-sliced sweep (sweep_bits.cu)
+int bits_variant_occupancy(int nw, int stages, int* ctas_per_sm, size_t* smem);
+void bits_sweep_launch(const BulkParams& p, int grid, int nw, int stages, size_t smem,
+                       cudaStream_t st);
+void bits_expand_launch(const BulkParams& p, int blocks, const unsigned long long* seg_off,
+                        uint64_t* face_ids, int8_t* winding, unsigned long long capacity,
+                        uint64_t* offsets, cudaStream_t st);
 int batch_layout(int num_sms, int nsnap, const qtv_grid* grids, const float2* const* psis,
                  const TileConfig& tc, uint64_t capacity, uint64_t max_warps, BatchLayout* B);
 int batch_launch(qtv_handle h, BatchLayout& B, const IdentScratch& sc, uint64_t* face_ids,
@@ -265,8 +280,8 @@ int batch_launch(qtv_handle h, BatchLayout& B, const IdentScratch& sc, uint64_t*
 int batch_sweep_only(qtv_handle h, BatchLayout& B, const IdentScratch& sc, cudaStream_t st,
                      const SweepBranches* br);
 bool sweep_bulk_supported(int nx, int ny, int nz, const void* psi);
-int bulk_needs(int num_sms, const qtv_grid& g, uint64_t capacity, uint64_t max_warps,
-               BulkNeeds* n);
+int bulk_needs(qtv_handle h, int num_sms, const qtv_grid& g, uint64_t capacity,
+               uint64_t max_warps, BulkNeeds* n);
 int bulk_identify(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* face_ids,
                   int8_t* winding, uint64_t capacity, uint64_t* count, qtv_stats* stats,
                   cudaStream_t st, const IdentScratch& sc, uint64_t max_warps,

@@ -1,0 +1,655 @@
+// sweep_bits.cu -- bit-sliced identification sweep (Sec. 2.2.2, Eq. 5).
+//
+// Decomposition.  A CTA owns a band of 16 rows (+1 halo row) of an x tile and
+// marches z.  Lane l of warp w owns the grid column x = 31 w + l of the tile;
+// lane 31 is the halo column of the warp (the first column of the next warp)
+// and owns no faces, so every quantity of column x + 1 that a lane needs comes
+// from lane l + 1 by a shuffle.  Each lane walks its 17 rows and keeps one bit
+// per row in 32-bit words: the sign bit of Im psi (the half-plane of the node)
+// and the sign bits of the cross products of its x, y and z edges.
+//
+// Edge test.  As in the nibble sweep (sweep_bulk.cu): with s the sign bit of
+// Im psi (IEEE atan2 convention) and n the sign bit of the FP32 FMA value of
+// cross(a, b) = Re a Im b - Im a Re b, the branch-crossing integer of edge
+// a -> b is +1 when s_a = 0, s_b = 1, n = 0, and -1 when s_a = 1, s_b = 0,
+// n = 1, else 0.  Per word of 17 rows: P = ~s_a & s_b & ~n, N = s_a & ~s_b &
+// n, and Z = P | N.
+//
+// Plaquette sums.  W = r1 + r2 - r3 - r4 lies in {-1, 0, 1, 2} (four wrapped
+// differences in (-pi, pi] add to a multiple of 2 pi in (-4 pi, 4 pi]), so W
+// is fixed by W mod 4.  A term t = +-r has the 2-bit code (Z, N) for +r and
+// (Z, P) for -r (1 = 01, -1 = 11); the sum of four codes mod 4 has low bit
+// L = xor of the four Z and high bit H = xor of the four high bits xor the
+// parity of the pairs of Z (the carry), so W = 1, 2, -1 for (L, H) = (1, 0),
+// (0, 1), (1, 1).  Each orientation takes nine 3-input logic operations for
+// 16 rows.
+//
+// Zero and non-finite nodes.  A warp-uniform test per plane (a packed FP32x2
+// product of the Re and Im values, zero if a component of a node is, or
+// non-finite) selects a path that builds zero-node bits (their edges count 0:
+// phase 0) and non-finite bits (their faces are dropped).  Padding holds
+// (1, 1), finite with nonzero components.
+//
+// Staging.  Planes of the band arrive by cp.async.bulk row copies (one per row,
+// issued by the lanes of warp 0) into a ring of shared-memory slots with a
+// "full" mbarrier (transaction bytes) and an "empty" mbarrier (one arrival per
+// warp after it has read the slot) per slot, so warps are not held in lockstep.
+// A lane keeps the 17 values of plane k in registers while it reads plane
+// k + 1.  Waits are bounded (about 2^32 SM cycles); a timeout sets a status
+// bit that turns the reported count into QTV_COUNT_TIMEOUT.
+//
+// Compaction and finalize.  Each lane with faces in a plane writes one 16-byte
+// record (L and H words of the three orientations, 16 rows each, and the lane)
+// into per-warp chunks of the staging buffer, with a table entry per (plane,
+// band, tile, warp) and a face total per (plane, band) segment; the scan of the
+// nibble sweep gives segment offsets, and the expand pass below writes faces in
+// ascending face-id order (row, then x, then orientation).
+#include <algorithm>
+
+#include "qtv_internal.cuh"
+#include "sweep_common.cuh"
+
+namespace qtv {
+namespace {
+
+using namespace sweep;
+
+constexpr int BR = 16;            // owned rows per band
+constexpr int BRH = BR + 1;       // plus the halo row
+constexpr int BL = 31;            // owned columns per warp
+constexpr uint32_t kChunk = 32;   // records per staging chunk
+constexpr uint32_t kLowWater = 12;
+constexpr uint32_t kRows16 = 0xFFFFu;
+
+// acc' = (acc << 1) | sign bit of x
+__device__ __forceinline__ uint32_t push1(uint32_t acc, float x) {
+  return __funnelshift_l(__float_as_uint(x), acc, 1);
+}
+
+struct Edge {
+  uint32_t P, N, Z;
+};
+
+// edges a -> b from the sign words of a and b, the cross-sign word n, and the
+// edges E that touch a zero node (contribute 0)
+__device__ __forceinline__ Edge edge_words(uint32_t sa, uint32_t sb, uint32_t n, uint32_t E) {
+  Edge e;
+  e.P = ~sa & sb & ~n & ~E;
+  e.N = sa & ~sb & n & ~E;
+  e.Z = e.P | e.N;
+  return e;
+}
+
+__device__ __forceinline__ Edge edge_words(uint32_t sa, uint32_t sb, uint32_t n) {
+  Edge e;
+  e.P = ~sa & sb & ~n;
+  e.N = sa & ~sb & n;
+  e.Z = e.P | e.N;
+  return e;
+}
+
+// packed product of the (Re, Im) values of a plane: zero when a component of
+// a node is zero, non-finite when a node is (or on FP32 under- or overflow,
+// which merely selects the masking path)
+__device__ __forceinline__ unsigned long long prod_step(unsigned long long acc, float2 v) {
+  return mul_f32x2(acc, (unsigned long long)__float_as_uint(v.x) |
+                            ((unsigned long long)__float_as_uint(v.y) << 32));
+}
+__device__ __forceinline__ bool prod_special(unsigned long long acc) {
+  const float px = fabsf(__uint_as_float((uint32_t)acc)), py = fabsf(__uint_as_float((uint32_t)(acc >> 32)));
+  return !(px > 0.f && px <= 3.402823466e38f && py > 0.f && py <= 3.402823466e38f);
+}
+constexpr unsigned long long kProdOne = 0x3f8000003f800000ull;  // (1.f, 1.f)
+
+// sum mod 4 of four terms given as (low, high) bit words
+__device__ __forceinline__ void mod4(uint32_t a, uint32_t a1, uint32_t b, uint32_t b1, uint32_t c,
+                                     uint32_t c1, uint32_t d, uint32_t d1, uint32_t& L,
+                                     uint32_t& H) {
+  const uint32_t x = a ^ b, y = c ^ d;
+  L = x ^ y;
+  const uint32_t e2 = (a & b) ^ (c & d) ^ (x & y);
+  H = a1 ^ b1 ^ c1 ^ d1 ^ e2;
+}
+
+__device__ __forceinline__ uint32_t zero_bit(float2 v) {
+  return ((__float_as_uint(v.x) | __float_as_uint(v.y)) << 1) == 0u ? 1u : 0u;
+}
+__device__ __forceinline__ uint32_t bad_bit(float2 v) {
+  return (finite_f(v.x) && finite_f(v.y)) ? 0u : 1u;
+}
+
+template <int NW, int MINB, int STAGES>
+__global__ void __launch_bounds__(NW * 32, MINB) sweep_bits_kernel(const __grid_constant__ BulkParams a) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int w = tid >> 5;
+  constexpr int W2 = BL * NW + 2;  // row pitch of a slot, in elements
+  float2* ring = reinterpret_cast<float2*>(dsm);
+  uint64_t* full = reinterpret_cast<uint64_t*>(dsm + (size_t)STAGES * BRH * W2 * sizeof(float2));
+  uint64_t* empty = full + STAGES;
+  const int xl = BL * w + lane;  // tile-local column of this lane
+  const uint32_t lt = (1u << lane) - 1u;
+
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1u);
+      mbar_init(&empty[s], (uint32_t)NW);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  uint32_t fill = 0, use = 0;  // planes issued (warp 0) / consumed, counted over the whole CTA
+  bool timeout = false;
+  uint32_t cb = 0, cl = 0, nb_l0 = 0;
+  bool have_next = false;
+  bool overflow = false;
+  int valid_w = W2, valid_r = BRH;  // padding bookkeeping, as in the nibble sweep
+
+  const long long U = a.units;
+  long long u = U * blockIdx.x / gridDim.x;
+  const long long uend = U * (blockIdx.x + 1) / gridDim.x;
+
+  while (u < uend) {
+    int si = 0;
+    while (si + 1 < a.nsnap && a.s[si + 1].unit0 <= u) ++si;
+    const SnapDesc& sd = a.s[si];
+    const int nx = sd.nx, ny = sd.ny, nz = sd.nz, ntx = sd.ntx;
+    long long col;
+    int kb, kblk;
+    unit_pos(u - sd.unit0, (long long)sd.nbands * ntx, nz, sd.hblock, col, kb, kblk);
+    const int band = (int)(col / ntx), tile = (int)(col % ntx);
+    const int ke = (int)min((long long)kblk, (long long)kb + (uend - u));
+    u += ke - kb;
+    const int j0 = band * BR;
+    const int nrows = min(BRH, ny - j0);
+    const int klast = min(ke, nz - 1);
+    const int nplanes = klast - kb + 1;
+    const int nsteps = ke - kb;
+    const int xt0 = tile * sd.st;
+    const bool last_tile = tile == ntx - 1;
+    const int tw = last_tile ? nx - xt0 : sd.st + 2;
+    const int own_end = last_tile ? tw : sd.st;
+    const uint32_t row_bytes = (uint32_t)tw * 8u;
+    const size_t plane = (size_t)nx * ny;
+
+    if (tw < valid_w || nrows < valid_r) {
+      const int cw = valid_w - tw;
+      if (cw > 0)
+        for (int idx = tid; idx < STAGES * BRH * cw; idx += blockDim.x)
+          ring[(size_t)(idx / cw) * W2 + tw + idx % cw] = make_float2(1.f, 1.f);
+      const int rr = valid_r - nrows;
+      if (rr > 0) {
+        const int per = rr * W2;
+        for (int idx = tid; idx < STAGES * per; idx += blockDim.x) {
+          const int sl = idx / per, rem = idx % per;
+          ring[((size_t)sl * BRH + nrows + rem / W2) * W2 + rem % W2] = make_float2(1.f, 1.f);
+        }
+      }
+      fence_proxy_async();
+      __syncthreads();
+    }
+    valid_w = tw;
+    valid_r = nrows;
+
+    // warp 0: plane m into the next slot once every warp has released it
+    auto produce = [&](int m) {
+      const uint32_t q = fill;
+      const int sl = (int)(q % STAGES);
+      if (q >= (uint32_t)STAGES && !mbar_wait(&empty[sl], ((q / STAGES) - 1u) & 1u)) timeout = true;
+      if (lane == 0) {
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&full[sl], row_bytes * (uint32_t)nrows);
+      }
+      __syncwarp();
+      if (lane < nrows)
+        bulk_g2s(ring + ((size_t)sl * BRH + lane) * W2,
+                 sd.psi + (size_t)m * plane + (size_t)(j0 + lane) * nx + xt0, row_bytes, &full[sl]);
+      ++fill;
+    };
+    auto acquire = [&]() -> const float2* {
+      const int sl = (int)(use % STAGES);
+      if (!mbar_wait(&full[sl], (use / STAGES) & 1u)) timeout = true;
+      return ring + (size_t)sl * BRH * W2;
+    };
+    auto release = [&]() {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[use % STAGES]);
+      ++use;
+    };
+
+    // masks of the faces this lane owns (rows 0..15 of the band)
+    const int avail = ny - j0;  // rows of the band that exist
+    const uint32_t rv = avail >= BR ? kRows16 : ((1u << avail) - 1u);
+    const uint32_t rv1 = avail - 1 >= BR ? kRows16 : (avail > 1 ? ((1u << (avail - 1)) - 1u) : 0u);
+    const bool own = lane < BL && xl < own_end;
+    const uint32_t m_xy = (own && xl + 1 < tw) ? rv1 : 0u;
+    const uint32_t m_yz = (own && xl < tw) ? rv1 : 0u;
+    const uint32_t m_zx = (own && xl + 1 < tw) ? rv : 0u;
+    const unsigned long long tstride = (unsigned long long)sd.nbands * ntx * NW;
+    const unsigned long long tbase =
+        (unsigned long long)sd.tab0 + ((unsigned long long)band * ntx + tile) * NW + w;
+    unsigned int* const segf = a.segf + sd.seg0 + band;
+    const unsigned sstride = (unsigned)sd.nbands;
+
+    if (w == 0)
+      for (int i = 0; i < min(STAGES, nplanes); ++i) produce(kb + i);
+
+    // ---- prologue: plane kb (values into vA)
+    float2 vA[BRH], vB[BRH];
+    uint32_t S0, S0n, ZB0 = 0, ZB0n = 0, BB0 = 0, BB0n = 0;
+    Edge X0, Y0, Y0n;
+    bool bad0;
+    {
+      const float2* sp = acquire();
+      uint32_t SX = 0, SY = 0;
+      unsigned long long prod = kProdOne;
+      S0 = 0;
+#pragma unroll
+      for (int r = BRH - 1; r >= 0; --r) {
+        const float2 v = sp[r * W2 + xl];
+        const float2 nb = sp[r * W2 + xl + 1];
+        S0 = push1(S0, v.y);
+        SX = push1(SX, cross_f(v.x, v.y, nb.x, nb.y));
+        if (r < BR) SY = push1(SY, cross_f(v.x, v.y, vA[r + 1].x, vA[r + 1].y));
+        prod = prod_step(prod, v);
+        vA[r] = v;
+      }
+      release();
+      if (w == 0 && kb + STAGES <= klast) produce(kb + STAGES);
+      bad0 = __any_sync(0xffffffffu, prod_special(prod));
+      if (bad0) {
+#pragma unroll
+        for (int r = 0; r < BRH; ++r) {
+          ZB0 |= zero_bit(vA[r]) << r;
+          BB0 |= bad_bit(vA[r]) << r;
+        }
+      }
+      S0n = __shfl_down_sync(0xffffffffu, S0, 1);
+      const uint32_t SYn = __shfl_down_sync(0xffffffffu, SY, 1);
+      ZB0n = __shfl_down_sync(0xffffffffu, ZB0, 1);
+      BB0n = __shfl_down_sync(0xffffffffu, BB0, 1);
+      X0 = edge_words(S0, S0n, SX, ZB0 | ZB0n);
+      Y0 = edge_words(S0, S0 >> 1, SY, ZB0 | (ZB0 >> 1));
+      Y0n = edge_words(S0n, S0n >> 1, SYn, ZB0n | (ZB0n >> 1));
+    }
+
+    // one z step: plane k = kb + t in V0 (values) and the plane-k words,
+    // plane k + 1 read into V1
+    auto step = [&](float2(&V0)[BRH], float2(&V1)[BRH], int t) {
+      const int k = kb + t;
+      const bool has_up = k + 1 < nz;
+      uint32_t Lxy, Hxy, Lyz = 0, Hyz = 0, Lzx = 0, Hzx = 0;
+      // xy faces of plane k: +x(r), +y_{x+1}(r), -x(r+1), -y_x(r)
+      mod4(X0.Z, X0.N, Y0n.Z, Y0n.N, X0.Z >> 1, X0.P >> 1, Y0.Z, Y0.P, Lxy, Hxy);
+      uint32_t Mxy = (Lxy | Hxy) & m_xy, Myz = 0, Mzx = 0;
+      uint32_t S1 = 0, S1n = 0, ZB1 = 0, ZB1n = 0, BB1 = 0, BB1n = 0;
+      Edge X1{0, 0, 0}, Y1{0, 0, 0}, Y1n{0, 0, 0};
+      bool bad1 = false;
+      if (has_up) {
+        const float2* sp = acquire();
+        uint32_t SX = 0, SY = 0, SZ = 0;
+        unsigned long long prod = kProdOne;
+#pragma unroll
+        for (int r = BRH - 1; r >= 0; --r) {
+          const float2 v = sp[r * W2 + xl];
+          const float2 nb = sp[r * W2 + xl + 1];
+          S1 = push1(S1, v.y);
+          SX = push1(SX, cross_f(v.x, v.y, nb.x, nb.y));
+          SZ = push1(SZ, cross_f(V0[r].x, V0[r].y, v.x, v.y));
+          if (r < BR) SY = push1(SY, cross_f(v.x, v.y, V1[r + 1].x, V1[r + 1].y));
+          prod = prod_step(prod, v);
+          V1[r] = v;
+        }
+        release();
+        if (w == 0 && k + 1 + STAGES <= klast) produce(k + 1 + STAGES);
+        bad1 = __any_sync(0xffffffffu, prod_special(prod));
+        S1n = __shfl_down_sync(0xffffffffu, S1, 1);
+        const uint32_t SYn = __shfl_down_sync(0xffffffffu, SY, 1);
+        const uint32_t SZn = __shfl_down_sync(0xffffffffu, SZ, 1);
+        Edge Zk, Zkn;
+        if (bad0 || bad1) {
+          if (bad1) {
+#pragma unroll
+            for (int r = 0; r < BRH; ++r) {
+              ZB1 |= zero_bit(V1[r]) << r;
+              BB1 |= bad_bit(V1[r]) << r;
+            }
+          }
+          ZB1n = __shfl_down_sync(0xffffffffu, ZB1, 1);
+          BB1n = __shfl_down_sync(0xffffffffu, BB1, 1);
+          X1 = edge_words(S1, S1n, SX, ZB1 | ZB1n);
+          Y1 = edge_words(S1, S1 >> 1, SY, ZB1 | (ZB1 >> 1));
+          Y1n = edge_words(S1n, S1n >> 1, SYn, ZB1n | (ZB1n >> 1));
+          Zk = edge_words(S0, S1, SZ, ZB0 | ZB1);
+          Zkn = edge_words(S0n, S1n, SZn, ZB0n | ZB1n);
+        } else {
+          X1 = edge_words(S1, S1n, SX);
+          Y1 = edge_words(S1, S1 >> 1, SY);
+          Y1n = edge_words(S1n, S1n >> 1, SYn);
+          Zk = edge_words(S0, S1, SZ);
+          Zkn = edge_words(S0n, S1n, SZn);
+        }
+        // yz faces of plane k: +y_k(r), +z(r+1), -y_{k+1}(r), -z(r)
+        mod4(Y0.Z, Y0.N, Zk.Z >> 1, Zk.N >> 1, Y1.Z, Y1.P, Zk.Z, Zk.P, Lyz, Hyz);
+        // zx faces of plane k: +z_x(r), +x_{k+1}(r), -z_{x+1}(r), -x_k(r)
+        mod4(Zk.Z, Zk.N, X1.Z, X1.N, Zkn.Z, Zkn.P, X0.Z, X0.P, Lzx, Hzx);
+        Myz = (Lyz | Hyz) & m_yz;
+        Mzx = (Lzx | Hzx) & m_zx;
+      }
+      if (bad0 || bad1) {  // drop faces that touch a non-finite node
+        Mxy &= ~(BB0 | BB0n | (BB0 >> 1) | (BB0n >> 1));
+        Myz &= ~(BB0 | (BB0 >> 1) | BB1 | (BB1 >> 1));
+        Mzx &= ~(BB0 | BB0n | BB1 | BB1n);
+      }
+      Lxy &= Mxy;
+      Hxy &= Mxy;
+      Lyz &= Myz;
+      Hyz &= Myz;
+      Lzx &= Mzx;
+      Hzx &= Mzx;
+      const uint32_t cnt = __popc(Mxy) + __popc(Myz) + __popc(Mzx);
+      const bool anyf = cnt != 0u;
+
+      // ---- per-warp compaction: one record per lane with faces
+      const uint32_t faces_w = __reduce_add_sync(0xffffffffu, cnt);
+      const uint32_t bal = __ballot_sync(0xffffffffu, anyf);
+      const uint32_t T = __popc(bal);
+      uint32_t base1 = cb, base2 = 0, n1 = T;
+      if (T > cl) {
+        const uint32_t need = T - cl;
+        uint32_t nbase, ncap;
+        if (have_next && need <= kChunk) {
+          nbase = __shfl_sync(0xffffffffu, nb_l0, 0);
+          ncap = kChunk;
+          have_next = false;
+        } else {
+          ncap = need > kChunk ? need : kChunk;
+          uint32_t x = 0;
+          if (lane == 0) {
+            const unsigned long long got = atomicAdd(a.counters, (unsigned long long)ncap);
+            x = (uint32_t)got;
+            if (got + ncap > a.recs_cap) overflow = true;
+          }
+          nbase = __shfl_sync(0xffffffffu, x, 0);
+        }
+        n1 = cl;
+        base2 = nbase;
+        cb = nbase + need;
+        cl = ncap - need;
+      } else {
+        cb += T;
+        cl -= T;
+      }
+      if (cl < kLowWater && !have_next) {
+        if (lane == 0) {
+          const unsigned long long got = atomicAdd(a.counters, (unsigned long long)kChunk);
+          nb_l0 = (uint32_t)got;
+          if (got + kChunk > a.recs_cap) overflow = true;
+        }
+        have_next = true;
+      }
+      if (lane == 0) {
+        a.table[tbase + (unsigned long long)k * tstride] =
+            make_uint4(base1, base2, T | (n1 << 6) | (faces_w << 12), 0u);
+        if (faces_w) atomicAdd(&segf[(size_t)k * sstride], faces_w);
+      }
+      if (anyf) {
+        const uint32_t q = __popc(bal & lt);
+        const unsigned long long idx =
+            q < n1 ? (unsigned long long)base1 + q : (unsigned long long)base2 + (q - n1);
+        if (idx < a.recs_cap)
+          reinterpret_cast<uint4*>(a.recs)[idx] =
+              make_uint4(Lxy | (Hxy << 16), Lyz | (Hyz << 16), Lzx | (Hzx << 16), (uint32_t)lane);
+      }
+      // plane k + 1 becomes plane k
+      S0 = S1;
+      S0n = S1n;
+      ZB0 = ZB1;
+      ZB0n = ZB1n;
+      BB0 = BB1;
+      BB0n = BB1n;
+      X0 = X1;
+      Y0 = Y1;
+      Y0n = Y1n;
+      bad0 = bad1;
+    };
+
+    for (int t = 0; t < nsteps; t += 2) {
+      step(vA, vB, t);
+      if (t + 1 < nsteps) step(vB, vA, t + 1);
+    }
+    __syncthreads();
+  }
+  if (timeout) atomicOr(reinterpret_cast<unsigned int*>(a.counters + 1), 1u);
+  if (overflow) atomicOr(reinterpret_cast<unsigned int*>(a.counters + 1), 2u);
+}
+
+// ---------------------------------------------------------------------------
+// Expand: one warp per (snapshot, plane, band) segment writes its faces in
+// ascending face-id order: row by row, within a row by x (tile, warp, lane
+// order of the records), within a node by orientation.
+// ---------------------------------------------------------------------------
+constexpr int kExpandWarps = 8;
+
+// bits 4q..4q+3 of m spread to the low bit of bytes 0..3
+__device__ __forceinline__ uint32_t spread4(uint32_t m, int q) {
+  return (((m >> (4 * q)) & 0xFu) * 0x00204081u) & 0x01010101u;
+}
+
+__global__ void __launch_bounds__(32 * kExpandWarps, 4) expand_bits_kernel(
+    const __grid_constant__ BulkParams a, const unsigned long long* __restrict__ seg_off,
+    uint64_t* __restrict__ face_ids, int8_t* __restrict__ winding, unsigned long long capacity,
+    uint64_t* __restrict__ offsets) {
+  __shared__ uint32_t s_rowbase[kExpandWarps][BR];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const uint4* __restrict__ table = a.table;
+  const uint4* __restrict__ recs = reinterpret_cast<const uint4*>(a.recs);
+  const unsigned long long recs_cap = a.recs_cap;
+  const long long nseg = a.nseg;
+  if (offsets && blockIdx.x == 0 && threadIdx.x < (unsigned)a.nsnap)
+    offsets[threadIdx.x] = a.s[threadIdx.x].seg0 < nseg ? seg_off[a.s[threadIdx.x].seg0] : 0ull;
+  if (capacity == 0) return;
+  const long long nwarps = (long long)gridDim.x * kExpandWarps;
+  auto locate = [&](long long sg, int& si, long long& local, int& NWs) {
+    si = 0;
+    while (si + 1 < a.nsnap && a.s[si + 1].seg0 <= sg) ++si;
+    local = sg - a.s[si].seg0;
+    NWs = a.s[si].ntx * a.s[si].nwt;
+  };
+  for (long long s = (long long)blockIdx.x * kExpandWarps + wib; s < nseg; s += nwarps) {
+    int si, NW;
+    long long local;
+    locate(s, si, local, NW);
+    const SnapDesc& sd = a.s[si];
+    uint4 e = make_uint4(0u, 0u, 0u, 0u);
+    if (lane < NW) e = table[sd.tab0 + local * NW + lane];
+    const uint32_t n = e.z & 63u, n1 = (e.z >> 6) & 63u;
+    uint32_t incl = n;
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+      const uint32_t x = __shfl_up_sync(0xffffffffu, incl, dd);
+      if (lane >= dd) incl += x;
+    }
+    const uint32_t start = lane < NW ? incl - n : 0xFFFFFFFFu;
+    const uint32_t rtot = __shfl_sync(0xffffffffu, incl, 31);
+    if (rtot == 0) continue;
+    const unsigned long long fbase = seg_off[s];
+    const int nbands = sd.nbands;
+    const unsigned long long nx = (unsigned)sd.nx, ny = (unsigned)sd.ny;
+    const long long k = local / nbands;
+    const long long j0 = (local % nbands) * BR;
+    const int nwt = sd.nwt;
+    const uint32_t nchunks = (rtot + 31) / 32;
+
+    // record of flattened index g = g0 + lane (zero past the end); ww = its warp
+    auto load = [&](uint32_t g0, uint4& rec, int& ww) {
+      const uint32_t g = g0 + lane;
+      int lo = 0;
+#pragma unroll
+      for (int stp = 16; stp >= 1; stp >>= 1) {
+        const int cand = lo + stp;
+        const uint32_t sv = __shfl_sync(0xffffffffu, start, cand & 31);
+        if (cand < NW && sv <= g) lo = cand;
+      }
+      ww = lo;
+      const uint32_t qi = g - __shfl_sync(0xffffffffu, start, lo);
+      const uint32_t b1 = __shfl_sync(0xffffffffu, e.x, lo);
+      const uint32_t b2 = __shfl_sync(0xffffffffu, e.y, lo);
+      const uint32_t m1 = __shfl_sync(0xffffffffu, n1, lo);
+      const unsigned long long idx =
+          qi < m1 ? (unsigned long long)b1 + qi : (unsigned long long)b2 + (qi - m1);
+      rec = make_uint4(0u, 0u, 0u, 0u);
+      if (g < rtot && idx < recs_cap) rec = recs[idx];
+    };
+    // per-row face counts of a record, 4 rows per word (one byte each)
+    auto counts = [&](const uint4& rec, uint32_t* cw) {
+      const uint32_t mx = (rec.x | (rec.x >> 16)) & kRows16;
+      const uint32_t my = (rec.y | (rec.y >> 16)) & kRows16;
+      const uint32_t mz = (rec.z | (rec.z >> 16)) & kRows16;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cw[q] = spread4(mx, q) + spread4(my, q) + spread4(mz, q);
+    };
+    auto scan4 = [&](const uint32_t* cw, uint32_t* ex, uint32_t* tot) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t v = cw[q];
+#pragma unroll
+        for (int dd = 1; dd < 32; dd <<= 1) {
+          const uint32_t x = __shfl_up_sync(0xffffffffu, v, dd);
+          if (lane >= dd) v += x;
+        }
+        ex[q] = v - cw[q];
+        tot[q] = __shfl_sync(0xffffffffu, v, 31);
+      }
+    };
+    auto byte_of = [](const uint32_t* wv, int r) -> uint32_t {
+      return (wv[r >> 2] >> (8 * (r & 3))) & 0xFFu;
+    };
+
+    uint32_t rowbase[BR];
+    {
+      uint32_t rowtot[BR];
+#pragma unroll
+      for (int r = 0; r < BR; ++r) rowtot[r] = 0;
+      for (uint32_t c = 0; c < nchunks; ++c) {
+        uint4 rec;
+        int ww;
+        load(c * 32, rec, ww);
+        uint32_t cw[4], ex[4], tot[4];
+        counts(rec, cw);
+        scan4(cw, ex, tot);
+#pragma unroll
+        for (int r = 0; r < BR; ++r) rowtot[r] += byte_of(tot, r);
+      }
+      uint32_t acc = 0;
+#pragma unroll
+      for (int r = 0; r < BR; ++r) {
+        rowbase[r] = acc;
+        acc += rowtot[r];
+      }
+    }
+    for (uint32_t c = 0; c < nchunks; ++c) {
+      uint4 rec;
+      int ww;
+      load(c * 32, rec, ww);
+      uint32_t cw[4], ex[4], tot[4];
+      counts(rec, cw);
+      scan4(cw, ex, tot);
+      const uint32_t mx = (rec.x | (rec.x >> 16)) & kRows16;
+      const uint32_t my = (rec.y | (rec.y >> 16)) & kRows16;
+      const uint32_t mz = (rec.z | (rec.z >> 16)) & kRows16;
+      const uint32_t rows = mx | my | mz;
+      if (rows) {
+#pragma unroll
+        for (int r = 0; r < BR; ++r) s_rowbase[wib][r] = rowbase[r];
+        // column of the record: tile ww / nwt at tile * st, warp ww % nwt of
+        // the tile at 31 columns each, lane in the record
+        const unsigned tile = (unsigned)ww / (unsigned)nwt;
+        const unsigned long long x = (unsigned long long)tile * (unsigned)sd.st +
+                                     (unsigned long long)BL * ((unsigned)ww - tile * (unsigned)nwt) +
+                                     (rec.w & 31u);
+        uint32_t rm = rows;
+        while (rm) {
+          const int r = __ffs(rm) - 1;
+          rm &= rm - 1u;
+          unsigned long long pos = fbase + s_rowbase[wib][r] + byte_of(ex, r);
+          const unsigned long long lin = ((unsigned long long)k * ny + (unsigned long long)(j0 + r)) * nx + x;
+          const uint32_t Ls[3] = {rec.x, rec.y, rec.z};
+#pragma unroll
+          for (int o = 0; o < 3; ++o) {
+            const uint32_t L = (Ls[o] >> r) & 1u, H = (Ls[o] >> (16 + r)) & 1u;
+            if (L | H) {
+              if (pos < capacity) {
+                face_ids[pos] = (lin << 2) | (unsigned)o;
+                winding[pos] = (int8_t)(L ? (H ? -1 : 1) : 2);
+              }
+              ++pos;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < BR; ++r) rowbase[r] += byte_of(tot, r);
+    }
+  }
+}
+
+using BitsFn = void (*)(BulkParams);
+
+template <int STAGES>
+BitsFn bits_fn_stages(int nw) {
+  if (nw <= 2) return sweep_bits_kernel<2, 8, STAGES>;
+  if (nw <= 4) return sweep_bits_kernel<4, 4, STAGES>;
+  return sweep_bits_kernel<8, 2, STAGES>;
+}
+
+BitsFn bits_fn(int nw, int stages) {
+  return stages <= 2 ? bits_fn_stages<2>(nw) : bits_fn_stages<3>(nw);
+}
+
+int bits_fn_index(int nw, int stages) {
+  return (nw <= 2 ? 0 : (nw <= 4 ? 1 : 2)) + (stages <= 2 ? 0 : 3);
+}
+
+}  // namespace
+
+size_t bits_smem_bytes(int nw, int stages) {
+  return (size_t)stages * BRH * (BL * nw + 2) * sizeof(float2) + 2 * stages * sizeof(uint64_t);
+}
+
+int bits_variant_occupancy(int nw, int stages, int* ctas_per_sm, size_t* smem) {
+  static bool attr_set[6] = {false, false, false, false, false, false};
+  if (nw != 2 && nw != 4 && nw != 8)
+    return set_error(QTV_ERR_ARG, "bit-sliced sweep: %d warps per tile (2, 4 or 8)", nw);
+  const int which = bits_fn_index(nw, stages);
+  BitsFn fn = bits_fn(nw, stages);
+  if (!attr_set[which]) {
+    cudaError_t e =
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return check_cuda(e, "cudaFuncSetAttribute(sweep_bits)");
+    attr_set[which] = true;
+  }
+  *smem = bits_smem_bytes(nw, stages);
+  int bps = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, nw * 32, *smem);
+  if (e != cudaSuccess) return check_cuda(e, "occupancy(sweep_bits)");
+  if (bps < 1) return set_error(QTV_ERR_ARG, "sweep_bits: no resident CTA with %d warps", nw);
+  *ctas_per_sm = bps;
+  return QTV_OK;
+}
+
+void bits_sweep_launch(const BulkParams& p, int grid, int nw, int stages, size_t smem,
+                       cudaStream_t st) {
+  bits_fn(nw, stages)<<<grid, nw * 32, smem, st>>>(p);
+}
+
+void bits_expand_launch(const BulkParams& p, int blocks, const unsigned long long* seg_off,
+                        uint64_t* face_ids, int8_t* winding, unsigned long long capacity,
+                        uint64_t* offsets, cudaStream_t st) {
+  expand_bits_kernel<<<blocks, 32 * kExpandWarps, 0, st>>>(p, seg_off, face_ids, winding,
+                                                           capacity, offsets);
+}
+
+}  // namespace qtv

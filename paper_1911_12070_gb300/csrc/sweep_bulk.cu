@@ -52,9 +52,12 @@
 #include <algorithm>
 
 #include "qtv_internal.cuh"
+#include "sweep_common.cuh"
 
 namespace qtv {
 namespace {
+
+using namespace sweep;
 
 constexpr int R = kRows;
 constexpr int RH = R + 1;
@@ -69,68 +72,6 @@ __device__ __forceinline__ uint32_t nz_fields(uint32_t d) {
   uint32_t t = d | (d >> 2);
   t = t | (t >> 1);
   return t & kOnes;
-}
-
-__device__ __forceinline__ bool finite_f(float v) { return fabsf(v) <= 3.402823466e38f; }
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
-                                         uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n"
-      " .reg .pred p;\n"
-      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n"
-      "}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait for the phase with the given parity; false after ~2^32 cycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > (1ll << 32)) return false;
-  }
-  return true;
-}
-
-__device__ __forceinline__ float cross_f(float ar, float ai, float br, float bi) {
-  return fmaf(ar, bi, -(ai * br));
 }
 
 // acc' = (acc << 4) | top nibble of x: the sign bit of x lands in bit 3 of a
@@ -259,28 +200,6 @@ __device__ __forceinline__ bool plane_special(const float4* v, const float2* nbv
     prod *= (fabsf(v[r].x) + fabsf(v[r].y)) * (fabsf(v[r].z) + fabsf(v[r].w)) *
             (fabsf(nbv[r].x) + fabsf(nbv[r].y));
   return !(prod > 0.f && prod <= 3.402823466e38f);
-}
-
-// unit u of one snapshot's (z block, band, tile, plane) order -> column
-// (band * ntx + tile), plane, end of its z block
-__device__ __forceinline__ void unit_pos(long long u, long long cols, int nz, int H, long long& col,
-                                         int& k, int& kend) {
-  const long long full = nz / H;
-  const long long per_full = cols * H;
-  long long zb, rem;
-  int h;
-  if (u < full * per_full) {
-    zb = u / per_full;
-    rem = u % per_full;
-    h = H;
-  } else {
-    zb = full;
-    rem = u - full * per_full;
-    h = nz - (int)full * H;
-  }
-  col = rem / h;
-  k = (int)zb * H + (int)(rem % h);
-  kend = (int)zb * H + h;
 }
 
 template <int MAXT, int MINB>
@@ -995,6 +914,15 @@ int batch_layout(int num_sms, int nsnap, const qtv_grid* grids, const float2* co
     return set_error(QTV_ERR_ARG, "%d snapshots (1 to %d supported)", nsnap, kMaxSnaps);
   if (tc.nwt < 0 || tc.nwt > 16)
     return set_error(QTV_ERR_ARG, "tile of %d warps (1 to 16 supported)", tc.nwt);
+  const bool bits = tc.variant == 1;
+  if (tc.variant != 0 && tc.variant != 1)
+    return set_error(QTV_ERR_ARG, "unknown sweep variant %d", tc.variant);
+  if (bits && tc.nwt != 0 && tc.nwt != 2 && tc.nwt != 4 && tc.nwt != 8)
+    return set_error(QTV_ERR_ARG, "bit-sliced sweep: %d warps per tile (2, 4 or 8)", tc.nwt);
+  const int stages = tc.stages <= 2 ? 2 : 3;
+  B->variant = tc.variant;
+  B->stages = stages;
+  B->rec_words = bits ? 4 : kRecWords;
   BulkParams& fin = B->fin;
   fin = BulkParams();
   fin.nsnap = nsnap;
@@ -1011,10 +939,18 @@ int batch_layout(int num_sms, int nsnap, const qtv_grid* grids, const float2* co
     d.nx = g.nx;
     d.ny = g.ny;
     d.nz = g.nz;
-    d.nbands = (g.ny + R - 1) / R;
-    d.nwt = tc.nwt > 0 ? tc.nwt : (g.nx + 63) / 64;
-    int rc = snap_tiles(g.nx, d.nwt, &d.ntx, &d.st);
-    if (rc) return rc;
+    if (bits) {
+      // 16-row bands; tiles of 31 nwt owned columns, each staging 2 more
+      d.nbands = (g.ny + 15) / 16;
+      d.nwt = tc.nwt > 0 ? tc.nwt : 4;
+      d.st = 31 * d.nwt;
+      d.ntx = (g.nx + d.st - 1) / d.st;
+    } else {
+      d.nbands = (g.ny + R - 1) / R;
+      d.nwt = tc.nwt > 0 ? tc.nwt : (g.nx + 63) / 64;
+      int rc = snap_tiles(g.nx, d.nwt, &d.ntx, &d.st);
+      if (rc) return rc;
+    }
     if (d.ntx * d.nwt > 32)
       return set_error(QTV_ERR_ARG, "snapshot %d: %d tiles of %d warps exceed 32 warps per row",
                        i, d.ntx, d.nwt);
@@ -1056,7 +992,8 @@ int batch_layout(int num_sms, int nsnap, const qtv_grid* grids, const float2* co
     p.nseg = nseg;
     int bps = 0;
     size_t smem = 0;
-    int rc = bulk_variant_occupancy(p.nwt, &bps, &smem);
+    int rc = bits ? bits_variant_occupancy(p.nwt, stages, &bps, &smem)
+                  : bulk_variant_occupancy(p.nwt, &bps, &smem);
     if (rc) return rc;
     if (tc.ctas_per_sm > 0 && tc.ctas_per_sm < bps) bps = tc.ctas_per_sm;
     long long grid = (long long)bps * num_sms;
@@ -1100,7 +1037,7 @@ int batch_layout(int num_sms, int nsnap, const qtv_grid* grids, const float2* co
 namespace {
 
 int check_scratch(const BatchLayout& B, const IdentScratch& sc, bool scan) {
-  if (sc.staging_cap < B.recs_need * kRecWords || sc.table_cap < B.table_need ||
+  if (sc.staging_cap < B.recs_need * B.rec_words || sc.table_cap < B.table_need ||
       sc.seg_cap * 2 < (uint64_t)B.fin.nseg ||
       (scan && (sc.seg_off_cap < (uint64_t)B.fin.nseg || sc.tiles_cap < (uint64_t)B.ntiles)))
     return set_error(QTV_ERR_CAPACITY, "identification scratch too small for this layout");
@@ -1133,7 +1070,8 @@ int launch_sweeps(qtv_handle h, BatchLayout& B, const IdentScratch& sc, cudaStre
     }
     {
       TraceScope ts(h, K_SWEEP, s);
-      bulk_fn(p.nwt)<<<L.grid, L.threads, L.smem, s>>>(p);
+      if (B.variant == 1) bits_sweep_launch(p, L.grid, p.nwt, B.stages, L.smem, s);
+      else bulk_fn(p.nwt)<<<L.grid, L.threads, L.smem, s>>>(p);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return check_cuda(e, "sweep_bulk_kernel launch");
@@ -1180,8 +1118,11 @@ int batch_launch(qtv_handle h, BatchLayout& B, const IdentScratch& sc, uint64_t*
     p.table = sc.table;
     p.segf = reinterpret_cast<unsigned int*>(sc.seg);
     TraceScope ts(h, K_SCATTER, st);
-    v3_expand_kernel<<<(unsigned)B.expand_blocks, 32 * kExpandWarps, 0, st>>>(
-        p, sc.seg_off, face_ids, winding, capacity, offsets);
+    if (B.variant == 1)
+      bits_expand_launch(p, B.expand_blocks, sc.seg_off, face_ids, winding, capacity, offsets, st);
+    else
+      v3_expand_kernel<<<(unsigned)B.expand_blocks, 32 * kExpandWarps, 0, st>>>(
+          p, sc.seg_off, face_ids, winding, capacity, offsets);
     e = cudaGetLastError();
     if (e != cudaSuccess) return check_cuda(e, "v3_expand_kernel launch");
   }
@@ -1199,14 +1140,44 @@ int batch_sweep_only(qtv_handle h, BatchLayout& B, const IdentScratch& sc, cudaS
   return launch_sweeps(h, B, sc, st, br);
 }
 
-int bulk_needs(int num_sms, const qtv_grid& g, uint64_t capacity, uint64_t max_warps,
-               BulkNeeds* n) {
+// Sweep shape of a single-snapshot call: the handle's choice
+// (qtv_configure_sweep), else the library default.
+constexpr int kDefaultSweepVariant = 1;
+
+TileConfig handle_sweep_config(const qtv_handle_s* h) {
+  TileConfig tc;
+  tc.variant = (h && h->sweep_variant >= 0) ? h->sweep_variant : kDefaultSweepVariant;
+  if (h) {
+    tc.nwt = h->sweep_nwt;
+    tc.ctas_per_sm = h->sweep_ctas;
+    if (h->sweep_stages > 0) tc.stages = h->sweep_stages;
+  }
+  return tc;
+}
+
+namespace {
+// Layout of a single snapshot in the handle's shape; a grid the bit-sliced
+// sweep cannot tile (more than 32 warps per row) takes the nibble sweep.
+int single_layout(qtv_handle h, int num_sms, const qtv_grid& g, const float2* psi,
+                  uint64_t capacity, uint64_t max_warps, BatchLayout* B) {
+  TileConfig tc = handle_sweep_config(h);
+  int rc = batch_layout(num_sms, 1, &g, &psi, tc, capacity, max_warps, B);
+  if (rc && tc.variant == 1) {
+    TileConfig t0;
+    rc = batch_layout(num_sms, 1, &g, &psi, t0, capacity, max_warps, B);
+  }
+  return rc;
+}
+}  // namespace
+
+int bulk_needs(qtv_handle h, int num_sms, const qtv_grid& g, uint64_t capacity,
+               uint64_t max_warps, BulkNeeds* n) {
   BatchLayout B;
   // alignment is checked by the caller; sizing needs only a 16-byte aligned stand-in
   const float2* psi = reinterpret_cast<const float2*>(uintptr_t(256));
-  const int rc = batch_layout(num_sms, 1, &g, &psi, TileConfig(), capacity, max_warps, &B);
+  const int rc = single_layout(h, num_sms, g, psi, capacity, max_warps, &B);
   if (rc) return rc;
-  n->recs = B.recs_need * kRecWords;  // staging words
+  n->recs = B.recs_need * B.rec_words;  // staging words
   n->table = B.table_need;
   n->seg_off = (unsigned long long)B.fin.nseg;
   n->tiles = (unsigned long long)B.ntiles;
@@ -1219,7 +1190,7 @@ int bulk_identify(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* 
                   cudaStream_t st, const IdentScratch& sc, uint64_t max_warps, float* xyz,
                   float* resid, uint8_t* flags) {
   BatchLayout B;
-  int rc = batch_layout(h->num_sms, 1, &g, &psi, TileConfig(), capacity, max_warps, &B);
+  int rc = single_layout(h, h->num_sms, g, psi, capacity, max_warps, &B);
   if (rc) return rc;
   const unsigned long long nx = g.nx, ny = g.ny, nz = g.nz;
   const unsigned long long scanned =

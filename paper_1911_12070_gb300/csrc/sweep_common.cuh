@@ -1,0 +1,112 @@
+// sweep_common.cuh -- device helpers shared by the identification sweeps:
+// bulk copies into shared memory with mbarrier completion, bounded waits, the
+// cross-product sign evaluation of the edge test, and the decoding of a work
+// unit of the (z block, band, tile, plane) order.
+#pragma once
+
+#include "qtv_internal.cuh"
+
+namespace qtv {
+namespace sweep {
+
+__device__ __forceinline__ bool finite_f(float v) { return fabsf(v) <= 3.402823466e38f; }
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// One try: true once the phase with the given parity has completed.  The
+// waiting thread may be suspended by the hardware for up to about 20 us (or
+// until the phase completes) instead of spinning.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false after ~2^32 cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > (1ll << 32)) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ float cross_f(float ar, float ai, float br, float bi) {
+  return fmaf(ar, bi, -(ai * br));
+}
+
+// unit u of one snapshot's (z block, band, tile, plane) order -> column
+// (band * ntx + tile), plane, end of its z block
+__device__ __forceinline__ void unit_pos(long long u, long long cols, int nz, int H, long long& col,
+                                         int& k, int& kend) {
+  const long long full = nz / H;
+  const long long per_full = cols * H;
+  long long zb, rem;
+  int h;
+  if (u < full * per_full) {
+    zb = u / per_full;
+    rem = u % per_full;
+    h = H;
+  } else {
+    zb = full;
+    rem = u - full * per_full;
+    h = nz - (int)full * H;
+  }
+  col = rem / h;
+  k = (int)zb * H + (int)(rem % h);
+  kend = (int)zb * H + h;
+}
+
+
+// d = a * b for two packed FP32 values (RN per component)
+__device__ __forceinline__ unsigned long long mul_f32x2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+}  // namespace sweep
+}  // namespace qtv

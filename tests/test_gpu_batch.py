@@ -4,9 +4,11 @@ launch, one finalize pass and one localization pass, replayed as a CUDA graph.
 
 * every snapshot's slice of the batch output equals the FP64 oracle bit for
   bit on unambiguous faces (windings) and within 1e-4 h (positions), for each
-  sweep shape (one tile width of 64 to 1024 columns for all snapshots, or one
-  sweep per row-width group, serial or concurrent; various CTAs per SM and
-  z-block heights), shapes pinned through a tune-cache line with the key "*";
+  sweep shape (nibble sweep: one tile width of 64 to 1024 columns for all
+  snapshots, or one sweep per row-width group, serial or concurrent;
+  bit-sliced sweep: tiles of 62, 124 or 248 columns, 2 or 3 ring stages;
+  various CTAs per SM and z-block heights), shapes pinned through a
+  tune-cache line with the key "*";
 * the slices equal the single-snapshot calls bit for bit (ids, windings, plain
   and learned positions and flags);
 * capacity overflow reports the total, replays are deterministic, and new data
@@ -31,6 +33,9 @@ torch = pytest.importorskip("torch")
 
 SMALL = [(20, 40, 130), (13, 29, 64), (9, 15, 1024), (7, 33, 200), (16, 16, 2), (1, 5, 6),
          (25, 31, 384), (3, 8, 66)]
+# the bit-sliced sweep tiles rows of at most 32 warps x 31 columns = 992
+SMALL_BITS = [(20, 40, 130), (13, 33, 64), (9, 15, 992), (7, 34, 200), (16, 16, 2), (1, 5, 6),
+              (25, 31, 384), (3, 8, 66), (6, 17, 124), (5, 18, 126)]
 
 
 @pytest.fixture(scope="module")
@@ -43,16 +48,24 @@ def q():
     h.close()
 
 
+def _fields(shapes, seed0):
+    hosts = [synth.random_waves_numpy(s, synth.wave_spec(seed0 + i, 512)) for i, s in enumerate(shapes)]
+    return hosts, [torch.from_numpy(h).cuda() for h in hosts]
+
+
 @pytest.fixture(scope="module")
 def small_batch():
-    hosts = [synth.random_waves_numpy(s, synth.wave_spec(300 + i, 512)) for i, s in enumerate(SMALL)]
-    devs = [torch.from_numpy(h).cuda() for h in hosts]
-    return hosts, devs
+    return _fields(SMALL, 300)
 
 
-def _pin(path, nwt, ctas, zscale, concurrent=0):
+@pytest.fixture(scope="module")
+def small_batch_bits():
+    return _fields(SMALL_BITS, 350)
+
+
+def _pin(path, nwt, ctas, zscale, concurrent=0, variant=0, stages=3):
     with open(path, "w") as f:
-        f.write(f"qtv-tune-v2 * {nwt} {ctas} {zscale} {concurrent} 0.0\n")
+        f.write(f"qtv-tune-v3 * {variant} {nwt} {ctas} {zscale} {concurrent} {stages} 0.0\n")
 
 
 def _check_slices(hosts, out):
@@ -88,9 +101,23 @@ def test_small_batch_matches_oracle_for_each_tile_shape(q, small_batch, shape):
         _pin(path, nwt, ctas, zs, conc)
         info = q.batch_plan(devs, tune_cache=path)
     assert info["source"] == 1 and info["warps_per_tile"] == nwt
-    assert info["concurrent"] == conc
+    assert info["concurrent"] == conc and info["variant"] == 0
     # per-snapshot widths: one sweep per distinct row width in warps
     assert info["sweeps"] == (1 if nwt else len({(s[2] + 63) // 64 for s in SMALL}))
+    out = q.batch_run()
+    _check_slices(hosts, out)
+
+
+@pytest.mark.parametrize("shape", [(2, 0, 1.0, 2), (4, 0, 1.0, 3), (8, 0, 2.0, 2), (4, 1, 0.5, 3),
+                                   (8, 1, 1.0, 3)])
+def test_small_batch_bit_sliced_sweep_matches_oracle(q, small_batch_bits, shape):
+    hosts, devs = small_batch_bits
+    nwt, ctas, zs, stages = shape
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "tune.txt")
+        _pin(path, nwt, ctas, zs, 0, variant=1, stages=stages)
+        info = q.batch_plan(devs, tune_cache=path)
+    assert info["source"] == 1 and info["variant"] == 1 and info["warps_per_tile"] == nwt
     out = q.batch_run()
     _check_slices(hosts, out)
 
@@ -177,10 +204,10 @@ def test_autotuner_stores_and_reuses_choice(q, small_batch):
         info = q.batch_plan(devs, tune_cache=path)
         assert info["source"] == 2 and info["candidates"] >= 6 and info["tuned_ms"] > 0
         lines = open(path).read().splitlines()
-        assert len(lines) == 1 and lines[0].startswith("qtv-tune-v2 ")
+        assert len(lines) == 1 and lines[0].startswith("qtv-tune-v3 ")
         info2 = q.batch_plan(devs, tune_cache=path)
         assert info2["source"] == 1
-        for k in ("warps_per_tile", "ctas_per_sm", "zscale", "concurrent"):
+        for k in ("variant", "warps_per_tile", "ctas_per_sm", "zscale", "concurrent", "stages"):
             assert info2[k] == info[k]
 
 

@@ -5,7 +5,8 @@ whose edge phase differences lie at least 1e-4 rad from +-pi; the remaining
 faces are counted and reported.  Sizes span several CTA bands and warps,
 ragged tails in x, y and z, odd nx (scalar-load path), nx above 512 (wider
 CTAs), degenerate grids, non-finite input, capacity overflow, and the full
-512^3 workload that the benchmark times (checked on sampled planes).
+512^3 workload that the benchmark times (checked on sampled planes), each
+with the nibble sweep and with the bit-sliced sweep.
 """
 import numpy as np
 import pytest
@@ -19,12 +20,16 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.fixture(scope="module")
-def q():
+@pytest.fixture(scope="module", params=[0, 1], ids=["nibble", "bits"])
+def q(request):
+    """A handle whose single-snapshot calls use the nibble sweep or the
+    bit-sliced sweep (rows wider than 992 columns fall back to the nibble
+    sweep); every test runs with both."""
     import paper_1911_12070_gb300 as qtv
 
     qtv.build()
     h = qtv.Qtv(0)
+    h.configure_sweep(variant=request.param)
     yield h
     h.close()
 
@@ -58,7 +63,9 @@ def test_config0_analytic_bit_exact(q):
 
 
 @pytest.mark.parametrize("shape", [(33, 45, 67), (40, 50, 130), (20, 29, 200), (9, 15, 1024),
-                                   (6, 8, 1999), (7, 14, 64), (17, 7, 128), (12, 13, 2)])
+                                   (6, 8, 1999), (7, 14, 64), (17, 7, 128), (12, 13, 2),
+                                   (11, 33, 248), (5, 16, 126), (8, 17, 992), (6, 31, 124),
+                                   (4, 48, 250), (13, 3, 62)])
 def test_ragged_random_waves_bit_exact(q, shape):
     psi = _waves(shape, seed=sum(shape))
     n, namb, damb = _check_full(q, psi)
