@@ -66,6 +66,42 @@ def parse():
     return p.parse_args()
 
 
+# ncu summary holding the DRAM bytes per node of the default (bit-sliced)
+# sweep, valid while the kernel sources hash to the value recorded with it
+SWEEP_SOURCES = ("paper_1911_12070_gb300/csrc/sweep_bits.cu",
+                 "paper_1911_12070_gb300/csrc/sweep_common.cuh")
+TRAFFIC_PROFILE = "profiles/sweep_bits_384_full.md"
+
+
+def sweep_sources_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    for rel in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(variant):
+    """(DRAM bytes per node, profile name) from the committed ncu summary of
+    the bit-sliced sweep, or (None, reason) when the sweep timed is another
+    kernel or has changed since the capture."""
+    if variant == 0:
+        return None, "nibble sweep: no current capture"
+    path = os.path.join(ROOT, TRAFFIC_PROFILE)
+    if not os.path.exists(path):
+        return None, "no capture"
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith(("traffic_bytes_per_node", "source_sha256")):
+            k, v = line.strip().split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_sha256") != sweep_sources_hash():
+        return None, "kernel changed since the capture"
+    return float(vals["traffic_bytes_per_node"]), TRAFFIC_PROFILE
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -486,17 +522,14 @@ def run_qtv(args):
 
     # ---- roofline of the dominant kernel (the sweep)
     peak, peak_kind = peaks()
-    nbands = (n + 6) // 7
-    nwarps_x = (n + 63) // 64
-    nseg = n * nbands
     sweep_launches, sweep_ms = trace.get("sweep", (0, 0.0))
     sweep_avg_ms = sweep_ms / max(1, sweep_launches)
-    # psi read once + one 16-byte table entry per (plane, band, warp) + one
-    # 4-byte face total per (plane, band); the staged records (24 B per lane
-    # and plane with faces, < 0.3 B/node) are left out, so this is a lower
-    # bound of the sweep's traffic
-    sweep_bytes = 8 * nodes + 16 * nseg * nwarps_x + 4 * nseg
+    # algorithmic bytes of one sweep: psi read once (8 B per node); halo rows,
+    # tile overlaps, the per-warp tables and the staged records are overhead
+    sweep_bytes = 8 * nodes
     achieved = sweep_bytes / (sweep_avg_ms * 1e-3) / 1e9 if sweep_avg_ms > 0 else 0.0
+    traffic_per_node, traffic_src = profiled_traffic(args.sweep_variant)
+    traffic = traffic_per_node * nodes if traffic_per_node is not None else None
     step_bytes = 8 * nodes + 9 * F + F * (9 + 32 + 17)
     ms_per_step = ms / args.steps
     launches = sum(v[0] for v in trace.values())
@@ -519,7 +552,8 @@ def run_qtv(args):
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": "sweep", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                     "traffic": None, "algorithmic_bytes": sweep_bytes,
+                     "traffic": traffic, "traffic_source": traffic_src,
+                     "algorithmic_bytes": sweep_bytes,
                      "avg_ms": sweep_avg_ms},
         "step_hbm_gbs": step_bytes / (ms_per_step * 1e-3) / 1e9,
         "kernels_ms": {k: v[1] / max(1, v[0]) for k, v in trace.items()},

@@ -104,7 +104,12 @@ extern "C" int qtv_identify_static(const qtv_grid* grid, const void* psi, uint64
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (nn == 0) return check_cuda(cudaMemsetAsync(count, 0, sizeof(uint64_t), st), "cudaMemsetAsync");
   IdentNeeds need;
-  rc = identify_needs(nullptr, num_sms, g, capacity, psi, kMaxWarps, &need);
+  // the nibble sweep: its staging grows with the pierced faces, not the grid
+  qtv_handle_s tmp;
+  tmp.device = dev;
+  tmp.num_sms = num_sms;
+  tmp.sweep_variant = 0;
+  rc = identify_needs(&tmp, num_sms, g, capacity, psi, kMaxWarps, &need);
   if (rc) return rc;
   if (need.table > kTableEntries)
     return set_error(QTV_ERR_ARG,
@@ -133,11 +138,9 @@ extern "C" int qtv_identify_static(const qtv_grid* grid, const void* psi, uint64
   p += kCounterBytes;
   sc.staging = reinterpret_cast<uint32_t*>(p);
   sc.staging_cap = kStagingWords;
-  // identify_launch only reads the SM count and the (off) trace switch of its
-  // handle argument; a stack handle carries them without any allocation.
-  qtv_handle_s tmp;
-  tmp.device = dev;
-  tmp.num_sms = num_sms;
+  // identify_launch only reads the SM count, the sweep choice and the (off)
+  // trace switch of its handle argument; a stack handle carries them without
+  // any allocation.
   return identify_launch(&tmp, g, reinterpret_cast<const float2*>(psi), face_ids, winding,
                          capacity, count, nullptr, st, sc, kMaxWarps);
 }

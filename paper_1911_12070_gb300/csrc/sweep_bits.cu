@@ -38,12 +38,16 @@
 // k + 1.  Waits are bounded (about 2^32 SM cycles); a timeout sets a status
 // bit that turns the reported count into QTV_COUNT_TIMEOUT.
 //
-// Compaction and finalize.  Each lane with faces in a plane writes one 16-byte
+// Output and finalize.  Each lane with faces in a plane writes one 16-byte
 // record (L and H words of the three orientations, 16 rows each, and the lane)
-// into per-warp chunks of the staging buffer, with a table entry per (plane,
-// band, tile, warp) and a face total per (plane, band) segment; the scan of the
-// nibble sweep gives segment offsets, and the expand pass below writes faces in
-// ascending face-id order (row, then x, then orientation).
+// into the fixed slot block of its (plane, band, tile, warp) step (32 records,
+// one per lane); the step's table entry (ballot of the lanes with records,
+// face count) is held by lane t % 32 and 32 consecutive planes' entries are
+// stored at once; face totals per (plane, band) segment accumulate in shared
+// memory for the CTA's run of planes and are added to the segment totals at
+// its end.  The scan of the nibble sweep gives segment offsets, and the expand
+// pass below writes faces in ascending face-id order (row, then x, then
+// orientation).
 #include <algorithm>
 
 #include "qtv_internal.cuh"
@@ -57,9 +61,8 @@ using namespace sweep;
 constexpr int BR = 16;            // owned rows per band
 constexpr int BRH = BR + 1;       // plus the halo row
 constexpr int BL = 31;            // owned columns per warp
-constexpr uint32_t kChunk = 32;   // records per staging chunk
-constexpr uint32_t kLowWater = 12;
 constexpr uint32_t kRows16 = 0xFFFFu;
+constexpr int kMaxRun = 256;      // planes per run (bounds the shared face totals)
 
 // acc' = (acc << 1) | sign bit of x
 __device__ __forceinline__ uint32_t push1(uint32_t acc, float x) {
@@ -128,6 +131,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) sweep_bits_kernel(const __grid_
   float2* ring = reinterpret_cast<float2*>(dsm);
   uint64_t* full = reinterpret_cast<uint64_t*>(dsm + (size_t)STAGES * BRH * W2 * sizeof(float2));
   uint64_t* empty = full + STAGES;
+  unsigned int* s_faces = reinterpret_cast<unsigned int*>(empty + STAGES);  // [kMaxRun]
   const int xl = BL * w + lane;  // tile-local column of this lane
   const uint32_t lt = (1u << lane) - 1u;
 
@@ -142,9 +146,6 @@ __global__ void __launch_bounds__(NW * 32, MINB) sweep_bits_kernel(const __grid_
 
   uint32_t fill = 0, use = 0;  // planes issued (warp 0) / consumed, counted over the whole CTA
   bool timeout = false;
-  uint32_t cb = 0, cl = 0, nb_l0 = 0;
-  bool have_next = false;
-  bool overflow = false;
   int valid_w = W2, valid_r = BRH;  // padding bookkeeping, as in the nibble sweep
 
   const long long U = a.units;
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) sweep_bits_kernel(const __grid_
     int kb, kblk;
     unit_pos(u - sd.unit0, (long long)sd.nbands * ntx, nz, sd.hblock, col, kb, kblk);
     const int band = (int)(col / ntx), tile = (int)(col % ntx);
-    const int ke = (int)min((long long)kblk, (long long)kb + (uend - u));
+    const int ke = (int)min(min((long long)kblk, (long long)kb + (uend - u)), (long long)kb + kMaxRun);
     u += ke - kb;
     const int j0 = band * BR;
     const int nrows = min(BRH, ny - j0);
@@ -192,6 +193,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) sweep_bits_kernel(const __grid_
     }
     valid_w = tw;
     valid_r = nrows;
+    for (int i = tid; i < nsteps; i += blockDim.x) s_faces[i] = 0u;
+    __syncthreads();
 
     // warp 0: plane m into the next slot once every warp has released it
     auto produce = [&](int m) {
@@ -227,11 +230,13 @@ __global__ void __launch_bounds__(NW * 32, MINB) sweep_bits_kernel(const __grid_
     const uint32_t m_xy = (own && xl + 1 < tw) ? rv1 : 0u;
     const uint32_t m_yz = (own && xl < tw) ? rv1 : 0u;
     const uint32_t m_zx = (own && xl + 1 < tw) ? rv : 0u;
-    const unsigned long long tstride = (unsigned long long)sd.nbands * ntx * NW;
-    const unsigned long long tbase =
-        (unsigned long long)sd.tab0 + ((unsigned long long)band * ntx + tile) * NW + w;
-    unsigned int* const segf = a.segf + sd.seg0 + band;
-    const unsigned sstride = (unsigned)sd.nbands;
+    // table entries of this (band, tile, warp): one per plane, contiguous in k;
+    // records of entry e in the fixed slots 32 e .. 32 e + 31 (one per lane)
+    const unsigned long long ebase =
+        (unsigned long long)sd.tab0 + (((unsigned long long)band * ntx + tile) * NW + w) * nz;
+    uint2* const table = reinterpret_cast<uint2*>(a.table);
+    uint4* const recs = reinterpret_cast<uint4*>(a.recs);
+    uint2 tent = make_uint2(0u, 0u);  // entry of step t held by lane t % 32
 
     if (w == 0)
       for (int i = 0; i < min(STAGES, nplanes); ++i) produce(kb + i);
@@ -352,57 +357,20 @@ __global__ void __launch_bounds__(NW * 32, MINB) sweep_bits_kernel(const __grid_
       const uint32_t cnt = __popc(Mxy) + __popc(Myz) + __popc(Mzx);
       const bool anyf = cnt != 0u;
 
-      // ---- per-warp compaction: one record per lane with faces
+      // ---- output: records in the fixed slots of this warp step, the
+      // table entry (lane mask, faces) held by lane t % 32 and stored for 32
+      // steps at once, the face total added to the CTA's count of plane k
       const uint32_t faces_w = __reduce_add_sync(0xffffffffu, cnt);
       const uint32_t bal = __ballot_sync(0xffffffffu, anyf);
-      const uint32_t T = __popc(bal);
-      uint32_t base1 = cb, base2 = 0, n1 = T;
-      if (T > cl) {
-        const uint32_t need = T - cl;
-        uint32_t nbase, ncap;
-        if (have_next && need <= kChunk) {
-          nbase = __shfl_sync(0xffffffffu, nb_l0, 0);
-          ncap = kChunk;
-          have_next = false;
-        } else {
-          ncap = need > kChunk ? need : kChunk;
-          uint32_t x = 0;
-          if (lane == 0) {
-            const unsigned long long got = atomicAdd(a.counters, (unsigned long long)ncap);
-            x = (uint32_t)got;
-            if (got + ncap > a.recs_cap) overflow = true;
-          }
-          nbase = __shfl_sync(0xffffffffu, x, 0);
-        }
-        n1 = cl;
-        base2 = nbase;
-        cb = nbase + need;
-        cl = ncap - need;
-      } else {
-        cb += T;
-        cl -= T;
+      const unsigned long long e = ebase + (unsigned long long)k;
+      if (anyf && e * 32ull + lane < a.recs_cap)
+        recs[e * 32ull + lane] =
+            make_uint4(Lxy | (Hxy << 16), Lyz | (Hyz << 16), Lzx | (Hzx << 16), (uint32_t)lane);
+      if (lane == (t & 31)) tent = make_uint2(bal, faces_w);
+      if ((t & 31) == 31 || t == nsteps - 1) {
+        if (lane <= (t & 31)) table[ebase + (unsigned long long)(kb + (t & ~31) + lane)] = tent;
       }
-      if (cl < kLowWater && !have_next) {
-        if (lane == 0) {
-          const unsigned long long got = atomicAdd(a.counters, (unsigned long long)kChunk);
-          nb_l0 = (uint32_t)got;
-          if (got + kChunk > a.recs_cap) overflow = true;
-        }
-        have_next = true;
-      }
-      if (lane == 0) {
-        a.table[tbase + (unsigned long long)k * tstride] =
-            make_uint4(base1, base2, T | (n1 << 6) | (faces_w << 12), 0u);
-        if (faces_w) atomicAdd(&segf[(size_t)k * sstride], faces_w);
-      }
-      if (anyf) {
-        const uint32_t q = __popc(bal & lt);
-        const unsigned long long idx =
-            q < n1 ? (unsigned long long)base1 + q : (unsigned long long)base2 + (q - n1);
-        if (idx < a.recs_cap)
-          reinterpret_cast<uint4*>(a.recs)[idx] =
-              make_uint4(Lxy | (Hxy << 16), Lyz | (Hyz << 16), Lzx | (Hzx << 16), (uint32_t)lane);
-      }
+      if (lane == 0 && faces_w) atomicAdd(&s_faces[t], faces_w);
       // plane k + 1 becomes plane k
       S0 = S1;
       S0n = S1n;
@@ -421,9 +389,12 @@ __global__ void __launch_bounds__(NW * 32, MINB) sweep_bits_kernel(const __grid_
       if (t + 1 < nsteps) step(vB, vA, t + 1);
     }
     __syncthreads();
+    // face totals of the run's planes into the (plane, band) segments
+    for (int i = tid; i < nsteps; i += blockDim.x)
+      if (s_faces[i]) atomicAdd(&a.segf[sd.seg0 + (size_t)(kb + i) * sd.nbands + band], s_faces[i]);
+    __syncthreads();
   }
   if (timeout) atomicOr(reinterpret_cast<unsigned int*>(a.counters + 1), 1u);
-  if (overflow) atomicOr(reinterpret_cast<unsigned int*>(a.counters + 1), 2u);
 }
 
 // ---------------------------------------------------------------------------
@@ -444,7 +415,7 @@ __global__ void __launch_bounds__(32 * kExpandWarps, 4) expand_bits_kernel(
     uint64_t* __restrict__ offsets) {
   __shared__ uint32_t s_rowbase[kExpandWarps][BR];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const uint4* __restrict__ table = a.table;
+  const uint2* __restrict__ table = reinterpret_cast<const uint2*>(a.table);
   const uint4* __restrict__ recs = reinterpret_cast<const uint4*>(a.recs);
   const unsigned long long recs_cap = a.recs_cap;
   const long long nseg = a.nseg;
@@ -463,9 +434,17 @@ __global__ void __launch_bounds__(32 * kExpandWarps, 4) expand_bits_kernel(
     long long local;
     locate(s, si, local, NW);
     const SnapDesc& sd = a.s[si];
-    uint4 e = make_uint4(0u, 0u, 0u, 0u);
-    if (lane < NW) e = table[sd.tab0 + local * NW + lane];
-    const uint32_t n = e.z & 63u, n1 = (e.z >> 6) & 63u;
+    const int nbands = sd.nbands;
+    const long long k = local / nbands;
+    const long long band = local % nbands;
+    // entry of (tile, warp) i = lane: ((band ntx + tile) nwt + warp) nz + k
+    uint2 e = make_uint2(0u, 0u);
+    unsigned long long eidx = 0;
+    if (lane < NW) {
+      eidx = (unsigned long long)sd.tab0 + ((unsigned long long)band * NW + lane) * sd.nz + k;
+      e = table[eidx];
+    }
+    const uint32_t n = __popc(e.x);
     uint32_t incl = n;
 #pragma unroll
     for (int dd = 1; dd < 32; dd <<= 1) {
@@ -476,10 +455,8 @@ __global__ void __launch_bounds__(32 * kExpandWarps, 4) expand_bits_kernel(
     const uint32_t rtot = __shfl_sync(0xffffffffu, incl, 31);
     if (rtot == 0) continue;
     const unsigned long long fbase = seg_off[s];
-    const int nbands = sd.nbands;
     const unsigned long long nx = (unsigned)sd.nx, ny = (unsigned)sd.ny;
-    const long long k = local / nbands;
-    const long long j0 = (local % nbands) * BR;
+    const long long j0 = band * BR;
     const int nwt = sd.nwt;
     const uint32_t nchunks = (rtot + 31) / 32;
 
@@ -495,13 +472,13 @@ __global__ void __launch_bounds__(32 * kExpandWarps, 4) expand_bits_kernel(
       }
       ww = lo;
       const uint32_t qi = g - __shfl_sync(0xffffffffu, start, lo);
-      const uint32_t b1 = __shfl_sync(0xffffffffu, e.x, lo);
-      const uint32_t b2 = __shfl_sync(0xffffffffu, e.y, lo);
-      const uint32_t m1 = __shfl_sync(0xffffffffu, n1, lo);
-      const unsigned long long idx =
-          qi < m1 ? (unsigned long long)b1 + qi : (unsigned long long)b2 + (qi - m1);
+      const uint32_t mask = __shfl_sync(0xffffffffu, e.x, lo);
+      const unsigned long long ei = __shfl_sync(0xffffffffu, eidx, lo);
       rec = make_uint4(0u, 0u, 0u, 0u);
-      if (g < rtot && idx < recs_cap) rec = recs[idx];
+      if (g < rtot) {
+        const unsigned long long idx = ei * 32ull + (unsigned)(__fns(mask, 0, (int)qi + 1));
+        if (idx < recs_cap) rec = recs[idx];
+      }
     };
     // per-row face counts of a record, 4 rows per word (one byte each)
     auto counts = [&](const uint4& rec, uint32_t* cw) {
@@ -616,7 +593,8 @@ int bits_fn_index(int nw, int stages) {
 }  // namespace
 
 size_t bits_smem_bytes(int nw, int stages) {
-  return (size_t)stages * BRH * (BL * nw + 2) * sizeof(float2) + 2 * stages * sizeof(uint64_t);
+  return (size_t)stages * BRH * (BL * nw + 2) * sizeof(float2) + 2 * stages * sizeof(uint64_t) +
+         kMaxRun * sizeof(unsigned int);
 }
 
 int bits_variant_occupancy(int nw, int stages, int* ctas_per_sm, size_t* smem) {

@@ -1025,9 +1025,10 @@ int batch_layout(int num_sms, int nsnap, const qtv_grid* grids, const float2* co
   }
   B->concurrent = tc.concurrent && gw.size() > 1;
   B->ntiles = (nseg + kScanTile - 1) / kScanTile;
-  // records (kRecWords words each): at most one per pierced face, plus two
-  // partly used chunks per warp of every sweep
-  B->recs_need = capacity + slack;
+  // records: nibble sweep, at most one per pierced face plus two partly used
+  // chunks per warp of every sweep; bit-sliced sweep, fixed slots of 32 per
+  // (plane, band, tile, warp)
+  B->recs_need = bits ? (unsigned long long)tab * 32ull : capacity + slack;
   B->table_need = (unsigned long long)tab;
   B->expand_blocks = (int)std::min<long long>((nseg + kExpandWarps - 1) / kExpandWarps,
                                               (long long)num_sms * 4);
