@@ -133,7 +133,6 @@ __global__ void __launch_bounds__(NW * 32, MINB) sweep_bits_kernel(const __grid_
   uint64_t* empty = full + STAGES;
   unsigned int* s_faces = reinterpret_cast<unsigned int*>(empty + STAGES);  // [kMaxRun]
   const int xl = BL * w + lane;  // tile-local column of this lane
-  const uint32_t lt = (1u << lane) - 1u;
 
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {

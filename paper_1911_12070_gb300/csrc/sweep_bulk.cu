@@ -1148,6 +1148,9 @@ constexpr int kDefaultSweepVariant = 1;
 TileConfig handle_sweep_config(const qtv_handle_s* h) {
   TileConfig tc;
   tc.variant = (h && h->sweep_variant >= 0) ? h->sweep_variant : kDefaultSweepVariant;
+  // the bit-sliced sweep runs its CTAs over z blocks twice as tall as the
+  // even split (fewer run changes, measured slightly faster)
+  if (tc.variant == 1) tc.zscale = 2.f;
   if (h) {
     tc.nwt = h->sweep_nwt;
     tc.ctas_per_sm = h->sweep_ctas;
