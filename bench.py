@@ -331,6 +331,22 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+def slowest_ms(ms, device):
+    """The largest of every rank's time (the job ends with its slowest rank)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world_size, nodes_per_rank, steps, ms):
+    """Whole-job grid points per second: all ranks' points over the slowest
+    rank's time (each rank processes its own replica)."""
+    return world_size * nodes_per_rank * steps / (ms * 1e-3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -471,9 +487,7 @@ def run_qtv(args):
         import torch.distributed as dist
 
         dist.barrier()
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = slowest_ms(ms, dev)
     F = int(count.item())
     clocks = clk.summary(t0 - 2.0, t1)
 
@@ -513,11 +527,7 @@ def run_qtv(args):
     torch.cuda.synchronize()
     ms_e2e = e0.elapsed_time(e1)
     if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+        ms_e2e = slowest_ms(ms_e2e, dev)
     clk.stop()
 
     # ---- roofline of the dominant kernel (the sweep)
@@ -536,7 +546,7 @@ def run_qtv(args):
 
     line = {
         "metric": METRIC,
-        "value": ws * nodes * args.steps / (ms * 1e-3),
+        "value": job_value(ws, nodes, args.steps, ms),
         "unit": UNIT,
         "n_gpus": ws,
         "steps": args.steps,
@@ -557,7 +567,7 @@ def run_qtv(args):
                      "avg_ms": sweep_avg_ms},
         "step_hbm_gbs": step_bytes / (ms_per_step * 1e-3) / 1e9,
         "kernels_ms": {k: v[1] / max(1, v[0]) for k, v in trace.items()},
-        "e2e": {"value": ws * nodes * ke / (ms_e2e * 1e-3), "unit": UNIT,
+        "e2e": {"value": job_value(ws, nodes, ke, ms_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * nodes, "d2h_bytes_per_step": d2h // ke},
         "gpu_launches": launches,
         "clocks": clocks,
