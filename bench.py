@@ -175,9 +175,10 @@ def make_field(n, device):
 
 def learned_report(q, psi, ids, wnd, F, stream, reps=20):
     """Trains the learned locator (12 seeds of 256^3, about 2e6 faces, the
-    library's own training kernels), then times learned and plain localization
-    of the F faces of the bench field and measures the learned positions
-    against the plain ones (the plain solve is the judge)."""
+    library's own training kernels), then times plain localization and learned
+    localization (dense layers on tcgen05, and on mma.sync for comparison) of
+    the F faces of the bench field and measures the learned positions against
+    the plain ones (the plain solve is the judge)."""
     import torch
 
     import paper_1911_12070_gb300 as qtv
@@ -192,11 +193,13 @@ def learned_report(q, psi, ids, wnd, F, stream, reps=20):
     dev = psi.device
     outs = {}
     ms = {}
-    for mode in (qtv.PLAIN, qtv.LEARNED):
+    for key, mode, path in (("plain", qtv.PLAIN, 0), ("mma", qtv.LEARNED, 0),
+                            ("tcgen05", qtv.LEARNED, 1)):
         o = (torch.empty((F, 3), dtype=torch.float32, device=dev),
              torch.empty(F, dtype=torch.float32, device=dev),
              torch.empty(F, dtype=torch.uint8, device=dev))
-        outs[mode] = o
+        outs[key] = o
+        q.locator_set_tensor_path(path)
         for _ in range(3):
             q.localize_into(psi, fid, w, *o, mode=mode, fallback_resid=1e-3)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -207,9 +210,10 @@ def learned_report(q, psi, ids, wnd, F, stream, reps=20):
             q.localize_into(psi, fid, w, *o, mode=mode, fallback_resid=1e-3)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms[mode] = e0.elapsed_time(e1) / reps
-    xyz_p, _, fl_p = outs[qtv.PLAIN]
-    xyz_l, _, fl_l = outs[qtv.LEARNED]
+        ms[key] = e0.elapsed_time(e1) / reps
+    q.locator_set_tensor_path(1 if ms["tcgen05"] < ms["mma"] else 0)
+    xyz_p, _, fl_p = outs["plain"]
+    xyz_l, _, fl_l = outs["tcgen05"]
     good = (fl_p & qtv.FLAG_ANOMALOUS) == 0
     accepted = (fl_l & qtv.FLAG_LEARNED) != 0
     d2 = torch.sum((xyz_l - xyz_p) ** 2, 1)
@@ -221,8 +225,10 @@ def learned_report(q, psi, ids, wnd, F, stream, reps=20):
         "train": {"faces": "12 random-wave fields 256^3 (4096 waves, seeds 101-112), 5% noise "
                            "inputs, clean plain labels", "steps": int(len(losses)),
                   "seconds": fit_s, "final_loss": float(np.mean(losses[-50:]))},
-        "plain_ms": ms[qtv.PLAIN], "learned_ms": ms[qtv.LEARNED],
-        "learned_mlp_tflops": flop / (ms[qtv.LEARNED] * 1e-3) / 1e12,
+        "plain_ms": ms["plain"], "learned_ms": ms["tcgen05"],
+        "learned_mma_sync_ms": ms["mma"],
+        "learned_mlp_tflops": flop / (ms["tcgen05"] * 1e-3) / 1e12,
+        "tensor_path": "tcgen05 (accumulators in tensor memory)",
         "accepted_frac": float(accepted.float().mean()),
         "rms_vs_plain_h": rms_all, "rms_vs_plain_accepted_h": rms_acc,
         "fallback_resid": 1e-3,

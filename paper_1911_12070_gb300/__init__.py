@@ -125,6 +125,8 @@ def lib() -> ctypes.CDLL:
         L.qtv_locator_train_step.argtypes = [P, P, P, u64, f32, P, P]
         L.qtv_locator_save.argtypes = [P, ctypes.c_char_p]
         L.qtv_locator_load.argtypes = [P, ctypes.c_char_p]
+        L.qtv_locator_set_tensor_path.argtypes = [P, i32]
+        L.qtv_locator_set_tensor_path.restype = i32
         for name in ("qtv_locator_init", "qtv_locator_get", "qtv_locator_set", "qtv_locator_encode",
                      "qtv_locator_forward", "qtv_locator_gradients", "qtv_locator_train_step",
                      "qtv_locator_save", "qtv_locator_load"):
@@ -363,6 +365,10 @@ class Qtv:
     # -- learned locator ------------------------------------------------------------
     def locator_init(self, seed: int = 0):
         _check(lib().qtv_locator_init(self.h, int(seed)))
+
+    def locator_set_tensor_path(self, path: int):
+        """Dense layers of forward passes on mma.sync (0) or tcgen05 (1)."""
+        _check(lib().qtv_locator_set_tensor_path(self.h, int(path)))
 
     def locator_get(self):
         """(params float32 [P], adam float32 [2P], step) copied to the host."""

@@ -516,6 +516,10 @@ struct Locator {
   // activations for up to `cap` rows; rows_gen counts their reallocations
   unsigned long long cap = 0;
   unsigned long long rows_gen = 0;
+  // dense layers of forward passes: 0 = mma.sync kernel, 1 = tcgen05 kernel
+  int tensor_path = 1;
+  int num_sms = 0;
+  unsigned int* status = nullptr;  // timeout flag of the tcgen05 kernel
   uint16_t *A1 = nullptr, *A2 = nullptr, *D1 = nullptr, *D2 = nullptr, *X = nullptr;
   float *Y = nullptr, *DY = nullptr, *rms = nullptr;
   uint8_t* ok = nullptr;
@@ -538,6 +542,7 @@ void locator_free(Locator* L) {
   cudaFree(L->DY);
   cudaFree(L->rms);
   cudaFree(L->ok);
+  cudaFree(L->status);
   delete L;
 }
 
@@ -553,10 +558,13 @@ static int locator_alloc(qtv_handle h) {
   if (e == cudaSuccess) e = cudaMalloc(&L->V, pb);
   if (e == cudaSuccess) e = cudaMalloc(&L->w1b, (size_t)kH * kIn * 2);
   if (e == cudaSuccess) e = cudaMalloc(&L->w2b, (size_t)kH * kH * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&L->status, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(L->status, 0, sizeof(unsigned int));
   if (e != cudaSuccess) {
     locator_free(L);
     return check_cuda(e, "cudaMalloc(locator)");
   }
+  L->num_sms = h->num_sms;
   h->loc = L;
   return QTV_OK;
 }
@@ -601,6 +609,19 @@ static int forward_hidden(Locator* L, const uint16_t* X, unsigned long long n, c
   if (rc) return rc;
   return gemm<false, false, EPI_BIAS_RELU_BF16>((int)n, kH, kH, L->A1, kH, L->w2b, kH, L->A2, kH,
                                                 L->P + kOffB2, nullptr, st);
+}
+
+// network outputs Y[n][3] of inputs X (forward passes of inference)
+static int forward_y(Locator* L, const uint16_t* X, unsigned long long n, float* Y,
+                     cudaStream_t st) {
+  if (L->tensor_path == 1)
+    return tc_mlp_forward(X, (long long)n, L->w1b, L->w2b, L->P + kOffB1, L->P + kOffB2,
+                          L->P + kOffW3, L->P + kOffB3, Y, L->status, L->num_sms, st);
+  int rc = forward_hidden(L, X, n, st);
+  if (rc) return rc;
+  out_layer_kernel<<<blocks_for(n, 256, 4096), 256, 0, st>>>(L->A2, L->P, n, Y, nullptr, nullptr,
+                                                              nullptr);
+  return check_cuda(cudaGetLastError(), "out_layer_kernel launch");
 }
 
 // forward + backward into L->G; loss (device float) accumulated
@@ -656,10 +677,8 @@ int locator_localize(qtv_handle h, const FaceGeo& geo, const uint64_t* face_ids,
     const unsigned long long m = n - f0 < chunk ? n - f0 : chunk;
     encode_kernel<<<blocks_for(m * 32, 256, 65535), 256, 0, st>>>(geo, f0, m, n, n_dev, face_ids,
                                                                   winding, L->X, L->ok, L->rms);
-    rc = forward_hidden(L, L->X, m, st);
+    rc = forward_y(L, L->X, m, L->Y, st);
     if (rc) return rc;
-    out_layer_kernel<<<blocks_for(m, 256, 4096), 256, 0, st>>>(L->A2, L->P, m, L->Y, nullptr,
-                                                                nullptr, nullptr);
     head_kernel<<<blocks_for(m, 256, 65535), 256, 0, st>>>(geo, f0, m, n, n_dev, face_ids, winding,
                                                            L->Y, L->ok, L->rms, thresh, xyz, resid,
                                                            flags, nullptr);
@@ -685,6 +704,15 @@ int qtv_locator_init(qtv_handle h, uint64_t seed) {
   L->step = 0;
   L->ready = true;
   return check_cuda(cudaDeviceSynchronize(), "qtv_locator_init");
+}
+
+int qtv_locator_set_tensor_path(qtv_handle h, int path) {
+  if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
+  if (path != 0 && path != 1) return set_error(QTV_ERR_ARG, "tensor path %d (0 or 1)", path);
+  int rc = locator_alloc(h);
+  if (rc) return rc;
+  h->loc->tensor_path = path;
+  return QTV_OK;
 }
 
 int qtv_locator_get(qtv_handle h, float* params, float* adam, uint64_t* step) {
@@ -742,11 +770,7 @@ int qtv_locator_forward(qtv_handle h, const uint16_t* x, uint64_t n, float* y, v
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int rc = locator_rows(h, n, st);
   if (rc) return rc;
-  rc = forward_hidden(h->loc, x, n, st);
-  if (rc) return rc;
-  out_layer_kernel<<<blocks_for(n, 256, 4096), 256, 0, st>>>(h->loc->A2, h->loc->P, n, y, nullptr,
-                                                              nullptr, nullptr);
-  return check_cuda(cudaGetLastError(), "qtv_locator_forward");
+  return forward_y(h->loc, x, n, y, st);
 }
 
 int qtv_locator_gradients(qtv_handle h, const uint16_t* x, const float* targets, uint64_t n,

@@ -1,0 +1,442 @@
+// locator_tc.cu -- the learned locator's network on the 5th-generation tensor
+// cores (tcgen05, accumulators in tensor memory): a dense layer
+// out[M][256] = relu(A[M][K] W[256][K]^T + b) in BF16 (K = 128 or 256), and
+// the whole 128-256-256-3 network fused per 128-row tile (tc_mlp_kernel).
+//
+// A persistent CTA of 4 warps keeps W in shared memory for all its 128-row
+// tiles of A.  Operands are stored in the canonical K-major layout without
+// swizzle: 8 x 8 core matrices of 128 contiguous bytes (8 rows of 16 bytes),
+// core matrix (r / 8, k / 8) at ((r / 8) (K / 8) + k / 8) 128 bytes, so the
+// leading-dimension offset (next core matrix along K) is 128 bytes and the
+// stride offset (next 8-row group) is 16 K bytes.  One elected thread issues
+// K / 16 tcgen05.mma instructions of M = 128, N = 256, K = 16 into a 256-column
+// FP32 accumulator in tensor memory and commits them to an mbarrier; then each
+// warp reads its 32 rows back with tcgen05.ld (32 columns at a time), adds the
+// bias, applies ReLU, rounds to BF16 and stores 64 contiguous bytes per row.
+// The accumulator columns are allocated once per CTA and freed before exit;
+// the mbarrier wait is bounded and sets a status flag on timeout.
+#include <cuda_bf16.h>
+
+#include "qtv_internal.cuh"
+#include "sweep_common.cuh"
+
+namespace qtv {
+namespace {
+
+using namespace sweep;
+
+constexpr int TM = 128;   // rows per tile (M of one instruction, TMEM lanes)
+constexpr int TN = 256;   // outputs (N of one instruction, TMEM columns)
+
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// shared-memory matrix descriptor: no swizzle, K-major
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
+  d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of the 5th-generation tensor cores
+  return d;                // base offset 0, swizzle none
+}
+
+// instruction descriptor of kind::f16: D F32, A and B BF16, both K-major
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                            ((uint32_t)(TM >> 4) << 24);
+
+// rows [r0, r0 + R) of a row-major BF16 matrix (K columns, row pitch K) into
+// the canonical layout at dst; rows at or beyond nrows become zero.  Piece c
+// (16 bytes) goes to byte 16 c of dst: c = ((r / 8) (K / 8) + k / 8) 8 + r % 8,
+// so consecutive threads fill consecutive shared-memory slots (no bank
+// conflicts) and read 8 rows x 16 bytes per group of 8 threads.
+__device__ __forceinline__ void load_canon(unsigned char* dst, const uint16_t* __restrict__ src,
+                                           long long r0, int R, long long nrows, int K) {
+  const int kc8 = K / 8;
+  const int chunks = R * kc8;
+  for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+    const int rr = c & 7, kc = (c >> 3) % kc8, rg = (c >> 3) / kc8;
+    const int r = rg * 8 + rr;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (r0 + r < nrows) v = __ldg(reinterpret_cast<const uint4*>(src + (r0 + r) * K) + kc);
+    *reinterpret_cast<uint4*>(dst + (size_t)c * 16) = v;
+  }
+}
+
+// as load_canon, with cp.async (16 bytes per piece, zero fill past nrows);
+// completion by cp_async_wait_all
+__device__ __forceinline__ void load_canon_async(unsigned char* dst, const uint16_t* __restrict__ src,
+                                                 long long r0, int R, long long nrows, int K) {
+  const int kc8 = K / 8;
+  const int chunks = R * kc8;
+  for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+    const int rr = c & 7, kc = (c >> 3) % kc8, rg = (c >> 3) / kc8;
+    const long long r = r0 + rg * 8 + rr;
+    const bool in = r < nrows;
+    const uint16_t* g = src + (in ? r : 0) * K + kc * 8;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst + (size_t)c * 16)),
+                 "l"(g), "r"(in ? 16 : 0)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128, 1) tc_dense_kernel(const uint16_t* __restrict__ A,
+                                                          long long M, int K,
+                                                          const uint16_t* __restrict__ W,
+                                                          const float* __restrict__ bias,
+                                                          uint16_t* __restrict__ out,
+                                                          unsigned int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  unsigned char* sW = dsm;                                 // TN x K
+  unsigned char* sA = dsm + (size_t)TN * K * 2;            // TM x K
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sA + (size_t)TM * K * 2);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  float* sb = reinterpret_cast<float*>(tslot + 4);         // bias [TN]
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+
+  if (w == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"((uint32_t)TN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(mbar, 1u);
+    fence_mbar_init();
+  }
+  for (int i = tid; i < TN; i += blockDim.x) sb[i] = bias[i];
+  load_canon(sW, W, 0, TN, TN, K);
+  fence_proxy_async();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t lbo = 128u, sbo = (uint32_t)(K / 8) * 128u;
+  const uint64_t adesc0 = smem_desc(smem_u32(sA), lbo, sbo);
+  const uint64_t bdesc0 = smem_desc(smem_u32(sW), lbo, sbo);
+  bool timeout = false;
+  uint32_t phase = 0;
+
+  const long long ntiles = (M + TM - 1) / TM;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long r0 = tile * TM;
+    load_canon(sA, A, r0, TM, M, K);
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int kb = 0; kb < K / 16; ++kb) {
+        // advance both start addresses by two core matrices (256 bytes) per K step
+        const uint64_t adv = (uint64_t)((kb * 256) >> 4);
+        const uint32_t acc = kb > 0 ? 1u : 0u;
+        asm volatile(
+            "{\n"
+            " .reg .pred p;\n"
+            " setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+            "}\n" ::"r"(tmem),
+            "l"(adesc0 + adv), "l"(bdesc0 + adv), "r"(kIdesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(mbar))
+          : "memory");
+    }
+    if (!mbar_wait(mbar, phase)) timeout = true;
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // epilogue: warp w owns TMEM lanes (rows) 32 w .. 32 w + 31
+    const long long row = r0 + 32 * w + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < TN; c0 += 32) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(32 * w) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+          "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+          "%28, %29, %30, %31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+            "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+            "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+            "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < M) {
+        uint32_t pk[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float lo = fmaxf(__uint_as_float(v[2 * j]) + sb[c0 + 2 * j], 0.f);
+          const float hi = fmaxf(__uint_as_float(v[2 * j + 1]) + sb[c0 + 2 * j + 1], 0.f);
+          pk[j] = bf16x2_bits(lo, hi);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(out + row * TN + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  if (timeout) atomicOr(status, 1u);
+  __syncthreads();
+  if (w == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)TN)
+                 : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// The whole network for 128-row tiles: Y[M][3] = W3 relu(W2 relu(W1 x + b1) +
+// b2) + b3.  W1 (64 KB) and W2 (128 KB) stay in shared memory; per tile the X
+// rows (32 KB) are loaded, layer 1 accumulates into TMEM columns [0, 256),
+// its epilogue writes relu(. + b1) as BF16 pairs back into TMEM columns
+// [0, 128) (row = lane, two consecutive K values per 32-bit column), layer 2
+// takes that A operand from TMEM and accumulates into columns [256, 512), and
+// its epilogue applies relu(. + b2) and the 3-output layer in FP32.  The next
+// tile's X is prefetched with cp.async once layer 1 has read the current one,
+// and the next tile's layer 1 runs on the tensor cores during epilogue 2.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kMlpSmemW1 = 256 * 128 * 2, kMlpSmemW2 = 256 * 256 * 2, kMlpSmemX = 128 * 128 * 2;
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+      "r"(v[15])
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+      "r"(a_tmem), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__global__ void __launch_bounds__(128, 1) tc_mlp_kernel(
+    const uint16_t* __restrict__ X, long long M, const uint16_t* __restrict__ W1,
+    const uint16_t* __restrict__ W2, const float* __restrict__ b1, const float* __restrict__ b2,
+    const float* __restrict__ w3, const float* __restrict__ b3, float* __restrict__ Y,
+    unsigned int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  unsigned char* sW1 = dsm;
+  unsigned char* sW2 = dsm + kMlpSmemW1;
+  unsigned char* sX = sW2 + kMlpSmemW2;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sX + kMlpSmemX);  // layer 1 done
+  uint64_t* mbar2 = mbar + 1;                                          // layer 2 done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+
+  if (w == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(mbar, 1u);
+    mbar_init(mbar2, 1u);
+    fence_mbar_init();
+  }
+  load_canon(sW1, W1, 0, 256, 256, 128);
+  load_canon(sW2, W2, 0, 256, 256, 256);
+  fence_proxy_async();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t lane_off = (uint32_t)(32 * w) << 16;
+  const uint64_t xdesc = smem_desc(smem_u32(sX), 128u, 16u * 128u);
+  const uint64_t w1desc = smem_desc(smem_u32(sW1), 128u, 16u * 128u);
+  const uint64_t w2desc = smem_desc(smem_u32(sW2), 128u, 32u * 128u);
+  bool timeout = false;
+  uint32_t phase = 0;
+
+  const long long ntiles = (M + TM - 1) / TM;
+  uint32_t phase2 = 0;
+  auto issue_layer1 = [&]() {  // D1 (columns 0..255) = X W1^T, 8 steps of K = 16
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int kb = 0; kb < 8; ++kb)
+        mma_ss(tmem, xdesc + (uint64_t)(kb * 16), w1desc + (uint64_t)(kb * 16), kb > 0 ? 1u : 0u);
+      mma_commit(mbar);
+    }
+  };
+  if ((long long)blockIdx.x < ntiles) {
+    load_canon_async(sX, X, (long long)blockIdx.x * TM, TM, M, 128);
+    cp_async_wait_all();
+    fence_proxy_async();
+    __syncthreads();
+    issue_layer1();
+  }
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long r0 = tile * TM;
+    const long long row = r0 + 32 * w + lane;
+    const long long next = tile + gridDim.x;
+    if (!mbar_wait(mbar, phase)) timeout = true;  // layer 1 of this tile
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // X of the next tile streams into shared memory during the rest of this tile
+    if (next < ntiles) load_canon_async(sX, X, next * TM, TM, M, 128);
+    // epilogue 1: columns 32 j .. 32 j + 31 of D1 -> BF16 pairs in columns 16 j .. 16 j + 15
+#pragma unroll 1
+    for (int j = 0; j < 8; ++j) {
+      uint32_t v[32], pk[16];
+      tmem_ld32(tmem + lane_off + 32u * j, v);
+      const float4* bb = reinterpret_cast<const float4*>(b1 + 32 * j);
+#pragma unroll
+      for (int i4 = 0; i4 < 8; ++i4) {
+        const float4 b = __ldg(bb + i4);
+        pk[2 * i4] = bf16x2_bits(fmaxf(__uint_as_float(v[4 * i4]) + b.x, 0.f),
+                                 fmaxf(__uint_as_float(v[4 * i4 + 1]) + b.y, 0.f));
+        pk[2 * i4 + 1] = bf16x2_bits(fmaxf(__uint_as_float(v[4 * i4 + 2]) + b.z, 0.f),
+                                     fmaxf(__uint_as_float(v[4 * i4 + 3]) + b.w, 0.f));
+      }
+      tmem_st16(tmem + lane_off + 16u * j, pk);
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    // layer 2: D2 (columns 256..511) = A1 W2^T, A1 from TMEM columns 8 kb .. 8 kb + 7
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int kb = 0; kb < 16; ++kb)
+        mma_ts(tmem + 256u, tmem + 8u * kb, w2desc + (uint64_t)(kb * 16), kb > 0 ? 1u : 0u);
+      mma_commit(mbar2);
+    }
+    if (!mbar_wait(mbar2, phase2)) timeout = true;
+    phase2 ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // layer 1 of the next tile runs on the tensor cores during epilogue 2
+    // (D1 and A1 are free now; its X is complete and visible)
+    cp_async_wait_all();
+    fence_proxy_async();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (next < ntiles) issue_layer1();
+    // epilogue 2: relu(. + b2) and the 3-output layer in FP32
+    float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+#pragma unroll 1
+    for (int j = 0; j < 8; ++j) {
+      uint32_t v[32];
+      tmem_ld32(tmem + lane_off + 256u + 32u * j, v);
+      const float4* bb = reinterpret_cast<const float4*>(b2 + 32 * j);
+      const float4* q0 = reinterpret_cast<const float4*>(w3 + 32 * j);
+      const float4* q1 = reinterpret_cast<const float4*>(w3 + 256 + 32 * j);
+      const float4* q2 = reinterpret_cast<const float4*>(w3 + 512 + 32 * j);
+#pragma unroll
+      for (int i4 = 0; i4 < 8; ++i4) {
+        const float4 b = __ldg(bb + i4), c0 = __ldg(q0 + i4), c1 = __ldg(q1 + i4), c2 = __ldg(q2 + i4);
+        const float a0 = fmaxf(__uint_as_float(v[4 * i4]) + b.x, 0.f);
+        const float a1 = fmaxf(__uint_as_float(v[4 * i4 + 1]) + b.y, 0.f);
+        const float a2 = fmaxf(__uint_as_float(v[4 * i4 + 2]) + b.z, 0.f);
+        const float a3 = fmaxf(__uint_as_float(v[4 * i4 + 3]) + b.w, 0.f);
+        y0 = fmaf(c0.x, a0, fmaf(c0.y, a1, fmaf(c0.z, a2, fmaf(c0.w, a3, y0))));
+        y1 = fmaf(c1.x, a0, fmaf(c1.y, a1, fmaf(c1.z, a2, fmaf(c1.w, a3, y1))));
+        y2 = fmaf(c2.x, a0, fmaf(c2.y, a1, fmaf(c2.z, a2, fmaf(c2.w, a3, y2))));
+      }
+    }
+    if (row < M) {
+      Y[3 * row] = y0 + __ldg(b3);
+      Y[3 * row + 1] = y1 + __ldg(b3 + 1);
+      Y[3 * row + 2] = y2 + __ldg(b3 + 2);
+    }
+    // D2 is read before layer 2 of the next tile overwrites it
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  if (timeout) atomicOr(status, 1u);
+  __syncthreads();
+  if (w == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
+                 : "memory");
+}
+
+}  // namespace
+
+size_t tc_dense_smem(int K) {
+  return (size_t)(TN + TM) * K * 2 + 8 + 16 + TN * sizeof(float);
+}
+
+// out[M][256] = relu(A W^T + b) (BF16, row-major); A [M][K], W [256][K] BF16.
+int tc_dense_relu(const uint16_t* A, long long M, int K, const uint16_t* W, const float* bias,
+                  uint16_t* out, unsigned int* status, int num_sms, cudaStream_t st) {
+  if (K != 128 && K != 256) return set_error(QTV_ERR_ARG, "tc_dense: K = %d (128 or 256)", K);
+  if (M <= 0) return QTV_OK;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(tc_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             227 * 1024);
+    if (e != cudaSuccess) return check_cuda(e, "cudaFuncSetAttribute(tc_dense)");
+    attr = true;
+  }
+  const long long ntiles = (M + TM - 1) / TM;
+  const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
+  tc_dense_kernel<<<grid, 128, tc_dense_smem(K), st>>>(A, M, K, W, bias, out, status);
+  return check_cuda(cudaGetLastError(), "tc_dense_kernel launch");
+}
+
+// Y[M][3] of the whole network on the tensor cores (see tc_mlp_kernel).
+int tc_mlp_forward(const uint16_t* X, long long M, const uint16_t* W1, const uint16_t* W2,
+                   const float* b1, const float* b2, const float* w3, const float* b3, float* Y,
+                   unsigned int* status, int num_sms, cudaStream_t st) {
+  if (M <= 0) return QTV_OK;
+  const size_t smem = (size_t)kMlpSmemW1 + kMlpSmemW2 + kMlpSmemX + 16 + 16;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tc_mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return check_cuda(e, "cudaFuncSetAttribute(tc_mlp)");
+    attr = true;
+  }
+  const long long ntiles = (M + TM - 1) / TM;
+  const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
+  tc_mlp_kernel<<<grid, 128, smem, st>>>(X, M, W1, W2, b1, b2, w3, b3, Y, status);
+  return check_cuda(cudaGetLastError(), "tc_mlp_kernel launch");
+}
+
+}  // namespace qtv

@@ -303,6 +303,16 @@ int locator_localize(qtv_handle h, const FaceGeo& geo, const uint64_t* face_ids,
 // locator is loaded.
 int locator_prepare(qtv_handle h, uint64_t n, uint64_t* generation);
 
+// Dense layer on the 5th-generation tensor cores (locator_tc.cu):
+// out[M][256] = relu(A[M][K] W[256][K]^T + b) in BF16, K = 128 or 256.
+int tc_dense_relu(const uint16_t* A, long long M, int K, const uint16_t* W, const float* bias,
+                  uint16_t* out, unsigned int* status, int num_sms, cudaStream_t st);
+// The whole network, fused: Y[M][3] from X[M][128] (W1, W2 BF16; biases and
+// W3 FP32).
+int tc_mlp_forward(const uint16_t* X, long long M, const uint16_t* W1, const uint16_t* W2,
+                   const float* b1, const float* b2, const float* w3, const float* b3, float* Y,
+                   unsigned int* status, int num_sms, cudaStream_t st);
+
 // Emission pack (localize.cu)
 int emit_pack_launch(qtv_handle h, uint64_t n, const uint64_t* face_ids, const int8_t* winding, const float* xyz,
                      const float* resid, const uint8_t* flags, qtv_sample* out, cudaStream_t st);

@@ -110,6 +110,24 @@ def _oracle_with_bf16_weights(q):
 
 
 def test_forward_matches_oracle(q, small_faces):
+    """The mma.sync layer kernels (the path training uses) against the FP64
+    oracle."""
+    q.locator_init(7)
+    xb, _ = _batch(q, small_faces)
+    q.locator_set_tensor_path(0)
+    try:
+        y = q.locator_forward(xb).cpu().numpy().astype(np.float64)
+    finally:
+        q.locator_set_tensor_path(1)
+    _, d = _oracle_with_bf16_weights(q)
+    yo, _ = mlp.forward(d, bf16_to_f64(xb))
+    scale = np.sqrt(np.mean(yo ** 2))
+    assert np.max(np.abs(y - yo)) < 2e-2 * scale
+
+
+def test_tcgen05_forward_matches_oracle(q, small_faces):
+    """The fused tcgen05 network (the default inference path: accumulators and
+    hidden activations in tensor memory) against the FP64 oracle."""
     q.locator_init(7)
     xb, _ = _batch(q, small_faces)
     y = q.locator_forward(xb).cpu().numpy().astype(np.float64)
@@ -117,6 +135,31 @@ def test_forward_matches_oracle(q, small_faces):
     yo, _ = mlp.forward(d, bf16_to_f64(xb))
     scale = np.sqrt(np.mean(yo ** 2))
     assert np.max(np.abs(y - yo)) < 2e-2 * scale
+
+
+def test_tcgen05_matches_mma_path_on_many_tiles(q):
+    """Ragged row count over many 128-row tiles (more tiles than SMs, so every
+    persistent CTA loops and prefetches): the two tensor paths agree to
+    accumulation order."""
+    q.locator_init(3)
+    n = 128 * 152 * 3 + 77
+    g = torch.Generator(device="cpu").manual_seed(5)
+    xf = torch.randn((n, 128), generator=g) * 0.7
+    x = xf.to(torch.bfloat16).view(torch.int16).cuda()
+    q.locator_set_tensor_path(0)
+    try:
+        y0 = q.locator_forward(x)
+    finally:
+        q.locator_set_tensor_path(1)
+    y1 = q.locator_forward(x)
+    scale = float(torch.sqrt(torch.mean(y0 ** 2)))
+    assert torch.isfinite(y1).all()
+    assert float(torch.max(torch.abs(y1 - y0))) < 2e-2 * scale
+    # rows on both sides of tile and CTA boundaries against the FP64 oracle
+    _, d = _oracle_with_bf16_weights(q)
+    rows = np.r_[0:3, 125:131, 127 * 152 - 2:127 * 152 + 3, n - 80:n]
+    yo, _ = mlp.forward(d, bf16_to_f64(x[torch.from_numpy(rows).cuda()]))
+    assert np.max(np.abs(y1[torch.from_numpy(rows).cuda()].cpu().numpy() - yo)) < 2e-2 * scale
 
 
 def test_gradients_match_oracle(q, small_faces):
@@ -219,6 +262,31 @@ def test_gain_over_plain_on_noisy_field(q, trained):
     rms_plain = learned.rms_h(uv_plain_noisy, test["t"][:, :2])
     print(f"noisy field vs clean cores: plain {rms_plain:.4f} h, learned {rms_learned:.4f} h")
     assert rms_plain <= 0.05 and rms_learned <= 0.05
+
+
+def test_learned_localize_tcgen05_path(q, trained):
+    """Learned localization on the tcgen05 network: the same faces accepted (up
+    to a handful at the acceptance threshold) and positions close to the
+    mma.sync layer kernels: RMS difference below 1e-3 h, every face within
+    1e-2 h (the accumulation orders differ, which can flip the BF16 rounding of
+    a hidden activation)."""
+    import paper_1911_12070_gb300 as qtv
+
+    _, test, clean, noisy = trained
+    ids, w = test["ids"], test["w"]
+    q.locator_set_tensor_path(0)
+    try:
+        xyz0, _, fl0 = q.localize(clean, ids, w, mode=qtv.LEARNED, fallback_resid=1e-3)
+    finally:
+        q.locator_set_tensor_path(1)
+    xyz1, _, fl1 = q.localize(clean, ids, w, mode=qtv.LEARNED, fallback_resid=1e-3)
+    same = fl0 == fl1
+    assert float(same.float().mean()) > 0.999
+    d = torch.linalg.norm(xyz1 - xyz0, dim=1)[same]
+    print(f"tcgen05 vs mma.sync: RMS {float(torch.sqrt(torch.mean(d ** 2))):.2e} h, "
+          f"max {float(d.max()):.2e} h")
+    assert float(torch.sqrt(torch.mean(d ** 2))) < 1e-3
+    assert float(d.max()) < 1e-2
 
 
 def test_learned_localize_fallback_is_plain(q, trained):
