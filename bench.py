@@ -212,6 +212,16 @@ def learned_report(q, psi, ids, wnd, F, stream, reps=20):
         torch.cuda.synchronize()
         ms[key] = e0.elapsed_time(e1) / reps
     q.locator_set_tensor_path(1 if ms["tcgen05"] < ms["mma"] else 0)
+    # split of learned localization (library trace, tcgen05 path)
+    q.trace_enable(True)
+    q.trace_read(reset=True)
+    q.locator_set_tensor_path(1)
+    for _ in range(reps):
+        q.localize_into(psi, fid, w, *outs["tcgen05"], mode=qtv.LEARNED, fallback_resid=1e-3)
+    torch.cuda.synchronize()
+    q.trace_enable(False)
+    split = {k: v[1] / reps for k, v in q.trace_read(reset=True).items()
+             if k in ("encode", "network", "head")}
     xyz_p, _, fl_p = outs["plain"]
     xyz_l, _, fl_l = outs["tcgen05"]
     good = (fl_p & qtv.FLAG_ANOMALOUS) == 0
@@ -227,6 +237,7 @@ def learned_report(q, psi, ids, wnd, F, stream, reps=20):
                   "seconds": fit_s, "final_loss": float(np.mean(losses[-50:]))},
         "plain_ms": ms["plain"], "learned_ms": ms["tcgen05"],
         "learned_mma_sync_ms": ms["mma"],
+        "learned_split_ms": split,
         "learned_mlp_tflops": flop / (ms["tcgen05"] * 1e-3) / 1e12,
         "tensor_path": "tcgen05 (accumulators in tensor memory)",
         "accepted_frac": float(accepted.float().mean()),

@@ -363,8 +363,9 @@ QTV_API int qtv_batch_run(qtv_handle h, uint64_t* face_ids, int8_t* winding, uin
 /*
  * Kernel timing trace.  While enabled, the handle records a pair of CUDA
  * events on the launching stream around each of its kernel launches (names:
- * "sweep", "seg_scan", "scatter", "stats", "localize", "emit_pack", and
- * "batch" for one replay of a batch graph).
+ * "sweep", "seg_scan", "scatter", "stats", "localize", "emit_pack", "batch"
+ * for one replay of a batch graph, and "encode", "network", "head" for the
+ * parts of learned localization).
  * qtv_trace_read waits for the recorded events, writes up to max_entries
  * per-kernel totals (launch count and summed device time) and, if reset is
  * nonzero, clears the record.  Tracing adds host work per launch; leave it

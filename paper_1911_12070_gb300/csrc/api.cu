@@ -117,8 +117,9 @@ cudaEvent_t take_event(qtv_handle h) {
   if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
   return e;
 }
-const char* kKernelNames[K_COUNT] = {"sweep", "seg_scan", "scatter", "stats", "localize",
-                                     "emit_pack", "batch"};
+const char* kKernelNames[K_COUNT] = {"sweep",     "seg_scan", "scatter", "stats",
+                                     "localize",  "emit_pack", "batch",  "encode",
+                                     "network",   "head"};
 }  // namespace
 
 TraceScope::TraceScope(qtv_handle h_, int k, cudaStream_t s) : h(h_), kernel(k), st(s) {

@@ -672,13 +672,19 @@ int locator_localize(qtv_handle h, const FaceGeo& geo, const uint64_t* face_ids,
   const unsigned long long chunk = n < kLocChunk ? n : kLocChunk;
   int rc = locator_rows(h, chunk, st);
   if (rc) return rc;
-  TraceScope ts(h, K_LOCALIZE, st);
   for (unsigned long long f0 = 0; f0 < n; f0 += chunk) {
     const unsigned long long m = n - f0 < chunk ? n - f0 : chunk;
-    encode_kernel<<<blocks_for(m * 32, 256, 65535), 256, 0, st>>>(geo, f0, m, n, n_dev, face_ids,
-                                                                  winding, L->X, L->ok, L->rms);
-    rc = forward_y(L, L->X, m, L->Y, st);
+    {
+      TraceScope ts(h, K_ENCODE, st);
+      encode_kernel<<<blocks_for(m * 32, 256, 65535), 256, 0, st>>>(
+          geo, f0, m, n, n_dev, face_ids, winding, L->X, L->ok, L->rms);
+    }
+    {
+      TraceScope ts(h, K_NETWORK, st);
+      rc = forward_y(L, L->X, m, L->Y, st);
+    }
     if (rc) return rc;
+    TraceScope ts(h, K_HEAD, st);
     head_kernel<<<blocks_for(m, 256, 65535), 256, 0, st>>>(geo, f0, m, n, n_dev, face_ids, winding,
                                                            L->Y, L->ok, L->rms, thresh, xyz, resid,
                                                            flags, nullptr);

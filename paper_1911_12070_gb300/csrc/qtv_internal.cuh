@@ -75,7 +75,8 @@ namespace qtv {
 struct Locator;  // learned locator state (locator.cu)
 void locator_free(Locator* L);
 enum KernelId {
-  K_SWEEP = 0, K_SEG_SCAN, K_SCATTER, K_STATS, K_LOCALIZE, K_EMIT_PACK, K_BATCH, K_COUNT
+  K_SWEEP = 0, K_SEG_SCAN, K_SCATTER, K_STATS, K_LOCALIZE, K_EMIT_PACK, K_BATCH,
+  K_ENCODE, K_NETWORK, K_HEAD, K_COUNT
 };
 struct BatchPlan;  // batched snapshots (batch.cu)
 void batch_free(BatchPlan* b);
