@@ -63,6 +63,8 @@ def parse():
                    help="skip the 16-snapshot batch against per-snapshot launches")
     p.add_argument("--no-learned", action="store_true",
                    help="skip training the learned locator and its report against plain")
+    p.add_argument("--no-node-form", action="store_true",
+                   help="skip the node-form circulation and density-error report")
     return p.parse_args()
 
 
@@ -243,6 +245,66 @@ def learned_report(q, psi, ids, wnd, F, stream, reps=20):
         "accepted_frac": float(accepted.float().mean()),
         "rms_vs_plain_h": rms_all, "rms_vs_plain_accepted_h": rms_acc,
         "fallback_resid": 1e-3,
+    }
+
+
+def node_form_report(q, psi, xyz, count, stream, reps=20):
+    """Node form of the circulation (Sec. 2.2.2: ring of 8 neighbours per node and
+    plane, vortex node iff max |C| > pi) on the bench field, and the density error
+    of Eq. 7 at the plain samples of the timed step (count read on the device)."""
+    import torch
+
+    from paper_1911_12070_gb300 import QtvError
+
+    nodes = psi.numel()
+    dev = psi.device
+    cap = int(0.04 * nodes) + 1024
+    ids = torch.empty(cap, dtype=torch.int64, device=dev)
+    circ = torch.empty((cap, 3), dtype=torch.int8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    try:
+        for _ in range(3):
+            q.node_circulation_into(psi, ids, circ, cnt)
+            q.density_error(psi, xyz, n_dev=count)
+        torch.cuda.synchronize()
+        nv = int(cnt.item())
+        if nv > cap:
+            return {"error": f"capacity {cap} below {nv} vortex nodes"}
+        q.trace_enable(True)
+        q.trace_read(reset=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            q.node_circulation_into(psi, ids, circ, cnt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tr = q.trace_read(reset=True)
+        for _ in range(reps):
+            e, mean_rho, rho_bar = q.density_error(psi, xyz, n_dev=count)
+        tr_d = q.trace_read(reset=True)
+        q.trace_enable(False)
+    except QtvError as err:
+        return {"error": str(err)}
+    peak, peak_kind = peaks()
+    kms = {k: v[1] / max(1, v[0]) for k, v in tr.items()}
+    nf_ms = kms.get("node_form", 0.0)
+    # algorithmic bytes: psi read once (8 B per node) + the vortex-node list
+    # (8 B id + 3 B of windings per vortex node)
+    alg = 8 * nodes + 11 * nv
+    ach = alg / (nf_ms * 1e-3) / 1e9 if nf_ms > 0 else 0.0
+    d_ms = tr_d.get("density", (1, 0.0))
+    return {
+        "ms_per_call": e0.elapsed_time(e1) / reps,
+        "kernels_ms": kms,
+        "vortex_nodes": nv,
+        "vortex_node_fraction": nv / nodes,
+        "roofline": {"bound": "hbm", "kernel": "node_form", "achieved": ach, "peak": peak,
+                     "unit": "GB/s", "frac": ach / peak, "peak_source": peak_kind,
+                     "algorithmic_bytes": alg},
+        "density_error": {"e": e, "mean_abs_rho": mean_rho, "rho_bar": rho_bar,
+                          "ms": d_ms[1] / max(1, d_ms[0]),
+                          "points": "plain samples of the timed step"},
     }
 
 
@@ -589,6 +651,9 @@ def run_qtv(args):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+
+    if rank == 0 and not args.no_node_form:
+        line["node_form"] = node_form_report(q, psi, xyz, count, stream)
 
     if rank == 0 and not args.no_learned:
         line["learned"] = learned_report(q, psi, ids, wnd, F, stream)

@@ -361,11 +361,65 @@ QTV_API int qtv_batch_run(qtv_handle h, uint64_t* face_ids, int8_t* winding, uin
                           float fallback_resid, void* stream);
 
 /*
+ * Node form of the circulation (Sec. 2.2.2): for every node and each of the
+ * three grid planes through it, the circulation of Eq. 5 around the ring of
+ * the node's eight in-plane neighbours (the 2h x 2h square centred on the
+ * node, counter-clockwise about the plane normal +z, +x, +y for the planes
+ * xy, yz, zx), reported as the integer S = C / (2 pi) in [-4, 4].  A node is a
+ * vortex node when max over its planes |C| > pi, i.e. some S != 0.  S = 0 where
+ * the ring leaves the grid or passes through a NaN/Inf node (the centre node
+ * is not on its ring).  Each ring edge uses the integer branch crossing of
+ * qtv_identify, so S equals the sum of the four incident plaquette windings
+ * whenever those are defined; it equals the FP64 definition on every ring
+ * whose eight edge phase differences lie at least 1e-4 rad from +-pi.
+ *
+ *   psi       device, complex64 field (conventions above; 8-byte aligned).
+ *   node_ids  device, uint64[capacity]: linear indices (k*ny + j)*nx + i of
+ *             the vortex nodes, ascending.
+ *   circ      device, int8[capacity][3]: S of the planes xy, yz, zx of each
+ *             listed node.
+ *   capacity  length of node_ids (and of circ in triples).
+ *   count     device, one uint64: receives the number of vortex nodes; if it
+ *             exceeds capacity the lists are incomplete (retry with a larger
+ *             capacity).  capacity = 0 with NULL lists counts only.
+ *   dense     device int8[3][nz][ny][nx] receiving S of every node and plane,
+ *             or NULL.
+ * The handle keeps its own workspace for this call (staging of capacity
+ * records, per-(plane, band) tables); it grows on demand outside stream
+ * capture.  Grids must have fewer than 2^52 nodes.
+ */
+QTV_API int qtv_node_circulation(qtv_handle h, const qtv_grid* grid, const void* psi,
+                                 uint64_t* node_ids, int8_t* circ, uint64_t capacity,
+                                 uint64_t* count, int8_t* dense, void* stream);
+
+/*
+ * Density error of the sample points (Eq. 7, Sec. 5):
+ *   e = (sum over the n points of |rho(p)|) / (n * rho_bar),
+ * rho = |psi|^2 of the trilinearly interpolated field at p (Sec. 5: psi is
+ * linearly interpolated between nodes), rho_bar = mean |psi|^2 over all nodes.
+ *
+ *   xyz    device float[n][3], positions origin + h * (grid coordinates), as
+ *          written by qtv_localize.  A point outside the grid gets rho = NaN
+ *          (and e becomes NaN).
+ *   n      host bound on the number of points; n_dev (optional device uint64)
+ *          limits it to min(n, *n_dev) without a host synchronisation.
+ *   rho    optional device float[n]: rho at each point (FP32 interpolation).
+ *   out    device double[3]: {e, mean |rho| over the points, rho_bar}; e = 0
+ *          for no points.
+ * Sums are FP32 over runs of at most 8 squares and FP64 across runs, in an
+ * order fixed by the device's SM count, so repeated calls agree bit for bit.
+ */
+QTV_API int qtv_density_error(qtv_handle h, const qtv_grid* grid, const void* psi,
+                              const float* xyz, uint64_t n, const uint64_t* n_dev, float* rho,
+                              double* out, void* stream);
+
+/*
  * Kernel timing trace.  While enabled, the handle records a pair of CUDA
  * events on the launching stream around each of its kernel launches (names:
  * "sweep", "seg_scan", "scatter", "stats", "localize", "emit_pack", "batch"
- * for one replay of a batch graph, and "encode", "network", "head" for the
- * parts of learned localization).
+ * for one replay of a batch graph, "encode", "network", "head" for the
+ * parts of learned localization, "node_form", "node_scan", "node_scatter"
+ * for the node form and "density" for the density error).
  * qtv_trace_read waits for the recorded events, writes up to max_entries
  * per-kernel totals (launch count and summed device time) and, if reset is
  * nonzero, clears the record.  Tracing adds host work per launch; leave it

@@ -139,6 +139,10 @@ def lib() -> ctypes.CDLL:
         L.qtv_batch_run.argtypes = [P, P, P, u64, P, P, P, P, i32, f32, P]
         for name in ("qtv_batch_plan", "qtv_batch_info_get", "qtv_batch_run"):
             getattr(L, name).restype = i32
+        L.qtv_node_circulation.argtypes = [P, ctypes.POINTER(Grid), P, P, P, u64, P, P, P]
+        L.qtv_density_error.argtypes = [P, ctypes.POINTER(Grid), P, P, u64, P, P, P, P]
+        for name in ("qtv_node_circulation", "qtv_density_error"):
+            getattr(L, name).restype = i32
         L.qtv_trace_enable.argtypes = [P, i32]
         L.qtv_trace_read.argtypes = [P, ctypes.POINTER(TraceEntry), i32, ctypes.POINTER(i32), i32]
         for name in ("qtv_create", "qtv_destroy", "qtv_reserve", "qtv_identify", "qtv_localize",
@@ -433,6 +437,59 @@ class Qtv:
 
     def locator_load(self, path: str):
         _check(lib().qtv_locator_load(self.h, path.encode()))
+
+    # -- node form of the circulation and the density error ---------------------------
+    def node_circulation_into(self, psi, node_ids, circ, count, dense=None, grid=None,
+                              stream=None):
+        """Raw call: preallocated device outputs (count: uint64[1])."""
+        g = grid or Grid.of(tuple(psi.shape))
+        cap = 0 if node_ids is None else node_ids.numel()
+        _check(lib().qtv_node_circulation(self.h, ctypes.byref(g), _ptr(psi), _ptr(node_ids),
+                                          _ptr(circ), cap, _ptr(count), _ptr(dense),
+                                          _stream_ptr(stream)))
+
+    def node_circulation(self, psi, capacity: int | None = None, dense: bool = False,
+                         stream=None):
+        """Vortex nodes of psi by the ring circulation of every node and plane.
+
+        Returns (node_ids int64 [n] ascending, circ int8 [n, 3] = C / (2 pi) of the
+        planes xy, yz, zx, dense int8 [3, nz, ny, nx] or None).  Grows the output
+        and retries when the capacity is too small."""
+        import torch
+
+        dev = psi.device
+        nz, ny, nx = psi.shape
+        if capacity is None:
+            capacity = max(1024, int(0.06 * nx * ny * nz))
+        count = torch.zeros(1, dtype=torch.int64, device=dev)
+        d = torch.empty((3, nz, ny, nx), dtype=torch.int8, device=dev) if dense else None
+        for _ in range(2):
+            ids = torch.empty(capacity, dtype=torch.int64, device=dev)
+            circ = torch.empty((capacity, 3), dtype=torch.int8, device=dev)
+            self.node_circulation_into(psi, ids, circ, count, d, stream=stream)
+            n = int(count.item())
+            if n <= capacity:
+                break
+            capacity = n
+        return ids[:n], circ[:n], d
+
+    def density_error(self, psi, xyz, n_dev=None, want_rho: bool = False, grid=None,
+                      stream=None):
+        """Eq. 7 at the points xyz (float32 [n, 3] on the device).
+
+        Returns (e, mean |rho| over the points, rho_bar) as floats, plus rho
+        (float32 [n]) when want_rho."""
+        import torch
+
+        g = grid or Grid.of(tuple(psi.shape))
+        n = xyz.shape[0]
+        out = torch.zeros(3, dtype=torch.float64, device=psi.device)
+        rho = torch.empty(max(n, 1), dtype=torch.float32, device=psi.device) if want_rho else None
+        _check(lib().qtv_density_error(self.h, ctypes.byref(g), _ptr(psi),
+                                       _ptr(xyz) if n else None, n, _ptr(n_dev), _ptr(rho),
+                                       _ptr(out), _stream_ptr(stream)))
+        e, m, rb = (float(v) for v in out.cpu().tolist())
+        return (e, m, rb, rho[:n]) if want_rho else (e, m, rb)
 
     # -- emission -------------------------------------------------------------------
     def emit_samples(self, face_ids, winding, xyz, resid, flags, out=None, stream=None):

@@ -117,9 +117,10 @@ cudaEvent_t take_event(qtv_handle h) {
   if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
   return e;
 }
-const char* kKernelNames[K_COUNT] = {"sweep",     "seg_scan", "scatter", "stats",
-                                     "localize",  "emit_pack", "batch",  "encode",
-                                     "network",   "head"};
+const char* kKernelNames[K_COUNT] = {"sweep",     "seg_scan",  "scatter",      "stats",
+                                     "localize",  "emit_pack", "batch",        "encode",
+                                     "network",   "head",      "node_form",    "node_scan",
+                                     "node_scatter", "density"};
 }  // namespace
 
 TraceScope::TraceScope(qtv_handle h_, int k, cudaStream_t s) : h(h_), kernel(k), st(s) {
@@ -189,6 +190,7 @@ int qtv_destroy(qtv_handle h) {
   cudaFree(h->ws.tiles);
   locator_free(h->loc);
   batch_free(h->batch);
+  node_work_free(h->node);
   for (auto& r : h->trace) {
     cudaEventDestroy(r.start);
     cudaEventDestroy(r.stop);
@@ -337,6 +339,50 @@ int qtv_identify_localize(qtv_handle h, const qtv_grid* grid, const void* psi,
   return identify_launch(h, g, reinterpret_cast<const float2*>(psi), face_ids, winding, capacity,
                          count, stats, st, scratch_of(h), 0, capacity > 0 ? xyz : nullptr, resid,
                          flags);
+}
+
+int qtv_node_circulation(qtv_handle h, const qtv_grid* grid, const void* psi, uint64_t* node_ids,
+                         int8_t* circ, uint64_t capacity, uint64_t* count, int8_t* dense,
+                         void* stream) {
+  if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
+  int rc = validate_grid(grid);
+  if (rc) return rc;
+  if (!count) return set_error(QTV_ERR_ARG, "count is NULL");
+  if (capacity > 0 && (!node_ids || !circ))
+    return set_error(QTV_ERR_ARG, "an output list is NULL with capacity %llu",
+                     (unsigned long long)capacity);
+  if (capacity > 0xFFFFFFFFull)
+    return set_error(QTV_ERR_ARG, "capacity above 2^32-1 is not supported");
+  const qtv_grid& g = *grid;
+  const unsigned long long nn = (unsigned long long)g.nx * g.ny * g.nz;
+  if (nn >> 52) return set_error(QTV_ERR_ARG, "grid of 2^52 nodes or more");
+  if (nn > 0 && !psi) return set_error(QTV_ERR_ARG, "psi is NULL");
+  if (reinterpret_cast<uintptr_t>(psi) & 7u)
+    return set_error(QTV_ERR_ARG, "psi must be 8-byte aligned");
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return set_error(QTV_ERR_CUDA, "cudaSetDevice failed");
+  return node_circulation_launch(h, g, reinterpret_cast<const float2*>(psi), node_ids, circ,
+                                 capacity, count, dense, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int qtv_density_error(qtv_handle h, const qtv_grid* grid, const void* psi, const float* xyz,
+                      uint64_t n, const uint64_t* n_dev, float* rho, double* out, void* stream) {
+  if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
+  int rc = validate_grid(grid);
+  if (rc) return rc;
+  if (!out) return set_error(QTV_ERR_ARG, "out is NULL");
+  const qtv_grid& g = *grid;
+  const unsigned long long nn = (unsigned long long)g.nx * g.ny * g.nz;
+  if (nn == 0) return set_error(QTV_ERR_ARG, "empty grid");
+  if (!psi) return set_error(QTV_ERR_ARG, "psi is NULL");
+  if (reinterpret_cast<uintptr_t>(psi) & 7u)
+    return set_error(QTV_ERR_ARG, "psi must be 8-byte aligned");
+  if (n > 0 && !xyz)
+    return set_error(QTV_ERR_ARG, "xyz is NULL with n = %llu", (unsigned long long)n);
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return set_error(QTV_ERR_CUDA, "cudaSetDevice failed");
+  return density_error_launch(h, g, reinterpret_cast<const float2*>(psi), xyz, n, n_dev, rho, out,
+                              reinterpret_cast<cudaStream_t>(stream));
 }
 
 int qtv_localize(qtv_handle h, const qtv_grid* grid, const void* psi, const uint64_t* face_ids,

@@ -76,10 +76,12 @@ struct Locator;  // learned locator state (locator.cu)
 void locator_free(Locator* L);
 enum KernelId {
   K_SWEEP = 0, K_SEG_SCAN, K_SCATTER, K_STATS, K_LOCALIZE, K_EMIT_PACK, K_BATCH,
-  K_ENCODE, K_NETWORK, K_HEAD, K_COUNT
+  K_ENCODE, K_NETWORK, K_HEAD, K_NODE_FORM, K_NODE_SCAN, K_NODE_SCATTER, K_DENSITY, K_COUNT
 };
 struct BatchPlan;  // batched snapshots (batch.cu)
 void batch_free(BatchPlan* b);
+struct NodeWork;   // node-form and density-error workspace (node_form.cu)
+void node_work_free(NodeWork* w);
 struct TraceRec {
   int kernel;
   cudaEvent_t start, stop;
@@ -95,6 +97,7 @@ struct qtv_handle_s {
   std::vector<cudaEvent_t> event_pool;   // free events
   qtv::Locator* loc = nullptr;           // learned locator (weights, Adam state, buffers)
   qtv::BatchPlan* batch = nullptr;       // batch plan, scratch and captured graph
+  qtv::NodeWork* node = nullptr;         // node-form / density-error workspace
   // sweep shape of single-snapshot calls (qtv_configure_sweep); -1 / 0 = default
   int sweep_variant = -1, sweep_nwt = 0, sweep_stages = 0, sweep_ctas = 0;
 };
@@ -313,6 +316,16 @@ int tc_dense_relu(const uint16_t* A, long long M, int K, const uint16_t* W, cons
 int tc_mlp_forward(const uint16_t* X, long long M, const uint16_t* W1, const uint16_t* W2,
                    const float* b1, const float* b2, const float* w3, const float* b3, float* Y,
                    unsigned int* status, int num_sms, cudaStream_t st);
+
+// Node form of the circulation: vortex nodes in ascending order with their
+// three ring windings, optional dense field (node_form.cu)
+int node_circulation_launch(qtv_handle h, const qtv_grid& g, const float2* psi,
+                            uint64_t* node_ids, int8_t* circ, uint64_t capacity, uint64_t* count,
+                            int8_t* dense, cudaStream_t st);
+// Density error of Eq. 7 at n sample points (node_form.cu)
+int density_error_launch(qtv_handle h, const qtv_grid& g, const float2* psi, const float* xyz,
+                         uint64_t n, const uint64_t* n_dev, float* rho, double* out,
+                         cudaStream_t st);
 
 // Emission pack (localize.cu)
 int emit_pack_launch(qtv_handle h, uint64_t n, const uint64_t* face_ids, const int8_t* winding, const float* xyz,
