@@ -3,7 +3,9 @@
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` are the only callers.  It shares no code with
 the CUDA path.  ``qtv_oracle.c`` holds identification (Sec. 2.2.2, Eq. 5) and
-plaquette localization (Sec. 3.3.3, Eq. 6); ``graph.py`` holds the graph
+plaquette localization (Sec. 3.3.3, Eq. 6), the node form of the circulation,
+the density of the interpolated field and the refinement of sample points in
+the plane normal to the pseudo-vorticity (Sec. 3.3.3); ``graph.py`` holds the graph
 pipeline of Sec. 3.1-3.4; ``mlp.py`` holds the learned-locator network in FP64.
 
 Flag bits returned by :func:`identify` (per face):
@@ -23,6 +25,7 @@ import numpy as np
 
 AMBIGUOUS, ZERO_NODE, NONFINITE, ABSENT, RESIDUAL = 1, 2, 4, 8, 16
 L_ANOMALOUS, L_ILLCOND = 1, 2
+R_CONVERGED, R_NO_TANGENT, R_MAX_ITER = 1, 2, 4
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qtv_oracle.c")
@@ -60,6 +63,9 @@ def lib() -> ctypes.CDLL:
         L.oracle_localize.restype = i64
         L.oracle_density.argtypes = [i32, i32, i32, P, i64, P, P]
         L.oracle_density.restype = None
+        L.oracle_refine.argtypes = [i32, i32, i32, P, i64, P, i32, ctypes.c_double, P, P, P, P,
+                                    P, P]
+        L.oracle_refine.restype = None
         L.oracle_set_threads.argtypes = [i32]
         L.oracle_max_threads.restype = i32
         _lib = L
@@ -146,3 +152,26 @@ def density(psi: np.ndarray, points: np.ndarray) -> np.ndarray:
     rho = np.zeros(p.shape[0])
     lib().oracle_density(nx, ny, nz, psi.ctypes.data, p.shape[0], p.ctypes.data, rho.ctypes.data)
     return rho
+
+
+def refine(psi: np.ndarray, x0: np.ndarray, max_iter: int = 200, tol: float = 1e-7):
+    """Sample refinement of Sec. 3.3.3: gradient descent of rho in the plane
+    through each x0 (grid coordinates, [n, 3]) normal to the pseudo-vorticity.
+
+    Returns dict: xyz [n, 3], rho [n], t [n, 3] (unit tangent), detj [n] (2x2
+    in-plane Jacobian determinant of psi at the result), iters [n], flags [n]
+    (R_CONVERGED, R_NO_TANGENT, R_MAX_ITER)."""
+    psi = _psi_f32(psi)
+    nz, ny, nx = psi.shape
+    p = np.ascontiguousarray(x0, dtype=np.float64).reshape(-1, 3)
+    n = p.shape[0]
+    xyz = np.zeros((n, 3))
+    rho = np.zeros(n)
+    t = np.zeros((n, 3))
+    dj = np.zeros(n)
+    it = np.zeros(n, np.int32)
+    fl = np.zeros(n, np.uint8)
+    lib().oracle_refine(nx, ny, nz, psi.ctypes.data, n, p.ctypes.data, int(max_iter), float(tol),
+                        xyz.ctypes.data, rho.ctypes.data, t.ctypes.data, dj.ctypes.data,
+                        it.ctypes.data, fl.ctypes.data)
+    return {"xyz": xyz, "rho": rho, "t": t, "detj": dj, "iters": it, "flags": fl}

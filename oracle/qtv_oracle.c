@@ -478,3 +478,233 @@ void oracle_density(int nx, int ny, int nz, const float* psi, long n, const doub
     rho[q] = cabs2(acc);
   }
 }
+
+/* ---------------------------------------------------------------------------
+ * Sample refinement (Sec. 3.3.3, "Locating more accurate sample points"): an
+ * initial estimate x0 of a core sample (the paper uses the box means of the
+ * graph reduction) is moved to a minimizer of rho = |psi|^2 (Eq. 6) within
+ * the plane through x0 perpendicular to the local core direction t, which the
+ * paper takes from the pseudo-vorticity of Rorai et al.:
+ *   t = grad Re psi x grad Im psi at x0, normalized.
+ * Readings where the paper is silent:
+ *   - psi between nodes is the trilinear interpolant (Sec. 5: linearly
+ *     interpolated); rho and its gradient are those of that interpolant,
+ *     the gradient taken within the cell floor(x) (index clamped to
+ *     [0, n - 2], as in oracle_density);
+ *   - grad Re psi and grad Im psi at x0 are the node gradients by central
+ *     differences (one-sided on the boundary, 0 along an axis of one node)
+ *     interpolated trilinearly;
+ *   - gradient descent on the in-plane gradient g = grad rho - (grad rho . t) t;
+ *     each step starts at alpha = 2 rho / |g|^2 (the exact step for a round
+ *     bowl whose minimum is 0) and halves alpha until the Armijo condition
+ *     rho(x - alpha g) <= rho(x) - 1e-4 alpha |g|^2 holds with the new point
+ *     inside the grid and inside the box |x - x0|_inf <= 1 (grid units); a
+ *     step that would leave either is rejected, not projected, so a result on
+ *     the grid or box boundary is a constrained stop;
+ *   - it stops, converged, when no step of length >= tol decreases rho that
+ *     way (or g = 0), or after max_iter accepted steps.
+ * Per sample: x, rho(x), t, the determinant of the 2x2 real Jacobian of psi
+ * with respect to in-plane coordinates (e1, e2) at x (conditioning), the
+ * number of steps taken, and flags: 1 converged, 2 no tangent (the cross
+ * product is zero or x0 lies outside the grid: x = x0), 4 step limit.
+ * ------------------------------------------------------------------------- */
+#define OR_CONVERGED 1u
+#define OR_NO_TANGENT 2u
+#define OR_MAX_ITER 4u
+
+/* cell of x along an axis of n nodes: floor(x) clamped to [0, n-2] (0 if n < 2) */
+static long cell_of(double x, long n) {
+  long i = (long)floor(x);
+  if (i > n - 2) i = n - 2;
+  if (i < 0) i = 0;
+  return i;
+}
+
+static int inside_grid(const double x[3], long nx, long ny, long nz) {
+  return x[0] >= 0 && x[1] >= 0 && x[2] >= 0 && x[0] <= nx - 1 && x[1] <= ny - 1 &&
+         x[2] <= nz - 1;
+}
+
+/* trilinear psi at x and its partial derivatives d[0..2] within cell floor(x) */
+static ocplx trilinear_eval(const float* psi, long nx, long ny, long nz, const double x[3],
+                            ocplx d[3]) {
+  const long i = cell_of(x[0], nx), j = cell_of(x[1], ny), k = cell_of(x[2], nz);
+  const double f[3] = {x[0] - i, x[1] - j, x[2] - k};
+  const long base[3] = {i, j, k}, n[3] = {nx, ny, nz};
+  ocplx acc = {0.0, 0.0};
+  for (int a = 0; a < 3; ++a) d[a].re = d[a].im = 0.0;
+  for (int c = 0; c < 8; ++c) {
+    long idx[3];
+    double w[3], dw[3];
+    for (int a = 0; a < 3; ++a) {
+      const int bit = (c >> a) & 1;
+      idx[a] = base[a] + bit < n[a] ? base[a] + bit : base[a];
+      w[a] = bit ? f[a] : 1.0 - f[a];
+      dw[a] = bit ? 1.0 : -1.0;
+    }
+    const ocplx v = node_value(psi, nx, ny, idx[0], idx[1], idx[2]);
+    const double wt = w[0] * w[1] * w[2];
+    acc.re += wt * v.re;
+    acc.im += wt * v.im;
+    const double dd[3] = {dw[0] * w[1] * w[2], w[0] * dw[1] * w[2], w[0] * w[1] * dw[2]};
+    for (int a = 0; a < 3; ++a) {
+      d[a].re += dd[a] * v.re;
+      d[a].im += dd[a] * v.im;
+    }
+  }
+  return acc;
+}
+
+/* central-difference gradient of psi at node (i,j,k) along axis a */
+static ocplx node_grad(const float* psi, long nx, long ny, long nz, long i, long j, long k, int a) {
+  const long n[3] = {nx, ny, nz};
+  long p[3] = {i, j, k}, q[3] = {i, j, k};
+  double s = 0.5;
+  if (n[a] < 2) {
+    ocplx z = {0.0, 0.0};
+    return z;
+  }
+  if (p[a] == 0) {
+    q[a] = 1;
+    s = 1.0;
+  } else if (p[a] == n[a] - 1) {
+    p[a] = n[a] - 2;
+    s = 1.0;
+  } else {
+    p[a] -= 1;
+    q[a] += 1;
+  }
+  const ocplx lo = node_value(psi, nx, ny, p[0], p[1], p[2]);
+  const ocplx hi = node_value(psi, nx, ny, q[0], q[1], q[2]);
+  return cscale(csub(hi, lo), s);
+}
+
+/* pseudo-vorticity direction at x: interpolated node gradients, cross product */
+static void pseudo_vorticity(const float* psi, long nx, long ny, long nz, const double x[3],
+                             double t[3]) {
+  const long i = cell_of(x[0], nx), j = cell_of(x[1], ny), k = cell_of(x[2], nz);
+  const double f[3] = {x[0] - i, x[1] - j, x[2] - k};
+  const long base[3] = {i, j, k}, n[3] = {nx, ny, nz};
+  double gr[3] = {0, 0, 0}, gi[3] = {0, 0, 0};
+  for (int c = 0; c < 8; ++c) {
+    long idx[3];
+    double wt = 1.0;
+    for (int a = 0; a < 3; ++a) {
+      const int bit = (c >> a) & 1;
+      idx[a] = base[a] + bit < n[a] ? base[a] + bit : base[a];
+      wt *= bit ? f[a] : 1.0 - f[a];
+    }
+    for (int a = 0; a < 3; ++a) {
+      const ocplx g = node_grad(psi, nx, ny, nz, idx[0], idx[1], idx[2], a);
+      gr[a] += wt * g.re;
+      gi[a] += wt * g.im;
+    }
+  }
+  t[0] = gr[1] * gi[2] - gr[2] * gi[1];
+  t[1] = gr[2] * gi[0] - gr[0] * gi[2];
+  t[2] = gr[0] * gi[1] - gr[1] * gi[0];
+}
+
+static double rho_at(const float* psi, long nx, long ny, long nz, const double x[3],
+                     double grad[3]) {
+  ocplx d[3];
+  const ocplx v = trilinear_eval(psi, nx, ny, nz, x, d);
+  for (int a = 0; a < 3; ++a) grad[a] = 2.0 * (v.re * d[a].re + v.im * d[a].im);
+  return cabs2(v);
+}
+
+void oracle_refine(int nx, int ny, int nz, const float* psi, long n, const double* x0s,
+                   int max_iter, double tol, double* xout, double* rho_out, double* tang,
+                   double* detj, int32_t* iters, uint8_t* flags) {
+  const long NX = nx, NY = ny, NZ = nz;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (long q = 0; q < n; ++q) {
+    const double* x0 = x0s + 3 * q;
+    double x[3] = {x0[0], x0[1], x0[2]}, t[3] = {0, 0, 0}, grad[3];
+    unsigned fl = 0;
+    int it = 0;
+    double rho = NAN, dj = 0.0;
+    if (!inside_grid(x0, NX, NY, NZ)) {
+      fl = OR_NO_TANGENT;
+    } else {
+      pseudo_vorticity(psi, NX, NY, NZ, x0, t);
+      const double tn = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+      rho = rho_at(psi, NX, NY, NZ, x, grad);
+      if (!(tn > 0.0) || !isfinite(tn)) {
+        fl = OR_NO_TANGENT;
+      } else {
+        for (int a = 0; a < 3; ++a) t[a] /= tn;
+        fl = OR_MAX_ITER;
+        for (it = 0; it < max_iter;) {
+          const double gt = grad[0] * t[0] + grad[1] * t[1] + grad[2] * t[2];
+          double g[3];
+          for (int a = 0; a < 3; ++a) g[a] = grad[a] - gt * t[a];
+          const double gg = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+          if (!(gg > 0.0)) {
+            fl = OR_CONVERGED;
+            break;
+          }
+          const double gn = sqrt(gg);
+          double alpha = 2.0 * rho / gg;
+          int accepted = 0;
+          double xn[3], rn = 0.0, gnext[3];
+          while (alpha * gn >= tol) {
+            for (int a = 0; a < 3; ++a) xn[a] = x[a] - alpha * g[a];
+            if (inside_grid(xn, NX, NY, NZ) && fabs(xn[0] - x0[0]) <= 1.0 &&
+                fabs(xn[1] - x0[1]) <= 1.0 && fabs(xn[2] - x0[2]) <= 1.0) {
+              rn = rho_at(psi, NX, NY, NZ, xn, gnext);
+              if (rn <= rho - 1e-4 * alpha * gg) {
+                accepted = 1;
+                break;
+              }
+            }
+            alpha *= 0.5;
+          }
+          if (!accepted) {
+            fl = OR_CONVERGED;
+            break;
+          }
+          ++it;
+          for (int a = 0; a < 3; ++a) {
+            x[a] = xn[a];
+            grad[a] = gnext[a];
+          }
+          rho = rn;
+        }
+      }
+    }
+    if (!(fl & OR_NO_TANGENT)) {
+      /* in-plane Jacobian of psi at x: basis e1 = normalize(t x a), e2 = t x e1
+         with a the coordinate axis least aligned with t */
+      int m = 0;
+      for (int a = 1; a < 3; ++a)
+        if (fabs(t[a]) < fabs(t[m])) m = a;
+      double ax[3] = {0, 0, 0};
+      ax[m] = 1.0;
+      double e1[3] = {t[1] * ax[2] - t[2] * ax[1], t[2] * ax[0] - t[0] * ax[2],
+                      t[0] * ax[1] - t[1] * ax[0]};
+      const double en = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+      for (int a = 0; a < 3; ++a) e1[a] /= en;
+      const double e2[3] = {t[1] * e1[2] - t[2] * e1[1], t[2] * e1[0] - t[0] * e1[2],
+                            t[0] * e1[1] - t[1] * e1[0]};
+      ocplx d[3];
+      (void)trilinear_eval(psi, NX, NY, NZ, x, d);
+      double a1r = 0, a1i = 0, a2r = 0, a2i = 0;
+      for (int a = 0; a < 3; ++a) {
+        a1r += d[a].re * e1[a];
+        a1i += d[a].im * e1[a];
+        a2r += d[a].re * e2[a];
+        a2i += d[a].im * e2[a];
+      }
+      dj = a1r * a2i - a2r * a1i;
+    }
+    for (int a = 0; a < 3; ++a) {
+      xout[3 * q + a] = x[a];
+      if (tang) tang[3 * q + a] = t[a];
+    }
+    if (rho_out) rho_out[q] = rho;
+    if (detj) detj[q] = dj;
+    if (iters) iters[q] = it;
+    flags[q] = (uint8_t)fl;
+  }
+}
