@@ -64,7 +64,7 @@ def parse():
     p.add_argument("--no-learned", action="store_true",
                    help="skip training the learned locator and its report against plain")
     p.add_argument("--no-node-form", action="store_true",
-                   help="skip the node-form circulation and density-error report")
+                   help="skip the node-form circulation, density-error and refinement reports")
     return p.parse_args()
 
 
@@ -306,6 +306,38 @@ def node_form_report(q, psi, xyz, count, stream, reps=20):
                           "ms": d_ms[1] / max(1, d_ms[0]),
                           "points": "plain samples of the timed step"},
     }
+
+
+def refine_report(q, psi, ids, count, F, stream, reps=5):
+    """Sample refinement of Sec. 3.3.3 (descent of rho in the plane normal to the
+    pseudo-vorticity) from the centres of the pierced faces of the timed step."""
+    import torch
+
+    from paper_1911_12070_gb300 import QtvError
+
+    try:
+        for _ in range(2):
+            out = q.refine_samples(psi, face_ids=ids[:F], n_dev=count)
+        torch.cuda.synchronize()
+        q.trace_enable(True)
+        q.trace_read(reset=True)
+        for _ in range(reps):
+            out = q.refine_samples(psi, face_ids=ids[:F], n_dev=count)
+        tr = q.trace_read(reset=True)
+        q.trace_enable(False)
+        e_ref, _, _ = q.density_error(psi, out["xyz"], n_dev=count)
+    except QtvError as err:
+        return {"error": str(err)}
+    fl = out["flags"]
+    it = out["iters"].float()
+    r = tr.get("refine", (1, 0.0))
+    ms = r[1] / max(1, r[0])
+    return {"ms": ms, "samples_per_s": F / (ms * 1e-3) if ms > 0 else None,
+            "converged_fraction": (fl == 1).float().mean().item(),
+            "no_tangent_fraction": ((fl & 2) != 0).float().mean().item(),
+            "mean_steps": it.mean().item(), "max_steps": int(it.max().item()),
+            "density_error_e": e_ref,
+            "start": "centres of the pierced faces (one-cell estimates)"}
 
 
 def batch_report(q, stream, reps=10, learned=False):
@@ -654,6 +686,7 @@ def run_qtv(args):
 
     if rank == 0 and not args.no_node_form:
         line["node_form"] = node_form_report(q, psi, xyz, count, stream)
+        line["refine"] = refine_report(q, psi, ids, count, F, stream)
 
     if rank == 0 and not args.no_learned:
         line["learned"] = learned_report(q, psi, ids, wnd, F, stream)

@@ -414,12 +414,61 @@ QTV_API int qtv_density_error(qtv_handle h, const qtv_grid* grid, const void* ps
                               double* out, void* stream);
 
 /*
+ * Sample refinement (Sec. 3.3.3, "Locating more accurate sample points"): an
+ * estimate x0 of a core sample (the paper starts from the box means of its
+ * graph reduction; here any points, or the centres of pierced faces) moves to
+ * a minimizer of the density rho = |psi|^2 (Eq. 6) within the plane through x0
+ * perpendicular to the local core direction t, taken from the pseudo-vorticity
+ * t = grad Re psi x grad Im psi at x0 (normalized).
+ *
+ *   psi between nodes is the trilinear interpolant; rho and grad rho are those
+ *   of the interpolant within the cell floor(x).  grad Re psi and grad Im psi
+ *   are central-difference node gradients (one-sided on the boundary)
+ *   interpolated trilinearly.  Descent on the in-plane gradient g: each step
+ *   starts at alpha = 2 rho / |g|^2 and halves alpha until
+ *   rho(x - alpha g) <= rho(x) - 1e-4 alpha |g|^2 with the new point inside
+ *   the grid and inside the box |x - x0|_inf <= 1 grid spacing (steps leaving
+ *   either are rejected, not projected); it stops, converged, when no step of
+ *   length >= tol grid spacings decreases rho that way, or after max_iter
+ *   accepted steps.  FP32 arithmetic, positions carried relative to the cell
+ *   of x0.
+ *
+ *   xyz0      device float[n][3] world positions (origin + h * grid coords),
+ *             or NULL;
+ *   face_ids  device uint64[n] face ids whose face centres are x0, or NULL;
+ *             exactly one of the two is given.
+ *   n, n_dev  host bound on the count; optional device uint64 limiting it to
+ *             min(n, *n_dev) (to follow qtv_identify without a host sync).
+ *   max_iter  step limit (200 in the tests); tol  step length in grid
+ *             spacings below which the search stops (1e-7 in the tests).
+ *   xyz       device float[n][3]: refined world positions (x0 when no
+ *             tangent exists).
+ *   rho       optional device float[n]: rho at the result (NaN for x0 outside
+ *             the grid).
+ *   tangent   optional device float[n][3]: t (0 when none).
+ *   detj      optional device float[n]: determinant of the 2x2 real Jacobian
+ *             of psi in an orthonormal in-plane basis at the result (the
+ *             conditioning of the zero).
+ *   iters     optional device int32[n]: accepted steps.
+ *   flags     device uint8[n]: QTV_REFINE_* bits.
+ */
+#define QTV_REFINE_CONVERGED 1u
+#define QTV_REFINE_NO_TANGENT 2u /* zero pseudo-vorticity or x0 outside the grid */
+#define QTV_REFINE_MAX_ITER 4u
+QTV_API int qtv_refine_samples(qtv_handle h, const qtv_grid* grid, const void* psi,
+                               const float* xyz0, const uint64_t* face_ids, uint64_t n,
+                               const uint64_t* n_dev, int max_iter, float tol, float* xyz,
+                               float* rho, float* tangent, float* detj, int32_t* iters,
+                               uint8_t* flags, void* stream);
+
+/*
  * Kernel timing trace.  While enabled, the handle records a pair of CUDA
  * events on the launching stream around each of its kernel launches (names:
  * "sweep", "seg_scan", "scatter", "stats", "localize", "emit_pack", "batch"
  * for one replay of a batch graph, "encode", "network", "head" for the
  * parts of learned localization, "node_form", "node_scan", "node_scatter"
- * for the node form and "density" for the density error).
+ * for the node form, "density" for the density error and "refine" for
+ * sample refinement).
  * qtv_trace_read waits for the recorded events, writes up to max_entries
  * per-kernel totals (launch count and summed device time) and, if reset is
  * nonzero, clears the record.  Tracing adds host work per launch; leave it

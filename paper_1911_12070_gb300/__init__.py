@@ -29,6 +29,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libqtv.so")
 
 
+REFINE_CONVERGED, REFINE_NO_TANGENT, REFINE_MAX_ITER = 1, 2, 4
+
+
 class QtvError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"qtv error {code}: {msg}")
@@ -141,7 +144,9 @@ def lib() -> ctypes.CDLL:
             getattr(L, name).restype = i32
         L.qtv_node_circulation.argtypes = [P, ctypes.POINTER(Grid), P, P, P, u64, P, P, P]
         L.qtv_density_error.argtypes = [P, ctypes.POINTER(Grid), P, P, u64, P, P, P, P]
-        for name in ("qtv_node_circulation", "qtv_density_error"):
+        L.qtv_refine_samples.argtypes = [P, ctypes.POINTER(Grid), P, P, P, u64, P, i32, f32, P, P,
+                                         P, P, P, P, P]
+        for name in ("qtv_node_circulation", "qtv_density_error", "qtv_refine_samples"):
             getattr(L, name).restype = i32
         L.qtv_trace_enable.argtypes = [P, i32]
         L.qtv_trace_read.argtypes = [P, ctypes.POINTER(TraceEntry), i32, ctypes.POINTER(i32), i32]
@@ -490,6 +495,32 @@ class Qtv:
                                        _ptr(out), _stream_ptr(stream)))
         e, m, rb = (float(v) for v in out.cpu().tolist())
         return (e, m, rb, rho[:n]) if want_rho else (e, m, rb)
+
+    def refine_samples(self, psi, xyz0=None, face_ids=None, n_dev=None, max_iter: int = 200,
+                       tol: float = 1e-7, grid=None, stream=None):
+        """Sample refinement of Sec. 3.3.3 from points xyz0 (float32 [n, 3], world
+        coordinates) or from the centres of faces face_ids.
+
+        Returns dict of device tensors: xyz [n, 3], rho [n], t [n, 3], detj [n],
+        iters int32 [n], flags uint8 [n] (REFINE_* bits)."""
+        import torch
+
+        g = grid or Grid.of(tuple(psi.shape))
+        src = xyz0 if xyz0 is not None else face_ids
+        n = src.shape[0]
+        dev = psi.device
+        out = {"xyz": torch.empty((n, 3), dtype=torch.float32, device=dev),
+               "rho": torch.empty(n, dtype=torch.float32, device=dev),
+               "t": torch.empty((n, 3), dtype=torch.float32, device=dev),
+               "detj": torch.empty(n, dtype=torch.float32, device=dev),
+               "iters": torch.empty(n, dtype=torch.int32, device=dev),
+               "flags": torch.empty(n, dtype=torch.uint8, device=dev)}
+        _check(lib().qtv_refine_samples(self.h, ctypes.byref(g), _ptr(psi), _ptr(xyz0),
+                                        _ptr(face_ids), n, _ptr(n_dev), int(max_iter),
+                                        float(tol), _ptr(out["xyz"]), _ptr(out["rho"]),
+                                        _ptr(out["t"]), _ptr(out["detj"]), _ptr(out["iters"]),
+                                        _ptr(out["flags"]), _stream_ptr(stream)))
+        return out
 
     # -- emission -------------------------------------------------------------------
     def emit_samples(self, face_ids, winding, xyz, resid, flags, out=None, stream=None):

@@ -120,7 +120,7 @@ cudaEvent_t take_event(qtv_handle h) {
 const char* kKernelNames[K_COUNT] = {"sweep",     "seg_scan",  "scatter",      "stats",
                                      "localize",  "emit_pack", "batch",        "encode",
                                      "network",   "head",      "node_form",    "node_scan",
-                                     "node_scatter", "density"};
+                                     "node_scatter", "density",   "refine"};
 }  // namespace
 
 TraceScope::TraceScope(qtv_handle h_, int k, cudaStream_t s) : h(h_), kernel(k), st(s) {
@@ -383,6 +383,30 @@ int qtv_density_error(qtv_handle h, const qtv_grid* grid, const void* psi, const
   if (!dg.ok) return set_error(QTV_ERR_CUDA, "cudaSetDevice failed");
   return density_error_launch(h, g, reinterpret_cast<const float2*>(psi), xyz, n, n_dev, rho, out,
                               reinterpret_cast<cudaStream_t>(stream));
+}
+
+int qtv_refine_samples(qtv_handle h, const qtv_grid* grid, const void* psi, const float* xyz0,
+                       const uint64_t* face_ids, uint64_t n, const uint64_t* n_dev, int max_iter,
+                       float tol, float* xyz, float* rho, float* tangent, float* detj,
+                       int32_t* iters, uint8_t* flags, void* stream) {
+  if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
+  int rc = validate_grid(grid);
+  if (rc) return rc;
+  if (n == 0) return QTV_OK;
+  if ((xyz0 == nullptr) == (face_ids == nullptr))
+    return set_error(QTV_ERR_ARG, "give exactly one of xyz0 and face_ids");
+  if (!psi || !xyz || !flags) return set_error(QTV_ERR_ARG, "a required pointer is NULL");
+  if (reinterpret_cast<uintptr_t>(psi) & 7u)
+    return set_error(QTV_ERR_ARG, "psi must be 8-byte aligned");
+  const qtv_grid& g = *grid;
+  if ((unsigned long long)g.nx * g.ny * g.nz == 0) return set_error(QTV_ERR_ARG, "empty grid");
+  if (max_iter < 0) return set_error(QTV_ERR_ARG, "max_iter must be >= 0");
+  if (!(tol > 0.f)) return set_error(QTV_ERR_ARG, "tol must be positive");
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return set_error(QTV_ERR_CUDA, "cudaSetDevice failed");
+  return refine_launch(h, g, reinterpret_cast<const float2*>(psi), xyz0, face_ids, n, n_dev,
+                       max_iter, tol, xyz, rho, tangent, detj, iters, flags,
+                       reinterpret_cast<cudaStream_t>(stream));
 }
 
 int qtv_localize(qtv_handle h, const qtv_grid* grid, const void* psi, const uint64_t* face_ids,

@@ -76,7 +76,7 @@ struct Locator;  // learned locator state (locator.cu)
 void locator_free(Locator* L);
 enum KernelId {
   K_SWEEP = 0, K_SEG_SCAN, K_SCATTER, K_STATS, K_LOCALIZE, K_EMIT_PACK, K_BATCH,
-  K_ENCODE, K_NETWORK, K_HEAD, K_NODE_FORM, K_NODE_SCAN, K_NODE_SCATTER, K_DENSITY, K_COUNT
+  K_ENCODE, K_NETWORK, K_HEAD, K_NODE_FORM, K_NODE_SCAN, K_NODE_SCATTER, K_DENSITY, K_REFINE, K_COUNT
 };
 struct BatchPlan;  // batched snapshots (batch.cu)
 void batch_free(BatchPlan* b);
@@ -326,6 +326,12 @@ int node_circulation_launch(qtv_handle h, const qtv_grid& g, const float2* psi,
 int density_error_launch(qtv_handle h, const qtv_grid& g, const float2* psi, const float* xyz,
                          uint64_t n, const uint64_t* n_dev, float* rho, double* out,
                          cudaStream_t st);
+
+// Sample refinement in the plane normal to the pseudo-vorticity (refine.cu)
+int refine_launch(qtv_handle h, const qtv_grid& g, const float2* psi, const float* xyz0,
+                  const uint64_t* face_ids, uint64_t n, const uint64_t* n_dev, int max_iter,
+                  float tol, float* xyz, float* rho, float* tangent, float* detj, int32_t* iters,
+                  uint8_t* flags, cudaStream_t st);
 
 // Emission pack (localize.cu)
 int emit_pack_launch(qtv_handle h, uint64_t n, const uint64_t* face_ids, const int8_t* winding, const float* xyz,

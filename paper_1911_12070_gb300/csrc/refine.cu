@@ -1,0 +1,360 @@
+// refine.cu -- sample refinement of Sec. 3.3.3 ("Locating more accurate
+// sample points") on the GPU: an estimate x0 of a core sample is moved to a
+// minimizer of the density rho = |psi|^2 (Eq. 6) within the plane through x0
+// perpendicular to the local core direction t, which the paper takes from the
+// pseudo-vorticity t = grad Re psi x grad Im psi.
+//
+// Arithmetic, per sample (one thread; FP32):
+//   - psi between nodes is the trilinear interpolant; rho and grad rho are
+//     those of the interpolant within the cell floor(x) (cell index clamped
+//     to [0, n - 2]);
+//   - grad Re psi and grad Im psi at x0 are the central-difference node
+//     gradients (one-sided on the boundary, 0 along an axis of one node),
+//     interpolated trilinearly; t is their cross product, normalized;
+//   - descent on g = grad rho - (grad rho . t) t: each step starts at
+//     alpha = 2 rho / |g|^2 (the exact step for a round bowl whose minimum is
+//     0) and halves alpha until rho(x - alpha g) <= rho(x) - 1e-4 alpha |g|^2
+//     with the new point in the grid and in the box |x - x0|_inf <= 1 (a step
+//     leaving either is rejected, not projected); it stops, converged, when
+//     no step of length >= tol decreases rho that way, or after max_iter
+//     accepted steps.
+// Positions are carried as an integer base (the cell of x0) plus an FP32
+// offset, so steps far below the FP32 spacing of absolute coordinates still
+// move the point.
+#include <cstdio>
+
+#include "qtv_internal.cuh"
+
+namespace qtv {
+namespace {
+
+constexpr int REF_THREADS = 128;
+
+struct RefArgs {
+  const float2* psi;
+  int nx, ny, nz;
+  float h, ox, oy, oz;
+  const float* xyz0;          // world positions [n][3], or null
+  const uint64_t* face_ids;   // faces whose centres are x0, or null
+  unsigned long long n;
+  const uint64_t* n_dev;
+  int max_iter;
+  float tol;
+  float* xyz;
+  float* rho;
+  float* tangent;
+  float* detj;
+  int32_t* iters;
+  uint8_t* flags;
+};
+
+struct Field {
+  const float2* psi;
+  int n[3];
+  __device__ __forceinline__ float2 at(int i, int j, int k) const {
+    return __ldg(psi + ((long long)k * n[1] + j) * n[0] + i);
+  }
+};
+
+// cell and fraction of base + off along an axis of m nodes
+__device__ __forceinline__ void cell_frac(int base, float off, int m, int& c, float& f) {
+  const float fl = floorf(off);
+  c = base + (int)fl;
+  f = off - fl;
+  const int hi = max(m - 2, 0);
+  if (c > hi) {
+    f += (float)(c - hi);
+    c = hi;
+  }
+  if (c < 0) {
+    f += (float)c;
+    c = 0;
+  }
+}
+
+// trilinear psi at the point (cells c, fractions f) and its partial derivatives
+__device__ __forceinline__ float2 tri_eval(const Field& F, const int c[3], const float f[3],
+                                           float2 d[3]) {
+  float2 acc = make_float2(0.f, 0.f);
+  d[0] = d[1] = d[2] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    int idx[3];
+    float w[3], s[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int bit = (q >> a) & 1;
+      idx[a] = c[a] + bit < F.n[a] ? c[a] + bit : c[a];
+      w[a] = bit ? f[a] : 1.f - f[a];
+      s[a] = bit ? 1.f : -1.f;
+    }
+    const float2 v = F.at(idx[0], idx[1], idx[2]);
+    const float wt = w[0] * w[1] * w[2];
+    acc.x = fmaf(wt, v.x, acc.x);
+    acc.y = fmaf(wt, v.y, acc.y);
+    const float dd[3] = {s[0] * w[1] * w[2], w[0] * s[1] * w[2], w[0] * w[1] * s[2]};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      d[a].x = fmaf(dd[a], v.x, d[a].x);
+      d[a].y = fmaf(dd[a], v.y, d[a].y);
+    }
+  }
+  return acc;
+}
+
+// central-difference gradient of psi at node (i,j,k) along axis a
+__device__ __forceinline__ float2 node_grad(const Field& F, int i, int j, int k, int a) {
+  int p[3] = {i, j, k}, q[3] = {i, j, k};
+  const int m = F.n[a];
+  if (m < 2) return make_float2(0.f, 0.f);
+  float s = 0.5f;
+  if (p[a] == 0) {
+    q[a] = 1;
+    s = 1.f;
+  } else if (p[a] == m - 1) {
+    p[a] = m - 2;
+    s = 1.f;
+  } else {
+    p[a] -= 1;
+    q[a] += 1;
+  }
+  const float2 lo = F.at(p[0], p[1], p[2]), hi = F.at(q[0], q[1], q[2]);
+  return make_float2(s * (hi.x - lo.x), s * (hi.y - lo.y));
+}
+
+struct Pos {
+  int base[3];    // integer base (cell of x0)
+  float off[3];   // offset from the base
+};
+
+__device__ __forceinline__ bool pos_inside(const Pos& P, const int n[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float v = (float)P.base[a] + P.off[a];
+    if (!(P.off[a] >= -(float)P.base[a] && v <= (float)(n[a] - 1))) return false;
+  }
+  return true;
+}
+
+// rho and grad rho at P
+__device__ __forceinline__ float rho_at(const Field& F, const Pos& P, float g[3]) {
+  int c[3];
+  float f[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) cell_frac(P.base[a], P.off[a], F.n[a], c[a], f[a]);
+  float2 d[3];
+  const float2 v = tri_eval(F, c, f, d);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) g[a] = 2.f * fmaf(v.x, d[a].x, v.y * d[a].y);
+  return fmaf(v.x, v.x, v.y * v.y);
+}
+
+__global__ void __launch_bounds__(REF_THREADS) refine_kernel(RefArgs A) {
+  unsigned long long nn = A.n;
+  if (A.n_dev) {
+    const unsigned long long d = *A.n_dev;
+    if (d < nn) nn = d;
+  }
+  Field F;
+  F.psi = A.psi;
+  F.n[0] = A.nx;
+  F.n[1] = A.ny;
+  F.n[2] = A.nz;
+  const float org[3] = {A.ox, A.oy, A.oz};
+  for (unsigned long long qi = (unsigned long long)blockIdx.x * REF_THREADS + threadIdx.x; qi < nn;
+       qi += (unsigned long long)gridDim.x * REF_THREADS) {
+    // x0 in grid coordinates, as base + offset
+    Pos P0;
+    bool in0 = true;
+    if (A.face_ids) {
+      const uint64_t id = A.face_ids[qi];
+      const int o = (int)(id & 3u);
+      const unsigned long long lin = id >> 2;
+      P0.base[0] = (int)(lin % (unsigned long long)A.nx);
+      P0.base[1] = (int)((lin / (unsigned long long)A.nx) % (unsigned long long)A.ny);
+      P0.base[2] = (int)(lin / ((unsigned long long)A.nx * A.ny));
+      // face centre: half a cell along the two in-plane axes
+      P0.off[0] = (o == 0 || o == 2) ? 0.5f : 0.f;
+      P0.off[1] = (o == 0 || o == 1) ? 0.5f : 0.f;
+      P0.off[2] = (o == 1 || o == 2) ? 0.5f : 0.f;
+      in0 = pos_inside(P0, F.n);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float g = (__ldg(A.xyz0 + 3 * qi + a) - org[a]) / A.h;
+        const float fl = floorf(g);
+        in0 = in0 && g >= 0.f && g <= (float)(F.n[a] - 1);
+        P0.base[a] = in0 ? (int)fl : 0;
+        P0.off[a] = in0 ? g - fl : g;
+      }
+    }
+    float t[3] = {0.f, 0.f, 0.f};
+    float rho = __int_as_float(0x7fc00000);
+    float dj = 0.f;
+    int it = 0;
+    uint8_t fl = 0;
+    Pos P = P0;
+    if (!in0) {
+      fl = QTV_REFINE_NO_TANGENT;
+    } else {
+      // pseudo-vorticity at x0
+      int c[3];
+      float f[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) cell_frac(P0.base[a], P0.off[a], F.n[a], c[a], f[a]);
+      float gr[3] = {0.f, 0.f, 0.f}, gi[3] = {0.f, 0.f, 0.f};
+      for (int q = 0; q < 8; ++q) {
+        int idx[3];
+        float wt = 1.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const int bit = (q >> a) & 1;
+          idx[a] = c[a] + bit < F.n[a] ? c[a] + bit : c[a];
+          wt *= bit ? f[a] : 1.f - f[a];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const float2 g = node_grad(F, idx[0], idx[1], idx[2], a);
+          gr[a] = fmaf(wt, g.x, gr[a]);
+          gi[a] = fmaf(wt, g.y, gi[a]);
+        }
+      }
+      t[0] = gr[1] * gi[2] - gr[2] * gi[1];
+      t[1] = gr[2] * gi[0] - gr[0] * gi[2];
+      t[2] = gr[0] * gi[1] - gr[1] * gi[0];
+      const float tn = sqrtf(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+      float grad[3];
+      rho = rho_at(F, P, grad);
+      if (!(tn > 0.f) || !(tn <= 3.402823466e38f)) {
+        fl = QTV_REFINE_NO_TANGENT;
+        t[0] = t[1] = t[2] = 0.f;
+      } else {
+        t[0] /= tn;
+        t[1] /= tn;
+        t[2] /= tn;
+        fl = QTV_REFINE_MAX_ITER;
+        while (it < A.max_iter) {
+          const float gt = grad[0] * t[0] + grad[1] * t[1] + grad[2] * t[2];
+          float g[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) g[a] = grad[a] - gt * t[a];
+          const float gg = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+          if (!(gg > 0.f)) {
+            fl = QTV_REFINE_CONVERGED;
+            break;
+          }
+          const float gn = sqrtf(gg);
+          float alpha = 2.f * rho / gg;
+          bool accepted = false;
+          Pos Pn;
+          float rn = 0.f, gnext[3];
+          while (alpha * gn >= A.tol) {
+            bool ok = true;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              Pn.base[a] = P.base[a];
+              Pn.off[a] = P.off[a] - alpha * g[a];
+              // box around x0 (same base as x0)
+              ok = ok && fabsf(Pn.off[a] - P0.off[a]) <= 1.f;
+            }
+            if (ok && pos_inside(Pn, F.n)) {
+              rn = rho_at(F, Pn, gnext);
+              if (rn <= rho - 1e-4f * alpha * gg) {
+                accepted = true;
+                break;
+              }
+            }
+            alpha *= 0.5f;
+          }
+          if (!accepted) {
+            fl = QTV_REFINE_CONVERGED;
+            break;
+          }
+          ++it;
+          P = Pn;
+          rho = rn;
+          grad[0] = gnext[0];
+          grad[1] = gnext[1];
+          grad[2] = gnext[2];
+        }
+        // in-plane Jacobian of psi at the result (conditioning): basis
+        // e1 = normalize(t x a), a the axis least aligned with t; e2 = t x e1
+        int m = 0;
+        if (fabsf(t[1]) < fabsf(t[m])) m = 1;
+        if (fabsf(t[2]) < fabsf(t[m])) m = 2;
+        const float ax[3] = {m == 0 ? 1.f : 0.f, m == 1 ? 1.f : 0.f, m == 2 ? 1.f : 0.f};
+        float e1[3] = {t[1] * ax[2] - t[2] * ax[1], t[2] * ax[0] - t[0] * ax[2],
+                       t[0] * ax[1] - t[1] * ax[0]};
+        const float en = sqrtf(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+        e1[0] /= en;
+        e1[1] /= en;
+        e1[2] /= en;
+        const float e2[3] = {t[1] * e1[2] - t[2] * e1[1], t[2] * e1[0] - t[0] * e1[2],
+                             t[0] * e1[1] - t[1] * e1[0]};
+        int cc[3];
+        float ff[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) cell_frac(P.base[a], P.off[a], F.n[a], cc[a], ff[a]);
+        float2 d[3];
+        (void)tri_eval(F, cc, ff, d);
+        float a1r = 0.f, a1i = 0.f, a2r = 0.f, a2i = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          a1r = fmaf(d[a].x, e1[a], a1r);
+          a1i = fmaf(d[a].y, e1[a], a1i);
+          a2r = fmaf(d[a].x, e2[a], a2r);
+          a2i = fmaf(d[a].y, e2[a], a2i);
+        }
+        dj = a1r * a2i - a2r * a1i;
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      A.xyz[3 * qi + a] = org[a] + A.h * ((float)P.base[a] + P.off[a]);
+      if (A.tangent) A.tangent[3 * qi + a] = t[a];
+    }
+    if (A.rho) A.rho[qi] = rho;
+    if (A.detj) A.detj[qi] = dj;
+    if (A.iters) A.iters[qi] = it;
+    A.flags[qi] = fl;
+  }
+}
+
+}  // namespace
+
+int refine_launch(qtv_handle h, const qtv_grid& g, const float2* psi, const float* xyz0,
+                  const uint64_t* face_ids, uint64_t n, const uint64_t* n_dev, int max_iter,
+                  float tol, float* xyz, float* rho, float* tangent, float* detj, int32_t* iters,
+                  uint8_t* flags, cudaStream_t st) {
+  if (n == 0) return QTV_OK;
+  RefArgs a;
+  a.psi = psi;
+  a.nx = g.nx;
+  a.ny = g.ny;
+  a.nz = g.nz;
+  a.h = g.h;
+  a.ox = g.origin[0];
+  a.oy = g.origin[1];
+  a.oz = g.origin[2];
+  a.xyz0 = xyz0;
+  a.face_ids = face_ids;
+  a.n = n;
+  a.n_dev = n_dev;
+  a.max_iter = max_iter;
+  a.tol = tol;
+  a.xyz = xyz;
+  a.rho = rho;
+  a.tangent = tangent;
+  a.detj = detj;
+  a.iters = iters;
+  a.flags = flags;
+  long long blocks = ((long long)n + REF_THREADS - 1) / REF_THREADS;
+  const long long maxb = (long long)h->num_sms * 16;
+  if (blocks > maxb) blocks = maxb;
+  TraceScope ts(h, K_REFINE, st);
+  refine_kernel<<<(int)blocks, REF_THREADS, 0, st>>>(a);
+  const cudaError_t e = cudaGetLastError();
+  return check_cuda(e, "refine_kernel launch");
+}
+
+}  // namespace qtv
