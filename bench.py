@@ -64,7 +64,7 @@ def parse():
     p.add_argument("--no-learned", action="store_true",
                    help="skip training the learned locator and its report against plain")
     p.add_argument("--no-node-form", action="store_true",
-                   help="skip the node-form circulation, density-error and refinement reports")
+                   help="skip the node-form, density-error, refinement and face-graph reports")
     return p.parse_args()
 
 
@@ -338,6 +338,35 @@ def refine_report(q, psi, ids, count, F, stream, reps=5):
             "mean_steps": it.mean().item(), "max_steps": int(it.max().item()),
             "density_error_e": e_ref,
             "start": "centres of the pierced faces (one-cell estimates)"}
+
+
+def graph_report(q, psi, ids, F, stream, reps=10):
+    """Sample graph over the pierced faces of the timed step (faces sharing a unit
+    cell, Sec. 3.1) and its connected components (Sec. 3.2)."""
+    import torch
+
+    from paper_1911_12070_gb300 import QtvError
+
+    try:
+        for _ in range(2):
+            nbr, deg, comp, ncomp = q.face_graph(tuple(psi.shape), ids[:F])
+        torch.cuda.synchronize()
+        q.trace_enable(True)
+        q.trace_read(reset=True)
+        for _ in range(reps):
+            nbr, deg, comp, ncomp = q.face_graph(tuple(psi.shape), ids[:F])
+        tr = q.trace_read(reset=True)
+        q.trace_enable(False)
+    except QtvError as err:
+        return {"error": str(err)}
+    g = tr.get("graph", (1, 0.0))
+    ms = g[1] / max(1, g[0])
+    d = deg.long()
+    sizes = torch.bincount(comp.long(), minlength=1)
+    return {"ms": ms, "faces": F, "edges": int(d.sum().item()) // 2, "components": ncomp,
+            "largest_component": int(sizes.max().item()),
+            "branch_faces": int((d > 2).sum().item()),
+            "faces_per_s": F / (ms * 1e-3) if ms > 0 else None}
 
 
 def batch_report(q, stream, reps=10, learned=False):
@@ -687,6 +716,7 @@ def run_qtv(args):
     if rank == 0 and not args.no_node_form:
         line["node_form"] = node_form_report(q, psi, xyz, count, stream)
         line["refine"] = refine_report(q, psi, ids, count, F, stream)
+        line["face_graph"] = graph_report(q, psi, ids, F, stream)
 
     if rank == 0 and not args.no_learned:
         line["learned"] = learned_report(q, psi, ids, wnd, F, stream)

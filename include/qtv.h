@@ -462,13 +462,40 @@ QTV_API int qtv_refine_samples(qtv_handle h, const qtv_grid* grid, const void* p
                                uint8_t* flags, void* stream);
 
 /*
+ * Sample graph over pierced faces (Sec. 3.1) and its connected components,
+ * the independent lines of Sec. 3.2.  Two pierced faces are adjacent when
+ * they bound the same unit cell (all eight corners in the grid): a core line
+ * through a cell pierces the face it enters by and the face it leaves by,
+ * and a cell with 4 or 6 pierced faces links all of them (a branch, as at a
+ * reconnection).  A face has at most 10 neighbours.
+ *
+ *   face_ids  device uint64[n], strictly ascending (as from qtv_identify).
+ *   n, n_dev  host bound on the count (< 2^32 - 1); optional device uint64
+ *             limiting it to min(n, *n_dev).
+ *   nbr       device uint32[n][10]: indices (into face_ids) of the
+ *             neighbours, ascending, then 0xFFFFFFFF.
+ *   deg       device uint8[n]: number of neighbours.
+ *   comp      device uint32[n]: component label of each face = the lowest
+ *             face index of its component (so components are numbered in
+ *             the order of their lowest index, as a depth-first traversal
+ *             from the lowest unvisited face finds them).
+ *   ncomp     device uint64: number of components (QTV_COUNT_TIMEOUT if a
+ *             bounded retry loop of the union-find gave up).
+ * Entries beyond min(n, *n_dev) are not written.  The handle keeps a row
+ * table of (ny * nz + 1) words.
+ */
+QTV_API int qtv_face_graph(qtv_handle h, const qtv_grid* grid, const uint64_t* face_ids, uint64_t n,
+                           const uint64_t* n_dev, uint32_t* nbr, uint8_t* deg, uint32_t* comp,
+                           uint64_t* ncomp, void* stream);
+
+/*
  * Kernel timing trace.  While enabled, the handle records a pair of CUDA
  * events on the launching stream around each of its kernel launches (names:
  * "sweep", "seg_scan", "scatter", "stats", "localize", "emit_pack", "batch"
  * for one replay of a batch graph, "encode", "network", "head" for the
  * parts of learned localization, "node_form", "node_scan", "node_scatter"
- * for the node form, "density" for the density error and "refine" for
- * sample refinement).
+ * for the node form, "density" for the density error, "refine" for
+ * sample refinement and "graph" for the face graph and its components).
  * qtv_trace_read waits for the recorded events, writes up to max_entries
  * per-kernel totals (launch count and summed device time) and, if reset is
  * nonzero, clears the record.  Tracing adds host work per launch; leave it

@@ -146,7 +146,9 @@ def lib() -> ctypes.CDLL:
         L.qtv_density_error.argtypes = [P, ctypes.POINTER(Grid), P, P, u64, P, P, P, P]
         L.qtv_refine_samples.argtypes = [P, ctypes.POINTER(Grid), P, P, P, u64, P, i32, f32, P, P,
                                          P, P, P, P, P]
-        for name in ("qtv_node_circulation", "qtv_density_error", "qtv_refine_samples"):
+        L.qtv_face_graph.argtypes = [P, ctypes.POINTER(Grid), P, u64, P, P, P, P, P, P]
+        for name in ("qtv_node_circulation", "qtv_density_error", "qtv_refine_samples",
+                     "qtv_face_graph"):
             getattr(L, name).restype = i32
         L.qtv_trace_enable.argtypes = [P, i32]
         L.qtv_trace_read.argtypes = [P, ctypes.POINTER(TraceEntry), i32, ctypes.POINTER(i32), i32]
@@ -521,6 +523,29 @@ class Qtv:
                                         _ptr(out["t"]), _ptr(out["detj"]), _ptr(out["iters"]),
                                         _ptr(out["flags"]), _stream_ptr(stream)))
         return out
+
+    def face_graph(self, shape, face_ids, n_dev=None, grid=None, stream=None):
+        """Adjacency (faces sharing a unit cell) and connected components of a
+        pierced-face list (ascending ids) on a grid of the given [nz, ny, nx] shape.
+
+        Returns (nbr int32 [n, 10] with -1 for none, deg uint8 [n], comp int32 [n]
+        = lowest face index of the component, number of components)."""
+        import torch
+
+        g = grid or Grid.of(tuple(shape))
+        n = face_ids.numel()
+        dev = face_ids.device
+        nbr = torch.empty((max(n, 1), 10), dtype=torch.int32, device=dev)
+        deg = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
+        comp = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        nc = torch.zeros(1, dtype=torch.int64, device=dev)
+        _check(lib().qtv_face_graph(self.h, ctypes.byref(g), _ptr(face_ids), n, _ptr(n_dev),
+                                    _ptr(nbr), _ptr(deg), _ptr(comp), _ptr(nc),
+                                    _stream_ptr(stream)))
+        k = int(nc.item())
+        if k < 0:
+            raise QtvError(ERR_TIMEOUT, "a bounded union-find retry loop gave up")
+        return nbr[:n], deg[:n], comp[:n], k
 
     # -- emission -------------------------------------------------------------------
     def emit_samples(self, face_ids, winding, xyz, resid, flags, out=None, stream=None):

@@ -120,7 +120,7 @@ cudaEvent_t take_event(qtv_handle h) {
 const char* kKernelNames[K_COUNT] = {"sweep",     "seg_scan",  "scatter",      "stats",
                                      "localize",  "emit_pack", "batch",        "encode",
                                      "network",   "head",      "node_form",    "node_scan",
-                                     "node_scatter", "density",   "refine"};
+                                     "node_scatter", "density",   "refine",       "graph"};
 }  // namespace
 
 TraceScope::TraceScope(qtv_handle h_, int k, cudaStream_t s) : h(h_), kernel(k), st(s) {
@@ -191,6 +191,7 @@ int qtv_destroy(qtv_handle h) {
   locator_free(h->loc);
   batch_free(h->batch);
   node_work_free(h->node);
+  graph_work_free(h->graph);
   for (auto& r : h->trace) {
     cudaEventDestroy(r.start);
     cudaEventDestroy(r.stop);
@@ -407,6 +408,29 @@ int qtv_refine_samples(qtv_handle h, const qtv_grid* grid, const void* psi, cons
   return refine_launch(h, g, reinterpret_cast<const float2*>(psi), xyz0, face_ids, n, n_dev,
                        max_iter, tol, xyz, rho, tangent, detj, iters, flags,
                        reinterpret_cast<cudaStream_t>(stream));
+}
+
+int qtv_face_graph(qtv_handle h, const qtv_grid* grid, const uint64_t* face_ids, uint64_t n,
+                   const uint64_t* n_dev, uint32_t* nbr, uint8_t* deg, uint32_t* comp,
+                   uint64_t* ncomp, void* stream) {
+  if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
+  int rc = validate_grid(grid);
+  if (rc) return rc;
+  if (!ncomp) return set_error(QTV_ERR_ARG, "ncomp is NULL");
+  if (n > 0 && (!face_ids || !nbr || !deg || !comp))
+    return set_error(QTV_ERR_ARG, "a required pointer is NULL");
+  if (n >= 0xFFFFFFFFull) return set_error(QTV_ERR_ARG, "2^32 - 1 faces or more");
+  const qtv_grid& g = *grid;
+  if ((unsigned long long)g.ny * g.nz >= 0xFFFFFFFFull)
+    return set_error(QTV_ERR_ARG, "too many grid rows");
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return set_error(QTV_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (n == 0 || (unsigned long long)g.nx * g.ny * g.nz == 0) {
+    const cudaError_t e = cudaMemsetAsync(ncomp, 0, sizeof(uint64_t), st);
+    return check_cuda(e, "cudaMemsetAsync(ncomp)");
+  }
+  return face_graph_launch(h, g, face_ids, n, n_dev, nbr, deg, comp, ncomp, st);
 }
 
 int qtv_localize(qtv_handle h, const qtv_grid* grid, const void* psi, const uint64_t* face_ids,

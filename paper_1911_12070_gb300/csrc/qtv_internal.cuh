@@ -76,12 +76,14 @@ struct Locator;  // learned locator state (locator.cu)
 void locator_free(Locator* L);
 enum KernelId {
   K_SWEEP = 0, K_SEG_SCAN, K_SCATTER, K_STATS, K_LOCALIZE, K_EMIT_PACK, K_BATCH,
-  K_ENCODE, K_NETWORK, K_HEAD, K_NODE_FORM, K_NODE_SCAN, K_NODE_SCATTER, K_DENSITY, K_REFINE, K_COUNT
+  K_ENCODE, K_NETWORK, K_HEAD, K_NODE_FORM, K_NODE_SCAN, K_NODE_SCATTER, K_DENSITY, K_REFINE, K_GRAPH, K_COUNT
 };
 struct BatchPlan;  // batched snapshots (batch.cu)
 void batch_free(BatchPlan* b);
 struct NodeWork;   // node-form and density-error workspace (node_form.cu)
 void node_work_free(NodeWork* w);
+struct GraphWork;  // face-graph workspace (graph.cu)
+void graph_work_free(GraphWork* w);
 struct TraceRec {
   int kernel;
   cudaEvent_t start, stop;
@@ -98,6 +100,7 @@ struct qtv_handle_s {
   qtv::Locator* loc = nullptr;           // learned locator (weights, Adam state, buffers)
   qtv::BatchPlan* batch = nullptr;       // batch plan, scratch and captured graph
   qtv::NodeWork* node = nullptr;         // node-form / density-error workspace
+  qtv::GraphWork* graph = nullptr;       // face-graph workspace
   // sweep shape of single-snapshot calls (qtv_configure_sweep); -1 / 0 = default
   int sweep_variant = -1, sweep_nwt = 0, sweep_stages = 0, sweep_ctas = 0;
 };
@@ -332,6 +335,11 @@ int refine_launch(qtv_handle h, const qtv_grid& g, const float2* psi, const floa
                   const uint64_t* face_ids, uint64_t n, const uint64_t* n_dev, int max_iter,
                   float tol, float* xyz, float* rho, float* tangent, float* detj, int32_t* iters,
                   uint8_t* flags, cudaStream_t st);
+
+// Face graph and connected components (graph.cu)
+int face_graph_launch(qtv_handle h, const qtv_grid& g, const uint64_t* face_ids, uint64_t n,
+                      const uint64_t* n_dev, uint32_t* nbr, uint8_t* deg, uint32_t* comp,
+                      uint64_t* ncomp, cudaStream_t st);
 
 // Emission pack (localize.cu)
 int emit_pack_launch(qtv_handle h, uint64_t n, const uint64_t* face_ids, const int8_t* winding, const float* xyz,
