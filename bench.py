@@ -64,7 +64,7 @@ def parse():
     p.add_argument("--no-learned", action="store_true",
                    help="skip training the learned locator and its report against plain")
     p.add_argument("--no-node-form", action="store_true",
-                   help="skip the node-form, density-error, refinement and face-graph reports")
+                   help="skip the node-form, density-error, refinement, face-graph and line reports")
     return p.parse_args()
 
 
@@ -367,6 +367,38 @@ def graph_report(q, psi, ids, F, stream, reps=10):
             "largest_component": int(sizes.max().item()),
             "branch_faces": int((d > 2).sum().item()),
             "faces_per_s": F / (ms * 1e-3) if ms > 0 else None}
+
+
+def lines_report(q, psi, ids, wnd, xyz, F, stream, reps=5):
+    """Vortex-core lines of the timed step's samples (Sec. 3.4): pieces of the face
+    graph in walk order, oriented, and their Catmull-Rom curves."""
+    import torch
+
+    import paper_1911_12070_gb300 as qtv
+
+    try:
+        nbr, deg, comp, ncomp = q.face_graph(tuple(psi.shape), ids[:F])
+        for _ in range(2):
+            pieces, nodes = q.line_pieces(nbr, deg, comp, xyz[:F], ids[:F], wnd[:F])
+            curve, first, length = q.piece_curves(xyz[:F], nodes, pieces, 8)
+        torch.cuda.synchronize()
+        q.trace_enable(True)
+        q.trace_read(reset=True)
+        for _ in range(reps):
+            pieces, nodes = q.line_pieces(nbr, deg, comp, xyz[:F], ids[:F], wnd[:F])
+            curve, first, length = q.piece_curves(xyz[:F], nodes, pieces, 8)
+        tr = q.trace_read(reset=True)
+        q.trace_enable(False)
+    except qtv.QtvError as err:
+        return {"error": str(err)}
+    P = qtv.pieces_numpy(pieces)
+    kms = {k: v[1] / max(1, v[0]) for k, v in tr.items()}
+    types = np.bincount(P["comp_type"].astype(np.int64), minlength=4)
+    return {"ms": kms, "pieces": int(len(P)), "closed_pieces": int(P["closed"].sum()),
+            "pieces_in_type_I_II_III": [int(types[1]), int(types[2]), int(types[3])],
+            "reversed_pieces": int(P["reversed"].sum()), "curve_points": int(curve.shape[0]),
+            "total_length_h": float(length.double().sum().item()),
+            "note": "line_pieces includes the host round trip of its count-only first call"}
 
 
 def batch_report(q, stream, reps=10, learned=False):
@@ -717,6 +749,7 @@ def run_qtv(args):
         line["node_form"] = node_form_report(q, psi, xyz, count, stream)
         line["refine"] = refine_report(q, psi, ids, count, F, stream)
         line["face_graph"] = graph_report(q, psi, ids, F, stream)
+        line["lines"] = lines_report(q, psi, ids, wnd, xyz, F, stream)
 
     if rank == 0 and not args.no_learned:
         line["learned"] = learned_report(q, psi, ids, wnd, F, stream)

@@ -489,13 +489,86 @@ QTV_API int qtv_face_graph(qtv_handle h, const qtv_grid* grid, const uint64_t* f
                            uint64_t* ncomp, void* stream);
 
 /*
+ * Vortex-core lines of a sample graph (Sec. 3.4): classification, ordering,
+ * orientation, and uniform Catmull-Rom curves, on the graph that
+ * qtv_face_graph builds over pierced faces (the paper first thins its samples
+ * by box means, Sec. 3.3.2; here the pieces run through every face sample).
+ *
+ * Classification of a component: Type III when a sample has more than two
+ * neighbours (branch points, as at reconnections), Type II (a closed loop)
+ * when every sample has exactly two and there is more than one, else Type I.
+ * Pieces: a Type I component is one open piece from its lower end sample; a
+ * Type II component is one closed piece from its lowest sample towards the
+ * lower of that sample's neighbours; a Type III component splits at its
+ * branch points into chains, each started at a branch point b through
+ * neighbour v, from the branch side that comes first in (b, v) order (a chain
+ * returning to b is closed; dead ends never start a chain).  A piece's
+ * samples run along the circulation direction (Sec. 3.4, right-hand rule):
+ * the piece is reversed when the sum over its segments of
+ * (p[i+1] - p[i]) . d[i] is negative, d the sample's face normal times W (a
+ * closed piece keeps its first sample).
+ */
+typedef struct {
+  uint64_t first;     /* offset of the piece's samples in the node list */
+  uint32_t count;     /* samples in the piece */
+  uint32_t component; /* component label (lowest face index) */
+  uint8_t closed;     /* 1: the last sample connects back to the first */
+  uint8_t comp_type;  /* 1, 2, 3: Type I, II, III of the component */
+  uint8_t reversed;   /* 1: flipped to follow the circulation direction */
+  uint8_t reserved[5];
+} qtv_piece;
+
+/*
+ *   n, n_dev     samples (faces) and an optional device bound on them.
+ *   nbr, deg, comp  the outputs of qtv_face_graph.
+ *   xyz          device float[n][3], the sample positions.
+ *   face_ids, winding  device, the faces and W of the samples (orientation);
+ *                both NULL: pieces keep their walk order.
+ *   pieces       device qtv_piece[piece_cap], ordered by (start sample, first
+ *                neighbour) of the walk that found them.
+ *   nodes        device uint32[node_cap]: sample indices of all pieces, each
+ *                piece a contiguous run (branch samples appear in every piece
+ *                they end).
+ *   counts       device uint64[2]: number of pieces and of node entries.  If
+ *                either exceeds its capacity the outputs are incomplete;
+ *                capacity 0 with NULL outputs counts only.
+ */
+QTV_API int qtv_line_pieces(qtv_handle h, uint64_t n, const uint64_t* n_dev, const uint32_t* nbr,
+                            const uint8_t* deg, const uint32_t* comp, const float* xyz,
+                            const uint64_t* face_ids, const int8_t* winding, qtv_piece* pieces,
+                            uint64_t piece_cap, uint32_t* nodes, uint64_t node_cap,
+                            uint64_t* counts, void* stream);
+
+/*
+ * Uniform Catmull-Rom curves through the samples of each piece (Sec. 3.4):
+ * per_segment points on each segment between consecutive samples, the end
+ * samples repeated as outer control points for open pieces and the samples
+ * wrapped for closed ones, plus the last sample of an open piece (a piece of
+ * one sample is that point).  FP32 points.
+ *
+ *   npieces, npieces_dev  piece count and an optional device bound on it.
+ *   curve        device float[curve_cap][3]; curve_first device uint64[npieces]:
+ *                each piece's first point; length device float[npieces]: the
+ *                polyline length of each curve (closing segment included for
+ *                closed pieces; FP64 sums in a fixed order).
+ *   total        device uint64: number of curve points (outputs incomplete
+ *                when it exceeds curve_cap).
+ */
+QTV_API int qtv_piece_curves(qtv_handle h, const float* xyz, const uint32_t* nodes,
+                             const qtv_piece* pieces, uint64_t npieces,
+                             const uint64_t* npieces_dev, int per_segment, float* curve,
+                             uint64_t curve_cap, uint64_t* curve_first, float* length,
+                             uint64_t* total, void* stream);
+
+/*
  * Kernel timing trace.  While enabled, the handle records a pair of CUDA
  * events on the launching stream around each of its kernel launches (names:
  * "sweep", "seg_scan", "scatter", "stats", "localize", "emit_pack", "batch"
  * for one replay of a batch graph, "encode", "network", "head" for the
  * parts of learned localization, "node_form", "node_scan", "node_scatter"
  * for the node form, "density" for the density error, "refine" for
- * sample refinement and "graph" for the face graph and its components).
+ * sample refinement, "graph" for the face graph and its components, "lines"
+ * and "curves" for line pieces and their curves).
  * qtv_trace_read waits for the recorded events, writes up to max_entries
  * per-kernel totals (launch count and summed device time) and, if reset is
  * nonzero, clears the record.  Tracing adds host work per launch; leave it

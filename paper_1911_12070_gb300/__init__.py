@@ -32,6 +32,16 @@ LIB_PATH = os.path.join(_HERE, "_build", "libqtv.so")
 REFINE_CONVERGED, REFINE_NO_TANGENT, REFINE_MAX_ITER = 1, 2, 4
 
 
+PIECE_DTYPE = np.dtype([("first", "<u8"), ("count", "<u4"), ("component", "<u4"),
+                        ("closed", "u1"), ("comp_type", "u1"), ("reversed", "u1"),
+                        ("reserved", "u1", 5)])
+
+
+def pieces_numpy(pieces):
+    """qtv_piece records (uint8 tensor [np, 24]) as a numpy structured array."""
+    return pieces.cpu().numpy().reshape(-1).view(PIECE_DTYPE)
+
+
 class QtvError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"qtv error {code}: {msg}")
@@ -147,8 +157,10 @@ def lib() -> ctypes.CDLL:
         L.qtv_refine_samples.argtypes = [P, ctypes.POINTER(Grid), P, P, P, u64, P, i32, f32, P, P,
                                          P, P, P, P, P]
         L.qtv_face_graph.argtypes = [P, ctypes.POINTER(Grid), P, u64, P, P, P, P, P, P]
+        L.qtv_line_pieces.argtypes = [P, u64, P, P, P, P, P, P, P, P, u64, P, u64, P, P]
+        L.qtv_piece_curves.argtypes = [P, P, P, P, u64, P, i32, P, u64, P, P, P, P]
         for name in ("qtv_node_circulation", "qtv_density_error", "qtv_refine_samples",
-                     "qtv_face_graph"):
+                     "qtv_face_graph", "qtv_line_pieces", "qtv_piece_curves"):
             getattr(L, name).restype = i32
         L.qtv_trace_enable.argtypes = [P, i32]
         L.qtv_trace_read.argtypes = [P, ctypes.POINTER(TraceEntry), i32, ctypes.POINTER(i32), i32]
@@ -546,6 +558,45 @@ class Qtv:
         if k < 0:
             raise QtvError(ERR_TIMEOUT, "a bounded union-find retry loop gave up")
         return nbr[:n], deg[:n], comp[:n], k
+
+    def line_pieces(self, nbr, deg, comp, xyz, face_ids=None, winding=None, stream=None):
+        """Pieces of the vortex-core lines of a face graph (qtv_line_pieces).
+
+        Returns (pieces: uint8 device tensor [np, 24] of qtv_piece records, use
+        pieces_numpy() to read them; nodes: int32 device tensor of sample indices)."""
+        import torch
+
+        n = deg.numel()
+        dev = deg.device
+        counts = torch.zeros(2, dtype=torch.int64, device=dev)
+        args = (_ptr(nbr), _ptr(deg), _ptr(comp), _ptr(xyz), _ptr(face_ids), _ptr(winding))
+        _check(lib().qtv_line_pieces(self.h, n, None, *args, None, 0, None, 0, _ptr(counts),
+                                     _stream_ptr(stream)))
+        npc, nnd = (int(v) for v in counts.cpu().tolist())
+        pieces = torch.empty((max(npc, 1), 24), dtype=torch.uint8, device=dev)
+        nodes = torch.empty(max(nnd, 1), dtype=torch.int32, device=dev)
+        _check(lib().qtv_line_pieces(self.h, n, None, *args, _ptr(pieces), npc, _ptr(nodes), nnd,
+                                     _ptr(counts), _stream_ptr(stream)))
+        return pieces[:npc], nodes[:nnd]
+
+    def piece_curves(self, xyz, nodes, pieces, per_segment: int = 8, stream=None):
+        """Catmull-Rom curves of line pieces (qtv_piece_curves): (curve float32 [m, 3],
+        first point of each piece int64 [np], length float32 [np])."""
+        import torch
+
+        npc = pieces.shape[0]
+        dev = xyz.device
+        first = torch.empty(max(npc, 1), dtype=torch.int64, device=dev)
+        length = torch.empty(max(npc, 1), dtype=torch.float32, device=dev)
+        total = torch.zeros(1, dtype=torch.int64, device=dev)
+        args = (_ptr(xyz), _ptr(nodes), _ptr(pieces), npc, None, int(per_segment))
+        _check(lib().qtv_piece_curves(self.h, *args, None, 0, _ptr(first), _ptr(length),
+                                      _ptr(total), _stream_ptr(stream)))
+        m = int(total.item())
+        curve = torch.empty((max(m, 1), 3), dtype=torch.float32, device=dev)
+        _check(lib().qtv_piece_curves(self.h, *args, _ptr(curve), m, _ptr(first), _ptr(length),
+                                      _ptr(total), _stream_ptr(stream)))
+        return curve[:m], first[:npc], length[:npc]
 
     # -- emission -------------------------------------------------------------------
     def emit_samples(self, face_ids, winding, xyz, resid, flags, out=None, stream=None):

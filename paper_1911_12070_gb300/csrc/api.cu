@@ -120,7 +120,8 @@ cudaEvent_t take_event(qtv_handle h) {
 const char* kKernelNames[K_COUNT] = {"sweep",     "seg_scan",  "scatter",      "stats",
                                      "localize",  "emit_pack", "batch",        "encode",
                                      "network",   "head",      "node_form",    "node_scan",
-                                     "node_scatter", "density",   "refine",       "graph"};
+                                     "node_scatter", "density",   "refine",       "graph",
+                                     "lines",     "curves"};
 }  // namespace
 
 TraceScope::TraceScope(qtv_handle h_, int k, cudaStream_t s) : h(h_), kernel(k), st(s) {
@@ -192,6 +193,7 @@ int qtv_destroy(qtv_handle h) {
   batch_free(h->batch);
   node_work_free(h->node);
   graph_work_free(h->graph);
+  line_work_free(h->lines);
   for (auto& r : h->trace) {
     cudaEventDestroy(r.start);
     cudaEventDestroy(r.stop);
@@ -431,6 +433,54 @@ int qtv_face_graph(qtv_handle h, const qtv_grid* grid, const uint64_t* face_ids,
     return check_cuda(e, "cudaMemsetAsync(ncomp)");
   }
   return face_graph_launch(h, g, face_ids, n, n_dev, nbr, deg, comp, ncomp, st);
+}
+
+int qtv_line_pieces(qtv_handle h, uint64_t n, const uint64_t* n_dev, const uint32_t* nbr,
+                    const uint8_t* deg, const uint32_t* comp, const float* xyz,
+                    const uint64_t* face_ids, const int8_t* winding, qtv_piece* pieces,
+                    uint64_t piece_cap, uint32_t* nodes, uint64_t node_cap, uint64_t* counts,
+                    void* stream) {
+  if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
+  if (!counts) return set_error(QTV_ERR_ARG, "counts is NULL");
+  if (n >= 0xFFFFFFFFull / 11) return set_error(QTV_ERR_ARG, "too many samples");
+  if (n > 0 && (!nbr || !deg || !comp || !xyz))
+    return set_error(QTV_ERR_ARG, "a required pointer is NULL");
+  if ((face_ids == nullptr) != (winding == nullptr))
+    return set_error(QTV_ERR_ARG, "give both face_ids and winding, or neither");
+  if ((piece_cap > 0 && !pieces) || (node_cap > 0 && !nodes))
+    return set_error(QTV_ERR_ARG, "an output is NULL with a nonzero capacity");
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return set_error(QTV_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (n == 0) {
+    const cudaError_t e = cudaMemsetAsync(counts, 0, 2 * sizeof(uint64_t), st);
+    return check_cuda(e, "cudaMemsetAsync(counts)");
+  }
+  return line_pieces_launch(h, n, n_dev, nbr, deg, comp, xyz, face_ids, winding, pieces,
+                            piece_cap, nodes, node_cap, counts, st);
+}
+
+int qtv_piece_curves(qtv_handle h, const float* xyz, const uint32_t* nodes,
+                     const qtv_piece* pieces, uint64_t npieces, const uint64_t* npieces_dev,
+                     int per_segment, float* curve, uint64_t curve_cap, uint64_t* curve_first,
+                     float* length, uint64_t* total, void* stream) {
+  if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
+  if (!total) return set_error(QTV_ERR_ARG, "total is NULL");
+  if (per_segment < 1 || per_segment > 1024)
+    return set_error(QTV_ERR_ARG, "per_segment must be in [1, 1024]");
+  if (npieces >= 0xFFFFFFFFull) return set_error(QTV_ERR_ARG, "too many pieces");
+  if (npieces > 0 && (!xyz || !nodes || !pieces || !curve_first || !length))
+    return set_error(QTV_ERR_ARG, "a required pointer is NULL");
+  if (curve_cap > 0 && !curve) return set_error(QTV_ERR_ARG, "curve is NULL");
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return set_error(QTV_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (npieces == 0) {
+    const cudaError_t e = cudaMemsetAsync(total, 0, sizeof(uint64_t), st);
+    return check_cuda(e, "cudaMemsetAsync(total)");
+  }
+  return piece_curves_launch(h, xyz, nodes, pieces, npieces, npieces_dev, per_segment, curve,
+                             curve_cap, curve_first, length, total, st);
 }
 
 int qtv_localize(qtv_handle h, const qtv_grid* grid, const void* psi, const uint64_t* face_ids,

@@ -1,0 +1,738 @@
+// lines.cu -- classification, ordering, orientation and Catmull-Rom curves of
+// the vortex-core lines of a sample graph (Sec. 3.4) on the GPU, parallel
+// over samples: no thread walks a line.
+//
+// Input: the pierced-face graph of qtv_face_graph (neighbour table, degrees,
+// component labels = lowest face index), the sample positions, and the face
+// ids and windings (a sample's circulation direction is W times its face
+// normal).
+//
+// Classification (per component, from the degrees of its samples): Type III
+// when some degree exceeds 2 (branch points, e.g. at reconnections), Type II
+// (closed loop) when every degree is 2 and the component has more than one
+// sample, else Type I (an open line, or a single sample).
+//
+// Pieces (the simple lines, as in a walk that always takes the lowest
+// unused neighbour): a Type I component is one piece from its lower end; a
+// Type II component is one closed piece from its lowest sample towards the
+// lower of that sample's two neighbours; a Type III component splits at its
+// branch points: every chain between branch points and ends is a piece,
+// started at a branch point b through neighbour v, and it is found from the
+// branch side that comes first in (b, v) order (from the lower branch point;
+// from the lower first neighbour for a chain that returns to b, which is then
+// closed; dead ends are never starts).
+//
+// Ordering without walking.  "Special" samples end the chains: samples of
+// degree other than 2, and the lowest sample of each Type II component.  On
+// the directed edges (u -> w) of the graph, the successor of (u -> w) is
+// (w -> x), x the neighbour of w other than u, unless w is special.  Pointer
+// jumping over this successor (double-buffered rounds, log2 of the sample
+// count of them) gives every directed edge its distance to the end of its
+// chain, the end sample and the sample before it.  A sample inside a chain
+// then knows both ends, which end starts its piece, its position from that
+// start (the distance back to it) and the piece's place in the output.
+//
+// Output order: pieces in ascending order of (start sample, first
+// neighbour); each piece's samples in order, oriented (Sec. 3.4, right-hand
+// rule) to run along their circulation direction: reversed when the sum over
+// segments of (p[i+1] - p[i]) . dir[i] (with the closing segment for closed
+// pieces) is negative, a closed piece keeping its first sample.  Curves:
+// uniform Catmull-Rom, 'per_segment' points per segment, end points repeated
+// for open pieces and wrapped for closed ones, plus the last sample of an open
+// piece; lengths are the polyline lengths of the curves.  Curve points are
+// one thread each; orientation sums use one warp and lengths one block per
+// piece, FP64 in a fixed order, so results do not depend on timing.
+#include <cstdio>
+
+#include "qtv_internal.cuh"
+
+namespace qtv {
+
+struct LineWork {
+  void* buf = nullptr;
+  size_t cap = 0;
+};
+
+void line_work_free(LineWork* w) {
+  if (!w) return;
+  cudaFree(w->buf);
+  delete w;
+}
+
+namespace {
+
+constexpr int LT = 256;
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr int kSlots = 10;
+
+__device__ __forceinline__ unsigned long long limit_n(unsigned long long n, const uint64_t* n_dev) {
+  if (n_dev) {
+    const unsigned long long d = *n_dev;
+    if (d < n) n = d;
+  }
+  return n;
+}
+
+struct LineArgs {
+  unsigned long long n;
+  const uint64_t* n_dev;
+  const uint32_t* nbr;
+  const uint8_t* deg;
+  const uint32_t* comp;
+  const float* xyz;
+  const uint64_t* face_ids;
+  const int8_t* winding;
+  // workspace
+  uint32_t* cmax;    // per component label: max degree
+  uint32_t* cmin;    // min degree
+  uint32_t* csize;   // samples
+  uint8_t* special;  // per sample
+  uint32_t* nxt[2];  // per directed-edge slot (u * 10 + s): successor edge
+  uint32_t* dst[2];  // distance (edges) to the end of the chain
+  uint32_t* lst[2];  // last edge of the chain
+  uint32_t* pcount;  // per sample: pieces started there
+  uint32_t* plen;    // per sample: nodes of the pieces started there
+  unsigned long long* pfirst;  // exclusive scan of pcount
+  unsigned long long* noff;    // exclusive scan of plen
+  unsigned long long* edge_node_off;  // per starting edge slot: node offset of its piece
+  uint32_t* tmp_nodes;   // unoriented node list
+  double* dots;          // per piece: orientation sum
+  // outputs
+  qtv_piece* pieces;
+  unsigned long long piece_cap;
+  uint32_t* nodes;
+  unsigned long long node_cap;
+};
+
+__device__ __forceinline__ int comp_type(const LineArgs& a, uint32_t L) {
+  if (a.cmax[L] > 2) return 3;
+  if (a.csize[L] > 1 && a.cmin[L] == 2) return 2;
+  return 1;
+}
+
+__global__ void stats_init_kernel(LineArgs a) {
+  const unsigned long long nn = limit_n(a.n, a.n_dev);
+  for (unsigned long long u = (unsigned long long)blockIdx.x * LT + threadIdx.x; u < nn;
+       u += (unsigned long long)gridDim.x * LT) {
+    a.cmax[u] = 0;
+    a.cmin[u] = 255;
+    a.csize[u] = 0;
+  }
+}
+
+__global__ void stats_kernel(LineArgs a) {
+  const unsigned long long nn = limit_n(a.n, a.n_dev);
+  for (unsigned long long u = (unsigned long long)blockIdx.x * LT + threadIdx.x; u < nn;
+       u += (unsigned long long)gridDim.x * LT) {
+    const uint32_t L = a.comp[u], d = a.deg[u];
+    atomicMax(a.cmax + L, d);
+    atomicMin(a.cmin + L, d);
+    atomicAdd(a.csize + L, 1u);
+  }
+}
+
+__global__ void special_kernel(LineArgs a) {
+  const unsigned long long nn = limit_n(a.n, a.n_dev);
+  for (unsigned long long u = (unsigned long long)blockIdx.x * LT + threadIdx.x; u < nn;
+       u += (unsigned long long)gridDim.x * LT) {
+    const uint32_t L = a.comp[u];
+    const int t = comp_type(a, L);
+    const int d = a.deg[u];
+    a.special[u] = (t == 2) ? (uint8_t)(u == L) : (uint8_t)(d != 2);
+  }
+}
+
+// slot of neighbour x in the row of w (rows are ascending, at most 10)
+__device__ __forceinline__ int slot_of(const LineArgs& a, uint32_t w, uint32_t x) {
+  const uint32_t* r = a.nbr + (unsigned long long)w * kSlots;
+  for (int s = 0; s < kSlots; ++s)
+    if (r[s] == x) return s;
+  return -1;
+}
+
+__global__ void edges_init_kernel(LineArgs a) {
+  const unsigned long long nn = limit_n(a.n, a.n_dev);
+  const unsigned long long ne = nn * kSlots;
+  for (unsigned long long e = (unsigned long long)blockIdx.x * LT + threadIdx.x; e < ne;
+       e += (unsigned long long)gridDim.x * LT) {
+    const uint32_t u = (uint32_t)(e / kSlots);
+    const int s = (int)(e % kSlots);
+    if (s >= a.deg[u]) continue;
+    const uint32_t w = a.nbr[e];
+    if (a.special[w]) {
+      a.nxt[0][e] = kNone;
+      a.lst[0][e] = (uint32_t)e;
+    } else {
+      // w has degree 2: continue to its other neighbour
+      const uint32_t* r = a.nbr + (unsigned long long)w * kSlots;
+      const int sx = (r[0] == u) ? 1 : 0;
+      a.nxt[0][e] = w * kSlots + sx;
+      a.lst[0][e] = kNone;
+    }
+    a.dst[0][e] = 1;
+  }
+}
+
+__global__ void jump_kernel(LineArgs a, int src) {
+  const unsigned long long nn = limit_n(a.n, a.n_dev);
+  const unsigned long long ne = nn * kSlots;
+  const int d = src ^ 1;
+  for (unsigned long long e = (unsigned long long)blockIdx.x * LT + threadIdx.x; e < ne;
+       e += (unsigned long long)gridDim.x * LT) {
+    const uint32_t u = (uint32_t)(e / kSlots);
+    if ((int)(e % kSlots) >= a.deg[u]) continue;
+    const uint32_t nx = a.nxt[src][e];
+    if (nx == kNone) {
+      a.nxt[d][e] = kNone;
+      a.dst[d][e] = a.dst[src][e];
+      a.lst[d][e] = a.lst[src][e];
+    } else {
+      a.nxt[d][e] = a.nxt[src][nx];
+      a.dst[d][e] = a.dst[src][e] + a.dst[src][nx];
+      a.lst[d][e] = a.lst[src][nx];
+    }
+  }
+}
+
+// end sample and the sample before it, of the chain that edge e starts
+__device__ __forceinline__ void chain_end(const LineArgs& a, int buf, uint32_t e, uint32_t& end,
+                                          uint32_t& before) {
+  const uint32_t l = a.lst[buf][e];
+  before = l / kSlots;
+  end = a.nbr[l];
+}
+
+// is the chain that starts at special sample s through neighbour y (edge e) a
+// piece start?
+__device__ __forceinline__ bool discovering(const LineArgs& a, int buf, uint32_t s, uint32_t y,
+                                            uint32_t e) {
+  uint32_t end, before;
+  chain_end(a, buf, e, end, before);
+  const int t = comp_type(a, a.comp[s]);
+  if (t == 1) return s < end;
+  if (t == 2) return y < before;
+  if (a.deg[s] <= 2) return false;  // dead end
+  if (end == s) return y < before;
+  if (a.deg[end] > 2) return s < end;
+  return true;
+}
+
+__global__ void count_kernel(LineArgs a, int buf) {
+  const unsigned long long nn = limit_n(a.n, a.n_dev);
+  for (unsigned long long u = (unsigned long long)blockIdx.x * LT + threadIdx.x; u < nn;
+       u += (unsigned long long)gridDim.x * LT) {
+    uint32_t pc = 0, nl = 0;
+    const int d = a.deg[u];
+    if (d == 0) {
+      pc = 1;
+      nl = 1;
+    } else if (a.special[u]) {
+      for (int s = 0; s < d; ++s) {
+        const unsigned long long e = (unsigned long long)u * kSlots + s;
+        const uint32_t y = a.nbr[e];
+        if (!discovering(a, buf, (uint32_t)u, y, (uint32_t)e)) continue;
+        uint32_t end, before;
+        chain_end(a, buf, (uint32_t)e, end, before);
+        ++pc;
+        nl += (end == (uint32_t)u) ? a.dst[buf][e] : a.dst[buf][e] + 1;
+      }
+    }
+    a.pcount[u] = pc;
+    a.plen[u] = nl;
+  }
+}
+
+// piece records, and the start and end samples of every piece
+__global__ void pieces_kernel(LineArgs a, int buf) {
+  const unsigned long long nn = limit_n(a.n, a.n_dev);
+  for (unsigned long long u = (unsigned long long)blockIdx.x * LT + threadIdx.x; u < nn;
+       u += (unsigned long long)gridDim.x * LT) {
+    if (a.pcount[u] == 0) continue;
+    unsigned long long p = a.pfirst[u], off = a.noff[u];
+    const uint32_t L = a.comp[u];
+    const uint8_t ct = (uint8_t)comp_type(a, L);
+    const int d = a.deg[u];
+    if (d == 0) {
+      if (p < a.piece_cap) {
+        qtv_piece r = {};
+        r.first = off;
+        r.count = 1;
+        r.component = L;
+        r.comp_type = ct;
+        a.pieces[p] = r;
+      }
+      a.tmp_nodes[off] = (uint32_t)u;
+      continue;
+    }
+    for (int s = 0; s < d; ++s) {
+      const unsigned long long e = (unsigned long long)u * kSlots + s;
+      const uint32_t y = a.nbr[e];
+      if (!discovering(a, buf, (uint32_t)u, y, (uint32_t)e)) continue;
+      uint32_t end, before;
+      chain_end(a, buf, (uint32_t)e, end, before);
+      const bool closed = end == (uint32_t)u;
+      const uint32_t cnt = closed ? a.dst[buf][e] : a.dst[buf][e] + 1;
+      if (p < a.piece_cap) {
+        qtv_piece r = {};
+        r.first = off;
+        r.count = cnt;
+        r.component = L;
+        r.closed = closed ? 1 : 0;
+        r.comp_type = ct;
+        a.pieces[p] = r;
+      }
+      a.edge_node_off[e] = off;
+      a.tmp_nodes[off] = (uint32_t)u;
+      if (!closed) a.tmp_nodes[off + cnt - 1] = end;
+      ++p;
+      off += cnt;
+    }
+  }
+}
+
+// samples inside chains: their piece and position from its start
+__global__ void interior_kernel(LineArgs a, int buf) {
+  const unsigned long long nn = limit_n(a.n, a.n_dev);
+  for (unsigned long long u = (unsigned long long)blockIdx.x * LT + threadIdx.x; u < nn;
+       u += (unsigned long long)gridDim.x * LT) {
+    if (a.special[u] || a.deg[u] != 2) continue;
+    const unsigned long long e0 = (unsigned long long)u * kSlots, e1 = e0 + 1;
+    uint32_t end0, bef0, end1, bef1;
+    chain_end(a, buf, (uint32_t)e0, end0, bef0);
+    chain_end(a, buf, (uint32_t)e1, end1, bef1);
+    // the chain's end edges, seen from the ends: (end0 -> bef0), (end1 -> bef1)
+    const int s0 = slot_of(a, end0, bef0), s1 = slot_of(a, end1, bef1);
+    if (s0 < 0 || s1 < 0) continue;
+    const unsigned long long f0 = (unsigned long long)end0 * kSlots + s0;
+    const unsigned long long f1 = (unsigned long long)end1 * kSlots + s1;
+    unsigned long long off;
+    uint32_t pos;
+    if (discovering(a, buf, end0, bef0, (uint32_t)f0)) {
+      off = a.edge_node_off[f0];
+      pos = a.dst[buf][e0];
+    } else if (discovering(a, buf, end1, bef1, (uint32_t)f1)) {
+      off = a.edge_node_off[f1];
+      pos = a.dst[buf][e1];
+    } else {
+      continue;
+    }
+    a.tmp_nodes[off + pos] = (uint32_t)u;
+  }
+}
+
+__device__ __forceinline__ void face_dir(const LineArgs& a, uint32_t u, double d[3]) {
+  const int o = (int)(a.face_ids[u] & 3u);
+  const double w = (double)a.winding[u];
+  d[0] = (o == 1) ? w : 0.0;  // yz face: normal +x
+  d[1] = (o == 2) ? w : 0.0;  // zx face: normal +y
+  d[2] = (o == 0) ? w : 0.0;  // xy face: normal +z
+}
+
+// one warp per piece: orientation sum in a fixed order
+__global__ void orient_kernel(LineArgs a, const unsigned long long* counts) {
+  const unsigned long long np = min((unsigned long long)counts[0], a.piece_cap);
+  const int lane = threadIdx.x & 31;
+  const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  for (unsigned long long p = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+       p < np; p += warps) {
+    const qtv_piece r = a.pieces[p];
+    double sum = 0.0;
+    if (a.face_ids && a.winding && r.count >= 2 && r.first + r.count <= a.node_cap) {
+      const unsigned long long nseg = r.closed ? r.count : r.count - 1;
+      for (unsigned long long i = lane; i < nseg; i += 32) {
+        const uint32_t u = a.tmp_nodes[r.first + i];
+        const uint32_t v = a.tmp_nodes[r.first + (i + 1 == r.count ? 0 : i + 1)];
+        double d[3];
+        face_dir(a, u, d);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          sum += ((double)a.xyz[3ull * v + c] - (double)a.xyz[3ull * u + c]) * d[c];
+      }
+    }
+#pragma unroll
+    for (int dd = 16; dd; dd >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, dd);
+    if (lane == 0) {
+      a.dots[p] = sum;
+      if (sum < 0.0) a.pieces[p].reversed = 1;
+    }
+  }
+}
+
+// final node list: each piece in order, or reversed (closed: first kept)
+__global__ void place_kernel(LineArgs a, const unsigned long long* counts) {
+  const unsigned long long np = min((unsigned long long)counts[0], a.piece_cap);
+  const int lane = threadIdx.x & 31;
+  const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  for (unsigned long long p = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+       p < np; p += warps) {
+    const qtv_piece r = a.pieces[p];
+    for (unsigned long long k = lane; k < r.count; k += 32) {
+      unsigned long long src = k;
+      if (r.reversed) src = r.closed ? (k == 0 ? 0 : r.count - k) : r.count - 1 - k;
+      const unsigned long long dst = r.first + k;
+      if (dst < a.node_cap) a.nodes[dst] = a.tmp_nodes[r.first + src];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of u32 values into u64 (three passes, deterministic)
+// ---------------------------------------------------------------------------
+constexpr int SB = 1024;        // threads per scan block
+constexpr int SPER = 4;         // values per thread
+constexpr int SCHUNK = SB * SPER;
+
+__global__ void __launch_bounds__(SB) scan_blocks_kernel(const uint32_t* in, const uint64_t* n_dev,
+                                                         unsigned long long n,
+                                                         unsigned long long* out,
+                                                         unsigned long long* bsum) {
+  __shared__ unsigned long long wt[32];
+  const unsigned long long nn = limit_n(n, n_dev);
+  const unsigned long long base = (unsigned long long)blockIdx.x * SCHUNK + threadIdx.x * SPER;
+  unsigned long long v[SPER], loc = 0;
+#pragma unroll
+  for (int i = 0; i < SPER; ++i) {
+    v[i] = base + i < nn ? in[base + i] : 0;
+    loc += v[i];
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long inc = loc;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned long long t = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += t;
+  }
+  if (lane == 31) wt[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const unsigned long long x = wt[lane];
+    unsigned long long y = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned long long t = __shfl_up_sync(0xffffffffu, y, d);
+      if (lane >= d) y += t;
+    }
+    wt[lane] = y - x;
+    if (lane == 31) bsum[blockIdx.x] = y;
+  }
+  __syncthreads();
+  unsigned long long run = wt[w] + inc - loc;
+#pragma unroll
+  for (int i = 0; i < SPER; ++i) {
+    if (base + i < nn) out[base + i] = run;
+    run += v[i];
+  }
+}
+
+__global__ void scan_sums_kernel(unsigned long long* bsum, int nb, unsigned long long* total) {
+  if (threadIdx.x == 0) {
+    unsigned long long run = 0;
+    for (int b = 0; b < nb; ++b) {
+      const unsigned long long x = bsum[b];
+      bsum[b] = run;
+      run += x;
+    }
+    *total = run;
+  }
+}
+
+__global__ void scan_add_kernel(const uint64_t* n_dev, unsigned long long n,
+                                unsigned long long* out, const unsigned long long* bsum) {
+  const unsigned long long nn = limit_n(n, n_dev);
+  for (unsigned long long i = (unsigned long long)blockIdx.x * LT + threadIdx.x; i < nn;
+       i += (unsigned long long)gridDim.x * LT)
+    out[i] += bsum[i / SCHUNK];
+}
+
+void scan_u32(const uint32_t* in, const uint64_t* n_dev, unsigned long long n,
+              unsigned long long* out, unsigned long long* bsum, unsigned long long* total,
+              int num_sms, cudaStream_t st) {
+  const int nb = (int)((n + SCHUNK - 1) / SCHUNK);
+  scan_blocks_kernel<<<nb > 0 ? nb : 1, SB, 0, st>>>(in, n_dev, n, out, bsum);
+  scan_sums_kernel<<<1, 32, 0, st>>>(bsum, nb > 0 ? nb : 1, total);
+  long long g = ((long long)n + LT - 1) / LT;
+  if (g > (long long)num_sms * 16) g = (long long)num_sms * 16;
+  scan_add_kernel<<<(int)(g > 0 ? g : 1), LT, 0, st>>>(n_dev, n, out, bsum);
+}
+
+// ---------------------------------------------------------------------------
+// curves
+// ---------------------------------------------------------------------------
+struct CurveArgs {
+  const float* xyz;
+  const uint32_t* nodes;
+  const qtv_piece* pieces;
+  unsigned long long np;
+  const uint64_t* np_dev;
+  int per;
+  uint32_t* npts;                 // per piece: curve points
+  unsigned long long* cfirst;     // exclusive scan of npts
+  float* curve;
+  unsigned long long curve_cap;
+  float* length;
+};
+
+__device__ __forceinline__ uint32_t curve_points(const qtv_piece& r, int per) {
+  if (r.count < 2) return r.count;
+  return r.closed ? r.count * (uint32_t)per : (r.count - 1) * (uint32_t)per + 1;
+}
+
+__global__ void curve_count_kernel(CurveArgs a) {
+  const unsigned long long np = limit_n(a.np, a.np_dev);
+  for (unsigned long long p = (unsigned long long)blockIdx.x * LT + threadIdx.x; p < np;
+       p += (unsigned long long)gridDim.x * LT)
+    a.npts[p] = curve_points(a.pieces[p], a.per);
+}
+
+__device__ __forceinline__ void sample_pos(const CurveArgs& a, const qtv_piece& r, long long i,
+                                           float p[3]) {
+  const uint32_t u = a.nodes[r.first + (unsigned long long)i];
+  p[0] = a.xyz[3ull * u];
+  p[1] = a.xyz[3ull * u + 1];
+  p[2] = a.xyz[3ull * u + 2];
+}
+
+// one thread per curve point: its piece by binary search over the first points
+__global__ void curve_kernel(CurveArgs a, const unsigned long long* total) {
+  const unsigned long long np = limit_n(a.np, a.np_dev);
+  const unsigned long long nt = min((unsigned long long)*total, a.curve_cap);
+  for (unsigned long long g = (unsigned long long)blockIdx.x * LT + threadIdx.x; g < nt;
+       g += (unsigned long long)gridDim.x * LT) {
+    unsigned long long lo = 0, hi = np;  // last piece with cfirst <= g
+    while (hi - lo > 1) {
+      const unsigned long long mid = (lo + hi) >> 1;
+      if (a.cfirst[mid] <= g) lo = mid;
+      else hi = mid;
+    }
+    const qtv_piece r = a.pieces[lo];
+    const long long k = (long long)(g - a.cfirst[lo]);
+    const long long m = r.count;
+    float out[3];
+    const long long nseg = r.closed ? m : m - 1;
+    if (m < 2 || k >= nseg * a.per) {
+      // a one-sample piece, or the last sample of an open piece
+      sample_pos(a, r, m < 2 ? 0 : m - 1, out);
+    } else {
+      const long long s = k / a.per;
+      const int ti = (int)(k % a.per);
+      // ext = closed: [P[m-1], P[0..m-1], P[0], P[1]]; open: [P[0], P[0..m-1], P[m-1]]
+      long long id[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        long long x = s + c - 1;
+        if (r.closed) x = ((x % m) + m) % m;
+        else x = x < 0 ? 0 : (x > m - 1 ? m - 1 : x);
+        id[c] = x;
+      }
+      float p0[3], p1[3], p2[3], p3[3];
+      sample_pos(a, r, id[0], p0);
+      sample_pos(a, r, id[1], p1);
+      sample_pos(a, r, id[2], p2);
+      sample_pos(a, r, id[3], p3);
+      const float t = (float)ti / (float)a.per, t2 = t * t, t3 = t2 * t;
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        out[c] = 0.5f * (2.f * p1[c] + t * (p2[c] - p0[c]) +
+                         t2 * (2.f * p0[c] - 5.f * p1[c] + 4.f * p2[c] - p3[c]) +
+                         t3 * (-p0[c] + 3.f * p1[c] - 3.f * p2[c] + p3[c]));
+    }
+    a.curve[3 * g] = out[0];
+    a.curve[3 * g + 1] = out[1];
+    a.curve[3 * g + 2] = out[2];
+  }
+}
+
+// one block per piece: polyline length of its curve (FP64; each thread sums a
+// fixed stride, then a fixed reduction tree)
+__global__ void __launch_bounds__(LT) length_kernel(CurveArgs a) {
+  __shared__ double part[LT / 32];
+  const unsigned long long np = limit_n(a.np, a.np_dev);
+  for (unsigned long long p = blockIdx.x; p < np; p += gridDim.x) {
+    const qtv_piece r = a.pieces[p];
+    const unsigned long long c0 = a.cfirst[p];
+    const unsigned long long n = a.npts[p];
+    double sum = 0.0;
+    if (n >= 2 && c0 + n <= a.curve_cap) {
+      const unsigned long long nseg = r.closed ? n : n - 1;
+      for (unsigned long long i = threadIdx.x; i < nseg; i += LT) {
+        const unsigned long long j = (i + 1 == n) ? 0 : i + 1;
+        double s2 = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const double d = (double)a.curve[3 * (c0 + j) + c] - (double)a.curve[3 * (c0 + i) + c];
+          s2 += d * d;
+        }
+        sum += sqrt(s2);
+      }
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, d);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < LT / 32; ++w) t += part[w];
+      a.length[p] = (float)t;
+    }
+    __syncthreads();
+  }
+}
+
+bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return false;
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+int ensure(qtv_handle h, size_t bytes, cudaStream_t st, void** out) {
+  if (!h->lines) h->lines = new LineWork();
+  LineWork* w = h->lines;
+  if (bytes > w->cap) {
+    if (capturing(st))
+      return set_error(QTV_ERR_STATE, "line workspace must grow outside stream capture");
+    cudaFree(w->buf);
+    w->buf = nullptr;
+    w->cap = 0;
+    const cudaError_t e = cudaMalloc(&w->buf, bytes);
+    if (e != cudaSuccess) return check_cuda(e, "cudaMalloc(line workspace)");
+    w->cap = bytes;
+  }
+  *out = w->buf;
+  return QTV_OK;
+}
+
+template <typename T>
+T* carve(char*& p, unsigned long long count) {
+  T* r = reinterpret_cast<T*>(p);
+  p += ((count * sizeof(T) + 255) / 256) * 256;
+  return r;
+}
+
+}  // namespace
+
+int line_pieces_launch(qtv_handle h, uint64_t n, const uint64_t* n_dev, const uint32_t* nbr,
+                       const uint8_t* deg, const uint32_t* comp, const float* xyz,
+                       const uint64_t* face_ids, const int8_t* winding, qtv_piece* pieces,
+                       uint64_t piece_cap, uint32_t* nodes, uint64_t node_cap, uint64_t* counts,
+                       cudaStream_t st) {
+  const unsigned long long ne = (unsigned long long)n * kSlots;
+  // each piece holds at least one edge and adds at most two end samples to
+  // its interior ones; edges <= 5 n (degree <= 10)
+  const unsigned long long nodes_max = 11ull * n + 1;
+  const unsigned long long nb = (n + SCHUNK - 1) / SCHUNK + 1;
+  size_t bytes = 0;
+  {
+    // sizes must match the carve sequence below
+    const unsigned long long sz[] = {n * 4, n * 4, n * 4, n, ne * 4, ne * 4, ne * 4, ne * 4,
+                                     ne * 4, ne * 4, n * 4, n * 4, n * 8, n * 8, ne * 8,
+                                     nodes_max * 4, n * 8, nb * 8, nb * 8, 16};
+    for (unsigned long long s : sz) bytes += ((s + 255) / 256) * 256;
+  }
+  void* buf = nullptr;
+  int rc = ensure(h, bytes, st, &buf);
+  if (rc) return rc;
+  char* p = static_cast<char*>(buf);
+  LineArgs a;
+  a.n = n;
+  a.n_dev = n_dev;
+  a.nbr = nbr;
+  a.deg = deg;
+  a.comp = comp;
+  a.xyz = xyz;
+  a.face_ids = face_ids;
+  a.winding = winding;
+  a.cmax = carve<uint32_t>(p, n);
+  a.cmin = carve<uint32_t>(p, n);
+  a.csize = carve<uint32_t>(p, n);
+  a.special = carve<uint8_t>(p, n);
+  a.nxt[0] = carve<uint32_t>(p, ne);
+  a.nxt[1] = carve<uint32_t>(p, ne);
+  a.dst[0] = carve<uint32_t>(p, ne);
+  a.dst[1] = carve<uint32_t>(p, ne);
+  a.lst[0] = carve<uint32_t>(p, ne);
+  a.lst[1] = carve<uint32_t>(p, ne);
+  a.pcount = carve<uint32_t>(p, n);
+  a.plen = carve<uint32_t>(p, n);
+  a.pfirst = carve<unsigned long long>(p, n);
+  a.noff = carve<unsigned long long>(p, n);
+  a.edge_node_off = carve<unsigned long long>(p, ne);
+  a.tmp_nodes = carve<uint32_t>(p, nodes_max);
+  a.dots = carve<double>(p, n);
+  unsigned long long* bs1 = carve<unsigned long long>(p, nb);
+  unsigned long long* bs2 = carve<unsigned long long>(p, nb);
+  unsigned long long* tot = carve<unsigned long long>(p, 2);
+  a.pieces = pieces;
+  a.piece_cap = piece_cap;
+  a.nodes = nodes;
+  a.node_cap = node_cap;
+
+  long long g = ((long long)n + LT - 1) / LT;
+  if (g > (long long)h->num_sms * 16) g = (long long)h->num_sms * 16;
+  if (g < 1) g = 1;
+  long long ge = ((long long)ne + LT - 1) / LT;
+  if (ge > (long long)h->num_sms * 32) ge = (long long)h->num_sms * 32;
+  if (ge < 1) ge = 1;
+  TraceScope ts(h, K_LINES, st);
+  stats_init_kernel<<<(int)g, LT, 0, st>>>(a);
+  stats_kernel<<<(int)g, LT, 0, st>>>(a);
+  special_kernel<<<(int)g, LT, 0, st>>>(a);
+  edges_init_kernel<<<(int)ge, LT, 0, st>>>(a);
+  int rounds = 1;
+  while ((1ull << rounds) < (unsigned long long)n + 1) ++rounds;
+  int buf_i = 0;
+  for (int r = 0; r < rounds; ++r) {
+    jump_kernel<<<(int)ge, LT, 0, st>>>(a, buf_i);
+    buf_i ^= 1;
+  }
+  count_kernel<<<(int)g, LT, 0, st>>>(a, buf_i);
+  scan_u32(a.pcount, n_dev, n, a.pfirst, bs1, tot, h->num_sms, st);
+  scan_u32(a.plen, n_dev, n, a.noff, bs2, tot + 1, h->num_sms, st);
+  cudaError_t e = cudaMemcpyAsync(counts, tot, 2 * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return check_cuda(e, "cudaMemcpyAsync(line counts)");
+  pieces_kernel<<<(int)g, LT, 0, st>>>(a, buf_i);
+  interior_kernel<<<(int)g, LT, 0, st>>>(a, buf_i);
+  orient_kernel<<<h->num_sms * 8, LT, 0, st>>>(a, tot);
+  place_kernel<<<h->num_sms * 8, LT, 0, st>>>(a, tot);
+  e = cudaGetLastError();
+  return check_cuda(e, "line pieces launch");
+}
+
+int piece_curves_launch(qtv_handle h, const float* xyz, const uint32_t* nodes,
+                        const qtv_piece* pieces, uint64_t np, const uint64_t* np_dev, int per,
+                        float* curve, uint64_t curve_cap, uint64_t* curve_first, float* length,
+                        uint64_t* total, cudaStream_t st) {
+  const unsigned long long nb = (np + SCHUNK - 1) / SCHUNK + 1;
+  size_t bytes = ((np * 4 + 255) / 256) * 256 + ((nb * 8 + 255) / 256) * 256 + 256;
+  void* buf = nullptr;
+  int rc = ensure(h, bytes, st, &buf);
+  if (rc) return rc;
+  char* p = static_cast<char*>(buf);
+  CurveArgs a;
+  a.xyz = xyz;
+  a.nodes = nodes;
+  a.pieces = pieces;
+  a.np = np;
+  a.np_dev = np_dev;
+  a.per = per;
+  a.npts = carve<uint32_t>(p, np);
+  unsigned long long* bs = carve<unsigned long long>(p, nb);
+  a.cfirst = reinterpret_cast<unsigned long long*>(curve_first);
+  a.curve = curve;
+  a.curve_cap = curve_cap;
+  a.length = length;
+  long long g = ((long long)np + LT - 1) / LT;
+  if (g > (long long)h->num_sms * 16) g = (long long)h->num_sms * 16;
+  if (g < 1) g = 1;
+  TraceScope ts(h, K_CURVES, st);
+  curve_count_kernel<<<(int)g, LT, 0, st>>>(a);
+  scan_u32(a.npts, np_dev, np, a.cfirst, bs, reinterpret_cast<unsigned long long*>(total),
+           h->num_sms, st);
+  curve_kernel<<<h->num_sms * 16, LT, 0, st>>>(a, reinterpret_cast<unsigned long long*>(total));
+  long long gp = (long long)np;
+  if (gp > (long long)h->num_sms * 16) gp = (long long)h->num_sms * 16;
+  length_kernel<<<(int)(gp > 0 ? gp : 1), LT, 0, st>>>(a);
+  const cudaError_t e = cudaGetLastError();
+  return check_cuda(e, "piece curves launch");
+}
+
+}  // namespace qtv

@@ -76,7 +76,7 @@ struct Locator;  // learned locator state (locator.cu)
 void locator_free(Locator* L);
 enum KernelId {
   K_SWEEP = 0, K_SEG_SCAN, K_SCATTER, K_STATS, K_LOCALIZE, K_EMIT_PACK, K_BATCH,
-  K_ENCODE, K_NETWORK, K_HEAD, K_NODE_FORM, K_NODE_SCAN, K_NODE_SCATTER, K_DENSITY, K_REFINE, K_GRAPH, K_COUNT
+  K_ENCODE, K_NETWORK, K_HEAD, K_NODE_FORM, K_NODE_SCAN, K_NODE_SCATTER, K_DENSITY, K_REFINE, K_GRAPH, K_LINES, K_CURVES, K_COUNT
 };
 struct BatchPlan;  // batched snapshots (batch.cu)
 void batch_free(BatchPlan* b);
@@ -84,6 +84,8 @@ struct NodeWork;   // node-form and density-error workspace (node_form.cu)
 void node_work_free(NodeWork* w);
 struct GraphWork;  // face-graph workspace (graph.cu)
 void graph_work_free(GraphWork* w);
+struct LineWork;   // line-extraction workspace (lines.cu)
+void line_work_free(LineWork* w);
 struct TraceRec {
   int kernel;
   cudaEvent_t start, stop;
@@ -101,6 +103,7 @@ struct qtv_handle_s {
   qtv::BatchPlan* batch = nullptr;       // batch plan, scratch and captured graph
   qtv::NodeWork* node = nullptr;         // node-form / density-error workspace
   qtv::GraphWork* graph = nullptr;       // face-graph workspace
+  qtv::LineWork* lines = nullptr;        // line-extraction workspace
   // sweep shape of single-snapshot calls (qtv_configure_sweep); -1 / 0 = default
   int sweep_variant = -1, sweep_nwt = 0, sweep_stages = 0, sweep_ctas = 0;
 };
@@ -340,6 +343,17 @@ int refine_launch(qtv_handle h, const qtv_grid& g, const float2* psi, const floa
 int face_graph_launch(qtv_handle h, const qtv_grid& g, const uint64_t* face_ids, uint64_t n,
                       const uint64_t* n_dev, uint32_t* nbr, uint8_t* deg, uint32_t* comp,
                       uint64_t* ncomp, cudaStream_t st);
+
+// Line pieces and curves of a sample graph (lines.cu)
+int line_pieces_launch(qtv_handle h, uint64_t n, const uint64_t* n_dev, const uint32_t* nbr,
+                       const uint8_t* deg, const uint32_t* comp, const float* xyz,
+                       const uint64_t* face_ids, const int8_t* winding, qtv_piece* pieces,
+                       uint64_t piece_cap, uint32_t* nodes, uint64_t node_cap, uint64_t* counts,
+                       cudaStream_t st);
+int piece_curves_launch(qtv_handle h, const float* xyz, const uint32_t* nodes,
+                        const qtv_piece* pieces, uint64_t np, const uint64_t* np_dev, int per,
+                        float* curve, uint64_t curve_cap, uint64_t* curve_first, float* length,
+                        uint64_t* total, cudaStream_t st);
 
 // Emission pack (localize.cu)
 int emit_pack_launch(qtv_handle h, uint64_t n, const uint64_t* face_ids, const int8_t* winding, const float* xyz,
