@@ -1,7 +1,10 @@
-"""The multi-GPU path of the benchmark on CPU ranks (gloo, world size 2):
-replicas only, so the only cross-rank steps are the barrier and the maximum
-of the ranks' times; the whole-job value counts every rank's grid points over
-the slowest rank's time; the reference arm runs on rank 0 alone."""
+"""The multi-GPU paths on CPU ranks (gloo, world size 2).  The benchmark runs
+replicas, so its only cross-rank steps are the barrier and the maximum of the
+ranks' times; the whole-job value counts every rank's grid points over the
+slowest rank's time; the reference arm runs on rank 0 alone.  The z-slab
+sharding of one snapshot: each rank identifies its planes plus a one-plane
+halo (here with the FP64 oracle on the host) and the face lists gathered in
+rank order equal the single-grid list."""
 import os
 import socket
 import sys
@@ -68,3 +71,47 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
             raise AssertionError(f"rank 1 read args.{name}")
 
     assert bench.run_reference(A()) == 0
+
+
+def _slab_rank(rank, world, port, out):
+    import numpy as np
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    import oracle
+    import synth
+    from paper_1911_12070_gb300 import slabs
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    host = synth.random_waves_numpy((23, 30, 34), synth.wave_spec(9, 256))
+    nz, ny, nx = host.shape
+    z0, z1 = slabs.slab_bounds(nz, world)[rank]
+    w, _ = oracle.identify(np.ascontiguousarray(host[z0:min(nz, z1 + 1)]))
+    ids, wv = oracle.face_list(w)
+    ids = torch.from_numpy(ids.astype(np.int64))
+    keep = slabs.owned_mask(ids, z0, z1, nx, ny)
+    gids = slabs.to_global(ids[keep], z0, nx, ny)
+    allids = slabs.gather_to_all(gids)
+    allw = slabs.gather_to_all(torch.from_numpy(wv.astype(np.int8))[keep])
+    if rank == 0:
+        fw, _ = oracle.identify(host)
+        fids, fwv = oracle.face_list(fw)
+        out.put((bool(np.array_equal(allids.numpy(), fids.astype(np.int64))),
+                 bool(np.array_equal(allw.numpy(), fwv)), int(len(fids))))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_shard_one_snapshot_by_z_slabs():
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_slab_rank, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    same_ids, same_w, n = out.get(timeout=180)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert same_ids and same_w and n > 50
