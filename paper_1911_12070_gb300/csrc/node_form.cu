@@ -12,9 +12,9 @@
 //
 // Arithmetic.  Every directed edge a -> b contributes the integer branch
 // crossing r (its wrapped phase difference minus theta_b - theta_a, over
-// 2 pi), decided from the sign bits of Im a, Im b and the sign of the exactly
-// evaluated determinant Re a Im b - Im a Re b; the theta terms telescope
-// around the ring, so S is the sum of the ring's eight r.  Each grid edge is
+// 2 pi), decided from the sign bits of Im a, Im b and the sign of the
+// determinant Re a Im b - Im a Re b; the theta terms telescope around the
+// ring, so S is the sum of the ring's eight r.  Each grid edge is
 // evaluated once, in its forward direction, and a ring that runs it backwards
 // adds -r (the argument of the conjugate is the exact negation).  Two
 // consecutive edges along a grid line make one side of a ring:
@@ -26,15 +26,19 @@
 //   S_yz = Y_{k-1}(i,j) + Z(i,j+1,k) - Y_{k+1}(i,j) - Z(i,j-1,k)
 //   S_zx = Z(i-1,j,k) + X_{k+1}(i,j) - Z(i+1,j,k) - X_{k-1}(i,j).
 //
-// Layout.  A warp owns 30 columns (lanes 1..30; lanes 0 and 31 hold the
-// neighbour columns) of a band of NB rows (plus a halo row on either side) and
-// marches z over a chunk of planes, with the line sums of three planes in
-// registers.  Each lane streams its column of the band through a private ring
-// of five plane slots in shared memory with cp.async, three planes ahead of
-// the plane it computes.  Neighbour columns come by warp shuffle, neighbour
-// rows and planes from the thread's own registers and ring slots; no barrier.
-// Line sums live in packed bit fields between planes (3 bits per row, biased
-// by +2), which halves the registers the march holds.
+// Layout (bit-sliced).  A warp owns 30 columns (lanes 1..30; lanes 0 and 31
+// hold the neighbour columns) of a band of NB = 14 rows, and each lane keeps
+// one bit per row (rows j0 - 1 .. j0 + NB, halo rows included) in words:
+// the sign bit of Im psi and the sign bits of the FP32 cross products of its
+// x, y and z edges, as the identification sweep does.  An edge term is +1 when
+// s_a = 0, s_b = 1 and the cross sign is 0, -1 when s_a = 1, s_b = 0 and the
+// sign is 1; edges that touch a zero node count 0.  The eight terms of a ring
+// are word shifts (rows) and shuffles (columns) of these edge words, and
+// their sum mod 8 comes from a carry-save adder tree over the words: S mod 8
+// = #nonzero - 2 #negative, exact in [-3, 4] because only a ring whose eight
+// differences are all exact +-pi ties reaches |S| = 4.  The warp marches z
+// over a chunk of planes, streaming each lane's column through a 3-slot ring
+// in shared memory with cp.async one plane ahead.
 //
 // Output.  Vortex nodes in ascending linear node index with their three S:
 // each warp step stages its records contiguously in a chunk of the staging
@@ -81,33 +85,121 @@ void node_work_free(NodeWork* w) {
 
 namespace {
 
-constexpr int NB = 8;          // owned rows per band
-constexpr int NT = NB + 2;     // rows held, with one halo row on either side
-constexpr uint32_t kOwnedRows = (1u << (NB + 1)) - 2u;  // rows t = 1..NB
-static_assert(NB <= 8, "per-row counts are packed into 8 bytes");
-static_assert(3 * NT <= 32, "line sums of a plane are packed into 32 bits");
-constexpr int NCOL = 30;       // owned columns per warp
-constexpr int NODE_WARPS = 8;  // warps per CTA
+constexpr int NT = 16;          // rows held: bit t = row j0 - 1 + t
+constexpr int NB = NT - 2;      // owned rows per band: bits 1..NB
+constexpr uint32_t kOwnedRows = (1u << (NB + 1)) - 2u;
+constexpr uint32_t kRowsHeld = NT == 32 ? 0xFFFFFFFFu : (1u << NT) - 1u;
+constexpr int NCOL = 30;        // owned columns per warp (lanes 1..30)
+constexpr int NODE_WARPS = 8;   // warps per CTA
+constexpr int kSlots = 3;       // plane slots of a warp's ring: p - 1, p, p + 1
+constexpr uint32_t kChunk = 4096;  // staging records a warp reserves at a time
+// table entry: base, count, then one row-count byte per row (NT bytes)
+constexpr int kTabVec = (2 + NT / 4 + 3) / 4;
+constexpr size_t kRingFloats2 = (size_t)NODE_WARPS * kSlots * NT * 32;
+// the rings, then NT bytes of per-row counts per warp, then per warp and row
+// the lane mask and the prefix of the step's records
+constexpr size_t kNodeSmem =
+    kRingFloats2 * sizeof(float2) + NODE_WARPS * NT + NODE_WARPS * 2 * NT * sizeof(uint32_t);
+static_assert(NT == 16 || NT == 32, "rows per band");
 constexpr int DENS_THREADS = 256;
 constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ bool fin(float v) { return fabsf(v) <= 3.402823466e38f; }
 
-// branch crossing r in {-1, 0, 1} of the directed edge a -> b: +1 when the
-// short arc from a to b crosses the negative real axis counter-clockwise
-// (Im a >= 0 > Im b, determinant > 0), -1 clockwise, else 0.  The
-// determinant's sign is exact: Im a Re b = p + e exactly (one FMA), and
-// RN(Re a Im b - p) compares with e in the same order as the exact values.
-__device__ __forceinline__ int crossing(float2 a, float2 b) {
-  const float p = a.y * b.x;
-  const float e = fmaf(a.y, b.x, -p);
-  const float c = fmaf(a.x, b.y, -p);
-  const bool sa = a.y < 0.f, sb = b.y < 0.f;
-  return (int)(!sa && sb && c > e) - (int)(sa && !sb && c < e);
+// acc' = (acc << 1) | sign bit of x
+__device__ __forceinline__ uint32_t push1(uint32_t acc, float x) {
+  return __funnelshift_l(__float_as_uint(x), acc, 1);
 }
 
-// 3-bit field t of a packed plane of line sums (values -2..2 stored + 2)
-__device__ __forceinline__ int fld(uint32_t w, int t) { return (int)((w >> (3 * t)) & 7u) - 2; }
+// FP32 value of Re a Im b - Im a Re b with one rounding of the second product
+// absorbed by the FMA; its sign bit decides the edge term
+__device__ __forceinline__ float cross_f(float2 a, float2 b) { return fmaf(a.x, b.y, -(a.y * b.x)); }
+
+// packed product of the (Re, Im) values: zero if a component of a node is
+// zero, non-finite if a node is (or on FP32 under- or overflow, which merely
+// selects the masking path)
+__device__ __forceinline__ unsigned long long prod_step(unsigned long long acc, float2 v) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;"
+      : "=l"(d)
+      : "l"(acc), "l"((unsigned long long)__float_as_uint(v.x) |
+                      ((unsigned long long)__float_as_uint(v.y) << 32)));
+  return d;
+}
+__device__ __forceinline__ bool prod_special(unsigned long long acc) {
+  const float px = fabsf(__uint_as_float((uint32_t)acc));
+  const float py = fabsf(__uint_as_float((uint32_t)(acc >> 32)));
+  return !(px > 0.f && px <= 3.402823466e38f && py > 0.f && py <= 3.402823466e38f);
+}
+constexpr unsigned long long kProdOne = 0x3f8000003f800000ull;  // (1.f, 1.f)
+
+// edge words of a -> b from sign words, the cross-sign word n and the edges E
+// that touch a zero node (which count 0): P = crossing +1, N = crossing -1
+struct EW {
+  uint32_t P, N;
+};
+__device__ __forceinline__ EW edge_w(uint32_t sa, uint32_t sb, uint32_t n, uint32_t E) {
+  EW e;
+  e.P = ~sa & sb & ~n & ~E;
+  e.N = sa & ~sb & n & ~E;
+  return e;
+}
+__device__ __forceinline__ EW shl(EW e) { return EW{e.P << 1, e.N << 1}; }
+__device__ __forceinline__ EW shr(EW e) { return EW{e.P >> 1, e.N >> 1}; }
+__device__ __forceinline__ EW sh_up(EW e) {
+  return EW{__shfl_up_sync(FULL, e.P, 1), __shfl_up_sync(FULL, e.N, 1)};
+}
+__device__ __forceinline__ EW sh_dn(EW e) {
+  return EW{__shfl_down_sync(FULL, e.P, 1), __shfl_down_sync(FULL, e.N, 1)};
+}
+
+// full adder on bit-sliced words
+__device__ __forceinline__ void fa(uint32_t a, uint32_t b, uint32_t c, uint32_t& s, uint32_t& cy) {
+  s = a ^ b ^ c;
+  cy = (a & b) | (c & (a ^ b));
+}
+
+// Sum mod 8 of eight terms in {-1, 0, 1} given as (nonzero, negative) words:
+// S = #nonzero - 2 #negative.  A ring of finite nodes has |S| <= 3 unless all
+// eight of its edge differences are exact +-pi ties (S = +-4, read as 4), so
+// the residue in [-3, 4] is S.
+struct Mod8 {
+  uint32_t b0, b1, b2;
+};
+__device__ __forceinline__ Mod8 ring_sum(const uint32_t z[8], const uint32_t g[8]) {
+  uint32_t s1, c1, s2, c2, c4, t1, c5;
+  fa(z[0], z[1], z[2], s1, c1);
+  fa(z[3], z[4], z[5], s2, c2);
+  const uint32_t s3 = z[6] ^ z[7], c3 = z[6] & z[7];
+  uint32_t a0, a1;
+  fa(s1, s2, s3, a0, c4);
+  fa(c1, c2, c3, t1, c5);
+  a1 = t1 ^ c4;
+  const uint32_t a2 = c5 ^ (t1 & c4);
+  // negatives mod 4
+  uint32_t u1, d1c, u2, d2c, d4, v1, d5;
+  fa(g[0], g[1], g[2], u1, d1c);
+  fa(g[3], g[4], g[5], u2, d2c);
+  const uint32_t u3 = g[6] ^ g[7], d3c = g[6] & g[7];
+  uint32_t e0;
+  fa(u1, u2, u3, e0, d4);
+  fa(d1c, d2c, d3c, v1, d5);
+  const uint32_t e1 = v1 ^ d4;
+  (void)d5;
+  // S = a - 2 e (mod 8)
+  Mod8 r;
+  r.b0 = a0;
+  r.b1 = a1 ^ e0;
+  r.b2 = a2 ^ e1 ^ (~a1 & e0);
+  return r;
+}
+
+// value in [-3, 4] of row t of a residue
+__device__ __forceinline__ int mod8_at(const Mod8& m, int t) {
+  const int v = (int)((m.b0 >> t) & 1u) | (int)(((m.b1 >> t) & 1u) << 1) |
+                (int)(((m.b2 >> t) & 1u) << 2);
+  return v >= 5 ? v - 8 : v;
+}
 
 struct NodeArgs {
   const float2* psi;
@@ -117,14 +209,10 @@ struct NodeArgs {
   unsigned long long* recs;
   unsigned long long recs_cap;
   unsigned long long* top;        // staging chunk counter
-  uint4* table;                   // [nz][nbands][nxseg]
+  uint4* table;                   // [nz][nbands][nxseg][3]
   unsigned int* segtot;           // [nz][nbands], zeroed before the launch
   int8_t* dense;                  // [3][nz][ny][nx] or null
 };
-
-constexpr int kSlots = 5;         // plane slots of a warp's ring: p-1 .. p+3
-constexpr uint32_t kChunk = 4096; // staging records a warp reserves at a time
-constexpr size_t kNodeSmem = (size_t)NODE_WARPS * kSlots * NT * 32 * sizeof(float2);
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -137,17 +225,28 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
 
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
-__device__ __forceinline__ void cp_wait3() { asm volatile("cp.async.wait_group 3;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
-// Every thread copies (and later reads) only its own elements of the ring, so
-// the asynchronous copies need no barrier: cp.async.wait_group orders them
-// with the thread's own reads, and plain zero stores go in program order.
-__global__ void __launch_bounds__(NODE_WARPS * 32, 2) node_form_kernel(NodeArgs a) {
+// Each lane streams its column of the band (32 rows) through the warp's ring
+// with cp.async; a lane also reads its right neighbour's column, so every
+// slot is fenced by __syncwarp after its copies complete and before it is
+// refilled.  Rows, columns and planes outside the grid hold (1, 1): finite
+// and nonzero, and only ever on rings that the validity masks reject.
+__global__ void __launch_bounds__(NODE_WARPS * 32) node_form_kernel(NodeArgs a) {
   extern __shared__ float2 node_ring[];
   const int lane = threadIdx.x & 31;
   float2* ring = node_ring + (size_t)(threadIdx.x >> 5) * kSlots * NT * 32;
+  uint8_t* rcnt = reinterpret_cast<uint8_t*>(node_ring + kRingFloats2) + (threadIdx.x >> 5) * NT;
+  // per row: lane mask of the vortex nodes and records of the rows before it
+  uint32_t* rbal = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(node_ring + kRingFloats2) +
+                                               NODE_WARPS * NT) + (threadIdx.x >> 5) * 2 * NT;
+  uint32_t* rpre = rbal + NT;
   const long long nwarps = (long long)gridDim.x * NODE_WARPS;
   const long long nxyz = (long long)a.nx * a.ny * a.nz;
+  const unsigned lt = (1u << lane) - 1u;
   unsigned long long chunk_at = 0;  // next free staging record of the warp's chunk
   uint32_t chunk_left = 0;
   for (long long it = (long long)blockIdx.x * NODE_WARPS + (threadIdx.x >> 5); it < a.nitems;
@@ -163,165 +262,199 @@ __global__ void __launch_bounds__(NODE_WARPS * 32, 2) node_form_kernel(NodeArgs 
     const bool xin = x >= 0 && x < a.nx;
     const bool own = lane >= 1 && lane <= NCOL && x < a.nx;
     const bool colring = x >= 1 && x <= a.nx - 2;
-    uint32_t rin = 0, rring = 0;  // owned rows in the grid / whose y-ring fits
-#pragma unroll
+    uint32_t rload = 0, rring = 0;  // rows in the grid / rows whose y-ring fits
     for (int t = 0; t < NT; ++t) {
       const int j = j0 - 1 + t;
-      if (j >= 0 && j < a.ny) rin |= 1u << t;
+      if (j >= 0 && j < a.ny) rload |= 1u << t;
       if (j >= 1 && j <= a.ny - 2) rring |= 1u << t;
     }
-    const uint32_t rload = rin;  // rows to load (halo rows included)
-    rin &= kOwnedRows;
+    const uint32_t rin = rload & kOwnedRows;
     rring &= kOwnedRows;
 
     // plane q (kz0 - 1 <= q <= kz1) lives in slot (q - kz0 + 1) mod kSlots
     auto issue = [&](int q, int slot) {
       float2* d = ring + slot * NT * 32 + lane;
       const bool qin = q >= 0 && q < a.nz && xin;
+      const float2* src = a.psi + ((long long)(qin ? q : 0) * a.ny + (j0 - 1)) * a.nx + x;
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
-        if (qin && ((rload >> t) & 1u))
-          cp_async8(d + t * 32, a.psi + ((long long)q * a.ny + (j0 - 1 + t)) * a.nx + x);
-        else
-          d[t * 32] = make_float2(0.f, 0.f);
+        if (qin && ((rload >> t) & 1u)) cp_async8(d + t * 32, src);
+        else d[t * 32] = make_float2(1.f, 1.f);
+        src += a.nx;
       }
       cp_commit();
     };
+    __syncwarp();
     issue(kz0 - 1, 0);
-    issue(kz0, 1);
-    issue(kz0 + 1, 2);  // kz1 >= kz0 + 1
-    int sp = 0;         // slot of plane p
+    int sp = 0;  // slot of plane p
 
-    // packed line sums: X of planes k-1, k and Y of planes k-1, k; r_z + 1 of
-    // the edges k-1 -> k (2 bits per row); non-finite node bits of k-1, k
-    uint32_t Xm = 0, Xc = 0, Ym = 0, Yc = 0, rzp = 0, Bm = 0, Bc = 0;
+    EW RXm{0, 0}, RXc{0, 0}, RYm{0, 0}, RYc{0, 0}, RZlo{0, 0};
+    uint32_t Sprev = 0, ZBc = 0, Bm = 0, Bc = 0;
 
     for (int p = kz0 - 1; p <= kz1; ++p) {
-      const int s3 = sp + 3 >= kSlots ? sp + 3 - kSlots : sp + 3;
-      if (p + 3 <= kz1) issue(p + 3, s3);
-      else cp_commit();  // an empty group keeps the group count uniform
-      cp_wait3();        // plane p has landed
-      const float2* cur = ring + sp * NT * 32 + lane;
-      float2 vn[NT];
-      uint32_t bn = 0;
-#pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        vn[t] = cur[t * 32];
-        if (!(fin(vn[t].x) && fin(vn[t].y))) bn |= 1u << t;
+      __syncwarp();  // every lane is done with the slot of plane p - 2
+      const int s1 = sp + 1 == kSlots ? 0 : sp + 1;
+      if (p + 1 <= kz1) issue(p + 1, s1);
+      else cp_commit();
+      cp_wait<1>();  // plane p has landed (this lane's copies)
+      __syncwarp();  // ... and every lane's
+      const float2* cur = ring + sp * NT * 32;
+      const float2* prv = (p == kz0 - 1) ? cur : ring + (sp == 0 ? kSlots - 1 : sp - 1) * NT * 32;
+      const int ln = lane < 31 ? lane + 1 : 31;
+      uint32_t Sp = 0, NX = 0, NY = 0, NZ = 0;
+      unsigned long long prod = kProdOne;
+      float2 vup = make_float2(1.f, 1.f);
+#pragma unroll (NT == 16 ? 16 : 4)
+      for (int t = NT - 1; t >= 0; --t) {
+        const float2 v = cur[t * 32 + lane];
+        const float2 nb = cur[t * 32 + ln];
+        const float2 pv = prv[t * 32 + lane];
+        Sp = push1(Sp, v.y);
+        NX = push1(NX, cross_f(v, nb));
+        NZ = push1(NZ, cross_f(pv, v));
+        NY = push1(NY, cross_f(v, vup));
+        prod = prod_step(prod, v);
+        vup = v;
       }
-      // line sums of plane p, packed
-      uint32_t Xn = 0, Yn = 0;
-#pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        float2 r;
-        r.x = __shfl_down_sync(FULL, vn[t].x, 1);
-        r.y = __shfl_down_sync(FULL, vn[t].y, 1);
-        const int rx = crossing(vn[t], r);
-        Xn |= (uint32_t)(rx + __shfl_up_sync(FULL, rx, 1) + 2) << (3 * t);
-      }
-      {
-        int ry_prev = crossing(vn[0], vn[1]);
-#pragma unroll
-        for (int t = 1; t <= NB; ++t) {
-          const int ry = crossing(vn[t], vn[t + 1]);
-          Yn |= (uint32_t)(ry_prev + ry + 2) << (3 * t);
-          ry_prev = ry;
+      NY &= kRowsHeld >> 1;  // the top row has no y-edge in the band
+      uint32_t ZBp = 0, Bn = 0;
+      if (__any_sync(FULL, prod_special(prod))) {
+        for (int t = 0; t < NT; ++t) {
+          const float2 v = cur[t * 32 + lane];
+          if (((__float_as_uint(v.x) | __float_as_uint(v.y)) << 1) == 0u) ZBp |= 1u << t;
+          if (!(fin(v.x) && fin(v.y))) Bn |= 1u << t;
         }
+        Bn &= xin ? rload : 0u;
       }
-      if (p >= kz0) {
-        const float2* prv = ring + (sp == 0 ? kSlots - 1 : sp - 1) * NT * 32 + lane;
-        uint32_t rzn = 0;
-#pragma unroll
-        for (int t = 0; t < NT; ++t) rzn |= (uint32_t)(crossing(prv[t * 32], vn[t]) + 1) << (2 * t);
-        if (p > kz0) {
-          // finalize node plane k = p - 1
-          const int k = p - 1;
-          const bool kring = k >= 1 && k <= a.nz - 2;
-          const uint32_t Bl = __shfl_up_sync(FULL, Bc, 1), Br = __shfl_down_sync(FULL, Bc, 1);
-          const uint32_t H = Bl | Bc | Br;
-          const uint32_t bad0 = (H << 1) | (H >> 1) | Bl | Br;
-          const uint32_t V = Bm | Bc | bn;
-          const uint32_t bad1 = (V << 1) | (V >> 1) | Bm | bn;
-          const uint32_t bad2 =
-              __shfl_up_sync(FULL, V, 1) | __shfl_down_sync(FULL, V, 1) | Bm | bn;
-          const uint32_t ok0 = (own && colring) ? (rring & ~bad0) : 0u;
-          const uint32_t ok1 = (own && kring) ? (rring & ~bad1) : 0u;
-          const uint32_t ok2 = (own && colring && kring) ? (rin & ~bad2) : 0u;
-          // Z + 2 per row, packed
-          uint32_t Zp = 0;
-#pragma unroll
-          for (int t = 0; t < NT; ++t)
-            Zp |= (((rzp >> (2 * t)) & 3u) + ((rzn >> (2 * t)) & 3u)) << (3 * t);
-          const uint32_t Yl = __shfl_up_sync(FULL, Yc, 1), Yr = __shfl_down_sync(FULL, Yc, 1);
-          const uint32_t Zl = __shfl_up_sync(FULL, Zp, 1), Zr = __shfl_down_sync(FULL, Zp, 1);
-          uint32_t pk[NT];
-          unsigned bal[NT];
-          uint32_t rc_lo = 0, rc_hi = 0, cnt = 0;
-#pragma unroll
+      const uint32_t Spn = __shfl_down_sync(FULL, Sp, 1);
+      const uint32_t ZBpn = __shfl_down_sync(FULL, ZBp, 1);
+      const EW RXn = edge_w(Sp, Spn, NX, ZBp | ZBpn);
+      const EW RYn = edge_w(Sp, Sp >> 1, NY, ZBp | (ZBp >> 1));
+      const EW RZhi = edge_w(Sprev, Sp, NZ, ZBc | ZBp);  // edges p - 1 -> p
+      if (p > kz0) {
+        // finalize node plane k = p - 1: planes k - 1, k, k + 1 are m, c, n
+        const int k = p - 1;
+        const bool kring = k >= 1 && k <= a.nz - 2;
+        const uint32_t Bl = __shfl_up_sync(FULL, Bc, 1), Br = __shfl_down_sync(FULL, Bc, 1);
+        const uint32_t H = Bl | Bc | Br;
+        const uint32_t bad0 = (H << 1) | (H >> 1) | Bl | Br;
+        const uint32_t V = Bm | Bc | Bn;
+        const uint32_t bad1 = (V << 1) | (V >> 1) | Bm | Bn;
+        const uint32_t bad2 =
+            __shfl_up_sync(FULL, V, 1) | __shfl_down_sync(FULL, V, 1) | Bm | Bn;
+        const uint32_t ok0 = (own && colring) ? (rring & ~bad0) : 0u;
+        const uint32_t ok1 = (own && kring) ? (rring & ~bad1) : 0u;
+        const uint32_t ok2 = (own && colring && kring) ? (rin & ~bad2) : 0u;
+        Mod8 S0, S1, S2;
+        {  // xy ring
+          const EW xl = sh_up(RXc), yr = sh_dn(RYc), yl = sh_up(RYc);
+          const EW t1 = shl(xl), t2 = shl(RXc), t3 = shl(yr), t4 = yr;  // + terms
+          const EW t5 = shr(RXc), t6 = shr(xl), t7 = yl, t8 = shl(yl);  // - terms
+          const uint32_t z[8] = {t1.P | t1.N, t2.P | t2.N, t3.P | t3.N, t4.P | t4.N,
+                                 t5.P | t5.N, t6.P | t6.N, t7.P | t7.N, t8.P | t8.N};
+          const uint32_t g[8] = {t1.N, t2.N, t3.N, t4.N, t5.P, t6.P, t7.P, t8.P};
+          S0 = ring_sum(z, g);
+        }
+        {  // yz ring (u = y, v = z)
+          const EW t1 = shl(RYm), t2 = RYm, t3 = shr(RZlo), t4 = shr(RZhi);  // + terms
+          const EW t5 = shl(RYn), t6 = RYn, t7 = shl(RZlo), t8 = shl(RZhi);  // - terms
+          const uint32_t z[8] = {t1.P | t1.N, t2.P | t2.N, t3.P | t3.N, t4.P | t4.N,
+                                 t5.P | t5.N, t6.P | t6.N, t7.P | t7.N, t8.P | t8.N};
+          const uint32_t g[8] = {t1.N, t2.N, t3.N, t4.N, t5.P, t6.P, t7.P, t8.P};
+          S1 = ring_sum(z, g);
+        }
+        {  // zx ring (u = z, v = x), all terms at the node's row
+          const EW t1 = sh_up(RZlo), t2 = sh_up(RZhi), t3 = sh_up(RXn), t4 = RXn;  // + terms
+          const EW t5 = sh_dn(RZlo), t6 = sh_dn(RZhi), t7 = sh_up(RXm), t8 = RXm;  // - terms
+          const uint32_t z[8] = {t1.P | t1.N, t2.P | t2.N, t3.P | t3.N, t4.P | t4.N,
+                                 t5.P | t5.N, t6.P | t6.N, t7.P | t7.N, t8.P | t8.N};
+          const uint32_t g[8] = {t1.N, t2.N, t3.N, t4.N, t5.P, t6.P, t7.P, t8.P};
+          S2 = ring_sum(z, g);
+        }
+        const uint32_t nz0 = (S0.b0 | S0.b1 | S0.b2) & ok0;
+        const uint32_t nz1 = (S1.b0 | S1.b1 | S1.b2) & ok1;
+        const uint32_t nz2 = (S2.b0 | S2.b1 | S2.b2) & ok2;
+        const uint32_t F = nz0 | nz1 | nz2;  // vortex nodes of this lane's owned rows
+        if (a.dense && own) {
+#pragma unroll 1
           for (int t = 1; t <= NB; ++t) {
-            int s0 = fld(Xc, t - 1) - fld(Xc, t + 1) + fld(Yr, t) - fld(Yl, t);
-            int s1 = fld(Ym, t) - fld(Yn, t) + fld(Zp, t + 1) - fld(Zp, t - 1);
-            int s2 = fld(Zl, t) + fld(Xn, t) - fld(Zr, t) - fld(Xm, t);
-            s0 = ((ok0 >> t) & 1u) ? s0 : 0;
-            s1 = ((ok1 >> t) & 1u) ? s1 : 0;
-            s2 = ((ok2 >> t) & 1u) ? s2 : 0;
-            if (a.dense && own && ((rin >> t) & 1u)) {
-              const long long q = ((long long)k * a.ny + (j0 - 1 + t)) * a.nx + x;
-              a.dense[q] = (int8_t)s0;
-              a.dense[nxyz + q] = (int8_t)s1;
-              a.dense[2 * nxyz + q] = (int8_t)s2;
-            }
-            // a ring of finite nodes has |S| <= 4 (eight wrapped differences
-            // of at most pi each), so S + 4 fits a 4-bit field
-            pk[t] = ((uint32_t)(s0 + 4) & 15u) | (((uint32_t)(s1 + 4) & 15u) << 4) |
-                    (((uint32_t)(s2 + 4) & 15u) << 8);
-            bal[t] = __ballot_sync(FULL, (s0 | s1 | s2) != 0);
-            const uint32_t c = (uint32_t)__popc(bal[t]);
-            cnt += c;
-            if (t <= 4) rc_lo |= c << (8 * (t - 1));
-            else rc_hi |= c << (8 * (t - 5));
-          }
-          // records of this step: contiguous in the warp's staging chunk
-          if (cnt > chunk_left) {
-            unsigned long long b = 0;
-            if (lane == 0) b = atomicAdd(a.top, (unsigned long long)kChunk);
-            chunk_at = __shfl_sync(FULL, b, 0);
-            chunk_left = kChunk;
-          }
-          const unsigned long long base = chunk_at;
-          chunk_at += cnt;
-          chunk_left -= cnt;
-          if (lane == 0) {
-            if (cnt) atomicAdd(a.segtot + (long long)k * a.nbands + band, cnt);
-            a.table[((long long)k * a.nbands + band) * a.nxseg + xs] =
-                make_uint4((uint32_t)base, cnt, rc_lo, rc_hi);
-          }
-          if (cnt) {
-            const unsigned lt = (1u << lane) - 1u;
-            unsigned long long at = base;
-#pragma unroll
-            for (int t = 1; t <= NB; ++t) {
-              if ((bal[t] >> lane) & 1u) {
-                const unsigned long long q = at + (unsigned long long)__popc(bal[t] & lt);
-                if (q < a.recs_cap) {
-                  const unsigned long long lin =
-                      ((unsigned long long)k * a.ny + (unsigned long long)(j0 - 1 + t)) * a.nx + x;
-                  a.recs[q] = (lin << 12) | pk[t];
-                }
-              }
-              at += (unsigned long long)__popc(bal[t]);
-            }
+            if (!((rin >> t) & 1u)) continue;
+            const long long q = ((long long)k * a.ny + (j0 - 1 + t)) * a.nx + x;
+            a.dense[q] = (int8_t)(((ok0 >> t) & 1u) ? mod8_at(S0, t) : 0);
+            a.dense[nxyz + q] = (int8_t)(((ok1 >> t) & 1u) ? mod8_at(S1, t) : 0);
+            a.dense[2 * nxyz + q] = (int8_t)(((ok2 >> t) & 1u) ? mod8_at(S2, t) : 0);
           }
         }
-        rzp = rzn;
+        const uint32_t cnt = __reduce_add_sync(FULL, (uint32_t)__popc(F));
+        const uint32_t rows_any = __reduce_or_sync(FULL, F);
+        // records of this step: contiguous in the warp's staging chunk, row-major
+        if (cnt > chunk_left) {
+          unsigned long long b = 0;
+          if (lane == 0) b = atomicAdd(a.top, (unsigned long long)kChunk);
+          chunk_at = __shfl_sync(FULL, b, 0);
+          chunk_left = kChunk;
+        }
+        const unsigned long long base = chunk_at;
+        chunk_at += cnt;
+        chunk_left -= cnt;
+        // uniform pass over the rows with vortex nodes: each row's lane mask
+        // and the records before it (warp-private shared memory); then every
+        // lane writes its own records
+        if (lane < NT / 4) reinterpret_cast<uint32_t*>(rcnt)[lane] = 0u;  // bytes of rows 1..NB
+        __syncwarp();
+        uint32_t run = 0;
+#pragma unroll 1
+        for (uint32_t rem = rows_any; rem; rem &= rem - 1u) {
+          const int t = __ffs(rem) - 1;
+          const unsigned bal = __ballot_sync(FULL, (F >> t) & 1u);
+          if (lane == 0) {
+            rbal[t] = bal;
+            rpre[t] = run;
+            rcnt[t - 1] = (uint8_t)__popc(bal);
+          }
+          run += (uint32_t)__popc(bal);
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (uint32_t mine = F; mine; mine &= mine - 1u) {
+          const int t = __ffs(mine) - 1;
+          const unsigned long long q =
+              base + rpre[t] + (unsigned long long)__popc(rbal[t] & lt);
+          if (q < a.recs_cap) {
+            const int v0 = ((ok0 >> t) & 1u) ? mod8_at(S0, t) : 0;
+            const int v1 = ((ok1 >> t) & 1u) ? mod8_at(S1, t) : 0;
+            const int v2 = ((ok2 >> t) & 1u) ? mod8_at(S2, t) : 0;
+            const unsigned long long lin =
+                ((unsigned long long)k * a.ny + (unsigned long long)(j0 - 1 + t)) * a.nx + x;
+            a.recs[q] = (lin << 12) | (uint32_t)(v0 + 4) | ((uint32_t)(v1 + 4) << 4) |
+                        ((uint32_t)(v2 + 4) << 8);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) {
+          if (cnt) atomicAdd(a.segtot + (long long)k * a.nbands + band, cnt);
+          const uint32_t* rc = reinterpret_cast<const uint32_t*>(rcnt);
+          uint32_t wv[4 * kTabVec] = {};
+          wv[0] = (uint32_t)base;
+          wv[1] = cnt;
+#pragma unroll
+          for (int q = 0; q < NT / 4; ++q) wv[2 + q] = rc[q];
+          uint4* te = a.table + (((long long)k * a.nbands + band) * a.nxseg + xs) * kTabVec;
+#pragma unroll
+          for (int q = 0; q < kTabVec; ++q)
+            te[q] = make_uint4(wv[4 * q], wv[4 * q + 1], wv[4 * q + 2], wv[4 * q + 3]);
+        }
       }
-      Xm = Xc;
-      Xc = Xn;
-      Ym = Yc;
-      Yc = Yn;
+      RXm = RXc;
+      RXc = RXn;
+      RYm = RYc;
+      RYc = RYn;
+      RZlo = RZhi;
+      Sprev = Sp;
+      ZBc = ZBp;
       Bm = Bc;
-      Bc = bn;
-      sp = sp + 1 == kSlots ? 0 : sp + 1;
+      Bc = Bn;
+      sp = s1;
     }
   }
 }
@@ -377,16 +510,30 @@ __global__ void node_scatter_kernel(const uint4* __restrict__ table,
   for (long long s = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < nseg;
        s += warps) {
     unsigned long long off = seg_off[s];
-    const uint4* te = table + s * nxseg;
+    const uint4* te = table + s * nxseg * kTabVec;
     for (int t = 1; t <= NB; ++t) {
       for (int xb = 0; xb < nxseg; xb += 32) {
         const int xsi = xb + lane;
-        uint4 e = make_uint4(0u, 0u, 0u, 0u);
-        if (xsi < nxseg) e = te[xsi];
-        const uint64_t rows = (uint64_t)e.z | ((uint64_t)e.w << 32);  // byte r-1: row r
-        const uint32_t c = (uint32_t)(rows >> (8 * (t - 1))) & 0xFFu;
-        uint32_t pre = 0;
-        for (int r = 1; r < t; ++r) pre += (uint32_t)(rows >> (8 * (r - 1))) & 0xFFu;
+        uint32_t wv[4 * kTabVec] = {};
+        if (xsi < nxseg) {
+#pragma unroll
+          for (int q = 0; q < kTabVec; ++q) {
+            const uint4 e = te[xsi * kTabVec + q];
+            wv[4 * q] = e.x;
+            wv[4 * q + 1] = e.y;
+            wv[4 * q + 2] = e.z;
+            wv[4 * q + 3] = e.w;
+          }
+        }
+        const uint32_t base = wv[0];
+        const uint32_t* rcw = wv + 2;
+        uint32_t c = 0, pre = 0;
+#pragma unroll
+        for (int r = 1; r <= NB; ++r) {
+          const uint32_t cr = (rcw[(r - 1) >> 2] >> (8 * ((r - 1) & 3))) & 0xFFu;
+          if (r < t) pre += cr;
+          if (r == t) c = cr;
+        }
         // exclusive scan of c over the lanes
         uint32_t incl = c;
 #pragma unroll
@@ -396,7 +543,7 @@ __global__ void node_scatter_kernel(const uint4* __restrict__ table,
         }
         const uint32_t tot = __shfl_sync(FULL, incl, 31);
         const unsigned long long dst0 = off + (incl - c);
-        const unsigned long long src0 = (unsigned long long)e.x + pre;
+        const unsigned long long src0 = (unsigned long long)base + pre;
         for (uint32_t q = 0; q < c; ++q) {
           const unsigned long long src = src0 + q, dst = dst0 + q;
           if (src >= recs_cap || dst >= capacity) continue;
@@ -622,13 +769,13 @@ int node_circulation_launch(qtv_handle h, const qtv_grid& g, const float2* psi,
   const int nzchunks = (nz + kchunk - 1) / kchunk;
   const long long nitems = (long long)nzchunks * per_chunk;
   const long long nseg = (long long)nz * nbands;
-  const uint64_t ntab = (uint64_t)nseg * nxseg;
+  const uint64_t ntab = (uint64_t)nseg * nxseg * kTabVec;
   // staging: the records, plus what chunk switches leave unused (under one
-  // step of at most NB * NCOL records per chunk of kChunk) and the open chunk
-  // of every warp
+  // step of at most NB * NCOL <= kChunk / 8 records per chunk, i.e. at most
+  // 1/7 of the records) and the open chunk of every warp
   const long long launch_warps = (long long)launch_blocks(w, nitems) * NODE_WARPS;
-  const uint64_t recs_need = capacity + capacity / 15 + (uint64_t)launch_warps * kChunk;
-  static_assert(NB * NCOL * 16 <= (int)kChunk, "chunk slack bound");
+  const uint64_t recs_need = capacity + capacity / 7 + 1 + (uint64_t)launch_warps * kChunk;
+  static_assert(NB * NCOL * 8 <= (int)kChunk, "chunk slack bound");
   rc = grow(w->recs, w->recs_cap, recs_need, st, "cudaMalloc(node records)");
   if (!rc) rc = grow(w->table, w->table_cap, ntab, st, "cudaMalloc(node table)");
   if (!rc) rc = grow(w->segtot, w->segtot_cap, (uint64_t)nseg, st, "cudaMalloc(node totals)");
