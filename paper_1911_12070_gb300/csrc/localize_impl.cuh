@@ -1,6 +1,10 @@
 // localize_impl.cuh -- device code of plaquette localization (Sec. 3.3.3,
 // Eq. 6): the zero of the bilinear interpolant of a pierced face, shared by
-// the stand-alone localization kernel and the fused expansion pass.
+// the stand-alone localization kernel, the batch localization kernel and the
+// learned locator's plain fallback.  Products that feed an addition are
+// rounded explicitly (__fmul_rn / __fadd_rn or fmaf), so the compiler cannot
+// contract them differently in different kernels: every entry point gives
+// the same samples bit for bit.
 //
 // Eq. 6 asks for x* = argmin rho(x), rho = |Phi|^2 (Eq. 3), with Phi linearly
 // interpolated between nodes (Sec. 5).  Restricted to a pierced plaquette with
@@ -26,9 +30,9 @@ struct C2 {
 __device__ __forceinline__ C2 mk(float x, float y) { return C2{x, y}; }
 __device__ __forceinline__ C2 sub(C2 p, C2 q) { return mk(p.x - q.x, p.y - q.y); }
 // Im(p conj q)
-__device__ __forceinline__ float crs(C2 p, C2 q) { return fmaf(p.y, q.x, -p.x * q.y); }
+__device__ __forceinline__ float crs(C2 p, C2 q) { return fmaf(p.y, q.x, __fmul_rn(-p.x, q.y)); }
 // Re(p conj q)
-__device__ __forceinline__ float dtr(C2 p, C2 q) { return fmaf(p.x, q.x, p.y * q.y); }
+__device__ __forceinline__ float dtr(C2 p, C2 q) { return fmaf(p.x, q.x, __fmul_rn(p.y, q.y)); }
 
 // real roots of q2 t^2 + q1 t + q0 (0, 1 or 2 of them)
 __device__ __forceinline__ int roots2(float q2, float q1, float q0, float& t0, float& t1) {
@@ -39,7 +43,7 @@ __device__ __forceinline__ int roots2(float q2, float q1, float q0, float& t0, f
     t0 = -q0 / q1;
     return 1;
   }
-  float disc = fmaf(q1, q1, -4.f * q2 * q0);
+  float disc = fmaf(q1, q1, __fmul_rn(__fmul_rn(-4.f, q2), q0));
   if (disc < 0.f) {
     if (disc > -1e-5f * q1 * q1) disc = 0.f;
     else return 0;
@@ -71,13 +75,15 @@ __device__ __forceinline__ void newton(const Bil& F, float& u, float& v) {
     const C2 f = eval(F, u, v);
     const C2 fu = mk(fmaf(v, F.d.x, F.b.x), fmaf(v, F.d.y, F.b.y));
     const C2 fv = mk(fmaf(u, F.d.x, F.c.x), fmaf(u, F.d.y, F.c.y));
-    const float det = fmaf(fu.x, fv.y, -fv.x * fu.y);
+    const float det = fmaf(fu.x, fv.y, __fmul_rn(-fv.x, fu.y));
     if (det == 0.f) return;
     const float inv = 1.f / det;
-    const float du = -fmaf(fv.y, f.x, -fv.x * f.y) * inv;
-    const float dv = -fmaf(fu.x, f.y, -fu.y * f.x) * inv;
-    u += du;
-    v += dv;
+    // explicit roundings: the same result in every kernel this is inlined
+    // into (no context-dependent multiply-add contraction)
+    const float du = __fmul_rn(-fmaf(fv.y, f.x, __fmul_rn(-fv.x, f.y)), inv);
+    const float dv = __fmul_rn(-fmaf(fu.x, f.y, __fmul_rn(-fu.y, f.x)), inv);
+    u = __fadd_rn(u, du);
+    v = __fadd_rn(v, dv);
   }
 }
 
@@ -95,7 +101,7 @@ __device__ __forceinline__ bool solve_face(const C2 P[4], float& uo, float& vo, 
     newton(F, u, v);
     if (!(u >= -1e-4f && u <= 1.f + 1e-4f && v >= -1e-4f && v <= 1.f + 1e-4f)) return;
     const C2 f = eval(F, u, v);
-    const float f2 = fmaf(f.x, f.x, f.y * f.y);
+    const float f2 = fmaf(f.x, f.x, __fmul_rn(f.y, f.y));
     if (f2 < best) {
       best = f2;
       bu = u;
@@ -105,7 +111,7 @@ __device__ __forceinline__ bool solve_face(const C2 P[4], float& uo, float& vo, 
   };
   float t0 = 0.f, t1 = 0.f;
   // eliminate u: (a + c v) + u (b + d v) = 0, u real <=> Im(p conj q) = 0
-  int nr = roots2(crs(F.c, F.d), crs(F.a, F.d) + crs(F.c, F.b), crs(F.a, F.b), t0, t1);
+  int nr = roots2(crs(F.c, F.d), __fadd_rn(crs(F.a, F.d), crs(F.c, F.b)), crs(F.a, F.b), t0, t1);
   for (int r = 0; r < nr; ++r) {
     const float v = r ? t1 : t0;
     const C2 p = mk(fmaf(v, F.c.x, F.a.x), fmaf(v, F.c.y, F.a.y));
@@ -115,7 +121,7 @@ __device__ __forceinline__ bool solve_face(const C2 P[4], float& uo, float& vo, 
   }
   if (!found) {
     // eliminate v: (a + b u) + v (c + d u) = 0
-    nr = roots2(crs(F.b, F.d), crs(F.a, F.d) + crs(F.b, F.c), crs(F.a, F.c), t0, t1);
+    nr = roots2(crs(F.b, F.d), __fadd_rn(crs(F.a, F.d), crs(F.b, F.c)), crs(F.a, F.c), t0, t1);
     for (int r = 0; r < nr; ++r) {
       const float u = r ? t1 : t0;
       const C2 p = mk(fmaf(u, F.b.x, F.a.x), fmaf(u, F.b.y, F.a.y));
@@ -126,7 +132,7 @@ __device__ __forceinline__ bool solve_face(const C2 P[4], float& uo, float& vo, 
   }
   if (!found) {
     const C2 f = eval(F, 0.5f, 0.5f);
-    best = fmaf(f.x, f.x, f.y * f.y);
+    best = fmaf(f.x, f.x, __fmul_rn(f.y, f.y));
   }
   uo = bu;
   vo = bv;
@@ -172,9 +178,9 @@ __device__ __forceinline__ void localize_face(const float2* __restrict__ psi, in
   uint8_t fl = 0;
   if (!ok || (wv != 1 && wv != -1)) fl |= QTV_FLAG_ANOMALOUS;
   float gx = (float)i, gy = (float)j, gz = (float)k;
-  if (o == 0) { gx += u; gy += v; }
-  else if (o == 1) { gy += u; gz += v; }
-  else { gz += u; gx += v; }
+  if (o == 0) { gx = __fadd_rn(gx, u); gy = __fadd_rn(gy, v); }
+  else if (o == 1) { gy = __fadd_rn(gy, u); gz = __fadd_rn(gz, v); }
+  else { gz = __fadd_rn(gz, u); gx = __fadd_rn(gx, v); }
   xyz[0] = fmaf(h, gx, ox);
   xyz[1] = fmaf(h, gy, oy);
   xyz[2] = fmaf(h, gz, oz);
