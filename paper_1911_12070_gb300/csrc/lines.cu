@@ -24,7 +24,8 @@
 //
 // Ordering without walking.  "Special" samples end the chains: samples of
 // degree other than 2, and the lowest sample of each Type II component.  On
-// the directed edges (u -> w) of the graph, the successor of (u -> w) is
+// the directed edges (u -> w) of the graph (numbered compactly: sample u owns
+// the edges from the exclusive scan of the degrees), the successor of (u -> w) is
 // (w -> x), x the neighbour of w other than u, unless w is special.  Pointer
 // jumping over this successor (double-buffered rounds, log2 of the sample
 // count of them) gives every directed edge its distance to the end of its
@@ -87,7 +88,12 @@ struct LineArgs {
   uint32_t* cmin;    // min degree
   uint32_t* csize;   // samples
   uint8_t* special;  // per sample
-  uint32_t* nxt[2];  // per directed-edge slot (u * 10 + s): successor edge
+  uint32_t* deg32;   // degrees as 32-bit values (scan input)
+  unsigned long long* aoff;   // per sample: first directed edge (exclusive scan of degrees)
+  const unsigned long long* narcs;  // device: number of directed edges
+  uint32_t* atail;   // per directed edge: tail sample
+  uint32_t* ahead;   // per directed edge: head sample
+  uint32_t* nxt[2];  // per directed edge: successor edge
   uint32_t* dst[2];  // distance (edges) to the end of the chain
   uint32_t* lst[2];  // last edge of the chain
   uint32_t* pcount;  // per sample: pieces started there
@@ -125,6 +131,7 @@ __global__ void stats_kernel(LineArgs a) {
   for (unsigned long long u = (unsigned long long)blockIdx.x * LT + threadIdx.x; u < nn;
        u += (unsigned long long)gridDim.x * LT) {
     const uint32_t L = a.comp[u], d = a.deg[u];
+    a.deg32[u] = d;
     atomicMax(a.cmax + L, d);
     atomicMin(a.cmin + L, d);
     atomicAdd(a.csize + L, 1u);
@@ -150,23 +157,32 @@ __device__ __forceinline__ int slot_of(const LineArgs& a, uint32_t w, uint32_t x
   return -1;
 }
 
-__global__ void edges_init_kernel(LineArgs a) {
+// directed edges in compact order: sample u owns edges aoff[u] .. + deg[u] - 1
+__global__ void arcs_kernel(LineArgs a) {
   const unsigned long long nn = limit_n(a.n, a.n_dev);
-  const unsigned long long ne = nn * kSlots;
+  for (unsigned long long u = (unsigned long long)blockIdx.x * LT + threadIdx.x; u < nn;
+       u += (unsigned long long)gridDim.x * LT) {
+    const int d = a.deg[u];
+    const unsigned long long e0 = a.aoff[u];
+    for (int s = 0; s < d; ++s) {
+      a.atail[e0 + s] = (uint32_t)u;
+      a.ahead[e0 + s] = a.nbr[u * kSlots + s];
+    }
+  }
+}
+
+__global__ void edges_init_kernel(LineArgs a) {
+  const unsigned long long ne = *a.narcs;
   for (unsigned long long e = (unsigned long long)blockIdx.x * LT + threadIdx.x; e < ne;
        e += (unsigned long long)gridDim.x * LT) {
-    const uint32_t u = (uint32_t)(e / kSlots);
-    const int s = (int)(e % kSlots);
-    if (s >= a.deg[u]) continue;
-    const uint32_t w = a.nbr[e];
+    const uint32_t u = a.atail[e], w = a.ahead[e];
     if (a.special[w]) {
       a.nxt[0][e] = kNone;
       a.lst[0][e] = (uint32_t)e;
     } else {
       // w has degree 2: continue to its other neighbour
-      const uint32_t* r = a.nbr + (unsigned long long)w * kSlots;
-      const int sx = (r[0] == u) ? 1 : 0;
-      a.nxt[0][e] = w * kSlots + sx;
+      const int sx = (a.nbr[(unsigned long long)w * kSlots] == u) ? 1 : 0;
+      a.nxt[0][e] = (uint32_t)(a.aoff[w] + sx);
       a.lst[0][e] = kNone;
     }
     a.dst[0][e] = 1;
@@ -174,13 +190,10 @@ __global__ void edges_init_kernel(LineArgs a) {
 }
 
 __global__ void jump_kernel(LineArgs a, int src) {
-  const unsigned long long nn = limit_n(a.n, a.n_dev);
-  const unsigned long long ne = nn * kSlots;
+  const unsigned long long ne = *a.narcs;
   const int d = src ^ 1;
   for (unsigned long long e = (unsigned long long)blockIdx.x * LT + threadIdx.x; e < ne;
        e += (unsigned long long)gridDim.x * LT) {
-    const uint32_t u = (uint32_t)(e / kSlots);
-    if ((int)(e % kSlots) >= a.deg[u]) continue;
     const uint32_t nx = a.nxt[src][e];
     if (nx == kNone) {
       a.nxt[d][e] = kNone;
@@ -198,8 +211,8 @@ __global__ void jump_kernel(LineArgs a, int src) {
 __device__ __forceinline__ void chain_end(const LineArgs& a, int buf, uint32_t e, uint32_t& end,
                                           uint32_t& before) {
   const uint32_t l = a.lst[buf][e];
-  before = l / kSlots;
-  end = a.nbr[l];
+  before = a.atail[l];
+  end = a.ahead[l];
 }
 
 // is the chain that starts at special sample s through neighbour y (edge e) a
@@ -228,8 +241,8 @@ __global__ void count_kernel(LineArgs a, int buf) {
       nl = 1;
     } else if (a.special[u]) {
       for (int s = 0; s < d; ++s) {
-        const unsigned long long e = (unsigned long long)u * kSlots + s;
-        const uint32_t y = a.nbr[e];
+        const unsigned long long e = a.aoff[u] + s;
+        const uint32_t y = a.nbr[u * kSlots + s];
         if (!discovering(a, buf, (uint32_t)u, y, (uint32_t)e)) continue;
         uint32_t end, before;
         chain_end(a, buf, (uint32_t)e, end, before);
@@ -265,8 +278,8 @@ __global__ void pieces_kernel(LineArgs a, int buf) {
       continue;
     }
     for (int s = 0; s < d; ++s) {
-      const unsigned long long e = (unsigned long long)u * kSlots + s;
-      const uint32_t y = a.nbr[e];
+      const unsigned long long e = a.aoff[u] + s;
+      const uint32_t y = a.nbr[u * kSlots + s];
       if (!discovering(a, buf, (uint32_t)u, y, (uint32_t)e)) continue;
       uint32_t end, before;
       chain_end(a, buf, (uint32_t)e, end, before);
@@ -296,15 +309,15 @@ __global__ void interior_kernel(LineArgs a, int buf) {
   for (unsigned long long u = (unsigned long long)blockIdx.x * LT + threadIdx.x; u < nn;
        u += (unsigned long long)gridDim.x * LT) {
     if (a.special[u] || a.deg[u] != 2) continue;
-    const unsigned long long e0 = (unsigned long long)u * kSlots, e1 = e0 + 1;
+    const unsigned long long e0 = a.aoff[u], e1 = e0 + 1;
     uint32_t end0, bef0, end1, bef1;
     chain_end(a, buf, (uint32_t)e0, end0, bef0);
     chain_end(a, buf, (uint32_t)e1, end1, bef1);
     // the chain's end edges, seen from the ends: (end0 -> bef0), (end1 -> bef1)
     const int s0 = slot_of(a, end0, bef0), s1 = slot_of(a, end1, bef1);
     if (s0 < 0 || s1 < 0) continue;
-    const unsigned long long f0 = (unsigned long long)end0 * kSlots + s0;
-    const unsigned long long f1 = (unsigned long long)end1 * kSlots + s1;
+    const unsigned long long f0 = a.aoff[end0] + s0;
+    const unsigned long long f1 = a.aoff[end1] + s1;
     unsigned long long off;
     uint32_t pos;
     if (discovering(a, buf, end0, bef0, (uint32_t)f0)) {
@@ -625,7 +638,8 @@ int line_pieces_launch(qtv_handle h, uint64_t n, const uint64_t* n_dev, const ui
     // sizes must match the carve sequence below
     const unsigned long long sz[] = {n * 4, n * 4, n * 4, n, ne * 4, ne * 4, ne * 4, ne * 4,
                                      ne * 4, ne * 4, n * 4, n * 4, n * 8, n * 8, ne * 8,
-                                     nodes_max * 4, n * 8, nb * 8, nb * 8, 16};
+                                     nodes_max * 4, n * 8, nb * 8, nb * 8, 16,
+                                     n * 4, n * 8, ne * 4, ne * 4, nb * 8, 8};
     for (unsigned long long s : sz) bytes += ((s + 255) / 256) * 256;
   }
   void* buf = nullptr;
@@ -661,6 +675,13 @@ int line_pieces_launch(qtv_handle h, uint64_t n, const uint64_t* n_dev, const ui
   unsigned long long* bs1 = carve<unsigned long long>(p, nb);
   unsigned long long* bs2 = carve<unsigned long long>(p, nb);
   unsigned long long* tot = carve<unsigned long long>(p, 2);
+  a.deg32 = carve<uint32_t>(p, n);
+  a.aoff = carve<unsigned long long>(p, n);
+  a.atail = carve<uint32_t>(p, ne);
+  a.ahead = carve<uint32_t>(p, ne);
+  unsigned long long* bs3 = carve<unsigned long long>(p, nb);
+  unsigned long long* narcs = carve<unsigned long long>(p, 1);
+  a.narcs = narcs;
   a.pieces = pieces;
   a.piece_cap = piece_cap;
   a.nodes = nodes;
@@ -676,6 +697,9 @@ int line_pieces_launch(qtv_handle h, uint64_t n, const uint64_t* n_dev, const ui
   stats_init_kernel<<<(int)g, LT, 0, st>>>(a);
   stats_kernel<<<(int)g, LT, 0, st>>>(a);
   special_kernel<<<(int)g, LT, 0, st>>>(a);
+  // compact directed edges: offsets by an exclusive scan of the degrees
+  scan_u32(a.deg32, n_dev, n, a.aoff, bs3, narcs, h->num_sms, st);
+  arcs_kernel<<<(int)g, LT, 0, st>>>(a);
   edges_init_kernel<<<(int)ge, LT, 0, st>>>(a);
   int rounds = 1;
   while ((1ull << rounds) < (unsigned long long)n + 1) ++rounds;
