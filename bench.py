@@ -663,40 +663,40 @@ def run_qtv(args):
     F = int(count.item())
     clocks = clk.summary(t0 - 2.0, t1)
 
-    # ---- end to end through the public API: pinned host field in, samples out
+    # ---- end to end through the public API: every step copies the pinned host
+    # field in and the packed samples and their count out
+    # (qtv_identify_localize_host: two device copies of the field, so one
+    # step's copy overlaps the previous step's identification)
     host_psi = torch.empty(psi.shape, dtype=torch.complex64, pin_memory=True)
     host_psi.copy_(psi)
-    host_out = torch.empty(cap * 32, dtype=torch.uint8, pin_memory=True)
-    psi_e2e = torch.empty_like(psi)
+    host_outs = [torch.empty(cap * 32, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+    host_cnts = [torch.zeros(1, dtype=torch.int64, pin_memory=True) for _ in range(2)]
     lib = qtv.lib()
     import ctypes
 
-    def e2e_step():
-        psi_e2e.copy_(host_psi, non_blocking=True)
-        q.identify_localize_into(psi_e2e, ids, wnd, count, xyz, resid, flags)
-        # emission needs the sample count on the host
-        nf = int(count.item())
-        rc = lib.qtv_emit_samples(q.h, nf, ctypes.c_void_p(ids.data_ptr()),
-                                  ctypes.c_void_p(wnd.data_ptr()), ctypes.c_void_p(xyz.data_ptr()),
-                                  ctypes.c_void_p(resid.data_ptr()),
-                                  ctypes.c_void_p(flags.data_ptr()),
-                                  ctypes.c_void_p(host_out.data_ptr()),
-                                  ctypes.c_void_p(stream.cuda_stream))
-        assert rc == 0, lib.qtv_last_error_string()
-        return nf
+    grid = qtv.Grid.of(tuple(psi.shape))
 
-    for _ in range(2):
-        e2e_step()
+    def e2e_step(i):
+        rc = lib.qtv_identify_localize_host(q.h, ctypes.byref(grid),
+                                            ctypes.c_void_p(host_psi.data_ptr()), cap,
+                                            ctypes.c_void_p(host_outs[i % 2].data_ptr()),
+                                            ctypes.c_void_p(host_cnts[i % 2].data_ptr()),
+                                            ctypes.c_void_p(stream.cuda_stream))
+        assert rc == 0, lib.qtv_last_error_string()
+
+    for i in range(2):
+        e2e_step(i)
     torch.cuda.synchronize()
     ke = max(1, args.e2e_steps)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    d2h = 0
     e0.record(stream)
-    for _ in range(ke):
-        d2h += e2e_step() * 32
+    for i in range(ke):
+        e2e_step(i)
     e1.record(stream)
     torch.cuda.synchronize()
+    assert all(int(c[0]) == F for c in host_cnts), "end-to-end sample count differs"
+    d2h = ke * (cap * 32 + 8)
     ms_e2e = e0.elapsed_time(e1)
     if ws > 1:
         ms_e2e = slowest_ms(ms_e2e, dev)

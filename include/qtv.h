@@ -204,6 +204,32 @@ QTV_API int qtv_emit_samples(qtv_handle h, uint64_t n, const uint64_t* face_ids,
                      qtv_sample* host_out, void* stream);
 
 /*
+ * Identification and plain localization from host memory, end to end: the
+ * field is copied from the caller's host buffer into one of two device copies
+ * the handle keeps, identified and localized as by qtv_identify_localize, and
+ * the samples (qtv_sample records, ascending face id) and their count are
+ * copied back to the caller's host buffers.
+ *
+ *   psi_host    host complex64 field (conventions above); page-locked memory
+ *               (cudaHostAlloc / cudaHostRegister) makes the copy asynchronous.
+ *   capacity    samples kept per call; host_out receives `capacity` records, of
+ *               which the first *host_count are the samples (if *host_count
+ *               exceeds capacity the list is incomplete: call again with a
+ *               larger capacity).
+ *   host_out    host qtv_sample[capacity]; host_count: host uint64.
+ * Asynchronous on `stream`: results are complete when the stream reaches the
+ * end of the call.  Consecutive calls alternate between the two device copies
+ * and copy the field on a stream of the handle, so the copy of one call
+ * overlaps the identification of the previous one; the caller gives
+ * consecutive calls different host_out / host_count buffers (or synchronises
+ * in between).  The device copies (2 x the field) and output buffers are
+ * handle workspace, allocated on first use (a synchronising step).
+ */
+QTV_API int qtv_identify_localize_host(qtv_handle h, const qtv_grid* grid, const void* psi_host,
+                                       uint64_t capacity, qtv_sample* host_out,
+                                       uint64_t* host_count, void* stream);
+
+/*
  * Identification without any allocation (the paper has no counterpart; this
  * is a deployment variant of qtv_identify).
  *

@@ -159,8 +159,10 @@ def lib() -> ctypes.CDLL:
         L.qtv_face_graph.argtypes = [P, ctypes.POINTER(Grid), P, u64, P, P, P, P, P, P]
         L.qtv_line_pieces.argtypes = [P, u64, P, P, P, P, P, P, P, P, u64, P, u64, P, P]
         L.qtv_piece_curves.argtypes = [P, P, P, P, u64, P, i32, P, u64, P, P, P, P]
+        L.qtv_identify_localize_host.argtypes = [P, ctypes.POINTER(Grid), P, u64, P, P, P]
         for name in ("qtv_node_circulation", "qtv_density_error", "qtv_refine_samples",
-                     "qtv_face_graph", "qtv_line_pieces", "qtv_piece_curves"):
+                     "qtv_face_graph", "qtv_line_pieces", "qtv_piece_curves",
+                     "qtv_identify_localize_host"):
             getattr(L, name).restype = i32
         L.qtv_trace_enable.argtypes = [P, i32]
         L.qtv_trace_read.argtypes = [P, ctypes.POINTER(TraceEntry), i32, ctypes.POINTER(i32), i32]
@@ -300,6 +302,35 @@ class Qtv:
                 break
             capacity = n
         return ids[:n], w[:n], xyz[:n], resid[:n], flags[:n]
+
+    def identify_localize_host_into(self, psi_host, capacity, out, count, grid=None,
+                                    stream=None):
+        """End-to-end call from host memory (qtv_identify_localize_host): psi_host a
+        pinned complex64 [nz, ny, nx] host tensor, out a pinned uint8 host tensor of
+        at least capacity * 32 bytes, count a pinned int64 host tensor of one element.
+        Asynchronous: synchronise the stream before reading out and count."""
+        g = grid or Grid.of(tuple(psi_host.shape))
+        _check(lib().qtv_identify_localize_host(self.h, ctypes.byref(g), _ptr(psi_host),
+                                                int(capacity), _ptr(out), _ptr(count),
+                                                _stream_ptr(stream)))
+
+    def identify_localize_host(self, psi_host, capacity: int | None = None, stream=None):
+        """Samples (numpy SAMPLE_DTYPE records) of a pinned host field, end to end."""
+        import torch
+
+        nz, ny, nx = psi_host.shape
+        if capacity is None:
+            capacity = max(1024, int(0.02 * nx * ny * nz))
+        count = torch.zeros(1, dtype=torch.int64, pin_memory=True)
+        for _ in range(2):
+            out = torch.empty(capacity * 32, dtype=torch.uint8, pin_memory=True)
+            self.identify_localize_host_into(psi_host, capacity, out, count, stream=stream)
+            (torch.cuda.current_stream() if stream is None else stream).synchronize()
+            n = int(count[0])
+            if n <= capacity:
+                break
+            capacity = n
+        return out.numpy()[: n * 32].view(SAMPLE_DTYPE)
 
     # -- localization ---------------------------------------------------------------
     def localize_into(self, psi, face_ids, winding, xyz, resid, flags, n=None, n_dev=None,

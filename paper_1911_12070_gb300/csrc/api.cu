@@ -141,6 +141,66 @@ TraceScope::~TraceScope() {
   h->trace.push_back(TraceRec{kernel, a, b});
 }
 
+// Double-buffered device state of qtv_identify_localize_host: call i uses
+// buffer i % 2; its copy from the host runs on the pipe's own stream and waits
+// only for the call that used the same buffer two calls earlier.
+struct HostPipe {
+  cudaStream_t copy = nullptr;
+  cudaEvent_t ready[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr};
+  bool used[2] = {false, false};
+  float2* psi[2] = {nullptr, nullptr};
+  size_t psi_bytes = 0;
+  uint64_t* ids[2] = {nullptr, nullptr};
+  int8_t* w[2] = {nullptr, nullptr};
+  float* xyz[2] = {nullptr, nullptr};
+  float* resid[2] = {nullptr, nullptr};
+  uint8_t* flags[2] = {nullptr, nullptr};
+  uint64_t* count[2] = {nullptr, nullptr};
+  qtv_sample* pack[2] = {nullptr, nullptr};
+  uint64_t cap = 0;
+  int next = 0;
+};
+
+namespace {
+void pipe_free_buffers(HostPipe* p, bool field, bool outputs) {
+  for (int b = 0; b < 2; ++b) {
+    if (field) {
+      cudaFree(p->psi[b]);
+      p->psi[b] = nullptr;
+    }
+    if (outputs) {
+      cudaFree(p->ids[b]);
+      cudaFree(p->w[b]);
+      cudaFree(p->xyz[b]);
+      cudaFree(p->resid[b]);
+      cudaFree(p->flags[b]);
+      cudaFree(p->count[b]);
+      cudaFree(p->pack[b]);
+      p->ids[b] = nullptr;
+      p->w[b] = nullptr;
+      p->xyz[b] = nullptr;
+      p->resid[b] = nullptr;
+      p->flags[b] = nullptr;
+      p->count[b] = nullptr;
+      p->pack[b] = nullptr;
+    }
+  }
+  if (field) p->psi_bytes = 0;
+  if (outputs) p->cap = 0;
+}
+}  // namespace
+
+void host_pipe_free(HostPipe* p) {
+  if (!p) return;
+  pipe_free_buffers(p, true, true);
+  for (int b = 0; b < 2; ++b) {
+    if (p->ready[b]) cudaEventDestroy(p->ready[b]);
+    if (p->done[b]) cudaEventDestroy(p->done[b]);
+  }
+  if (p->copy) cudaStreamDestroy(p->copy);
+  delete p;
+}
+
 }  // namespace qtv
 
 using namespace qtv;
@@ -194,6 +254,7 @@ int qtv_destroy(qtv_handle h) {
   node_work_free(h->node);
   graph_work_free(h->graph);
   line_work_free(h->lines);
+  host_pipe_free(h->pipe);
   for (auto& r : h->trace) {
     cudaEventDestroy(r.start);
     cudaEventDestroy(r.stop);
@@ -481,6 +542,104 @@ int qtv_piece_curves(qtv_handle h, const float* xyz, const uint32_t* nodes,
   }
   return piece_curves_launch(h, xyz, nodes, pieces, npieces, npieces_dev, per_segment, curve,
                              curve_cap, curve_first, length, total, st);
+}
+
+int qtv_identify_localize_host(qtv_handle h, const qtv_grid* grid, const void* psi_host,
+                               uint64_t capacity, qtv_sample* host_out, uint64_t* host_count,
+                               void* stream) {
+  if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
+  int rc = validate_grid(grid);
+  if (rc) return rc;
+  if (!host_count) return set_error(QTV_ERR_ARG, "host_count is NULL");
+  if (capacity > 0 && !host_out) return set_error(QTV_ERR_ARG, "host_out is NULL");
+  if (capacity > 0xFFFFFFFFull)
+    return set_error(QTV_ERR_ARG, "capacity above 2^32-1 is not supported");
+  const qtv_grid& g = *grid;
+  const unsigned long long nn = (unsigned long long)g.nx * g.ny * g.nz;
+  if (nn > 0 && !psi_host) return set_error(QTV_ERR_ARG, "psi_host is NULL");
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return set_error(QTV_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (capturing(st)) return set_error(QTV_ERR_STATE, "not available during stream capture");
+  if (!h->pipe) {
+    HostPipe* p = new (std::nothrow) HostPipe();
+    if (!p) return set_error(QTV_ERR_ARG, "out of host memory");
+    cudaError_t e = cudaStreamCreateWithFlags(&p->copy, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      e = cudaEventCreateWithFlags(&p->ready[b], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done[b], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+      host_pipe_free(p);
+      return check_cuda(e, "host pipe streams and events");
+    }
+    h->pipe = p;
+  }
+  HostPipe* p = h->pipe;
+  const size_t bytes = (size_t)nn * sizeof(float2);
+  // (re)allocation synchronises the device, so no call in flight uses the old buffers
+  cudaError_t e = cudaSuccess;
+  if (bytes > p->psi_bytes) {
+    pipe_free_buffers(p, true, false);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+      e = cudaMalloc(reinterpret_cast<void**>(&p->psi[b]), bytes > 0 ? bytes : 16);
+    if (e != cudaSuccess) {
+      pipe_free_buffers(p, true, false);
+      return check_cuda(e, "cudaMalloc(host pipe field)");
+    }
+    p->psi_bytes = bytes;
+  }
+  const uint64_t cap = capacity > 0 ? capacity : 1;
+  if (cap > p->cap) {
+    pipe_free_buffers(p, false, true);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      e = cudaMalloc(reinterpret_cast<void**>(&p->ids[b]), cap * sizeof(uint64_t));
+      if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->w[b]), cap);
+      if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->xyz[b]), cap * 12);
+      if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->resid[b]), cap * 4);
+      if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->flags[b]), cap);
+      if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->count[b]), 8);
+      if (e == cudaSuccess)
+        e = cudaMalloc(reinterpret_cast<void**>(&p->pack[b]), cap * sizeof(qtv_sample));
+    }
+    if (e != cudaSuccess) {
+      pipe_free_buffers(p, false, true);
+      return check_cuda(e, "cudaMalloc(host pipe outputs)");
+    }
+    p->cap = cap;
+  }
+  const int b = p->next;
+  p->next ^= 1;
+  rc = grow_identify(h, g, capacity, p->psi[b], st);
+  if (rc) return rc;
+  // copy of the field: waits only for the call that used this buffer before
+  if (p->used[b]) e = cudaStreamWaitEvent(p->copy, p->done[b], 0);
+  if (e == cudaSuccess && bytes > 0)
+    e = cudaMemcpyAsync(p->psi[b], psi_host, bytes, cudaMemcpyHostToDevice, p->copy);
+  if (e == cudaSuccess) e = cudaEventRecord(p->ready[b], p->copy);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->ready[b], 0);
+  if (e != cudaSuccess) return check_cuda(e, "host pipe copy");
+  if (nn == 0 || g.nx < 1 || g.ny < 1 || g.nz < 1) {
+    e = cudaMemsetAsync(p->count[b], 0, sizeof(uint64_t), st);
+  } else {
+    rc = identify_launch(h, g, p->psi[b], p->ids[b], p->w[b], capacity, p->count[b], nullptr, st,
+                         scratch_of(h), 0, capacity > 0 ? p->xyz[b] : nullptr, p->resid[b],
+                         p->flags[b]);
+    if (rc) return rc;
+    if (capacity > 0) {
+      rc = emit_pack_launch(h, capacity, p->ids[b], p->w[b], p->xyz[b], p->resid[b], p->flags[b],
+                            p->pack[b], st);
+      if (rc) return rc;
+      e = cudaMemcpyAsync(host_out, p->pack[b], capacity * sizeof(qtv_sample),
+                          cudaMemcpyDeviceToHost, st);
+    }
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(host_count, p->count[b], sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaEventRecord(p->done[b], st);
+  if (e != cudaSuccess) return check_cuda(e, "host pipe results");
+  p->used[b] = true;
+  return QTV_OK;
 }
 
 int qtv_localize(qtv_handle h, const qtv_grid* grid, const void* psi, const uint64_t* face_ids,

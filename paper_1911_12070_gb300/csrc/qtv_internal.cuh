@@ -86,6 +86,8 @@ struct GraphWork;  // face-graph workspace (graph.cu)
 void graph_work_free(GraphWork* w);
 struct LineWork;   // line-extraction workspace (lines.cu)
 void line_work_free(LineWork* w);
+struct HostPipe;   // double-buffered device copies for calls from host memory (api.cu)
+void host_pipe_free(HostPipe* p);
 struct TraceRec {
   int kernel;
   cudaEvent_t start, stop;
@@ -104,6 +106,7 @@ struct qtv_handle_s {
   qtv::NodeWork* node = nullptr;         // node-form / density-error workspace
   qtv::GraphWork* graph = nullptr;       // face-graph workspace
   qtv::LineWork* lines = nullptr;        // line-extraction workspace
+  qtv::HostPipe* pipe = nullptr;         // calls from host memory
   // sweep shape of single-snapshot calls (qtv_configure_sweep); -1 / 0 = default
   int sweep_variant = -1, sweep_nwt = 0, sweep_stages = 0, sweep_ctas = 0;
 };
