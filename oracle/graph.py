@@ -40,7 +40,12 @@ Readings where the text leaves details open:
 * vectorization: uniform Catmull-Rom through the ordered samples, 8 points
   per segment; open lines repeat their end points, loops wrap around;
 * Eq. 7: e = sum |rho(x_i)| / (mean rho over the field * N) over the spline
-  points x_i, rho trilinearly interpolated.
+  points x_i, rho trilinearly interpolated;
+* arc-length thinning (`thin_piece`, a parallel reading of the box means of
+  Sec. 3.3.2 on ordered pieces): consecutive samples of a piece are grouped by
+  the box index floor(s / d) of their arc length s along the piece, each group
+  collapsing to its mean; s is a sum of per-segment lengths rounded to units
+  of 2^-32 h, so it is exact in any summation order.
 """
 from __future__ import annotations
 
@@ -344,6 +349,40 @@ def curve_length(points, closed: bool) -> float:
     if closed:
         p = np.vstack([p, p[:1]])
     return float(np.sum(np.linalg.norm(np.diff(p, axis=0), axis=1)))
+
+
+THIN_UNIT = 2.0 ** 32  # arc-length units per h
+
+
+def thin_piece(points, closed: bool, d: float):
+    """Arc-length thinning of one ordered piece: (group means [g, 3] float64,
+    group index of every sample).  Segment i runs from sample i to i + 1 (the
+    last one of a closed piece back to sample 0, which does not move any
+    sample's arc length); s_i = sum of the rounded lengths of segments < i."""
+    P = np.asarray(points, np.float64).reshape(-1, 3)
+    m = len(P)
+    if m == 0:
+        return np.zeros((0, 3)), np.zeros(0, np.int64)
+    s = np.zeros(m, np.int64)
+    acc = 0
+    for i in range(1, m):
+        dx, dy, dz = P[i] - P[i - 1]
+        seg = np.sqrt((dx * dx + dy * dy) + dz * dz)
+        acc += int(np.rint(seg * THIN_UNIT))
+        s[i] = acc
+    D = int(np.rint(d * THIN_UNIT))
+    box = s // D
+    group = np.zeros(m, np.int64)
+    for i in range(1, m):
+        group[i] = group[i - 1] + (1 if box[i] != box[i - 1] else 0)
+    means = np.zeros((group[-1] + 1, 3))
+    for gi in range(group[-1] + 1):
+        members = np.flatnonzero(group == gi)
+        acc3 = np.zeros(3)
+        for a in members:
+            acc3 = acc3 + P[a]
+        means[gi] = acc3 / len(members)
+    return means, group
 
 
 def density_error(psi: np.ndarray, points) -> float:
