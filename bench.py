@@ -394,10 +394,33 @@ def lines_report(q, psi, ids, wnd, xyz, F, stream, reps=5):
     P = qtv.pieces_numpy(pieces)
     kms = {k: v[1] / max(1, v[0]) for k, v in tr.items()}
     types = np.bincount(P["comp_type"].astype(np.int64), minlength=4)
+    # the rest of the vectorization: box means along the pieces (4 h), their
+    # refinement in the plane normal to the pseudo-vorticity, and curves
+    try:
+        q.trace_enable(True)
+        q.trace_read(reset=True)
+        for _ in range(reps):
+            means, tp = q.thin_pieces(xyz[:F], nodes, pieces, 4.0)
+            ref = q.refine_samples(psi, xyz0=means)
+            idn = torch.arange(means.shape[0], dtype=torch.int32, device=psi.device)
+            rc_, rf_, rl_ = q.piece_curves(ref["xyz"], idn, tp, 8)
+        tr2 = q.trace_read(reset=True)
+        q.trace_enable(False)
+        e_means, _, _ = q.density_error(psi, means)
+        e_ref, _, _ = q.density_error(psi, ref["xyz"])
+    except qtv.QtvError as err:
+        return {"error": str(err)}
+    k2 = {k: v[1] / max(1, v[0]) for k, v in tr2.items()}
     return {"ms": kms, "pieces": int(len(P)), "closed_pieces": int(P["closed"].sum()),
             "pieces_in_type_I_II_III": [int(types[1]), int(types[2]), int(types[3])],
             "reversed_pieces": int(P["reversed"].sum()), "curve_points": int(curve.shape[0]),
             "total_length_h": float(length.double().sum().item()),
+            "thinned": {"box_h": 4.0, "means": int(means.shape[0]),
+                        "ms": {"thin": k2.get("thin", 0.0), "refine": k2.get("refine", 0.0),
+                               "curves": k2.get("curves", 0.0)},
+                        "refined_converged_fraction": (ref["flags"] == 1).float().mean().item(),
+                        "eq7_error_means": e_means, "eq7_error_refined": e_ref,
+                        "total_length_h": float(rl_.double().sum().item())},
             "note": "line_pieces includes the host round trip of its count-only first call"}
 
 

@@ -587,6 +587,33 @@ QTV_API int qtv_piece_curves(qtv_handle h, const float* xyz, const uint32_t* nod
                              uint64_t* total, void* stream);
 
 /*
+ * Thinning of line pieces by arc length, a parallel reading of the box means
+ * of Sec. 3.3.2 (which replace the samples inside a box of side d by their
+ * mean, so that the box size sets the spacing of the final samples): the
+ * samples of each ordered piece are grouped by the box index floor(s / box)
+ * of their arc length s along the piece, and each group becomes its mean.
+ * s sums the segment lengths (FP64, rounded to units of 2^-32 of the
+ * position unit), so it is exact in any order; means are FP64 sums in sample
+ * order, rounded to FP32.  The paper traverses the graph box by box instead,
+ * which is sequential; the groups here never span two pieces.
+ *
+ *   xyz, nodes, pieces  the sample positions and the output of
+ *                qtv_line_pieces (nnodes node entries, npieces pieces).
+ *   box          box length, in the units of xyz.
+ *   out_xyz      device float[out_cap][3]: the group means, piece by piece.
+ *   out_pieces   device qtv_piece[npieces]: the pieces over out_xyz (first,
+ *                count of the means; other fields copied).
+ *   total        device uint64: number of means (outputs incomplete when it
+ *                exceeds out_cap).
+ * The means can be refined with qtv_refine_samples and drawn with
+ * qtv_piece_curves (node list 0, 1, 2, ...).
+ */
+QTV_API int qtv_thin_pieces(qtv_handle h, const float* xyz, const uint32_t* nodes,
+                            const qtv_piece* pieces, uint64_t npieces, uint64_t nnodes, float box,
+                            float* out_xyz, uint64_t out_cap, qtv_piece* out_pieces,
+                            uint64_t* total, void* stream);
+
+/*
  * Kernel timing trace.  While enabled, the handle records a pair of CUDA
  * events on the launching stream around each of its kernel launches (names:
  * "sweep", "seg_scan", "scatter", "stats", "localize", "emit_pack", "batch"
@@ -594,7 +621,7 @@ QTV_API int qtv_piece_curves(qtv_handle h, const float* xyz, const uint32_t* nod
  * parts of learned localization, "node_form", "node_scan", "node_scatter"
  * for the node form, "density" for the density error, "refine" for
  * sample refinement, "graph" for the face graph and its components, "lines"
- * and "curves" for line pieces and their curves).
+ * and "curves" for line pieces and their curves, "thin" for their thinning).
  * qtv_trace_read waits for the recorded events, writes up to max_entries
  * per-kernel totals (launch count and summed device time) and, if reset is
  * nonzero, clears the record.  Tracing adds host work per launch; leave it

@@ -160,9 +160,10 @@ def lib() -> ctypes.CDLL:
         L.qtv_line_pieces.argtypes = [P, u64, P, P, P, P, P, P, P, P, u64, P, u64, P, P]
         L.qtv_piece_curves.argtypes = [P, P, P, P, u64, P, i32, P, u64, P, P, P, P]
         L.qtv_identify_localize_host.argtypes = [P, ctypes.POINTER(Grid), P, u64, P, P, P]
+        L.qtv_thin_pieces.argtypes = [P, P, P, P, u64, u64, f32, P, u64, P, P, P]
         for name in ("qtv_node_circulation", "qtv_density_error", "qtv_refine_samples",
                      "qtv_face_graph", "qtv_line_pieces", "qtv_piece_curves",
-                     "qtv_identify_localize_host"):
+                     "qtv_identify_localize_host", "qtv_thin_pieces"):
             getattr(L, name).restype = i32
         L.qtv_trace_enable.argtypes = [P, i32]
         L.qtv_trace_read.argtypes = [P, ctypes.POINTER(TraceEntry), i32, ctypes.POINTER(i32), i32]
@@ -628,6 +629,23 @@ class Qtv:
         _check(lib().qtv_piece_curves(self.h, *args, _ptr(curve), m, _ptr(first), _ptr(length),
                                       _ptr(total), _stream_ptr(stream)))
         return curve[:m], first[:npc], length[:npc]
+
+    def thin_pieces(self, xyz, nodes, pieces, box: float, stream=None):
+        """Arc-length thinning of line pieces (qtv_thin_pieces): (means float32 [m, 3],
+        pieces over the means as a uint8 tensor [np, 24] of qtv_piece records)."""
+        import torch
+
+        npc = pieces.shape[0]
+        nn = nodes.numel()
+        dev = xyz.device
+        out = torch.empty((max(nn, 1), 3), dtype=torch.float32, device=dev)
+        outp = torch.empty((max(npc, 1), 24), dtype=torch.uint8, device=dev)
+        total = torch.zeros(1, dtype=torch.int64, device=dev)
+        _check(lib().qtv_thin_pieces(self.h, _ptr(xyz), _ptr(nodes), _ptr(pieces), npc, nn,
+                                     float(box), _ptr(out), nn, _ptr(outp), _ptr(total),
+                                     _stream_ptr(stream)))
+        m = int(total.item())
+        return out[:m], outp[:npc]
 
     # -- emission -------------------------------------------------------------------
     def emit_samples(self, face_ids, winding, xyz, resid, flags, out=None, stream=None):

@@ -121,7 +121,7 @@ const char* kKernelNames[K_COUNT] = {"sweep",     "seg_scan",  "scatter",      "
                                      "localize",  "emit_pack", "batch",        "encode",
                                      "network",   "head",      "node_form",    "node_scan",
                                      "node_scatter", "density",   "refine",       "graph",
-                                     "lines",     "curves"};
+                                     "lines",     "curves",    "thin"};
 }  // namespace
 
 TraceScope::TraceScope(qtv_handle h_, int k, cudaStream_t s) : h(h_), kernel(k), st(s) {
@@ -640,6 +640,28 @@ int qtv_identify_localize_host(qtv_handle h, const qtv_grid* grid, const void* p
   if (e != cudaSuccess) return check_cuda(e, "host pipe results");
   p->used[b] = true;
   return QTV_OK;
+}
+
+int qtv_thin_pieces(qtv_handle h, const float* xyz, const uint32_t* nodes, const qtv_piece* pieces,
+                    uint64_t npieces, uint64_t nnodes, float box, float* out_xyz, uint64_t out_cap,
+                    qtv_piece* out_pieces, uint64_t* total, void* stream) {
+  if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
+  if (!total) return set_error(QTV_ERR_ARG, "total is NULL");
+  if (!(box > 0.f)) return set_error(QTV_ERR_ARG, "box must be positive");
+  if (npieces > 0 && (!xyz || !nodes || !pieces || !out_pieces))
+    return set_error(QTV_ERR_ARG, "a required pointer is NULL");
+  if (out_cap > 0 && !out_xyz) return set_error(QTV_ERR_ARG, "out_xyz is NULL");
+  if (nnodes >= 0xFFFFFFFFull || npieces > nnodes)
+    return set_error(QTV_ERR_ARG, "bad node or piece count");
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return set_error(QTV_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (npieces == 0) {
+    const cudaError_t e = cudaMemsetAsync(total, 0, sizeof(uint64_t), st);
+    return check_cuda(e, "cudaMemsetAsync(total)");
+  }
+  return thin_pieces_launch(h, xyz, nodes, pieces, npieces, nnodes, box, out_xyz, out_cap,
+                            out_pieces, total, st);
 }
 
 int qtv_localize(qtv_handle h, const qtv_grid* grid, const void* psi, const uint64_t* face_ids,

@@ -395,7 +395,8 @@ constexpr int SB = 1024;        // threads per scan block
 constexpr int SPER = 4;         // values per thread
 constexpr int SCHUNK = SB * SPER;
 
-__global__ void __launch_bounds__(SB) scan_blocks_kernel(const uint32_t* in, const uint64_t* n_dev,
+template <typename T>
+__global__ void __launch_bounds__(SB) scan_blocks_kernel(const T* in, const uint64_t* n_dev,
                                                          unsigned long long n,
                                                          unsigned long long* out,
                                                          unsigned long long* bsum) {
@@ -457,11 +458,12 @@ __global__ void scan_add_kernel(const uint64_t* n_dev, unsigned long long n,
     out[i] += bsum[i / SCHUNK];
 }
 
-void scan_u32(const uint32_t* in, const uint64_t* n_dev, unsigned long long n,
+template <typename T>
+void scan_u32(const T* in, const uint64_t* n_dev, unsigned long long n,
               unsigned long long* out, unsigned long long* bsum, unsigned long long* total,
               int num_sms, cudaStream_t st) {
   const int nb = (int)((n + SCHUNK - 1) / SCHUNK);
-  scan_blocks_kernel<<<nb > 0 ? nb : 1, SB, 0, st>>>(in, n_dev, n, out, bsum);
+  scan_blocks_kernel<T><<<nb > 0 ? nb : 1, SB, 0, st>>>(in, n_dev, n, out, bsum);
   scan_sums_kernel<<<1, 32, 0, st>>>(bsum, nb > 0 ? nb : 1, total);
   long long g = ((long long)n + LT - 1) / LT;
   if (g > (long long)num_sms * 16) g = (long long)num_sms * 16;
@@ -588,6 +590,110 @@ __global__ void __launch_bounds__(LT) length_kernel(CurveArgs a) {
       a.length[p] = (float)t;
     }
     __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// arc-length thinning of ordered pieces
+// ---------------------------------------------------------------------------
+constexpr double kThinUnit = 4294967296.0;  // arc-length units per length unit (2^32)
+
+struct ThinArgs {
+  const float* xyz;
+  const uint32_t* nodes;
+  const qtv_piece* pieces;
+  unsigned long long np, ne;
+  unsigned long long D;            // box length in arc-length units
+  unsigned long long* v;           // per entry: rounded length of the segment ending there
+  unsigned long long* X;           // exclusive scan of v
+  uint32_t* flag;                  // per entry: starts a group
+  unsigned long long* G;           // exclusive scan of flag
+  float* out;
+  unsigned long long out_cap;
+  qtv_piece* out_pieces;
+  const unsigned long long* total;  // groups (device)
+};
+
+// piece of node-list entry g (pieces are contiguous and in order)
+__device__ __forceinline__ unsigned long long piece_of(const ThinArgs& a, unsigned long long g) {
+  unsigned long long lo = 0, hi = a.np;
+  while (hi - lo > 1) {
+    const unsigned long long mid = (lo + hi) >> 1;
+    if (a.pieces[mid].first <= g) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ double coord(const ThinArgs& a, unsigned long long g, int c) {
+  return (double)a.xyz[3ull * a.nodes[g] + c];
+}
+
+__global__ void thin_len_kernel(ThinArgs a) {
+  for (unsigned long long g = (unsigned long long)blockIdx.x * LT + threadIdx.x; g < a.ne;
+       g += (unsigned long long)gridDim.x * LT) {
+    const qtv_piece r = a.pieces[piece_of(a, g)];
+    unsigned long long v = 0;
+    if (g > r.first) {
+      // FP64 length of the segment from the previous sample, summed in the
+      // order ((dx^2 + dy^2) + dz^2) without contraction, then rounded
+      const double dx = coord(a, g, 0) - coord(a, g - 1, 0);
+      const double dy = coord(a, g, 1) - coord(a, g - 1, 1);
+      const double dz = coord(a, g, 2) - coord(a, g - 1, 2);
+      const double q = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+      v = (unsigned long long)__double2ll_rn(sqrt(q) * kThinUnit);
+    }
+    a.v[g] = v;
+  }
+}
+
+__global__ void thin_flag_kernel(ThinArgs a) {
+  for (unsigned long long g = (unsigned long long)blockIdx.x * LT + threadIdx.x; g < a.ne;
+       g += (unsigned long long)gridDim.x * LT) {
+    const qtv_piece r = a.pieces[piece_of(a, g)];
+    uint32_t f = 1;
+    if (g > r.first) {
+      const unsigned long long s = a.X[g] + a.v[g] - a.X[r.first];
+      const unsigned long long sp = a.X[g - 1] + a.v[g - 1] - a.X[r.first];
+      f = (s / a.D) != (sp / a.D) ? 1u : 0u;
+    }
+    a.flag[g] = f;
+  }
+}
+
+__global__ void thin_mean_kernel(ThinArgs a) {
+  for (unsigned long long g = (unsigned long long)blockIdx.x * LT + threadIdx.x; g < a.ne;
+       g += (unsigned long long)gridDim.x * LT) {
+    if (!a.flag[g]) continue;
+    const qtv_piece r = a.pieces[piece_of(a, g)];
+    const unsigned long long end = r.first + r.count;
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    unsigned long long m = 0, e = g;
+    do {
+      sx = __dadd_rn(sx, coord(a, e, 0));
+      sy = __dadd_rn(sy, coord(a, e, 1));
+      sz = __dadd_rn(sz, coord(a, e, 2));
+      ++m;
+      ++e;
+    } while (e < end && !a.flag[e]);
+    const unsigned long long q = a.G[g];
+    if (q < a.out_cap) {
+      a.out[3 * q] = (float)(sx / (double)m);
+      a.out[3 * q + 1] = (float)(sy / (double)m);
+      a.out[3 * q + 2] = (float)(sz / (double)m);
+    }
+  }
+}
+
+__global__ void thin_pieces_kernel(ThinArgs a) {
+  for (unsigned long long p = (unsigned long long)blockIdx.x * LT + threadIdx.x; p < a.np;
+       p += (unsigned long long)gridDim.x * LT) {
+    qtv_piece r = a.pieces[p];
+    const unsigned long long g0 = a.G[r.first];
+    const unsigned long long g1 = p + 1 < a.np ? a.G[a.pieces[p + 1].first] : *a.total;
+    r.first = g0;
+    r.count = (uint32_t)(g1 - g0);
+    a.out_pieces[p] = r;
   }
 }
 
@@ -757,6 +863,56 @@ int piece_curves_launch(qtv_handle h, const float* xyz, const uint32_t* nodes,
   length_kernel<<<(int)(gp > 0 ? gp : 1), LT, 0, st>>>(a);
   const cudaError_t e = cudaGetLastError();
   return check_cuda(e, "piece curves launch");
+}
+
+int thin_pieces_launch(qtv_handle h, const float* xyz, const uint32_t* nodes,
+                       const qtv_piece* pieces, uint64_t np, uint64_t nnodes, float box,
+                       float* out_xyz, uint64_t out_cap, qtv_piece* out_pieces, uint64_t* total,
+                       cudaStream_t st) {
+  const unsigned long long ne = nnodes;
+  const unsigned long long nb = (ne + SCHUNK - 1) / SCHUNK + 1;
+  const unsigned long long sz[] = {ne * 8, ne * 8, ne * 4, ne * 8, nb * 8, nb * 8, 16};
+  size_t bytes = 0;
+  for (unsigned long long x : sz) bytes += ((x + 255) / 256) * 256;
+  void* buf = nullptr;
+  int rc = ensure(h, bytes, st, &buf);
+  if (rc) return rc;
+  char* p = static_cast<char*>(buf);
+  ThinArgs a;
+  a.xyz = xyz;
+  a.nodes = nodes;
+  a.pieces = pieces;
+  a.np = np;
+  a.ne = ne;
+  const double Dd = (double)box * kThinUnit;
+  a.D = Dd >= 1.0 ? (unsigned long long)llrint(Dd) : 1ull;
+  a.v = carve<unsigned long long>(p, ne);
+  a.X = carve<unsigned long long>(p, ne);
+  a.flag = carve<uint32_t>(p, ne);
+  a.G = carve<unsigned long long>(p, ne);
+  unsigned long long* bs1 = carve<unsigned long long>(p, nb);
+  unsigned long long* bs2 = carve<unsigned long long>(p, nb);
+  unsigned long long* tots = carve<unsigned long long>(p, 2);
+  a.out = out_xyz;
+  a.out_cap = out_cap;
+  a.out_pieces = out_pieces;
+  a.total = tots + 1;
+  long long g = ((long long)ne + LT - 1) / LT;
+  if (g > (long long)h->num_sms * 16) g = (long long)h->num_sms * 16;
+  if (g < 1) g = 1;
+  long long gp = ((long long)np + LT - 1) / LT;
+  if (gp > (long long)h->num_sms * 16) gp = (long long)h->num_sms * 16;
+  if (gp < 1) gp = 1;
+  TraceScope ts(h, K_THIN, st);
+  thin_len_kernel<<<(int)g, LT, 0, st>>>(a);
+  scan_u32(a.v, nullptr, ne, a.X, bs1, tots, h->num_sms, st);
+  thin_flag_kernel<<<(int)g, LT, 0, st>>>(a);
+  scan_u32(a.flag, nullptr, ne, a.G, bs2, tots + 1, h->num_sms, st);
+  thin_mean_kernel<<<(int)g, LT, 0, st>>>(a);
+  thin_pieces_kernel<<<(int)gp, LT, 0, st>>>(a);
+  cudaError_t e = cudaMemcpyAsync(total, tots + 1, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return check_cuda(e, "thin pieces launch");
 }
 
 }  // namespace qtv

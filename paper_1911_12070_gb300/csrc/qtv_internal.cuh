@@ -76,7 +76,7 @@ struct Locator;  // learned locator state (locator.cu)
 void locator_free(Locator* L);
 enum KernelId {
   K_SWEEP = 0, K_SEG_SCAN, K_SCATTER, K_STATS, K_LOCALIZE, K_EMIT_PACK, K_BATCH,
-  K_ENCODE, K_NETWORK, K_HEAD, K_NODE_FORM, K_NODE_SCAN, K_NODE_SCATTER, K_DENSITY, K_REFINE, K_GRAPH, K_LINES, K_CURVES, K_COUNT
+  K_ENCODE, K_NETWORK, K_HEAD, K_NODE_FORM, K_NODE_SCAN, K_NODE_SCATTER, K_DENSITY, K_REFINE, K_GRAPH, K_LINES, K_CURVES, K_THIN, K_COUNT
 };
 struct BatchPlan;  // batched snapshots (batch.cu)
 void batch_free(BatchPlan* b);
@@ -357,6 +357,12 @@ int piece_curves_launch(qtv_handle h, const float* xyz, const uint32_t* nodes,
                         const qtv_piece* pieces, uint64_t np, const uint64_t* np_dev, int per,
                         float* curve, uint64_t curve_cap, uint64_t* curve_first, float* length,
                         uint64_t* total, cudaStream_t st);
+
+// Arc-length thinning of line pieces (lines.cu)
+int thin_pieces_launch(qtv_handle h, const float* xyz, const uint32_t* nodes,
+                       const qtv_piece* pieces, uint64_t np, uint64_t nnodes, float box,
+                       float* out_xyz, uint64_t out_cap, qtv_piece* out_pieces, uint64_t* total,
+                       cudaStream_t st);
 
 // Emission pack (localize.cu)
 int emit_pack_launch(qtv_handle h, uint64_t n, const uint64_t* face_ids, const int8_t* winding, const float* xyz,

@@ -157,3 +157,49 @@ def test_512_workload(q):
     assert seen >= 200
     # all three types occur in a tangle of this size
     assert set(int(t) for t in P["comp_type"]) == {1, 2, 3}
+
+
+@pytest.mark.parametrize("box", [1.5, 4.0])
+def test_thinning_matches_oracle_bit_for_bit(q, box):
+    import paper_1911_12070_gb300 as qtv
+
+    host = synth.random_waves_numpy((48, 48, 48), synth.wave_spec(21, 512))
+    dev = torch.from_numpy(host).cuda()
+    ids, w, xyz, _, _ = q.identify_localize(dev)
+    nbr, deg, comp, _ = q.face_graph(host.shape, ids)
+    pieces, nodes = q.line_pieces(nbr, deg, comp, xyz, ids, w)
+    means, tp = q.thin_pieces(xyz, nodes, pieces, box)
+    P = qtv.pieces_numpy(pieces)
+    T = qtv.pieces_numpy(tp)
+    nd = nodes.cpu().numpy()
+    x64 = xyz.cpu().numpy().astype(np.float64)
+    m = means.cpu().numpy()
+    assert T["first"][0] == 0 and np.all(T["first"][1:] == T["first"][:-1] + T["count"][:-1])
+    assert int(T["first"][-1] + T["count"][-1]) == len(m)
+    for k in range(len(P)):
+        pts = x64[nd[P["first"][k]:P["first"][k] + P["count"][k]]]
+        want, _ = graph.thin_piece(pts, bool(P["closed"][k]), box)
+        got = m[T["first"][k]:T["first"][k] + T["count"][k]]
+        assert np.array_equal(got, want.astype(np.float32)), k
+        assert T["closed"][k] == P["closed"][k] and T["component"][k] == P["component"][k]
+    assert len(m) < 0.6 * len(nd)
+
+
+def test_thin_refine_curves_pipeline(q):
+    # identification -> samples -> lines -> box means -> refinement (Sec. 3.3.3)
+    # -> Catmull-Rom: refined means lie on cores (Eq. 7 error far below the means')
+    import paper_1911_12070_gb300 as qtv
+
+    host = synth.random_waves_numpy((48, 48, 48), synth.wave_spec(21, 512))
+    dev = torch.from_numpy(host).cuda()
+    ids, w, xyz, _, _ = q.identify_localize(dev)
+    nbr, deg, comp, _ = q.face_graph(host.shape, ids)
+    pieces, nodes = q.line_pieces(nbr, deg, comp, xyz, ids, w)
+    means, tp = q.thin_pieces(xyz, nodes, pieces, 4.0)
+    ref = q.refine_samples(dev, xyz0=means)
+    idn = torch.arange(means.shape[0], dtype=torch.int32, device="cuda")
+    curve, first, length = q.piece_curves(ref["xyz"], idn, tp, 8)
+    e_means, _, _ = q.density_error(dev, means)
+    e_ref, _, _ = q.density_error(dev, ref["xyz"])
+    assert e_ref < 0.2 * e_means
+    assert curve.shape[0] > means.shape[0] and float(length.sum()) > 0
