@@ -286,6 +286,18 @@ def node_form_report(q, psi, xyz, count, stream, reps=20):
         q.trace_enable(False)
     except QtvError as err:
         return {"error": str(err)}
+    # the paper's graph over the vortex nodes (6-connectivity) and its components
+    try:
+        q.trace_enable(True)
+        q.trace_read(reset=True)
+        for _ in range(3):
+            _, ndeg, ncmp, ncomp = q.node_graph(tuple(psi.shape), ids[:nv])
+        trg = q.trace_read(reset=True)
+        q.trace_enable(False)
+        ngraph = {"ms": trg.get("graph", (1, 0.0))[1] / max(1, trg.get("graph", (1, 0.0))[0]),
+                  "components": ncomp, "edges": int(ndeg.long().sum().item()) // 2}
+    except QtvError as err:
+        ngraph = {"error": str(err)}
     peak, peak_kind = peaks()
     kms = {k: v[1] / max(1, v[0]) for k, v in tr.items()}
     nf_ms = kms.get("node_form", 0.0)
@@ -302,6 +314,7 @@ def node_form_report(q, psi, xyz, count, stream, reps=20):
         "roofline": {"bound": "hbm", "kernel": "node_form", "achieved": ach, "peak": peak,
                      "unit": "GB/s", "frac": ach / peak, "peak_source": peak_kind,
                      "algorithmic_bytes": alg},
+        "vortex_node_graph": ngraph,
         "density_error": {"e": e, "mean_abs_rho": mean_rho, "rho_bar": rho_bar,
                           "ms": d_ms[1] / max(1, d_ms[0]),
                           "points": "plain samples of the timed step"},

@@ -515,6 +515,21 @@ QTV_API int qtv_face_graph(qtv_handle h, const qtv_grid* grid, const uint64_t* f
                            uint64_t* ncomp, void* stream);
 
 /*
+ * The paper's own graph (Sec. 3.1) over vortex nodes: two vortex nodes are
+ * adjacent when they are neighbours along a grid line (6-connectivity), and
+ * its connected components (Sec. 3.2), as for qtv_face_graph.
+ *
+ *   node_ids  device uint64[n]: strictly ascending linear node indices (as
+ *             from qtv_node_circulation).
+ *   nbr       device uint32[n][6]: neighbour indices (into node_ids),
+ *             ascending, then 0xFFFFFFFF; deg, comp, ncomp as in
+ *             qtv_face_graph (components labelled by their lowest index).
+ */
+QTV_API int qtv_node_graph(qtv_handle h, const qtv_grid* grid, const uint64_t* node_ids, uint64_t n,
+                           const uint64_t* n_dev, uint32_t* nbr, uint8_t* deg, uint32_t* comp,
+                           uint64_t* ncomp, void* stream);
+
+/*
  * Vortex-core lines of a sample graph (Sec. 3.4): classification, ordering,
  * orientation, and uniform Catmull-Rom curves, on the graph that
  * qtv_face_graph builds over pierced faces (the paper first thins its samples

@@ -161,9 +161,10 @@ def lib() -> ctypes.CDLL:
         L.qtv_piece_curves.argtypes = [P, P, P, P, u64, P, i32, P, u64, P, P, P, P]
         L.qtv_identify_localize_host.argtypes = [P, ctypes.POINTER(Grid), P, u64, P, P, P]
         L.qtv_thin_pieces.argtypes = [P, P, P, P, u64, u64, f32, P, u64, P, P, P]
+        L.qtv_node_graph.argtypes = [P, ctypes.POINTER(Grid), P, u64, P, P, P, P, P, P]
         for name in ("qtv_node_circulation", "qtv_density_error", "qtv_refine_samples",
                      "qtv_face_graph", "qtv_line_pieces", "qtv_piece_curves",
-                     "qtv_identify_localize_host", "qtv_thin_pieces"):
+                     "qtv_identify_localize_host", "qtv_thin_pieces", "qtv_node_graph"):
             getattr(L, name).restype = i32
         L.qtv_trace_enable.argtypes = [P, i32]
         L.qtv_trace_read.argtypes = [P, ctypes.POINTER(TraceEntry), i32, ctypes.POINTER(i32), i32]
@@ -584,6 +585,26 @@ class Qtv:
         comp = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
         nc = torch.zeros(1, dtype=torch.int64, device=dev)
         _check(lib().qtv_face_graph(self.h, ctypes.byref(g), _ptr(face_ids), n, _ptr(n_dev),
+                                    _ptr(nbr), _ptr(deg), _ptr(comp), _ptr(nc),
+                                    _stream_ptr(stream)))
+        k = int(nc.item())
+        if k < 0:
+            raise QtvError(ERR_TIMEOUT, "a bounded union-find retry loop gave up")
+        return nbr[:n], deg[:n], comp[:n], k
+
+    def node_graph(self, shape, node_ids, n_dev=None, grid=None, stream=None):
+        """Graph of vortex nodes (6-connectivity) and its components: (nbr int32
+        [n, 6] with -1 for none, deg uint8 [n], comp int32 [n], number of components)."""
+        import torch
+
+        g = grid or Grid.of(tuple(shape))
+        n = node_ids.numel()
+        dev = node_ids.device
+        nbr = torch.empty((max(n, 1), 6), dtype=torch.int32, device=dev)
+        deg = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
+        comp = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        nc = torch.zeros(1, dtype=torch.int64, device=dev)
+        _check(lib().qtv_node_graph(self.h, ctypes.byref(g), _ptr(node_ids), n, _ptr(n_dev),
                                     _ptr(nbr), _ptr(deg), _ptr(comp), _ptr(nc),
                                     _stream_ptr(stream)))
         k = int(nc.item())

@@ -664,6 +664,29 @@ int qtv_thin_pieces(qtv_handle h, const float* xyz, const uint32_t* nodes, const
                             out_pieces, total, st);
 }
 
+int qtv_node_graph(qtv_handle h, const qtv_grid* grid, const uint64_t* node_ids, uint64_t n,
+                   const uint64_t* n_dev, uint32_t* nbr, uint8_t* deg, uint32_t* comp,
+                   uint64_t* ncomp, void* stream) {
+  if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
+  int rc = validate_grid(grid);
+  if (rc) return rc;
+  if (!ncomp) return set_error(QTV_ERR_ARG, "ncomp is NULL");
+  if (n > 0 && (!node_ids || !nbr || !deg || !comp))
+    return set_error(QTV_ERR_ARG, "a required pointer is NULL");
+  if (n >= 0xFFFFFFFFull) return set_error(QTV_ERR_ARG, "2^32 - 1 nodes or more");
+  const qtv_grid& g = *grid;
+  if ((unsigned long long)g.ny * g.nz >= 0xFFFFFFFFull)
+    return set_error(QTV_ERR_ARG, "too many grid rows");
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return set_error(QTV_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (n == 0 || (unsigned long long)g.nx * g.ny * g.nz == 0) {
+    const cudaError_t e = cudaMemsetAsync(ncomp, 0, sizeof(uint64_t), st);
+    return check_cuda(e, "cudaMemsetAsync(ncomp)");
+  }
+  return face_graph_launch(h, g, node_ids, n, n_dev, nbr, deg, comp, ncomp, st, true);
+}
+
 int qtv_localize(qtv_handle h, const qtv_grid* grid, const void* psi, const uint64_t* face_ids,
                  const int8_t* winding, uint64_t n, const uint64_t* n_dev, int mode,
                  float fallback_resid, float* xyz, float* resid, uint8_t* flags, void* stream) {

@@ -1,5 +1,7 @@
-// graph.cu -- the sample graph of Sec. 3.1 over pierced faces, and its
-// connected components (the independent lines of Sec. 3.2), on the GPU.
+// graph.cu -- the sample graph of Sec. 3.1 over pierced faces (or over the
+// vortex nodes of the node form, 6-connected along grid lines as in the
+// paper), and its connected components (the independent lines of Sec. 3.2),
+// on the GPU.
 //
 // Adjacency.  Two pierced faces are adjacent when they bound the same unit
 // cell (a cell with all corners in the grid); a line through a cell enters
@@ -59,12 +61,12 @@ __device__ __forceinline__ unsigned long long limit_n(unsigned long long n, cons
 // rows[r] = first index a with face_ids[a] in row r or later (r = k*ny + j),
 // for r in [0, R]; rows[R] = n
 __global__ void row_table_kernel(const uint64_t* __restrict__ ids, unsigned long long n,
-                                 const uint64_t* n_dev, int nx, long long R,
+                                 const uint64_t* n_dev, int nx, long long R, int shift,
                                  uint32_t* __restrict__ rows) {
   const unsigned long long nn = limit_n(n, n_dev);
   for (long long r = (long long)blockIdx.x * GT + threadIdx.x; r <= R;
        r += (long long)gridDim.x * GT) {
-    const unsigned long long key = ((unsigned long long)r * (unsigned long long)nx) << 2;
+    const unsigned long long key = ((unsigned long long)r * (unsigned long long)nx) << shift;
     unsigned long long lo = 0, hi = nn;
     while (lo < hi) {
       const unsigned long long mid = (lo + hi) >> 1;
@@ -81,7 +83,9 @@ struct GraphArgs {
   const uint64_t* n_dev;
   int nx, ny, nz;
   const uint32_t* rows;
-  uint32_t* nbr;   // [n][10]
+  int shift;       // id = linear node index << shift (2 for faces, 0 for nodes)
+  int stride;      // neighbour slots per entry (10 for faces, 6 for nodes)
+  uint32_t* nbr;   // [n][stride]
   uint8_t* deg;
   uint32_t* comp;  // parents during the union-find
   unsigned long long* status;  // [0] components, [1] gave-up flag
@@ -89,7 +93,7 @@ struct GraphArgs {
 
 // index of face id f in the list, or kNone
 __device__ __forceinline__ uint32_t find_face(const GraphArgs& a, unsigned long long f) {
-  const unsigned long long row = (f >> 2) / (unsigned long long)a.nx;
+  const unsigned long long row = (f >> a.shift) / (unsigned long long)a.nx;
   unsigned long long lo = __ldg(a.rows + row), hi = __ldg(a.rows + row + 1);
   while (lo < hi) {
     const unsigned long long mid = (lo + hi) >> 1;
@@ -153,6 +157,42 @@ __global__ void __launch_bounds__(GT) adjacency_kernel(GraphArgs a) {
   }
 }
 
+// vortex-node graph: 6-connectivity along grid lines; candidates in the
+// order -z, -y, -x, +x, +y, +z are ascending linear indices
+__global__ void __launch_bounds__(GT) node_adjacency_kernel(GraphArgs a) {
+  const unsigned long long nn = limit_n(a.n, a.n_dev);
+  const long long nx = a.nx, ny = a.ny, nz = a.nz;
+  for (unsigned long long q = (unsigned long long)blockIdx.x * GT + threadIdx.x; q < nn;
+       q += (unsigned long long)gridDim.x * GT) {
+    const unsigned long long u = __ldg(a.ids + q);
+    const long long i = (long long)(u % (unsigned long long)nx);
+    const long long j = (long long)((u / (unsigned long long)nx) % (unsigned long long)ny);
+    const long long k = (long long)(u / ((unsigned long long)nx * ny));
+    const unsigned long long sxy = (unsigned long long)(nx * ny);
+    uint32_t nb[6];
+    int m = 0;
+    unsigned long long cand[6];
+    bool ok[6];
+    cand[0] = u - sxy;  ok[0] = k > 0;
+    cand[1] = u - nx;   ok[1] = j > 0;
+    cand[2] = u - 1;    ok[2] = i > 0;
+    cand[3] = u + 1;    ok[3] = i + 1 < nx;
+    cand[4] = u + nx;   ok[4] = j + 1 < ny;
+    cand[5] = u + sxy;  ok[5] = k + 1 < nz;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      if (!ok[c]) continue;
+      const uint32_t idx = find_face(a, cand[c]);
+      if (idx != kNone) nb[m++] = idx;
+    }
+    uint32_t* row = a.nbr + q * 6;
+#pragma unroll
+    for (int x = 0; x < 6; ++x) row[x] = x < m ? nb[x] : kNone;
+    a.deg[q] = (uint8_t)m;
+    a.comp[q] = (m > 0 && nb[0] < (uint32_t)q) ? nb[0] : (uint32_t)q;
+  }
+}
+
 __device__ __forceinline__ uint32_t find_root(uint32_t* parent, uint32_t x) {
   uint32_t p = *((volatile uint32_t*)parent + x);
   while (p != x) {
@@ -181,7 +221,7 @@ __global__ void __launch_bounds__(GT) link_kernel(GraphArgs a) {
        q += (unsigned long long)gridDim.x * GT) {
     const int m = a.deg[q];
     for (int x = 0; x < m; ++x) {
-      const uint32_t b = a.nbr[q * 10 + x];
+      const uint32_t b = a.nbr[q * a.stride + x];
       if (b <= (uint32_t)q) continue;
       int tries = 0;
       while (true) {
@@ -230,7 +270,7 @@ bool capturing(cudaStream_t st) {
 
 int face_graph_launch(qtv_handle h, const qtv_grid& g, const uint64_t* face_ids, uint64_t n,
                       const uint64_t* n_dev, uint32_t* nbr, uint8_t* deg, uint32_t* comp,
-                      uint64_t* ncomp, cudaStream_t st) {
+                      uint64_t* ncomp, cudaStream_t st, bool nodes) {
   if (!h->graph) {
     if (capturing(st))
       return set_error(QTV_ERR_STATE, "graph workspace must be created outside stream capture");
@@ -261,7 +301,8 @@ int face_graph_launch(qtv_handle h, const qtv_grid& g, const uint64_t* face_ids,
   {
     long long blocks = (R + 1 + GT - 1) / GT;
     if (blocks > (long long)h->num_sms * 16) blocks = (long long)h->num_sms * 16;
-    row_table_kernel<<<(int)blocks, GT, 0, st>>>(face_ids, n, n_dev, g.nx, R, w->rows);
+    row_table_kernel<<<(int)blocks, GT, 0, st>>>(face_ids, n, n_dev, g.nx, R, nodes ? 0 : 2,
+                                                 w->rows);
   }
   GraphArgs a;
   a.ids = face_ids;
@@ -271,6 +312,8 @@ int face_graph_launch(qtv_handle h, const qtv_grid& g, const uint64_t* face_ids,
   a.ny = g.ny;
   a.nz = g.nz;
   a.rows = w->rows;
+  a.shift = nodes ? 0 : 2;
+  a.stride = nodes ? 6 : 10;
   a.nbr = nbr;
   a.deg = deg;
   a.comp = comp;
@@ -278,7 +321,8 @@ int face_graph_launch(qtv_handle h, const qtv_grid& g, const uint64_t* face_ids,
   long long blocks = ((long long)n + GT - 1) / GT;
   if (blocks > (long long)h->num_sms * 16) blocks = (long long)h->num_sms * 16;
   if (blocks < 1) blocks = 1;
-  adjacency_kernel<<<(int)blocks, GT, 0, st>>>(a);
+  if (nodes) node_adjacency_kernel<<<(int)blocks, GT, 0, st>>>(a);
+  else adjacency_kernel<<<(int)blocks, GT, 0, st>>>(a);
   link_kernel<<<(int)blocks, GT, 0, st>>>(a);
   flatten_kernel<<<(int)blocks, GT, 0, st>>>(a);
   graph_status_kernel<<<1, 1, 0, st>>>(w->status, ncomp);

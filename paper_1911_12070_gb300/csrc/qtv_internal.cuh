@@ -343,9 +343,10 @@ int refine_launch(qtv_handle h, const qtv_grid& g, const float2* psi, const floa
                   uint8_t* flags, cudaStream_t st);
 
 // Face graph and connected components (graph.cu)
+// (nodes: the list holds vortex-node indices and the graph is 6-connected)
 int face_graph_launch(qtv_handle h, const qtv_grid& g, const uint64_t* face_ids, uint64_t n,
                       const uint64_t* n_dev, uint32_t* nbr, uint8_t* deg, uint32_t* comp,
-                      uint64_t* ncomp, cudaStream_t st);
+                      uint64_t* ncomp, cudaStream_t st, bool nodes = false);
 
 // Line pieces and curves of a sample graph (lines.cu)
 int line_pieces_launch(qtv_handle h, uint64_t n, const uint64_t* n_dev, const uint32_t* nbr,

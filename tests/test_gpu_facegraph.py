@@ -138,3 +138,26 @@ def test_512_workload(q):
     low = np.full(nlab, n)
     np.minimum.at(low, lab, np.arange(n))
     assert np.array_equal(low[lab], cp)
+
+
+@pytest.mark.parametrize("shape,seed", [((40, 36, 52), 13), ((30, 33, 70), 4)])
+def test_vortex_node_graph_matches_oracle(q, shape, seed):
+    # the paper's graph: vortex nodes of the node form, 6-connected
+    host = synth.random_waves_numpy(shape, synth.wave_spec(seed, 512))
+    dev = torch.from_numpy(host).cuda()
+    nid, circ, _ = q.node_circulation(dev)
+    nbr, deg, comp, ncomp = q.node_graph(shape, nid)
+    ids = nid.cpu().numpy()
+    mask = np.zeros(int(np.prod(shape)), bool)
+    mask[ids] = True
+    og = graph.node_graph(mask.reshape(shape))
+    nb = nbr.cpu().numpy().astype(np.int64)
+    dg = deg.cpu().numpy()
+    for a in range(len(ids)):
+        assert list(nb[a, :dg[a]]) == sorted(og.adj[a])
+    comps = graph.components(og)
+    want = np.empty(len(ids), np.int64)
+    for c in comps:
+        want[c] = min(c)
+    assert np.array_equal(comp.cpu().numpy().astype(np.int64), want)
+    assert ncomp == len(comps) and len(ids) > 500
