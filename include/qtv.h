@@ -391,7 +391,8 @@ QTV_API int qtv_batch_run(qtv_handle h, uint64_t* face_ids, int8_t* winding, uin
  * three grid planes through it, the circulation of Eq. 5 around the ring of
  * the node's eight in-plane neighbours (the 2h x 2h square centred on the
  * node, counter-clockwise about the plane normal +z, +x, +y for the planes
- * xy, yz, zx), reported as the integer S = C / (2 pi) in [-4, 4].  A node is a
+ * xy, yz, zx), reported as the integer S = C / (2 pi) in [-3, 4] (|S| = 4
+ * needs all eight edge differences at exact +-pi ties and reads 4).  A node is a
  * vortex node when max over its planes |C| > pi, i.e. some S != 0.  S = 0 where
  * the ring leaves the grid or passes through a NaN/Inf node (the centre node
  * is not on its ring).  Each ring edge uses the integer branch crossing of
