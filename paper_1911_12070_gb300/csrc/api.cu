@@ -255,6 +255,7 @@ int qtv_destroy(qtv_handle h) {
   graph_work_free(h->graph);
   line_work_free(h->lines);
   host_pipe_free(h->pipe);
+  cudaFree(h->refine_counter);
   for (auto& r : h->trace) {
     cudaEventDestroy(r.start);
     cudaEventDestroy(r.stop);

@@ -107,6 +107,7 @@ struct qtv_handle_s {
   qtv::GraphWork* graph = nullptr;       // face-graph workspace
   qtv::LineWork* lines = nullptr;        // line-extraction workspace
   qtv::HostPipe* pipe = nullptr;         // calls from host memory
+  unsigned long long* refine_counter = nullptr;  // work counter of the refinement kernel
   // sweep shape of single-snapshot calls (qtv_configure_sweep); -1 / 0 = default
   int sweep_variant = -1, sweep_nwt = 0, sweep_stages = 0, sweep_ctas = 0;
 };

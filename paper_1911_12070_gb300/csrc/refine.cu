@@ -20,7 +20,8 @@
 //     accepted steps.
 // Positions are carried as an integer base (the cell of x0) plus an FP32
 // offset, so steps far below the FP32 spacing of absolute coordinates still
-// move the point.
+// move the point.  Warps are persistent and each lane takes a new sample when
+// its search ends (the number of steps varies from 0 to max_iter).
 #include <cstdio>
 
 #include "qtv_internal.cuh"
@@ -149,7 +150,194 @@ __device__ __forceinline__ float rho_at(const Field& F, const Pos& P, float g[3]
   return fmaf(v.x, v.x, v.y * v.y);
 }
 
-__global__ void __launch_bounds__(REF_THREADS) refine_kernel(RefArgs A) {
+// state of one sample's search
+struct RState {
+  Pos P0, P;
+  float t[3];
+  float rho;
+  float grad[3];
+  int it;
+  uint8_t fl;
+  unsigned long long qi;
+};
+
+// x0, tangent, rho and grad rho at x0; true when the descent is to run
+__device__ __forceinline__ bool ref_init(const RefArgs& A, const Field& F, unsigned long long qi,
+                                         RState& S) {
+  const float org[3] = {A.ox, A.oy, A.oz};
+  S.qi = qi;
+  S.it = 0;
+  S.t[0] = S.t[1] = S.t[2] = 0.f;
+  S.rho = __int_as_float(0x7fc00000);
+  bool in0 = true;
+  if (A.face_ids) {
+    const uint64_t id = A.face_ids[qi];
+    const int o = (int)(id & 3u);
+    const unsigned long long lin = id >> 2;
+    S.P0.base[0] = (int)(lin % (unsigned long long)A.nx);
+    S.P0.base[1] = (int)((lin / (unsigned long long)A.nx) % (unsigned long long)A.ny);
+    S.P0.base[2] = (int)(lin / ((unsigned long long)A.nx * A.ny));
+    // face centre: half a cell along the two in-plane axes
+    S.P0.off[0] = (o == 0 || o == 2) ? 0.5f : 0.f;
+    S.P0.off[1] = (o == 0 || o == 1) ? 0.5f : 0.f;
+    S.P0.off[2] = (o == 1 || o == 2) ? 0.5f : 0.f;
+    in0 = pos_inside(S.P0, F.n);
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float g = (__ldg(A.xyz0 + 3 * qi + a) - org[a]) / A.h;
+      const float fl = floorf(g);
+      in0 = in0 && g >= 0.f && g <= (float)(F.n[a] - 1);
+      S.P0.base[a] = in0 ? (int)fl : 0;
+      S.P0.off[a] = in0 ? g - fl : g;
+    }
+  }
+  S.P = S.P0;
+  if (!in0) {
+    S.fl = QTV_REFINE_NO_TANGENT;
+    return false;
+  }
+  // pseudo-vorticity at x0
+  int c[3];
+  float f[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) cell_frac(S.P0.base[a], S.P0.off[a], F.n[a], c[a], f[a]);
+  float gr[3] = {0.f, 0.f, 0.f}, gi[3] = {0.f, 0.f, 0.f};
+  for (int q = 0; q < 8; ++q) {
+    int idx[3];
+    float wt = 1.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int bit = (q >> a) & 1;
+      idx[a] = c[a] + bit < F.n[a] ? c[a] + bit : c[a];
+      wt *= bit ? f[a] : 1.f - f[a];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float2 g = node_grad(F, idx[0], idx[1], idx[2], a);
+      gr[a] = fmaf(wt, g.x, gr[a]);
+      gi[a] = fmaf(wt, g.y, gi[a]);
+    }
+  }
+  float t[3];
+  t[0] = gr[1] * gi[2] - gr[2] * gi[1];
+  t[1] = gr[2] * gi[0] - gr[0] * gi[2];
+  t[2] = gr[0] * gi[1] - gr[1] * gi[0];
+  const float tn = sqrtf(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+  S.rho = rho_at(F, S.P, S.grad);
+  if (!(tn > 0.f) || !(tn <= 3.402823466e38f)) {
+    S.fl = QTV_REFINE_NO_TANGENT;
+    return false;
+  }
+  S.t[0] = t[0] / tn;
+  S.t[1] = t[1] / tn;
+  S.t[2] = t[2] / tn;
+  S.fl = QTV_REFINE_MAX_ITER;
+  return true;
+}
+
+// one accepted step, or the decision to stop; true when the sample is done
+__device__ __forceinline__ bool ref_step(const RefArgs& A, const Field& F, RState& S) {
+  if (S.it >= A.max_iter) return true;  // flag stays QTV_REFINE_MAX_ITER
+  const float gt = S.grad[0] * S.t[0] + S.grad[1] * S.t[1] + S.grad[2] * S.t[2];
+  float g[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) g[a] = S.grad[a] - gt * S.t[a];
+  const float gg = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+  if (!(gg > 0.f)) {
+    S.fl = QTV_REFINE_CONVERGED;
+    return true;
+  }
+  const float gn = sqrtf(gg);
+  float alpha = 2.f * S.rho / gg;
+  Pos Pn;
+  float rn = 0.f, gnext[3];
+  bool accepted = false;
+  while (alpha * gn >= A.tol) {
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      Pn.base[a] = S.P.base[a];
+      Pn.off[a] = S.P.off[a] - alpha * g[a];
+      // box around x0 (same base as x0)
+      ok = ok && fabsf(Pn.off[a] - S.P0.off[a]) <= 1.f;
+    }
+    if (ok && pos_inside(Pn, F.n)) {
+      rn = rho_at(F, Pn, gnext);
+      if (rn <= S.rho - 1e-4f * alpha * gg) {
+        accepted = true;
+        break;
+      }
+    }
+    alpha *= 0.5f;
+  }
+  if (!accepted) {
+    S.fl = QTV_REFINE_CONVERGED;
+    return true;
+  }
+  ++S.it;
+  S.P = Pn;
+  S.rho = rn;
+  S.grad[0] = gnext[0];
+  S.grad[1] = gnext[1];
+  S.grad[2] = gnext[2];
+  return false;
+}
+
+// conditioning at the result and the outputs of the sample
+__device__ __forceinline__ void ref_finish(const RefArgs& A, const Field& F, const RState& S) {
+  float dj = 0.f;
+  if (!(S.fl & QTV_REFINE_NO_TANGENT)) {
+    // in-plane Jacobian of psi at the result: basis e1 = normalize(t x a), a
+    // the axis least aligned with t; e2 = t x e1
+    const float* t = S.t;
+    int m = 0;
+    if (fabsf(t[1]) < fabsf(t[m])) m = 1;
+    if (fabsf(t[2]) < fabsf(t[m])) m = 2;
+    const float ax[3] = {m == 0 ? 1.f : 0.f, m == 1 ? 1.f : 0.f, m == 2 ? 1.f : 0.f};
+    float e1[3] = {t[1] * ax[2] - t[2] * ax[1], t[2] * ax[0] - t[0] * ax[2],
+                   t[0] * ax[1] - t[1] * ax[0]};
+    const float en = sqrtf(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    e1[0] /= en;
+    e1[1] /= en;
+    e1[2] /= en;
+    const float e2[3] = {t[1] * e1[2] - t[2] * e1[1], t[2] * e1[0] - t[0] * e1[2],
+                         t[0] * e1[1] - t[1] * e1[0]};
+    int cc[3];
+    float ff[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) cell_frac(S.P.base[a], S.P.off[a], F.n[a], cc[a], ff[a]);
+    float2 d[3];
+    (void)tri_eval(F, cc, ff, d);
+    float a1r = 0.f, a1i = 0.f, a2r = 0.f, a2i = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      a1r = fmaf(d[a].x, e1[a], a1r);
+      a1i = fmaf(d[a].y, e1[a], a1i);
+      a2r = fmaf(d[a].x, e2[a], a2r);
+      a2i = fmaf(d[a].y, e2[a], a2i);
+    }
+    dj = a1r * a2i - a2r * a1i;
+  }
+  const float org[3] = {A.ox, A.oy, A.oz};
+  const unsigned long long qi = S.qi;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    A.xyz[3 * qi + a] = org[a] + A.h * ((float)S.P.base[a] + S.P.off[a]);
+    if (A.tangent) A.tangent[3 * qi + a] = S.t[a];
+  }
+  if (A.rho) A.rho[qi] = S.rho;
+  if (A.detj) A.detj[qi] = dj;
+  if (A.iters) A.iters[qi] = S.it;
+  A.flags[qi] = S.fl;
+}
+
+// Persistent warps; each lane keeps one sample and takes the next one from
+// the counter (one atomic per warp and round) as soon as its search ends, so
+// lanes do not idle while the slowest sample of a warp finishes.  Each sample
+// is computed exactly as alone.
+__global__ void __launch_bounds__(REF_THREADS, 8) refine_kernel(RefArgs A,
+                                                             unsigned long long* counter) {
   unsigned long long nn = A.n;
   if (A.n_dev) {
     const unsigned long long d = *A.n_dev;
@@ -160,163 +348,32 @@ __global__ void __launch_bounds__(REF_THREADS) refine_kernel(RefArgs A) {
   F.n[0] = A.nx;
   F.n[1] = A.ny;
   F.n[2] = A.nz;
-  const float org[3] = {A.ox, A.oy, A.oz};
-  for (unsigned long long qi = (unsigned long long)blockIdx.x * REF_THREADS + threadIdx.x; qi < nn;
-       qi += (unsigned long long)gridDim.x * REF_THREADS) {
-    // x0 in grid coordinates, as base + offset
-    Pos P0;
-    bool in0 = true;
-    if (A.face_ids) {
-      const uint64_t id = A.face_ids[qi];
-      const int o = (int)(id & 3u);
-      const unsigned long long lin = id >> 2;
-      P0.base[0] = (int)(lin % (unsigned long long)A.nx);
-      P0.base[1] = (int)((lin / (unsigned long long)A.nx) % (unsigned long long)A.ny);
-      P0.base[2] = (int)(lin / ((unsigned long long)A.nx * A.ny));
-      // face centre: half a cell along the two in-plane axes
-      P0.off[0] = (o == 0 || o == 2) ? 0.5f : 0.f;
-      P0.off[1] = (o == 0 || o == 1) ? 0.5f : 0.f;
-      P0.off[2] = (o == 1 || o == 2) ? 0.5f : 0.f;
-      in0 = pos_inside(P0, F.n);
-    } else {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const float g = (__ldg(A.xyz0 + 3 * qi + a) - org[a]) / A.h;
-        const float fl = floorf(g);
-        in0 = in0 && g >= 0.f && g <= (float)(F.n[a] - 1);
-        P0.base[a] = in0 ? (int)fl : 0;
-        P0.off[a] = in0 ? g - fl : g;
-      }
-    }
-    float t[3] = {0.f, 0.f, 0.f};
-    float rho = __int_as_float(0x7fc00000);
-    float dj = 0.f;
-    int it = 0;
-    uint8_t fl = 0;
-    Pos P = P0;
-    if (!in0) {
-      fl = QTV_REFINE_NO_TANGENT;
-    } else {
-      // pseudo-vorticity at x0
-      int c[3];
-      float f[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) cell_frac(P0.base[a], P0.off[a], F.n[a], c[a], f[a]);
-      float gr[3] = {0.f, 0.f, 0.f}, gi[3] = {0.f, 0.f, 0.f};
-      for (int q = 0; q < 8; ++q) {
-        int idx[3];
-        float wt = 1.f;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const int bit = (q >> a) & 1;
-          idx[a] = c[a] + bit < F.n[a] ? c[a] + bit : c[a];
-          wt *= bit ? f[a] : 1.f - f[a];
-        }
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const float2 g = node_grad(F, idx[0], idx[1], idx[2], a);
-          gr[a] = fmaf(wt, g.x, gr[a]);
-          gi[a] = fmaf(wt, g.y, gi[a]);
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  RState S;
+  bool active = false, drained = false;
+  while (true) {
+    const unsigned need = __ballot_sync(0xffffffffu, !active && !drained);
+    if (need) {
+      const int leader = __ffs(need) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(need));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (!active && !drained) {
+        const unsigned long long qi = base + (unsigned long long)__popc(need & lt);
+        if (qi < nn) {
+          if (ref_init(A, F, qi, S)) active = true;
+          else ref_finish(A, F, S);
+        } else {
+          drained = true;
         }
       }
-      t[0] = gr[1] * gi[2] - gr[2] * gi[1];
-      t[1] = gr[2] * gi[0] - gr[0] * gi[2];
-      t[2] = gr[0] * gi[1] - gr[1] * gi[0];
-      const float tn = sqrtf(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
-      float grad[3];
-      rho = rho_at(F, P, grad);
-      if (!(tn > 0.f) || !(tn <= 3.402823466e38f)) {
-        fl = QTV_REFINE_NO_TANGENT;
-        t[0] = t[1] = t[2] = 0.f;
-      } else {
-        t[0] /= tn;
-        t[1] /= tn;
-        t[2] /= tn;
-        fl = QTV_REFINE_MAX_ITER;
-        while (it < A.max_iter) {
-          const float gt = grad[0] * t[0] + grad[1] * t[1] + grad[2] * t[2];
-          float g[3];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) g[a] = grad[a] - gt * t[a];
-          const float gg = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
-          if (!(gg > 0.f)) {
-            fl = QTV_REFINE_CONVERGED;
-            break;
-          }
-          const float gn = sqrtf(gg);
-          float alpha = 2.f * rho / gg;
-          bool accepted = false;
-          Pos Pn;
-          float rn = 0.f, gnext[3];
-          while (alpha * gn >= A.tol) {
-            bool ok = true;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              Pn.base[a] = P.base[a];
-              Pn.off[a] = P.off[a] - alpha * g[a];
-              // box around x0 (same base as x0)
-              ok = ok && fabsf(Pn.off[a] - P0.off[a]) <= 1.f;
-            }
-            if (ok && pos_inside(Pn, F.n)) {
-              rn = rho_at(F, Pn, gnext);
-              if (rn <= rho - 1e-4f * alpha * gg) {
-                accepted = true;
-                break;
-              }
-            }
-            alpha *= 0.5f;
-          }
-          if (!accepted) {
-            fl = QTV_REFINE_CONVERGED;
-            break;
-          }
-          ++it;
-          P = Pn;
-          rho = rn;
-          grad[0] = gnext[0];
-          grad[1] = gnext[1];
-          grad[2] = gnext[2];
-        }
-        // in-plane Jacobian of psi at the result (conditioning): basis
-        // e1 = normalize(t x a), a the axis least aligned with t; e2 = t x e1
-        int m = 0;
-        if (fabsf(t[1]) < fabsf(t[m])) m = 1;
-        if (fabsf(t[2]) < fabsf(t[m])) m = 2;
-        const float ax[3] = {m == 0 ? 1.f : 0.f, m == 1 ? 1.f : 0.f, m == 2 ? 1.f : 0.f};
-        float e1[3] = {t[1] * ax[2] - t[2] * ax[1], t[2] * ax[0] - t[0] * ax[2],
-                       t[0] * ax[1] - t[1] * ax[0]};
-        const float en = sqrtf(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
-        e1[0] /= en;
-        e1[1] /= en;
-        e1[2] /= en;
-        const float e2[3] = {t[1] * e1[2] - t[2] * e1[1], t[2] * e1[0] - t[0] * e1[2],
-                             t[0] * e1[1] - t[1] * e1[0]};
-        int cc[3];
-        float ff[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) cell_frac(P.base[a], P.off[a], F.n[a], cc[a], ff[a]);
-        float2 d[3];
-        (void)tri_eval(F, cc, ff, d);
-        float a1r = 0.f, a1i = 0.f, a2r = 0.f, a2i = 0.f;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          a1r = fmaf(d[a].x, e1[a], a1r);
-          a1i = fmaf(d[a].y, e1[a], a1i);
-          a2r = fmaf(d[a].x, e2[a], a2r);
-          a2i = fmaf(d[a].y, e2[a], a2i);
-        }
-        dj = a1r * a2i - a2r * a1i;
-      }
     }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      A.xyz[3 * qi + a] = org[a] + A.h * ((float)P.base[a] + P.off[a]);
-      if (A.tangent) A.tangent[3 * qi + a] = t[a];
+    if (!__any_sync(0xffffffffu, active || !drained)) break;
+    if (active && ref_step(A, F, S)) {
+      ref_finish(A, F, S);
+      active = false;
     }
-    if (A.rho) A.rho[qi] = rho;
-    if (A.detj) A.detj[qi] = dj;
-    if (A.iters) A.iters[qi] = it;
-    A.flags[qi] = fl;
   }
 }
 
@@ -348,12 +405,32 @@ int refine_launch(qtv_handle h, const qtv_grid& g, const float2* psi, const floa
   a.detj = detj;
   a.iters = iters;
   a.flags = flags;
+  if (!h->refine_counter) {
+    const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&h->refine_counter),
+                                     sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+      h->refine_counter = nullptr;
+      return check_cuda(e, "cudaMalloc(refine counter)");
+    }
+  }
+  // persistent: as many blocks as fit at once, fewer for short lists
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, refine_kernel, REF_THREADS, 0) !=
+            cudaSuccess ||
+        b < 1)
+      b = 1;
+    per_sm = b;
+  }
   long long blocks = ((long long)n + REF_THREADS - 1) / REF_THREADS;
-  const long long maxb = (long long)h->num_sms * 16;
+  const long long maxb = (long long)h->num_sms * per_sm;
   if (blocks > maxb) blocks = maxb;
   TraceScope ts(h, K_REFINE, st);
-  refine_kernel<<<(int)blocks, REF_THREADS, 0, st>>>(a);
-  const cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaMemsetAsync(h->refine_counter, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return check_cuda(e, "cudaMemsetAsync(refine counter)");
+  refine_kernel<<<(int)blocks, REF_THREADS, 0, st>>>(a, h->refine_counter);
+  e = cudaGetLastError();
   return check_cuda(e, "refine_kernel launch");
 }
 
