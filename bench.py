@@ -55,6 +55,8 @@ def parse():
                    help="planes of the field in the oracle's timed CPU sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=20)
+    p.add_argument("--eager", action="store_true",
+                   help="time K eager calls instead of one replay of their captured graph")
     p.add_argument("--soak", type=float, default=1.5,
                    help="seconds of untimed load before warm-up (clock sampling)")
     p.add_argument("--sweep-variant", type=int, default=-1,
@@ -674,23 +676,54 @@ def run_qtv(args):
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
+    # per-kernel times and launches per step from a traced pass (untimed: every
+    # traced launch adds two events and their device gaps)
     q.trace_enable(True)
     q.trace_read(reset=True)
+    for _ in range(10):
+        step()
+    torch.cuda.synchronize()
+    q.trace_enable(False)
+    per_kernel = q.trace_read(reset=True)
+    launches_per_step = sum(v[0] for v in per_kernel.values()) / 10
+
+    # the K timed steps as one CUDA graph (the calls allocate and synchronise
+    # nothing), the sweep of every step bracketed by event-record nodes
+    graph = torch.cuda.CUDAGraph()
+    if args.eager:
+        graph = None
+    else:
+        q.trace_enable(True, only="sweep")
+        with torch.cuda.graph(graph):
+            for _ in range(args.steps):
+                step()
+        q.trace_enable(False)
+        graph.replay()  # upload (its steps are untimed warm-up)
+        torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    if ws > 1:
+        torch.distributed.barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    if graph is None:
+        q.trace_enable(True, only="sweep")
+        q.trace_read(reset=True)
     torch.cuda.synchronize()
     t0 = time.time()
     ev0.record(stream)
-    for _ in range(args.steps):
-        step()
+    if graph is None:
+        for _ in range(args.steps):
+            step()
+    else:
+        graph.replay()
     ev1.record(stream)
     torch.cuda.synchronize()
     t1 = time.time()
-    q.trace_enable(False)
+    q.trace_enable(False, only=None)
     trace = q.trace_read(reset=True)
     ms = ev0.elapsed_time(ev1)
+    graphed = graph is not None
+    del graph  # its event-record nodes hold events the handle reuses
     if ws > 1:
         import torch.distributed as dist
 
@@ -750,7 +783,7 @@ def run_qtv(args):
     traffic = traffic_per_node * nodes if traffic_per_node is not None else None
     step_bytes = 8 * nodes + 9 * F + F * (9 + 32 + 17)
     ms_per_step = ms / args.steps
-    launches = sum(v[0] for v in trace.values())
+    launches = int(round(launches_per_step * args.steps))
 
     line = {
         "metric": METRIC,
@@ -774,7 +807,11 @@ def run_qtv(args):
                      "algorithmic_bytes": sweep_bytes,
                      "avg_ms": sweep_avg_ms},
         "step_hbm_gbs": step_bytes / (ms_per_step * 1e-3) / 1e9,
-        "kernels_ms": {k: v[1] / max(1, v[0]) for k, v in trace.items()},
+        "kernels_ms": {k: v[1] / max(1, v[0]) for k, v in per_kernel.items()},
+        "kernels_ms_source": "10 traced eager steps outside the timed region",
+        "timed_region": ("one replay of a CUDA graph of the K steps (sweeps bracketed by "
+                         "event-record nodes)" if graphed else
+                         "K eager steps (sweeps bracketed by events)"),
         "e2e": {"value": job_value(ws, nodes, ke, ms_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * nodes, "d2h_bytes_per_step": d2h // ke},
         "gpu_launches": launches,

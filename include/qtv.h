@@ -640,8 +640,21 @@ QTV_API int qtv_thin_pieces(qtv_handle h, const float* xyz, const uint32_t* node
  * and "curves" for line pieces and their curves, "thin" for their thinning).
  * qtv_trace_read waits for the recorded events, writes up to max_entries
  * per-kernel totals (launch count and summed device time) and, if reset is
- * nonzero, clears the record.  Tracing adds host work per launch; leave it
- * off outside measurement.
+ * nonzero, clears the record.  Tracing adds host work per launch and a gap
+ * of about two microseconds per event on the device; leave it off outside
+ * measurement.
+ *
+ * Calls are safe to capture into a CUDA graph (stream capture of the calling
+ * stream) once their workspace exists: the library allocates and
+ * synchronises nothing on the way, provided qtv_reserve (or one earlier call
+ * of the same shape) has sized the workspace.  A traced launch inside a
+ * capture becomes a pair of event-record nodes of the graph; the pair is
+ * timed on each replay and qtv_trace_read gives the last replay's time
+ * (read after the replay has finished; one record per captured launch).
+ *
+ * qtv_trace_filter restricts tracing to the launches of one kernel name
+ * (one of the names above; NULL or "" traces all).  QTV_ERR_ARG for an
+ * unknown name (the filter is left unchanged).
  */
 typedef struct {
   char name[24];
@@ -650,6 +663,7 @@ typedef struct {
 } qtv_trace_entry;
 
 QTV_API int qtv_trace_enable(qtv_handle h, int on);
+QTV_API int qtv_trace_filter(qtv_handle h, const char* name);
 QTV_API int qtv_trace_read(qtv_handle h, qtv_trace_entry* out, int max_entries, int* n_entries,
                            int reset);
 

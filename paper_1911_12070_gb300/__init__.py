@@ -167,9 +167,10 @@ def lib() -> ctypes.CDLL:
                      "qtv_identify_localize_host", "qtv_thin_pieces", "qtv_node_graph"):
             getattr(L, name).restype = i32
         L.qtv_trace_enable.argtypes = [P, i32]
+        L.qtv_trace_filter.argtypes = [P, ctypes.c_char_p]
         L.qtv_trace_read.argtypes = [P, ctypes.POINTER(TraceEntry), i32, ctypes.POINTER(i32), i32]
         for name in ("qtv_create", "qtv_destroy", "qtv_reserve", "qtv_identify", "qtv_localize",
-                     "qtv_emit_samples", "qtv_trace_enable", "qtv_trace_read"):
+                     "qtv_emit_samples", "qtv_trace_enable", "qtv_trace_filter", "qtv_trace_read"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -212,16 +213,19 @@ class Qtv:
         except Exception:
             pass
 
-    def trace_enable(self, on: bool = True):
+    def trace_enable(self, on: bool = True, only: str | None = None):
+        """Kernel timing trace on or off; `only` restricts it to one kernel name."""
+        _check(lib().qtv_trace_filter(self.h, (only or "").encode()))
         _check(lib().qtv_trace_enable(self.h, 1 if on else 0))
 
     def trace_read(self, reset: bool = True):
         """{kernel name: (launches, total device ms)} recorded since the last reset."""
-        buf = (TraceEntry * 16)()
+        cap = 64
+        buf = (TraceEntry * cap)()
         n = ctypes.c_int(0)
-        _check(lib().qtv_trace_read(self.h, buf, 16, ctypes.byref(n), 1 if reset else 0))
+        _check(lib().qtv_trace_read(self.h, buf, cap, ctypes.byref(n), 1 if reset else 0))
         return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
-                for i in range(min(n.value, 16))}
+                for i in range(min(n.value, cap))}
 
     def configure_sweep(self, variant: int = -1, warps_per_tile: int = 0, stages: int = 0,
                         ctas_per_sm: int = 0):

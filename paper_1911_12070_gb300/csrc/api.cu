@@ -124,11 +124,16 @@ const char* kKernelNames[K_COUNT] = {"sweep",     "seg_scan",  "scatter",      "
                                      "lines",     "curves",    "thin"};
 }  // namespace
 
+// Inside a stream capture the records become event-record nodes of the graph
+// (cudaEventRecordExternal), so each replay times the launch.
 TraceScope::TraceScope(qtv_handle h_, int k, cudaStream_t s) : h(h_), kernel(k), st(s) {
-  if (!h || !h->trace_on) return;
+  if (!h || !h->trace_on || (h->trace_only >= 0 && h->trace_only != k)) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return;
+  captured = cs == cudaStreamCaptureStatusActive;
   a = take_event(h);
   b = take_event(h);
-  if (a && b) cudaEventRecord(a, st);
+  if (a && b) cudaEventRecordWithFlags(a, st, captured ? cudaEventRecordExternal : 0u);
 }
 
 TraceScope::~TraceScope() {
@@ -137,7 +142,7 @@ TraceScope::~TraceScope() {
     if (b) h->event_pool.push_back(b);
     return;
   }
-  cudaEventRecord(b, st);
+  cudaEventRecordWithFlags(b, st, captured ? cudaEventRecordExternal : 0u);
   h->trace.push_back(TraceRec{kernel, a, b});
 }
 
@@ -286,6 +291,20 @@ int qtv_trace_enable(qtv_handle h, int on) {
   if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
   h->trace_on = on != 0;
   return QTV_OK;
+}
+
+int qtv_trace_filter(qtv_handle h, const char* name) {
+  if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
+  if (!name || !name[0]) {
+    h->trace_only = -1;
+    return QTV_OK;
+  }
+  for (int k = 0; k < K_COUNT; ++k)
+    if (strcmp(name, kKernelNames[k]) == 0) {
+      h->trace_only = k;
+      return QTV_OK;
+    }
+  return set_error(QTV_ERR_ARG, "unknown kernel name '%s'", name);
 }
 
 int qtv_trace_read(qtv_handle h, qtv_trace_entry* out, int max_entries, int* n_entries,

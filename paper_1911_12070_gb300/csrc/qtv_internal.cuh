@@ -99,6 +99,7 @@ struct qtv_handle_s {
   int num_sms = 0;
   qtv::Workspace ws;
   bool trace_on = false;
+  int trace_only = -1;                   // trace one kernel name only (-1 = all)
   std::vector<qtv::TraceRec> trace;      // recorded, not yet read
   std::vector<cudaEvent_t> event_pool;   // free events
   qtv::Locator* loc = nullptr;           // learned locator (weights, Adam state, buffers)
@@ -119,6 +120,7 @@ struct TraceScope {
   int kernel;
   cudaStream_t st;
   cudaEvent_t a = nullptr, b = nullptr;
+  bool captured = false;
   TraceScope(qtv_handle h_, int k, cudaStream_t s);
   ~TraceScope();
 };
