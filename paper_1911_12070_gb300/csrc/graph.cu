@@ -114,7 +114,8 @@ __global__ void __launch_bounds__(GT) adjacency_kernel(GraphArgs a) {
     const unsigned long long f = __ldg(a.ids + q);
     const int o = (int)(f & 3u);
     const long long lin = (long long)(f >> 2);
-    const long long i = lin % nx, j = (lin / nx) % ny, k = lin / (nx * ny);
+    long long i, j, k;
+    split_lin((unsigned long long)lin, nx, ny, i, j, k);
     uint32_t nb[10];
     int m = 0;
 #pragma unroll
@@ -165,9 +166,8 @@ __global__ void __launch_bounds__(GT) node_adjacency_kernel(GraphArgs a) {
   for (unsigned long long q = (unsigned long long)blockIdx.x * GT + threadIdx.x; q < nn;
        q += (unsigned long long)gridDim.x * GT) {
     const unsigned long long u = __ldg(a.ids + q);
-    const long long i = (long long)(u % (unsigned long long)nx);
-    const long long j = (long long)((u / (unsigned long long)nx) % (unsigned long long)ny);
-    const long long k = (long long)(u / ((unsigned long long)nx * ny));
+    long long i, j, k;
+    split_lin(u, nx, ny, i, j, k);
     const unsigned long long sxy = (unsigned long long)(nx * ny);
     uint32_t nb[6];
     int m = 0;

@@ -149,9 +149,8 @@ __device__ __forceinline__ void localize_face(const float2* __restrict__ psi, in
                                               float* resid, uint8_t* flags) {
   const int o = (int)(id & 3u);
   const unsigned long long lin = id >> 2;
-  const long long i = (long long)(lin % (unsigned long long)nx);
-  const long long j = (long long)((lin / (unsigned long long)nx) % (unsigned long long)ny);
-  const long long k = (long long)(lin / ((unsigned long long)nx * ny));
+  long long i, j, k;
+  split_lin(lin, nx, ny, i, j, k);
   const long long sx = 1, sy = nx, sz = (long long)nx * ny;
   long long du, dv;  // strides of the face axes u, v
   bool exists;

@@ -63,9 +63,8 @@ __global__ void encode_kernel(const __grid_constant__ FaceGeo geo, unsigned long
     const uint64_t id = face_ids[f];
     const int o = (int)(id & 3u);
     const unsigned long long lin = id >> 2;
-    const long long ci = (long long)(lin % (unsigned long long)nx);
-    const long long cj = (long long)((lin / (unsigned long long)nx) % (unsigned long long)ny);
-    const long long ck = (long long)(lin / ((unsigned long long)nx * ny));
+    long long ci, cj, ck;
+    split_lin(lin, nx, ny, ci, cj, ck);
     // frame axes as (dx, dy, dz) unit steps
     int ux = 0, uy = 0, uz = 0, vx = 0, vy = 0, vz = 0, wx = 0, wy = 0, wz = 0;
     if (o == 0) { ux = 1; vy = 1; wz = 1; }
@@ -452,9 +451,8 @@ __global__ void head_kernel(const __grid_constant__ FaceGeo geo, unsigned long l
     if (use) use = u >= -0.01f && u <= 1.01f && v >= -0.01f && v <= 1.01f;
     const int o = (int)(id & 3u);
     const unsigned long long lin = id >> 2;
-    const long long i = (long long)(lin % (unsigned long long)nx);
-    const long long j = (long long)((lin / (unsigned long long)nx) % (unsigned long long)ny);
-    const long long k = (long long)(lin / ((unsigned long long)nx * ny));
+    long long i, j, k;
+    split_lin(lin, nx, ny, i, j, k);
     if (use) {
       const long long sx = 1, sy = nx, sz = (long long)nx * ny;
       const long long du = o == 0 ? sx : (o == 1 ? sy : sz);

@@ -266,6 +266,23 @@ inline FaceGeo single_geo(const qtv_grid& g, const float2* psi) {
   return f;
 }
 #ifdef __CUDACC__
+// (i, j, k) of the linear node index lin = (k ny + j) nx + i; two divisions,
+// in 32 bits whenever lin fits (every grid below 2^32 nodes)
+__device__ __forceinline__ void split_lin(unsigned long long lin, long long nx, long long ny,
+                                          long long& i, long long& j, long long& k) {
+  if ((lin >> 32) == 0ull) {
+    const uint32_t l = (uint32_t)lin, q1 = l / (uint32_t)nx, q2 = q1 / (uint32_t)ny;
+    i = (long long)(l - q1 * (uint32_t)nx);
+    j = (long long)(q1 - q2 * (uint32_t)ny);
+    k = (long long)q2;
+  } else {
+    const unsigned long long q1 = lin / (unsigned long long)nx, q2 = q1 / (unsigned long long)ny;
+    i = (long long)(lin - q1 * (unsigned long long)nx);
+    j = (long long)(q1 - q2 * (unsigned long long)ny);
+    k = (long long)q2;
+  }
+}
+
 // snapshot of face f: the largest s with offsets[s] <= f
 __device__ __forceinline__ int geo_snapshot(const FaceGeo& G, unsigned long long f) {
   if (G.n <= 1) return 0;
@@ -284,6 +301,8 @@ int bulk_variant_occupancy(int nw, int* ctas_per_sm, size_t* smem);
 int bits_variant_occupancy(int nw, int stages, int* ctas_per_sm, size_t* smem);
 void bits_sweep_launch(const BulkParams& p, int grid, int nw, int stages, size_t smem,
                        cudaStream_t st);
+// resident CTAs per SM of the bit-sliced expand kernel (its launch bound)
+constexpr int kBitsExpandCtasPerSm = 3;
 void bits_expand_launch(const BulkParams& p, int blocks, const unsigned long long* seg_off,
                         uint64_t* face_ids, int8_t* winding, unsigned long long capacity,
                         uint64_t* offsets, cudaStream_t st);

@@ -174,9 +174,11 @@ __device__ __forceinline__ bool ref_init(const RefArgs& A, const Field& F, unsig
     const uint64_t id = A.face_ids[qi];
     const int o = (int)(id & 3u);
     const unsigned long long lin = id >> 2;
-    S.P0.base[0] = (int)(lin % (unsigned long long)A.nx);
-    S.P0.base[1] = (int)((lin / (unsigned long long)A.nx) % (unsigned long long)A.ny);
-    S.P0.base[2] = (int)(lin / ((unsigned long long)A.nx * A.ny));
+    long long i, j, k;
+    split_lin(lin, A.nx, A.ny, i, j, k);
+    S.P0.base[0] = (int)i;
+    S.P0.base[1] = (int)j;
+    S.P0.base[2] = (int)k;
     // face centre: half a cell along the two in-plane axes
     S.P0.off[0] = (o == 0 || o == 2) ? 0.5f : 0.f;
     S.P0.off[1] = (o == 0 || o == 1) ? 0.5f : 0.f;

@@ -402,13 +402,14 @@ __global__ void __launch_bounds__(NW * 32, MINB) sweep_bits_kernel(const __grid_
 // order of the records), within a node by orientation.
 // ---------------------------------------------------------------------------
 constexpr int kExpandWarps = 8;
+constexpr int kHeld = 3;  // record chunks (of 32) a warp keeps in registers
 
 // bits 4q..4q+3 of m spread to the low bit of bytes 0..3
 __device__ __forceinline__ uint32_t spread4(uint32_t m, int q) {
   return (((m >> (4 * q)) & 0xFu) * 0x00204081u) & 0x01010101u;
 }
 
-__global__ void __launch_bounds__(32 * kExpandWarps, 4) expand_bits_kernel(
+__global__ void __launch_bounds__(32 * kExpandWarps, kBitsExpandCtasPerSm) expand_bits_kernel(
     const __grid_constant__ BulkParams a, const unsigned long long* __restrict__ seg_off,
     uint64_t* __restrict__ face_ids, int8_t* __restrict__ winding, unsigned long long capacity,
     uint64_t* __restrict__ offsets) {
@@ -443,6 +444,7 @@ __global__ void __launch_bounds__(32 * kExpandWarps, 4) expand_bits_kernel(
       eidx = (unsigned long long)sd.tab0 + ((unsigned long long)band * NW + lane) * sd.nz + k;
       e = table[eidx];
     }
+    const unsigned long long fbase = seg_off[s];  // loaded alongside the entries
     const uint32_t n = __popc(e.x);
     uint32_t incl = n;
 #pragma unroll
@@ -453,7 +455,6 @@ __global__ void __launch_bounds__(32 * kExpandWarps, 4) expand_bits_kernel(
     const uint32_t start = lane < NW ? incl - n : 0xFFFFFFFFu;
     const uint32_t rtot = __shfl_sync(0xffffffffu, incl, 31);
     if (rtot == 0) continue;
-    const unsigned long long fbase = seg_off[s];
     const unsigned long long nx = (unsigned)sd.nx, ny = (unsigned)sd.ny;
     const long long j0 = band * BR;
     const int nwt = sd.nwt;
@@ -504,32 +505,20 @@ __global__ void __launch_bounds__(32 * kExpandWarps, 4) expand_bits_kernel(
       return (wv[r >> 2] >> (8 * (r & 3))) & 0xFFu;
     };
 
+    // faces per row (pass 1), then in place the running base of each row (pass 2)
     uint32_t rowbase[BR];
-    {
-      uint32_t rowtot[BR];
 #pragma unroll
-      for (int r = 0; r < BR; ++r) rowtot[r] = 0;
-      for (uint32_t c = 0; c < nchunks; ++c) {
-        uint4 rec;
-        int ww;
-        load(c * 32, rec, ww);
-        uint32_t cw[4], ex[4], tot[4];
-        counts(rec, cw);
-        scan4(cw, ex, tot);
+    for (int r = 0; r < BR; ++r) rowbase[r] = 0;
+    // pass 1: faces per row over the segment's records
+    auto tally = [&](const uint4& rec) {
+      uint32_t cw[4], ex[4], tot[4];
+      counts(rec, cw);
+      scan4(cw, ex, tot);
 #pragma unroll
-        for (int r = 0; r < BR; ++r) rowtot[r] += byte_of(tot, r);
-      }
-      uint32_t acc = 0;
-#pragma unroll
-      for (int r = 0; r < BR; ++r) {
-        rowbase[r] = acc;
-        acc += rowtot[r];
-      }
-    }
-    for (uint32_t c = 0; c < nchunks; ++c) {
-      uint4 rec;
-      int ww;
-      load(c * 32, rec, ww);
+      for (int r = 0; r < BR; ++r) rowbase[r] += byte_of(tot, r);
+    };
+    // pass 2: the faces of a chunk of records at their row-major positions
+    auto emit = [&](const uint4& rec, int ww) {
       uint32_t cw[4], ex[4], tot[4];
       counts(rec, cw);
       scan4(cw, ex, tot);
@@ -568,6 +557,46 @@ __global__ void __launch_bounds__(32 * kExpandWarps, 4) expand_bits_kernel(
       }
 #pragma unroll
       for (int r = 0; r < BR; ++r) rowbase[r] += byte_of(tot, r);
+    };
+    auto bases = [&]() {
+      uint32_t acc = 0;
+#pragma unroll
+      for (int r = 0; r < BR; ++r) {
+        const uint32_t t = rowbase[r];
+        rowbase[r] = acc;
+        acc += t;
+      }
+    };
+
+    if (nchunks <= (uint32_t)kHeld) {
+      // the usual case: every record load of the segment in flight at once,
+      // the records held in registers for both passes
+      uint4 hrec[kHeld];
+      int hww[kHeld];
+#pragma unroll
+      for (int c = 0; c < kHeld; ++c)
+        if ((uint32_t)c < nchunks) load(c * 32, hrec[c], hww[c]);
+#pragma unroll
+      for (int c = 0; c < kHeld; ++c)
+        if ((uint32_t)c < nchunks) tally(hrec[c]);
+      bases();
+#pragma unroll
+      for (int c = 0; c < kHeld; ++c)
+        if ((uint32_t)c < nchunks) emit(hrec[c], hww[c]);
+    } else {
+      for (uint32_t c = 0; c < nchunks; ++c) {
+        uint4 rec;
+        int ww;
+        load(c * 32, rec, ww);
+        tally(rec);
+      }
+      bases();
+      for (uint32_t c = 0; c < nchunks; ++c) {
+        uint4 rec;
+        int ww;
+        load(c * 32, rec, ww);
+        emit(rec, ww);
+      }
     }
   }
 }

@@ -1031,7 +1031,7 @@ int batch_layout(int num_sms, int nsnap, const qtv_grid* grids, const float2* co
   B->recs_need = bits ? (unsigned long long)tab * 32ull : capacity + slack;
   B->table_need = (unsigned long long)tab;
   B->expand_blocks = (int)std::min<long long>((nseg + kExpandWarps - 1) / kExpandWarps,
-                                              (long long)num_sms * 4);
+                                              (long long)num_sms * (bits ? kBitsExpandCtasPerSm : 4));
   return QTV_OK;
 }
 

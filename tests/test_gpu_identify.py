@@ -72,6 +72,16 @@ def test_ragged_random_waves_bit_exact(q, shape):
     assert n > 0
 
 
+@pytest.mark.parametrize("shape,kmin,kmax", [((10, 40, 992), 0.9, 1.5), ((9, 35, 500), 0.5, 0.9),
+                                             ((7, 20, 300), 1.2, 2.0)])
+def test_dense_tangles_bit_exact(q, shape, kmin, kmax):
+    # short wavelengths: a plane band holds hundreds of lanes with faces, so the
+    # expand pass takes both its register-held and its reloading path
+    psi = synth.random_waves_numpy(shape, synth.wave_spec(sum(shape), 512, kmin=kmin, kmax=kmax))
+    n, namb, damb = _check_full(q, psi)
+    assert n > 0.03 * psi.size
+
+
 @pytest.mark.parametrize("shape", [(1, 1, 1), (2, 2, 2), (1, 5, 6), (3, 1, 7), (4, 6, 1),
                                    (2, 9, 3)])
 def test_degenerate_grids(q, shape):
