@@ -6,18 +6,22 @@
 namespace qtv {
 namespace {
 
-__global__ void localize_kernel(const float2* __restrict__ psi, int nx, int ny, int nz, float h,
-                                float ox, float oy, float oz, const uint64_t* __restrict__ face_ids,
-                                const int8_t* __restrict__ winding, unsigned long long n,
-                                const uint64_t* __restrict__ n_dev, float* __restrict__ xyz,
-                                float* __restrict__ resid, uint8_t* __restrict__ flags) {
+// One face per thread (two per thread with both faces' loads in flight was
+// slower: 75 registers cost more occupancy than the second face hid latency).
+constexpr int kLocThreads = 256;
+
+__global__ void __launch_bounds__(kLocThreads) localize_kernel(
+    const float2* __restrict__ psi, int nx, int ny, int nz, float h, float ox, float oy, float oz,
+    const uint64_t* __restrict__ face_ids, const int8_t* __restrict__ winding,
+    unsigned long long n, const uint64_t* __restrict__ n_dev, float* __restrict__ xyz,
+    float* __restrict__ resid, uint8_t* __restrict__ flags) {
   unsigned long long nn = n;
   if (n_dev) {
     const unsigned long long d = *n_dev;
     nn = d < n ? d : n;
   }
-  for (unsigned long long f = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; f < nn;
-       f += (unsigned long long)gridDim.x * blockDim.x) {
+  for (unsigned long long f = (unsigned long long)blockIdx.x * kLocThreads + threadIdx.x; f < nn;
+       f += (unsigned long long)gridDim.x * kLocThreads) {
     float p[3], r;
     uint8_t fl;
     loc::localize_face(psi, nx, ny, nz, h, ox, oy, oz, face_ids[f], winding[f], p, &r, &fl);
@@ -56,9 +60,9 @@ int localize_launch(qtv_handle h, const qtv_grid& g, const float2* psi, const ui
                     float* resid, uint8_t* flags, cudaStream_t st) {
   if (n == 0) return QTV_OK;
   TraceScope ts(h, K_LOCALIZE, st);
-  unsigned long long blocks = (n + 255) / 256;
+  unsigned long long blocks = (n + kLocThreads - 1) / kLocThreads;
   if (blocks > 65535ull * 4) blocks = 65535ull * 4;
-  localize_kernel<<<(unsigned)blocks, 256, 0, st>>>(psi, g.nx, g.ny, g.nz, g.h, g.origin[0],
+  localize_kernel<<<(unsigned)blocks, kLocThreads, 0, st>>>(psi, g.nx, g.ny, g.nz, g.h, g.origin[0],
                                                     g.origin[1],
                                                     g.origin[2], face_ids, winding, n, n_dev, xyz,
                                                     resid, flags);

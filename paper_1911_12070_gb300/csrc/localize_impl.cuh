@@ -141,50 +141,70 @@ __device__ __forceinline__ bool solve_face(const C2 P[4], float& uo, float& vo, 
 }
 
 
-// Localize one face given its id, winding and the field: position (grid
-// coordinates scaled by h and shifted by the origin), residual, flags.
-__device__ __forceinline__ void localize_face(const float2* __restrict__ psi, int nx, int ny, int nz,
-                                              float h, float ox, float oy, float oz,
-                                              unsigned long long id, int wv, float* xyz,
-                                              float* resid, uint8_t* flags) {
+// A face's grid position and corner values (the loads of its localization).
+struct FaceIn {
+  long long i, j, k;
+  int o;
+  bool exists;
+  C2 P[4];
+};
+
+__device__ __forceinline__ void face_load(const float2* __restrict__ psi, int nx, int ny, int nz,
+                                          unsigned long long id, FaceIn& F) {
   const int o = (int)(id & 3u);
   const unsigned long long lin = id >> 2;
-  long long i, j, k;
-  split_lin(lin, nx, ny, i, j, k);
+  split_lin(lin, nx, ny, F.i, F.j, F.k);
+  F.o = o;
   const long long sx = 1, sy = nx, sz = (long long)nx * ny;
   long long du, dv;  // strides of the face axes u, v
   bool exists;
-  if (o == 0) { du = sx; dv = sy; exists = i + 1 < nx && j + 1 < ny; }
-  else if (o == 1) { du = sy; dv = sz; exists = j + 1 < ny && k + 1 < nz; }
-  else { du = sz; dv = sx; exists = k + 1 < nz && i + 1 < nx; }
-  if (o == 3 || !exists || k >= nz) {
-    // not a face of this grid: flag it and touch no node
+  if (o == 0) { du = sx; dv = sy; exists = F.i + 1 < nx && F.j + 1 < ny; }
+  else if (o == 1) { du = sy; dv = sz; exists = F.j + 1 < ny && F.k + 1 < nz; }
+  else { du = sz; dv = sx; exists = F.k + 1 < nz && F.i + 1 < nx; }
+  F.exists = o != 3 && exists && F.k < nz;
+  if (!F.exists) return;  // not a face of this grid: touch no node
+  const long long base = (long long)lin;
+  const float2 p0 = __ldg(psi + base), p1 = __ldg(psi + base + du);
+  const float2 p2 = __ldg(psi + base + du + dv), p3 = __ldg(psi + base + dv);
+  F.P[0] = mk(p0.x, p0.y);
+  F.P[1] = mk(p1.x, p1.y);
+  F.P[2] = mk(p2.x, p2.y);
+  F.P[3] = mk(p3.x, p3.y);
+}
+
+// The zero of a loaded face: position (grid coordinates scaled by h and
+// shifted by the origin), residual, flags.
+__device__ __forceinline__ void face_solve(const FaceIn& F, int wv, float h, float ox, float oy,
+                                           float oz, float* xyz, float* resid, uint8_t* flags) {
+  if (!F.exists) {
     xyz[0] = xyz[1] = xyz[2] = __int_as_float(0x7fc00000);
     *resid = __int_as_float(0x7fc00000);
     *flags = QTV_FLAG_ANOMALOUS;
     return;
   }
-  const long long base = (long long)lin;
-  C2 P[4];
-  const float2 p0 = __ldg(psi + base), p1 = __ldg(psi + base + du);
-  const float2 p2 = __ldg(psi + base + du + dv), p3 = __ldg(psi + base + dv);
-  P[0] = mk(p0.x, p0.y);
-  P[1] = mk(p1.x, p1.y);
-  P[2] = mk(p2.x, p2.y);
-  P[3] = mk(p3.x, p3.y);
   float u, v, f2;
-  const bool ok = solve_face(P, u, v, f2);
+  const bool ok = solve_face(F.P, u, v, f2);
   uint8_t fl = 0;
   if (!ok || (wv != 1 && wv != -1)) fl |= QTV_FLAG_ANOMALOUS;
-  float gx = (float)i, gy = (float)j, gz = (float)k;
-  if (o == 0) { gx = __fadd_rn(gx, u); gy = __fadd_rn(gy, v); }
-  else if (o == 1) { gy = __fadd_rn(gy, u); gz = __fadd_rn(gz, v); }
+  float gx = (float)F.i, gy = (float)F.j, gz = (float)F.k;
+  if (F.o == 0) { gx = __fadd_rn(gx, u); gy = __fadd_rn(gy, v); }
+  else if (F.o == 1) { gy = __fadd_rn(gy, u); gz = __fadd_rn(gz, v); }
   else { gz = __fadd_rn(gz, u); gx = __fadd_rn(gx, v); }
   xyz[0] = fmaf(h, gx, ox);
   xyz[1] = fmaf(h, gy, oy);
   xyz[2] = fmaf(h, gz, oz);
   *resid = f2;
   *flags = fl;
+}
+
+// Localize one face given its id, winding and the field.
+__device__ __forceinline__ void localize_face(const float2* __restrict__ psi, int nx, int ny, int nz,
+                                              float h, float ox, float oy, float oz,
+                                              unsigned long long id, int wv, float* xyz,
+                                              float* resid, uint8_t* flags) {
+  FaceIn F;
+  face_load(psi, nx, ny, nz, id, F);
+  face_solve(F, wv, h, ox, oy, oz, xyz, resid, flags);
 }
 
 }  // namespace loc

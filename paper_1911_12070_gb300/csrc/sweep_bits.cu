@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kBitsExpandCtasPerSm) expan
     const __grid_constant__ BulkParams a, const unsigned long long* __restrict__ seg_off,
     uint64_t* __restrict__ face_ids, int8_t* __restrict__ winding, unsigned long long capacity,
     uint64_t* __restrict__ offsets) {
-  __shared__ uint32_t s_rowbase[kExpandWarps][BR];
+  __shared__ uint32_t s_rowbase[kExpandWarps][BR / 2];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint2* __restrict__ table = reinterpret_cast<const uint2*>(a.table);
   const uint4* __restrict__ recs = reinterpret_cast<const uint4*>(a.recs);
@@ -501,22 +501,30 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kBitsExpandCtasPerSm) expan
         tot[q] = __shfl_sync(0xffffffffu, v, 31);
       }
     };
-    auto byte_of = [](const uint32_t* wv, int r) -> uint32_t {
-      return (wv[r >> 2] >> (8 * (r & 3))) & 0xFFu;
-    };
 
     // faces per row (pass 1), then in place the running base of each row (pass 2)
-    uint32_t rowbase[BR];
+    // Faces per row, then each row's running base, as 16-bit halves: row r in
+    // word 2 (r >> 2) + (r & 1), half (r >> 1) & 1 (the layout of the byte
+    // counts' even and odd bytes).  A segment holds at most 3 x 16 x 992 faces
+    // (32 warps of 31 columns), below 2^16.
+    uint32_t racc[BR / 2];
 #pragma unroll
-    for (int r = 0; r < BR; ++r) rowbase[r] = 0;
+    for (int q = 0; q < BR / 2; ++q) racc[q] = 0;
+    auto add_tot = [&](const uint32_t* tot) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        racc[2 * q] += tot[q] & 0x00FF00FFu;
+        racc[2 * q + 1] += (tot[q] >> 8) & 0x00FF00FFu;
+      }
+    };
     // pass 1: faces per row over the segment's records
     auto tally = [&](const uint4& rec) {
       uint32_t cw[4], ex[4], tot[4];
       counts(rec, cw);
       scan4(cw, ex, tot);
-#pragma unroll
-      for (int r = 0; r < BR; ++r) rowbase[r] += byte_of(tot, r);
+      add_tot(tot);
     };
+    const unsigned long long lin0 = ((unsigned long long)k * ny + (unsigned long long)j0) * nx;
     // pass 2: the faces of a chunk of records at their row-major positions
     auto emit = [&](const uint4& rec, int ww) {
       uint32_t cw[4], ex[4], tot[4];
@@ -528,19 +536,22 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kBitsExpandCtasPerSm) expan
       const uint32_t rows = mx | my | mz;
       if (rows) {
 #pragma unroll
-        for (int r = 0; r < BR; ++r) s_rowbase[wib][r] = rowbase[r];
+        for (int q = 0; q < BR / 2; ++q) s_rowbase[wib][q] = racc[q];
         // column of the record: tile ww / nwt at tile * st, warp ww % nwt of
         // the tile at 31 columns each, lane in the record
         const unsigned tile = (unsigned)ww / (unsigned)nwt;
-        const unsigned long long x = (unsigned long long)tile * (unsigned)sd.st +
-                                     (unsigned long long)BL * ((unsigned)ww - tile * (unsigned)nwt) +
-                                     (rec.w & 31u);
+        const uint32_t x = tile * (unsigned)sd.st + (uint32_t)BL * ((unsigned)ww - tile * (unsigned)nwt) +
+                           (rec.w & 31u);
         uint32_t rm = rows;
         while (rm) {
           const int r = __ffs(rm) - 1;
           rm &= rm - 1u;
-          unsigned long long pos = fbase + s_rowbase[wib][r] + byte_of(ex, r);
-          const unsigned long long lin = ((unsigned long long)k * ny + (unsigned long long)(j0 + r)) * nx + x;
+          const int q = r >> 2;
+          const uint32_t exq = q == 0 ? ex[0] : (q == 1 ? ex[1] : (q == 2 ? ex[2] : ex[3]));
+          const uint32_t rb =
+              (s_rowbase[wib][2 * q + (r & 1)] >> (16 * ((r >> 1) & 1))) & 0xFFFFu;
+          unsigned long long pos = fbase + rb + ((exq >> (8 * (r & 3))) & 0xFFu);
+          const unsigned long long lin = lin0 + (unsigned long long)((uint32_t)r * (uint32_t)nx + x);
           const uint32_t Ls[3] = {rec.x, rec.y, rec.z};
 #pragma unroll
           for (int o = 0; o < 3; ++o) {
@@ -555,17 +566,22 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kBitsExpandCtasPerSm) expan
           }
         }
       }
-#pragma unroll
-      for (int r = 0; r < BR; ++r) rowbase[r] += byte_of(tot, r);
+      add_tot(tot);
     };
+    // row totals -> exclusive row bases, in place
     auto bases = [&]() {
-      uint32_t acc = 0;
+      uint32_t acc = 0, out[BR / 2];
+#pragma unroll
+      for (int q = 0; q < BR / 2; ++q) out[q] = 0;
 #pragma unroll
       for (int r = 0; r < BR; ++r) {
-        const uint32_t t = rowbase[r];
-        rowbase[r] = acc;
+        const int wi = 2 * (r >> 2) + (r & 1), sh = 16 * ((r >> 1) & 1);
+        const uint32_t t = (racc[wi] >> sh) & 0xFFFFu;
+        out[wi] |= acc << sh;
         acc += t;
       }
+#pragma unroll
+      for (int q = 0; q < BR / 2; ++q) racc[q] = out[q];
     };
 
     if (nchunks <= (uint32_t)kHeld) {
