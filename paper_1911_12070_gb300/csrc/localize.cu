@@ -15,6 +15,7 @@ __global__ void __launch_bounds__(kLocThreads) localize_kernel(
     const uint64_t* __restrict__ face_ids, const int8_t* __restrict__ winding,
     unsigned long long n, const uint64_t* __restrict__ n_dev, float* __restrict__ xyz,
     float* __restrict__ resid, uint8_t* __restrict__ flags) {
+  pdl_wait();  // the face list (and its count) of the previous kernel
   unsigned long long nn = n;
   if (n_dev) {
     const unsigned long long d = *n_dev;
@@ -62,11 +63,12 @@ int localize_launch(qtv_handle h, const qtv_grid& g, const float2* psi, const ui
   TraceScope ts(h, K_LOCALIZE, st);
   unsigned long long blocks = (n + kLocThreads - 1) / kLocThreads;
   if (blocks > 65535ull * 4) blocks = 65535ull * 4;
-  localize_kernel<<<(unsigned)blocks, kLocThreads, 0, st>>>(psi, g.nx, g.ny, g.nz, g.h, g.origin[0],
-                                                    g.origin[1],
-                                                    g.origin[2], face_ids, winding, n, n_dev, xyz,
-                                                    resid, flags);
-  return check_cuda(cudaGetLastError(), "localize_kernel launch");
+  cudaError_t e = launch_dependent(localize_kernel, dim3((unsigned)blocks), dim3(kLocThreads), 0,
+                                   st, psi, g.nx, g.ny, g.nz, g.h, g.origin[0], g.origin[1],
+                                   g.origin[2], face_ids, winding, (unsigned long long)n, n_dev,
+                                   xyz, resid, flags);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return check_cuda(e, "localize_kernel launch");
 }
 
 int emit_pack_launch(qtv_handle h, uint64_t n, const uint64_t* face_ids, const int8_t* winding,

@@ -14,6 +14,36 @@ namespace qtv {
 int set_error(int code, const char* fmt, ...);
 int check_cuda(cudaError_t e, const char* what);
 
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch.  A kernel launched by launch_dependent may
+// start while the previous kernel of the stream is still running: its blocks
+// wait in pdl_wait() (first statement, before any global memory access) until
+// that kernel has finished and its writes are visible.  pdl_trigger() in the
+// previous kernel lets the dependent launch before all of its blocks exit
+// (once every block has triggered); without it, at exit.  Outside such a
+// launch both are no-ops.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dependent(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                    cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Makes a device current for a scope and restores the caller's device.
 struct DeviceGuard {
   int prev = -1;
@@ -303,9 +333,9 @@ void bits_sweep_launch(const BulkParams& p, int grid, int nw, int stages, size_t
                        cudaStream_t st);
 // resident CTAs per SM of the bit-sliced expand kernel (its launch bound)
 constexpr int kBitsExpandCtasPerSm = 3;
-void bits_expand_launch(const BulkParams& p, int blocks, const unsigned long long* seg_off,
-                        uint64_t* face_ids, int8_t* winding, unsigned long long capacity,
-                        uint64_t* offsets, cudaStream_t st);
+cudaError_t bits_expand_launch(const BulkParams& p, int blocks, const unsigned long long* seg_off,
+                               uint64_t* face_ids, int8_t* winding, unsigned long long capacity,
+                               uint64_t* offsets, cudaStream_t st);
 int batch_layout(int num_sms, int nsnap, const qtv_grid* grids, const float2* const* psis,
                  const TileConfig& tc, uint64_t capacity, uint64_t max_warps, BatchLayout* B);
 int batch_launch(qtv_handle h, BatchLayout& B, const IdentScratch& sc, uint64_t* face_ids,

@@ -124,6 +124,7 @@ __device__ __forceinline__ uint32_t bad_bit(float2 v) {
 template <int NW, int MINB, int STAGES>
 __global__ void __launch_bounds__(NW * 32, MINB) sweep_bits_kernel(const __grid_constant__ BulkParams a) {
   extern __shared__ __align__(128) unsigned char dsm[];
+  pdl_trigger();  // the segment scan may queue behind this grid's blocks
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int w = tid >> 5;
@@ -414,6 +415,8 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kBitsExpandCtasPerSm) expan
     uint64_t* __restrict__ face_ids, int8_t* __restrict__ winding, unsigned long long capacity,
     uint64_t* __restrict__ offsets) {
   __shared__ uint32_t s_rowbase[kExpandWarps][BR / 2];
+  pdl_wait();  // segment offsets and counts of the scan
+  pdl_trigger();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint2* __restrict__ table = reinterpret_cast<const uint2*>(a.table);
   const uint4* __restrict__ recs = reinterpret_cast<const uint4*>(a.recs);
@@ -667,11 +670,11 @@ void bits_sweep_launch(const BulkParams& p, int grid, int nw, int stages, size_t
   bits_fn(nw, stages)<<<grid, nw * 32, smem, st>>>(p);
 }
 
-void bits_expand_launch(const BulkParams& p, int blocks, const unsigned long long* seg_off,
-                        uint64_t* face_ids, int8_t* winding, unsigned long long capacity,
-                        uint64_t* offsets, cudaStream_t st) {
-  expand_bits_kernel<<<blocks, 32 * kExpandWarps, 0, st>>>(p, seg_off, face_ids, winding,
-                                                           capacity, offsets);
+cudaError_t bits_expand_launch(const BulkParams& p, int blocks, const unsigned long long* seg_off,
+                               uint64_t* face_ids, int8_t* winding, unsigned long long capacity,
+                               uint64_t* offsets, cudaStream_t st) {
+  return launch_dependent(expand_bits_kernel, dim3(blocks), dim3(32 * kExpandWarps), 0, st, p,
+                          seg_off, face_ids, winding, capacity, offsets);
 }
 
 }  // namespace qtv

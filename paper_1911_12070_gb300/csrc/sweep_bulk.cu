@@ -550,6 +550,8 @@ __global__ void __launch_bounds__(kScanThreads) v3_scan_kernel(
   __shared__ unsigned long long s_warp[kScanThreads / 32];
   __shared__ unsigned long long s_prefix;
   __shared__ long long s_tile;
+  pdl_wait();  // segment totals of the sweeps
+  pdl_trigger();
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid == 0) s_tile = (long long)atomicAdd(counters + 2, 1ull);
   __syncthreads();
@@ -651,6 +653,8 @@ __global__ void __launch_bounds__(32 * kExpandWarps, 4) v3_expand_kernel(
     uint64_t* __restrict__ face_ids, int8_t* __restrict__ winding, unsigned long long capacity,
     uint64_t* __restrict__ offsets) {
   __shared__ uint32_t s_rowbase[kExpandWarps][R];
+  pdl_wait();  // segment offsets and counts of the scan
+  pdl_trigger();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint4* __restrict__ table = a.table;
   const uint32_t* __restrict__ recs = a.recs;
@@ -1105,11 +1109,11 @@ int batch_launch(qtv_handle h, BatchLayout& B, const IdentScratch& sc, uint64_t*
   if (rc) return rc;
   {
     TraceScope ts(h, K_SEG_SCAN, st);
-    v3_scan_kernel<<<(unsigned)B.ntiles, kScanThreads, 0, st>>>(
-        reinterpret_cast<const unsigned int*>(sc.seg), B.fin.nseg, sc.seg_off, count, sc.counters,
-        sc.tiles, B.ntiles, stats, scanned);
+    e = launch_dependent(v3_scan_kernel, dim3((unsigned)B.ntiles), dim3(kScanThreads), 0, st,
+                         reinterpret_cast<const unsigned int*>(sc.seg), B.fin.nseg, sc.seg_off,
+                         count, sc.counters, sc.tiles, B.ntiles, stats, scanned);
   }
-  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return check_cuda(e, "v3_scan_kernel launch");
   if (capacity > 0 || expand_always) {
     BulkParams& p = B.fin;
@@ -1120,11 +1124,13 @@ int batch_launch(qtv_handle h, BatchLayout& B, const IdentScratch& sc, uint64_t*
     p.segf = reinterpret_cast<unsigned int*>(sc.seg);
     TraceScope ts(h, K_SCATTER, st);
     if (B.variant == 1)
-      bits_expand_launch(p, B.expand_blocks, sc.seg_off, face_ids, winding, capacity, offsets, st);
+      e = bits_expand_launch(p, B.expand_blocks, sc.seg_off, face_ids, winding, capacity, offsets,
+                             st);
     else
-      v3_expand_kernel<<<(unsigned)B.expand_blocks, 32 * kExpandWarps, 0, st>>>(
-          p, sc.seg_off, face_ids, winding, capacity, offsets);
-    e = cudaGetLastError();
+      e = launch_dependent(v3_expand_kernel, dim3((unsigned)B.expand_blocks),
+                           dim3(32 * kExpandWarps), 0, st, p, sc.seg_off, face_ids, winding,
+                           capacity, offsets);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return check_cuda(e, "v3_expand_kernel launch");
   }
   return QTV_OK;
