@@ -137,14 +137,58 @@ __device__ __forceinline__ bool pos_inside(const Pos& P, const int n[3]) {
   return true;
 }
 
-// rho and grad rho at P
-__device__ __forceinline__ float rho_at(const Field& F, const Pos& P, float g[3]) {
+// The eight corner values of the cell last evaluated: a search rarely
+// leaves its cell, so most evaluations read no memory.
+struct CellCache {
+  int c[3];
+  float2 v[8];
+};
+
+// rho and grad rho at P: trilinear psi and its derivatives from the corners
+// in the same order and arithmetic as tri_eval
+__device__ __forceinline__ float rho_at(const Field& F, const Pos& P, float g[3], CellCache& C) {
   int c[3];
   float f[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) cell_frac(P.base[a], P.off[a], F.n[a], c[a], f[a]);
+  if (c[0] != C.c[0] || c[1] != C.c[1] || c[2] != C.c[2]) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int idx[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int bit = (q >> a) & 1;
+        idx[a] = c[a] + bit < F.n[a] ? c[a] + bit : c[a];
+      }
+      C.v[q] = F.at(idx[0], idx[1], idx[2]);
+    }
+    C.c[0] = c[0];
+    C.c[1] = c[1];
+    C.c[2] = c[2];
+  }
+  float2 v = make_float2(0.f, 0.f);
   float2 d[3];
-  const float2 v = tri_eval(F, c, f, d);
+  d[0] = d[1] = d[2] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    float w[3], s[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int bit = (q >> a) & 1;
+      w[a] = bit ? f[a] : 1.f - f[a];
+      s[a] = bit ? 1.f : -1.f;
+    }
+    const float2 u = C.v[q];
+    const float wt = w[0] * w[1] * w[2];
+    v.x = fmaf(wt, u.x, v.x);
+    v.y = fmaf(wt, u.y, v.y);
+    const float dd[3] = {s[0] * w[1] * w[2], w[0] * s[1] * w[2], w[0] * w[1] * s[2]};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      d[a].x = fmaf(dd[a], u.x, d[a].x);
+      d[a].y = fmaf(dd[a], u.y, d[a].y);
+    }
+  }
 #pragma unroll
   for (int a = 0; a < 3; ++a) g[a] = 2.f * fmaf(v.x, d[a].x, v.y * d[a].y);
   return fmaf(v.x, v.x, v.y * v.y);
@@ -159,6 +203,7 @@ struct RState {
   int it;
   uint8_t fl;
   unsigned long long qi;
+  CellCache cache;
 };
 
 // x0, tangent, rho and grad rho at x0; true when the descent is to run
@@ -167,6 +212,7 @@ __device__ __forceinline__ bool ref_init(const RefArgs& A, const Field& F, unsig
   const float org[3] = {A.ox, A.oy, A.oz};
   S.qi = qi;
   S.it = 0;
+  S.cache.c[0] = -1;  // no cell loaded
   S.t[0] = S.t[1] = S.t[2] = 0.f;
   S.rho = __int_as_float(0x7fc00000);
   bool in0 = true;
@@ -226,7 +272,7 @@ __device__ __forceinline__ bool ref_init(const RefArgs& A, const Field& F, unsig
   t[1] = gr[2] * gi[0] - gr[0] * gi[2];
   t[2] = gr[0] * gi[1] - gr[1] * gi[0];
   const float tn = sqrtf(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
-  S.rho = rho_at(F, S.P, S.grad);
+  S.rho = rho_at(F, S.P, S.grad, S.cache);
   if (!(tn > 0.f) || !(tn <= 3.402823466e38f)) {
     S.fl = QTV_REFINE_NO_TANGENT;
     return false;
@@ -265,7 +311,7 @@ __device__ __forceinline__ bool ref_step(const RefArgs& A, const Field& F, RStat
       ok = ok && fabsf(Pn.off[a] - S.P0.off[a]) <= 1.f;
     }
     if (ok && pos_inside(Pn, F.n)) {
-      rn = rho_at(F, Pn, gnext);
+      rn = rho_at(F, Pn, gnext, S.cache);
       if (rn <= S.rho - 1e-4f * alpha * gg) {
         accepted = true;
         break;
@@ -292,10 +338,14 @@ __device__ __forceinline__ void ref_finish(const RefArgs& A, const Field& F, con
   if (!(S.fl & QTV_REFINE_NO_TANGENT)) {
     // in-plane Jacobian of psi at the result: basis e1 = normalize(t x a), a
     // the axis least aligned with t; e2 = t x e1
-    const float* t = S.t;
+    const float t[3] = {S.t[0], S.t[1], S.t[2]};
     int m = 0;
-    if (fabsf(t[1]) < fabsf(t[m])) m = 1;
-    if (fabsf(t[2]) < fabsf(t[m])) m = 2;
+    float am = fabsf(t[0]);
+    if (fabsf(t[1]) < am) {
+      m = 1;
+      am = fabsf(t[1]);
+    }
+    if (fabsf(t[2]) < am) m = 2;
     const float ax[3] = {m == 0 ? 1.f : 0.f, m == 1 ? 1.f : 0.f, m == 2 ? 1.f : 0.f};
     float e1[3] = {t[1] * ax[2] - t[2] * ax[1], t[2] * ax[0] - t[0] * ax[2],
                    t[0] * ax[1] - t[1] * ax[0]};
@@ -338,7 +388,7 @@ __device__ __forceinline__ void ref_finish(const RefArgs& A, const Field& F, con
 // the counter (one atomic per warp and round) as soon as its search ends, so
 // lanes do not idle while the slowest sample of a warp finishes.  Each sample
 // is computed exactly as alone.
-__global__ void __launch_bounds__(REF_THREADS, 8) refine_kernel(RefArgs A,
+__global__ void __launch_bounds__(REF_THREADS, 6) refine_kernel(RefArgs A,
                                                              unsigned long long* counter) {
   unsigned long long nn = A.n;
   if (A.n_dev) {
