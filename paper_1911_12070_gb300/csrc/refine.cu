@@ -384,10 +384,14 @@ __device__ __forceinline__ void ref_finish(const RefArgs& A, const Field& F, con
   A.flags[qi] = S.fl;
 }
 
-// Persistent warps; each lane keeps one sample and takes the next one from
-// the counter (one atomic per warp and round) as soon as its search ends, so
-// lanes do not idle while the slowest sample of a warp finishes.  Each sample
-// is computed exactly as alone.
+// Persistent warps; each lane keeps one sample.  A lane whose search ends
+// waits until kRefill lanes of its warp have (or none is searching); then
+// those lanes write their results and take the next samples from the counter
+// together (one atomic per warp and refill), so the long set-up and result
+// code runs with many lanes at once while searches of very different lengths
+// keep the warp busy.  Each sample is computed exactly as alone.
+constexpr int kRefill = 12;
+
 __global__ void __launch_bounds__(REF_THREADS, 6) refine_kernel(RefArgs A,
                                                              unsigned long long* counter) {
   unsigned long long nn = A.n;
@@ -403,16 +407,23 @@ __global__ void __launch_bounds__(REF_THREADS, 6) refine_kernel(RefArgs A,
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   RState S;
-  bool active = false, drained = false;
+  // active: searching; done: search ended, result not yet written;
+  // drained: no sample left for this lane
+  bool active = false, done = false, drained = false;
   while (true) {
-    const unsigned need = __ballot_sync(0xffffffffu, !active && !drained);
-    if (need) {
-      const int leader = __ffs(need) - 1;
+    const unsigned idle = __ballot_sync(0xffffffffu, !active && !drained);
+    const unsigned busy = __ballot_sync(0xffffffffu, active);
+    if (idle && (__popc(idle) >= kRefill || busy == 0u)) {
+      if (done) {
+        ref_finish(A, F, S);
+        done = false;
+      }
+      const int leader = __ffs(idle) - 1;
       unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(need));
+      if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(idle));
       base = __shfl_sync(0xffffffffu, base, leader);
       if (!active && !drained) {
-        const unsigned long long qi = base + (unsigned long long)__popc(need & lt);
+        const unsigned long long qi = base + (unsigned long long)__popc(idle & lt);
         if (qi < nn) {
           if (ref_init(A, F, qi, S)) active = true;
           else ref_finish(A, F, S);
@@ -421,10 +432,10 @@ __global__ void __launch_bounds__(REF_THREADS, 6) refine_kernel(RefArgs A,
         }
       }
     }
-    if (!__any_sync(0xffffffffu, active || !drained)) break;
+    if (!__any_sync(0xffffffffu, active || done || !drained)) break;
     if (active && ref_step(A, F, S)) {
-      ref_finish(A, F, S);
       active = false;
+      done = true;
     }
   }
 }
