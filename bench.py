@@ -73,7 +73,8 @@ def parse():
 # ncu summary holding the DRAM bytes per node of the default (bit-sliced)
 # sweep, valid while the kernel sources hash to the value recorded with it
 SWEEP_SOURCES = ("paper_1911_12070_gb300/csrc/sweep_bits.cu",
-                 "paper_1911_12070_gb300/csrc/sweep_common.cuh")
+                 "paper_1911_12070_gb300/csrc/sweep_common.cuh",
+                 "paper_1911_12070_gb300/csrc/bits_layout.cuh")
 TRAFFIC_PROFILE = "profiles/sweep_bits_384_full.md"
 
 
