@@ -64,6 +64,7 @@ namespace {
 
 constexpr int LT = 256;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr int kMaxRounds = 64;  // jump rounds: log2 of 2^32 samples plus slack
 constexpr int kSlots = 10;
 
 __device__ __forceinline__ unsigned long long limit_n(unsigned long long n, const uint64_t* n_dev) {
@@ -84,18 +85,20 @@ struct LineArgs {
   const uint64_t* face_ids;
   const int8_t* winding;
   // workspace
-  uint32_t* cmax;    // per component label: max degree
-  uint32_t* cmin;    // min degree
-  uint32_t* csize;   // samples
+  uint32_t* cflags;  // per component label: 1 = a sample of degree > 2,
+                     // 2 = a sample of degree < 2
   uint8_t* special;  // per sample
   uint32_t* deg32;   // degrees as 32-bit values (scan input)
   unsigned long long* aoff;   // per sample: first directed edge (exclusive scan of degrees)
   const unsigned long long* narcs;  // device: number of directed edges
   uint32_t* atail;   // per directed edge: tail sample
   uint32_t* ahead;   // per directed edge: head sample
-  uint32_t* nxt[2];  // per directed edge: successor edge
-  uint32_t* dst[2];  // distance (edges) to the end of the chain
-  uint32_t* lst[2];  // last edge of the chain
+  // per directed edge, double-buffered: x = successor edge, y = distance
+  // (edges) to the end of the chain, z = last edge of the chain (one 16-byte
+  // gather per jump)
+  uint4* jmp[2];
+  uint32_t* live;    // per round: 1 if an edge's chain has not ended yet
+  uint32_t* fbuf;    // buffer of the final jump results
   uint32_t* pcount;  // per sample: pieces started there
   uint32_t* plen;    // per sample: nodes of the pieces started there
   unsigned long long* pfirst;  // exclusive scan of pcount
@@ -111,8 +114,10 @@ struct LineArgs {
 };
 
 __device__ __forceinline__ int comp_type(const LineArgs& a, uint32_t L) {
-  if (a.cmax[L] > 2) return 3;
-  if (a.csize[L] > 1 && a.cmin[L] == 2) return 2;
+  // every degree 2 (a loop; a lone sample has degree 0) -> II; a branch -> III
+  const uint32_t f = a.cflags[L];
+  if (f & 1u) return 3;
+  if (f == 0u) return 2;
   return 1;
 }
 
@@ -120,9 +125,7 @@ __global__ void stats_init_kernel(LineArgs a) {
   const unsigned long long nn = limit_n(a.n, a.n_dev);
   for (unsigned long long u = (unsigned long long)blockIdx.x * LT + threadIdx.x; u < nn;
        u += (unsigned long long)gridDim.x * LT) {
-    a.cmax[u] = 0;
-    a.cmin[u] = 255;
-    a.csize[u] = 0;
+    a.cflags[u] = 0;
   }
 }
 
@@ -132,9 +135,12 @@ __global__ void stats_kernel(LineArgs a) {
        u += (unsigned long long)gridDim.x * LT) {
     const uint32_t L = a.comp[u], d = a.deg[u];
     a.deg32[u] = d;
-    atomicMax(a.cmax + L, d);
-    atomicMin(a.cmin + L, d);
-    atomicAdd(a.csize + L, 1u);
+    // only line ends and branch points mark their component (interior samples
+    // of degree 2 mark nothing), and a mark already set is not set again
+    if (d != 2u) {
+      const uint32_t bit = d > 2u ? 1u : 2u;
+      if ((a.cflags[L] & bit) == 0u) atomicOr(a.cflags + L, bit);
+    }
   }
 }
 
@@ -177,32 +183,47 @@ __global__ void edges_init_kernel(LineArgs a) {
        e += (unsigned long long)gridDim.x * LT) {
     const uint32_t u = a.atail[e], w = a.ahead[e];
     if (a.special[w]) {
-      a.nxt[0][e] = kNone;
-      a.lst[0][e] = (uint32_t)e;
+      a.jmp[0][e] = make_uint4(kNone, 1u, (uint32_t)e, 0u);
     } else {
       // w has degree 2: continue to its other neighbour
       const int sx = (a.nbr[(unsigned long long)w * kSlots] == u) ? 1 : 0;
-      a.nxt[0][e] = (uint32_t)(a.aoff[w] + sx);
-      a.lst[0][e] = kNone;
+      a.jmp[0][e] = make_uint4((uint32_t)(a.aoff[w] + sx), 1u, kNone, 0u);
     }
-    a.dst[0][e] = 1;
   }
 }
 
-__global__ void jump_kernel(LineArgs a, int src) {
+// Round r of pointer jumping (src = r & 1).  It is skipped once the previous
+// round left no edge with a successor (every chain has ended), so the rounds
+// beyond the longest chain cost a launch each; fbuf names the buffer that the
+// last round run wrote.
+__global__ void jump_kernel(LineArgs a, int src, int r) {
+  if (r > 0 && a.live[r - 1] == 0u) return;
   const unsigned long long ne = *a.narcs;
   const int d = src ^ 1;
-  for (unsigned long long e = (unsigned long long)blockIdx.x * LT + threadIdx.x; e < ne;
-       e += (unsigned long long)gridDim.x * LT) {
-    const uint32_t nx = a.nxt[src][e];
-    if (nx == kNone) {
-      a.nxt[d][e] = kNone;
-      a.dst[d][e] = a.dst[src][e];
-      a.lst[d][e] = a.lst[src][e];
-    } else {
-      a.nxt[d][e] = a.nxt[src][nx];
-      a.dst[d][e] = a.dst[src][e] + a.dst[src][nx];
-      a.lst[d][e] = a.lst[src][nx];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.fbuf = (uint32_t)d;
+  bool flagged = false;  // this block has seen the round's flag set
+  for (unsigned long long e0 = (unsigned long long)blockIdx.x * LT; e0 < ne;
+       e0 += (unsigned long long)gridDim.x * LT) {
+    const unsigned long long e = e0 + threadIdx.x;
+    bool more = false;
+    if (e < ne) {
+      const uint4 J = a.jmp[src][e];
+      if (J.x == kNone) {
+        // an edge whose chain ended two rounds ago already holds its final
+        // values in both buffers
+        if (r < 2 || a.jmp[d][e].x != kNone) a.jmp[d][e] = J;
+      } else {
+        const uint4 N = a.jmp[src][J.x];
+        a.jmp[d][e] = make_uint4(N.x, J.y + N.y, N.z, 0u);
+        more = N.x != kNone;
+      }
+    }
+    // one flag per round, set by the first block that finds a live edge (a
+    // block reads it at most once, so the flag's line sees few requests)
+    if (__syncthreads_or(more) && !flagged) {
+      flagged = true;
+      if (threadIdx.x == 0 && *reinterpret_cast<volatile uint32_t*>(a.live + r) == 0u)
+        a.live[r] = 1u;
     }
   }
 }
@@ -210,7 +231,7 @@ __global__ void jump_kernel(LineArgs a, int src) {
 // end sample and the sample before it, of the chain that edge e starts
 __device__ __forceinline__ void chain_end(const LineArgs& a, int buf, uint32_t e, uint32_t& end,
                                           uint32_t& before) {
-  const uint32_t l = a.lst[buf][e];
+  const uint32_t l = a.jmp[buf][e].z;
   before = a.atail[l];
   end = a.ahead[l];
 }
@@ -230,7 +251,8 @@ __device__ __forceinline__ bool discovering(const LineArgs& a, int buf, uint32_t
   return true;
 }
 
-__global__ void count_kernel(LineArgs a, int buf) {
+__global__ void count_kernel(LineArgs a) {
+  const int buf = (int)*a.fbuf;
   const unsigned long long nn = limit_n(a.n, a.n_dev);
   for (unsigned long long u = (unsigned long long)blockIdx.x * LT + threadIdx.x; u < nn;
        u += (unsigned long long)gridDim.x * LT) {
@@ -247,7 +269,7 @@ __global__ void count_kernel(LineArgs a, int buf) {
         uint32_t end, before;
         chain_end(a, buf, (uint32_t)e, end, before);
         ++pc;
-        nl += (end == (uint32_t)u) ? a.dst[buf][e] : a.dst[buf][e] + 1;
+        nl += (end == (uint32_t)u) ? a.jmp[buf][e].y : a.jmp[buf][e].y + 1;
       }
     }
     a.pcount[u] = pc;
@@ -256,7 +278,8 @@ __global__ void count_kernel(LineArgs a, int buf) {
 }
 
 // piece records, and the start and end samples of every piece
-__global__ void pieces_kernel(LineArgs a, int buf) {
+__global__ void pieces_kernel(LineArgs a) {
+  const int buf = (int)*a.fbuf;
   const unsigned long long nn = limit_n(a.n, a.n_dev);
   for (unsigned long long u = (unsigned long long)blockIdx.x * LT + threadIdx.x; u < nn;
        u += (unsigned long long)gridDim.x * LT) {
@@ -284,7 +307,7 @@ __global__ void pieces_kernel(LineArgs a, int buf) {
       uint32_t end, before;
       chain_end(a, buf, (uint32_t)e, end, before);
       const bool closed = end == (uint32_t)u;
-      const uint32_t cnt = closed ? a.dst[buf][e] : a.dst[buf][e] + 1;
+      const uint32_t cnt = closed ? a.jmp[buf][e].y : a.jmp[buf][e].y + 1;
       if (p < a.piece_cap) {
         qtv_piece r = {};
         r.first = off;
@@ -304,7 +327,8 @@ __global__ void pieces_kernel(LineArgs a, int buf) {
 }
 
 // samples inside chains: their piece and position from its start
-__global__ void interior_kernel(LineArgs a, int buf) {
+__global__ void interior_kernel(LineArgs a) {
+  const int buf = (int)*a.fbuf;
   const unsigned long long nn = limit_n(a.n, a.n_dev);
   for (unsigned long long u = (unsigned long long)blockIdx.x * LT + threadIdx.x; u < nn;
        u += (unsigned long long)gridDim.x * LT) {
@@ -322,10 +346,10 @@ __global__ void interior_kernel(LineArgs a, int buf) {
     uint32_t pos;
     if (discovering(a, buf, end0, bef0, (uint32_t)f0)) {
       off = a.edge_node_off[f0];
-      pos = a.dst[buf][e0];
+      pos = a.jmp[buf][e0].y;
     } else if (discovering(a, buf, end1, bef1, (uint32_t)f1)) {
       off = a.edge_node_off[f1];
-      pos = a.dst[buf][e1];
+      pos = a.jmp[buf][e1].y;
     } else {
       continue;
     }
@@ -742,10 +766,9 @@ int line_pieces_launch(qtv_handle h, uint64_t n, const uint64_t* n_dev, const ui
   size_t bytes = 0;
   {
     // sizes must match the carve sequence below
-    const unsigned long long sz[] = {n * 4, n * 4, n * 4, n, ne * 4, ne * 4, ne * 4, ne * 4,
-                                     ne * 4, ne * 4, n * 4, n * 4, n * 8, n * 8, ne * 8,
+    const unsigned long long sz[] = {n * 4, n, ne * 16, ne * 16, n * 4, n * 4, n * 8, n * 8, ne * 8,
                                      nodes_max * 4, n * 8, nb * 8, nb * 8, 16,
-                                     n * 4, n * 8, ne * 4, ne * 4, nb * 8, 8};
+                                     n * 4, n * 8, ne * 4, ne * 4, nb * 8, 8, kMaxRounds * 4 + 4};
     for (unsigned long long s : sz) bytes += ((s + 255) / 256) * 256;
   }
   void* buf = nullptr;
@@ -761,16 +784,10 @@ int line_pieces_launch(qtv_handle h, uint64_t n, const uint64_t* n_dev, const ui
   a.xyz = xyz;
   a.face_ids = face_ids;
   a.winding = winding;
-  a.cmax = carve<uint32_t>(p, n);
-  a.cmin = carve<uint32_t>(p, n);
-  a.csize = carve<uint32_t>(p, n);
+  a.cflags = carve<uint32_t>(p, n);
   a.special = carve<uint8_t>(p, n);
-  a.nxt[0] = carve<uint32_t>(p, ne);
-  a.nxt[1] = carve<uint32_t>(p, ne);
-  a.dst[0] = carve<uint32_t>(p, ne);
-  a.dst[1] = carve<uint32_t>(p, ne);
-  a.lst[0] = carve<uint32_t>(p, ne);
-  a.lst[1] = carve<uint32_t>(p, ne);
+  a.jmp[0] = carve<uint4>(p, ne);
+  a.jmp[1] = carve<uint4>(p, ne);
   a.pcount = carve<uint32_t>(p, n);
   a.plen = carve<uint32_t>(p, n);
   a.pfirst = carve<unsigned long long>(p, n);
@@ -788,6 +805,8 @@ int line_pieces_launch(qtv_handle h, uint64_t n, const uint64_t* n_dev, const ui
   unsigned long long* bs3 = carve<unsigned long long>(p, nb);
   unsigned long long* narcs = carve<unsigned long long>(p, 1);
   a.narcs = narcs;
+  a.live = carve<uint32_t>(p, kMaxRounds + 1);
+  a.fbuf = a.live + kMaxRounds;
   a.pieces = pieces;
   a.piece_cap = piece_cap;
   a.nodes = nodes;
@@ -809,18 +828,16 @@ int line_pieces_launch(qtv_handle h, uint64_t n, const uint64_t* n_dev, const ui
   edges_init_kernel<<<(int)ge, LT, 0, st>>>(a);
   int rounds = 1;
   while ((1ull << rounds) < (unsigned long long)n + 1) ++rounds;
-  int buf_i = 0;
-  for (int r = 0; r < rounds; ++r) {
-    jump_kernel<<<(int)ge, LT, 0, st>>>(a, buf_i);
-    buf_i ^= 1;
-  }
-  count_kernel<<<(int)g, LT, 0, st>>>(a, buf_i);
+  cudaError_t e = cudaMemsetAsync(a.live, 0, (kMaxRounds + 1) * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return check_cuda(e, "cudaMemsetAsync(line rounds)");
+  for (int r = 0; r < rounds; ++r) jump_kernel<<<(int)ge, LT, 0, st>>>(a, r & 1, r);
+  count_kernel<<<(int)g, LT, 0, st>>>(a);
   scan_u32(a.pcount, n_dev, n, a.pfirst, bs1, tot, h->num_sms, st);
   scan_u32(a.plen, n_dev, n, a.noff, bs2, tot + 1, h->num_sms, st);
-  cudaError_t e = cudaMemcpyAsync(counts, tot, 2 * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
+  e = cudaMemcpyAsync(counts, tot, 2 * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return check_cuda(e, "cudaMemcpyAsync(line counts)");
-  pieces_kernel<<<(int)g, LT, 0, st>>>(a, buf_i);
-  interior_kernel<<<(int)g, LT, 0, st>>>(a, buf_i);
+  pieces_kernel<<<(int)g, LT, 0, st>>>(a);
+  interior_kernel<<<(int)g, LT, 0, st>>>(a);
   orient_kernel<<<h->num_sms * 8, LT, 0, st>>>(a, tot);
   place_kernel<<<h->num_sms * 8, LT, 0, st>>>(a, tot);
   e = cudaGetLastError();
