@@ -592,7 +592,8 @@ QTV_API int qtv_line_pieces(qtv_handle h, uint64_t n, const uint64_t* n_dev, con
  *   curve        device float[curve_cap][3]; curve_first device uint64[npieces]:
  *                each piece's first point; length device float[npieces]: the
  *                polyline length of each curve (closing segment included for
- *                closed pieces; FP64 sums in a fixed order).
+ *                closed pieces; FP32 segment lengths summed in FP64 in a
+ *                fixed order).
  *   total        device uint64: number of curve points (outputs incomplete
  *                when it exceeds curve_cap).
  */

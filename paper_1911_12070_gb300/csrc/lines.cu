@@ -552,14 +552,24 @@ __global__ void curve_kernel(CurveArgs a, const unsigned long long* total) {
       // a one-sample piece, or the last sample of an open piece
       sample_pos(a, r, m < 2 ? 0 : m - 1, out);
     } else {
-      const long long s = k / a.per;
-      const int ti = (int)(k % a.per);
+      // segment s and step ti of point k (k < count * per < 2^32 * per)
+      long long s;
+      int ti;
+      if ((k >> 32) == 0) {
+        const uint32_t k32 = (uint32_t)k, q = k32 / (uint32_t)a.per;
+        s = q;
+        ti = (int)(k32 - q * (uint32_t)a.per);
+      } else {
+        s = k / a.per;
+        ti = (int)(k - s * a.per);
+      }
       // ext = closed: [P[m-1], P[0..m-1], P[0], P[1]]; open: [P[0], P[0..m-1], P[m-1]]
+      // (s + c - 1 lies in [-1, m + 1] and m >= 2, so one wrap suffices)
       long long id[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         long long x = s + c - 1;
-        if (r.closed) x = ((x % m) + m) % m;
+        if (r.closed) x = x < 0 ? x + m : (x >= m ? x - m : x);
         else x = x < 0 ? 0 : (x > m - 1 ? m - 1 : x);
         id[c] = x;
       }
@@ -581,7 +591,8 @@ __global__ void curve_kernel(CurveArgs a, const unsigned long long* total) {
   }
 }
 
-// one block per piece: polyline length of its curve (FP64; each thread sums a
+// one block per piece: polyline length of its curve (each segment's length in
+// FP32 from exact coordinate differences, summed in FP64: each thread sums a
 // fixed stride, then a fixed reduction tree)
 __global__ void __launch_bounds__(LT) length_kernel(CurveArgs a) {
   __shared__ double part[LT / 32];
@@ -595,13 +606,13 @@ __global__ void __launch_bounds__(LT) length_kernel(CurveArgs a) {
       const unsigned long long nseg = r.closed ? n : n - 1;
       for (unsigned long long i = threadIdx.x; i < nseg; i += LT) {
         const unsigned long long j = (i + 1 == n) ? 0 : i + 1;
-        double s2 = 0.0;
+        float s2 = 0.f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const double d = (double)a.curve[3 * (c0 + j) + c] - (double)a.curve[3 * (c0 + i) + c];
-          s2 += d * d;
+          const float d = a.curve[3 * (c0 + j) + c] - a.curve[3 * (c0 + i) + c];
+          s2 = fmaf(d, d, s2);
         }
-        sum += sqrt(s2);
+        sum += (double)sqrtf(s2);
       }
     }
 #pragma unroll
