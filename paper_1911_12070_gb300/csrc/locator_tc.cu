@@ -206,8 +206,14 @@ __global__ void __launch_bounds__(128, 1) tc_dense_kernel(const uint16_t* __rest
 // its epilogue applies relu(. + b2) and the 3-output layer in FP32.  The next
 // tile's X is prefetched with cp.async once layer 1 has read the current one,
 // and the next tile's layer 1 runs on the tensor cores during epilogue 2.
+// Eight warps: warps w and w + 4 read the same 32 TMEM lanes (rows) and split
+// the columns, so each SM sub-partition has two warps to hide tcgen05.ld
+// latency; the upper half's partial 3-output sums meet the lower half's in
+// shared memory.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kMlpSmemW1 = 256 * 128 * 2, kMlpSmemW2 = 256 * 256 * 2, kMlpSmemX = 128 * 128 * 2;
+constexpr int kMlpThreads = 256;
+constexpr uint32_t kMlpSmemPart = TM * 3 * sizeof(float);  // upper-half partial outputs
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
   asm volatile(
@@ -255,7 +261,7 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-__global__ void __launch_bounds__(128, 1) tc_mlp_kernel(
+__global__ void __launch_bounds__(kMlpThreads, 1) tc_mlp_kernel(
     const uint16_t* __restrict__ X, long long M, const uint16_t* __restrict__ W1,
     const uint16_t* __restrict__ W2, const float* __restrict__ b1, const float* __restrict__ b2,
     const float* __restrict__ w3, const float* __restrict__ b3, float* __restrict__ Y,
@@ -267,7 +273,10 @@ __global__ void __launch_bounds__(128, 1) tc_mlp_kernel(
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sX + kMlpSmemX);  // layer 1 done
   uint64_t* mbar2 = mbar + 1;                                          // layer 2 done
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  float* spart = reinterpret_cast<float*>(sX + kMlpSmemX + 32);  // [TM][3]
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int wq = w & 3;      // TMEM lane quarter (rows 32 wq .. 32 wq + 31)
+  const int half = w >> 2;   // column half of the epilogues
 
   if (w == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -288,7 +297,7 @@ __global__ void __launch_bounds__(128, 1) tc_mlp_kernel(
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
-  const uint32_t lane_off = (uint32_t)(32 * w) << 16;
+  const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
   const uint64_t xdesc = smem_desc(smem_u32(sX), 128u, 16u * 128u);
   const uint64_t w1desc = smem_desc(smem_u32(sW1), 128u, 16u * 128u);
   const uint64_t w2desc = smem_desc(smem_u32(sW2), 128u, 32u * 128u);
@@ -314,29 +323,38 @@ __global__ void __launch_bounds__(128, 1) tc_mlp_kernel(
   }
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long r0 = tile * TM;
-    const long long row = r0 + 32 * w + lane;
+    const long long row = r0 + 32 * wq + lane;
     const long long next = tile + gridDim.x;
     if (!mbar_wait(mbar, phase)) timeout = true;  // layer 1 of this tile
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // X of the next tile streams into shared memory during the rest of this tile
     if (next < ntiles) load_canon_async(sX, X, next * TM, TM, M, 128);
-    // epilogue 1: columns 32 j .. 32 j + 31 of D1 -> BF16 pairs in columns 16 j .. 16 j + 15
-#pragma unroll 1
-    for (int j = 0; j < 8; ++j) {
-      uint32_t v[32], pk[16];
+    // epilogue 1: columns 32 j .. 32 j + 31 of D1 -> BF16 pairs in columns 16 j .. 16 j + 15,
+    // this warp's half j = 4 half .. 4 half + 3.  The pairs of block j land on D1 columns that
+    // block j / 2 reads, which may be the other half's, so every warp reads all its blocks
+    // before any warp writes.
+    uint32_t pk[4][16];
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int j = 4 * half + jj;
+      uint32_t v[32];
       tmem_ld32(tmem + lane_off + 32u * j, v);
       const float4* bb = reinterpret_cast<const float4*>(b1 + 32 * j);
 #pragma unroll
       for (int i4 = 0; i4 < 8; ++i4) {
         const float4 b = __ldg(bb + i4);
-        pk[2 * i4] = bf16x2_bits(fmaxf(__uint_as_float(v[4 * i4]) + b.x, 0.f),
-                                 fmaxf(__uint_as_float(v[4 * i4 + 1]) + b.y, 0.f));
-        pk[2 * i4 + 1] = bf16x2_bits(fmaxf(__uint_as_float(v[4 * i4 + 2]) + b.z, 0.f),
-                                     fmaxf(__uint_as_float(v[4 * i4 + 3]) + b.w, 0.f));
+        pk[jj][2 * i4] = bf16x2_bits(fmaxf(__uint_as_float(v[4 * i4]) + b.x, 0.f),
+                                     fmaxf(__uint_as_float(v[4 * i4 + 1]) + b.y, 0.f));
+        pk[jj][2 * i4 + 1] = bf16x2_bits(fmaxf(__uint_as_float(v[4 * i4 + 2]) + b.z, 0.f),
+                                         fmaxf(__uint_as_float(v[4 * i4 + 3]) + b.w, 0.f));
       }
-      tmem_st16(tmem + lane_off + 16u * j, pk);
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) tmem_st16(tmem + lane_off + 16u * (4 * half + jj), pk[jj]);
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -360,7 +378,7 @@ __global__ void __launch_bounds__(128, 1) tc_mlp_kernel(
     // epilogue 2: relu(. + b2) and the 3-output layer in FP32
     float y0 = 0.f, y1 = 0.f, y2 = 0.f;
 #pragma unroll 1
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 4 * half; j < 4 * half + 4; ++j) {
       uint32_t v[32];
       tmem_ld32(tmem + lane_off + 256u + 32u * j, v);
       const float4* bb = reinterpret_cast<const float4*>(b2 + 32 * j);
@@ -379,10 +397,18 @@ __global__ void __launch_bounds__(128, 1) tc_mlp_kernel(
         y2 = fmaf(c2.x, a0, fmaf(c2.y, a1, fmaf(c2.z, a2, fmaf(c2.w, a3, y2))));
       }
     }
-    if (row < M) {
-      Y[3 * row] = y0 + __ldg(b3);
-      Y[3 * row + 1] = y1 + __ldg(b3 + 1);
-      Y[3 * row + 2] = y2 + __ldg(b3 + 2);
+    // the upper column half's partial sums join the lower half's
+    const int rl = 32 * wq + lane;
+    if (half) {
+      spart[3 * rl] = y0;
+      spart[3 * rl + 1] = y1;
+      spart[3 * rl + 2] = y2;
+    }
+    __syncthreads();
+    if (!half && row < M) {
+      Y[3 * row] = (y0 + spart[3 * rl]) + __ldg(b3);
+      Y[3 * row + 1] = (y1 + spart[3 * rl + 1]) + __ldg(b3 + 1);
+      Y[3 * row + 2] = (y2 + spart[3 * rl + 2]) + __ldg(b3 + 2);
     }
     // D2 is read before layer 2 of the next tile overwrites it
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -425,7 +451,7 @@ int tc_mlp_forward(const uint16_t* X, long long M, const uint16_t* W1, const uin
                    const float* b1, const float* b2, const float* w3, const float* b3, float* Y,
                    unsigned int* status, int num_sms, cudaStream_t st) {
   if (M <= 0) return QTV_OK;
-  const size_t smem = (size_t)kMlpSmemW1 + kMlpSmemW2 + kMlpSmemX + 16 + 16;
+  const size_t smem = (size_t)kMlpSmemW1 + kMlpSmemW2 + kMlpSmemX + 32 + kMlpSmemPart;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(tc_mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -435,7 +461,7 @@ int tc_mlp_forward(const uint16_t* X, long long M, const uint16_t* W1, const uin
   }
   const long long ntiles = (M + TM - 1) / TM;
   const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
-  tc_mlp_kernel<<<grid, 128, smem, st>>>(X, M, W1, W2, b1, b2, w3, b3, Y, status);
+  tc_mlp_kernel<<<grid, kMlpThreads, smem, st>>>(X, M, W1, W2, b1, b2, w3, b3, Y, status);
   return check_cuda(cudaGetLastError(), "tc_mlp_kernel launch");
 }
 
