@@ -334,21 +334,20 @@ __global__ void __launch_bounds__(kMlpThreads, 1) tc_mlp_kernel(
     // this warp's half j = 4 half .. 4 half + 3.  The pairs of block j land on D1 columns that
     // block j / 2 reads, which may be the other half's, so every warp reads all its blocks
     // before any warp writes.
+    // (the bias of column 32 j + i is lane i's coalesced load, broadcast by a
+    // shuffle: one load per block instead of eight per lane)
     uint32_t pk[4][16];
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {
       const int j = 4 * half + jj;
+      const float lb = __ldg(b1 + 32 * j + lane);
       uint32_t v[32];
       tmem_ld32(tmem + lane_off + 32u * j, v);
-      const float4* bb = reinterpret_cast<const float4*>(b1 + 32 * j);
 #pragma unroll
-      for (int i4 = 0; i4 < 8; ++i4) {
-        const float4 b = __ldg(bb + i4);
-        pk[jj][2 * i4] = bf16x2_bits(fmaxf(__uint_as_float(v[4 * i4]) + b.x, 0.f),
-                                     fmaxf(__uint_as_float(v[4 * i4 + 1]) + b.y, 0.f));
-        pk[jj][2 * i4 + 1] = bf16x2_bits(fmaxf(__uint_as_float(v[4 * i4 + 2]) + b.z, 0.f),
-                                         fmaxf(__uint_as_float(v[4 * i4 + 3]) + b.w, 0.f));
-      }
+      for (int i = 0; i < 32; i += 2)
+        pk[jj][i / 2] =
+            bf16x2_bits(fmaxf(__uint_as_float(v[i]) + __shfl_sync(0xffffffffu, lb, i), 0.f),
+                        fmaxf(__uint_as_float(v[i + 1]) + __shfl_sync(0xffffffffu, lb, i + 1), 0.f));
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -379,22 +378,25 @@ __global__ void __launch_bounds__(kMlpThreads, 1) tc_mlp_kernel(
     float y0 = 0.f, y1 = 0.f, y2 = 0.f;
 #pragma unroll 1
     for (int j = 4 * half; j < 4 * half + 4; ++j) {
+      // bias and output weights of column 32 j + i: lane i's loads, broadcast
+      const float lb = __ldg(b2 + 32 * j + lane), l0 = __ldg(w3 + 32 * j + lane),
+                  l1 = __ldg(w3 + 256 + 32 * j + lane), l2 = __ldg(w3 + 512 + 32 * j + lane);
       uint32_t v[32];
       tmem_ld32(tmem + lane_off + 256u + 32u * j, v);
-      const float4* bb = reinterpret_cast<const float4*>(b2 + 32 * j);
-      const float4* q0 = reinterpret_cast<const float4*>(w3 + 32 * j);
-      const float4* q1 = reinterpret_cast<const float4*>(w3 + 256 + 32 * j);
-      const float4* q2 = reinterpret_cast<const float4*>(w3 + 512 + 32 * j);
 #pragma unroll
       for (int i4 = 0; i4 < 8; ++i4) {
-        const float4 b = __ldg(bb + i4), c0 = __ldg(q0 + i4), c1 = __ldg(q1 + i4), c2 = __ldg(q2 + i4);
-        const float a0 = fmaxf(__uint_as_float(v[4 * i4]) + b.x, 0.f);
-        const float a1 = fmaxf(__uint_as_float(v[4 * i4 + 1]) + b.y, 0.f);
-        const float a2 = fmaxf(__uint_as_float(v[4 * i4 + 2]) + b.z, 0.f);
-        const float a3 = fmaxf(__uint_as_float(v[4 * i4 + 3]) + b.w, 0.f);
-        y0 = fmaf(c0.x, a0, fmaf(c0.y, a1, fmaf(c0.z, a2, fmaf(c0.w, a3, y0))));
-        y1 = fmaf(c1.x, a0, fmaf(c1.y, a1, fmaf(c1.z, a2, fmaf(c1.w, a3, y1))));
-        y2 = fmaf(c2.x, a0, fmaf(c2.y, a1, fmaf(c2.z, a2, fmaf(c2.w, a3, y2))));
+        float a[4], c0[4], c1[4], c2[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int i = 4 * i4 + e;
+          a[e] = fmaxf(__uint_as_float(v[i]) + __shfl_sync(0xffffffffu, lb, i), 0.f);
+          c0[e] = __shfl_sync(0xffffffffu, l0, i);
+          c1[e] = __shfl_sync(0xffffffffu, l1, i);
+          c2[e] = __shfl_sync(0xffffffffu, l2, i);
+        }
+        y0 = fmaf(c0[0], a[0], fmaf(c0[1], a[1], fmaf(c0[2], a[2], fmaf(c0[3], a[3], y0))));
+        y1 = fmaf(c1[0], a[0], fmaf(c1[1], a[1], fmaf(c1[2], a[2], fmaf(c1[3], a[3], y1))));
+        y2 = fmaf(c2[0], a[0], fmaf(c2[1], a[1], fmaf(c2[2], a[2], fmaf(c2[3], a[3], y2))));
       }
     }
     // the upper column half's partial sums join the lower half's
