@@ -7,6 +7,7 @@ Each translation unit under csrc/ is compiled in parallel with
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import glob
 import hashlib
 import os
@@ -48,14 +49,32 @@ def _stamp(extra_flags) -> str:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile and link libqtv.so; returns its path."""
+    """Compile and link libqtv.so; returns its path.  Processes that build at
+    the same time (one per rank) take turns on a lock file; the later ones find
+    the stamp current and return."""
     os.makedirs(OUT, exist_ok=True)
     stamp = _stamp(extra_flags)
     stamp_file = os.path.join(OUT, "libqtv.stamp")
-    if not force and os.path.exists(LIB) and os.path.exists(stamp_file):
+
+    def current():
+        if force or not (os.path.exists(LIB) and os.path.exists(stamp_file)):
+            return False
         with open(stamp_file) as fh:
-            if fh.read().strip() == stamp:
-                return LIB
+            return fh.read().strip() == stamp
+
+    if current():
+        return LIB
+    with open(os.path.join(OUT, "build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not current():
+                _compile_and_link(stamp, stamp_file, verbose, extra_flags)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+    return LIB
+
+
+def _compile_and_link(stamp, stamp_file, verbose, extra_flags):
     cc = nvcc()
     objs = []
 
@@ -79,7 +98,6 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     os.replace(tmp, LIB)
     with open(stamp_file, "w") as fh:
         fh.write(stamp)
-    return LIB
 
 
 if __name__ == "__main__":
