@@ -535,6 +535,71 @@ def oracle_sample(psi_host_slab, planes):
     return dt, planes * ny * nx, len(ids)
 
 
+def oracle_stage_baselines(psi, ids, wnd, xyz, F, planes=32, nref=50000):
+    """The oracle's own rate on the stages beyond the step (host cores, bounded
+    samples of the bench field): node form on the first `planes` z-planes,
+    refinement from the first `nref` face centres, and the face graph with its
+    components and the line pieces (classification, walk order, orientation)
+    of the faces inside those planes."""
+    import oracle
+    from oracle import graph
+
+    cores = oracle.max_threads()
+    nz, ny, nx = psi.shape
+    planes = max(2, min(planes, nz))
+    slab = np.ascontiguousarray(psi[:planes].cpu().numpy())
+    out = {}
+    t = time.perf_counter()
+    oracle.node_circulation(slab)
+    dt = time.perf_counter() - t
+    out["node_form"] = {"value": slab.size / dt, "unit": "nodes/s", "cores": cores,
+                        "kind": "oracle",
+                        "sample": f"{planes} z-planes ({slab.size} nodes), FP64, {dt:.2f} s"}
+    idh = ids[:F].cpu().numpy().view(np.uint64)
+    lin = (idh >> np.uint64(2)).astype(np.int64)
+    kk = lin // (nx * ny)
+    # refinement: face centres whose searches stay well inside the slab
+    sel = np.flatnonzero(kk < planes - 4)[:nref]
+    o = (idh[sel] & np.uint64(3)).astype(np.int64)
+    ls = lin[sel]
+    x0 = np.stack([ls % nx + 0.5 * ((o == 0) | (o == 2)),
+                   (ls // nx) % ny + 0.5 * ((o == 0) | (o == 1)),
+                   ls // (nx * ny) + 0.5 * ((o == 1) | (o == 2))], 1).astype(np.float64)
+    t = time.perf_counter()
+    oracle.refine(slab, x0)
+    dt = time.perf_counter() - t
+    out["refine"] = {"value": len(sel) / dt, "unit": "samples/s", "cores": cores,
+                     "kind": "oracle",
+                     "sample": f"{len(sel)} face centres of the first {planes - 4} planes, FP64, "
+                               f"{dt:.2f} s"}
+    # graph, components and lines: the faces that lie inside the slab
+    inside = np.flatnonzero(kk < planes - 1)
+    fid = idh[inside]
+    fw = wnd[:F].cpu().numpy()[inside]
+    fx = xyz[:F].cpu().numpy().astype(np.float64)[inside]
+    t = time.perf_counter()
+    g = graph.face_graph(fid, fw, fx, (planes, ny, nx))
+    comps = graph.components(g)
+    dt_graph = time.perf_counter() - t
+    t = time.perf_counter()
+    npieces = 0
+    for c in comps:
+        graph.classify(g, c)
+        for _, path, closed in graph.ordered_lines(g, c):
+            graph.orient(g, path, closed)
+            npieces += 1
+    dt_lines = time.perf_counter() - t
+    out["face_graph"] = {"value": len(fid) / dt_graph, "unit": "faces/s", "cores": 1,
+                         "kind": "oracle",
+                         "sample": f"{len(fid)} faces of the first {planes - 1} planes, "
+                                   f"{len(comps)} components, {dt_graph:.2f} s"}
+    out["lines"] = {"value": len(fid) / dt_lines, "unit": "samples/s", "cores": 1,
+                    "kind": "oracle",
+                    "sample": f"the same faces: {npieces} pieces classified, ordered and "
+                              f"oriented, {dt_lines:.2f} s"}
+    return out
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -830,6 +895,14 @@ def run_qtv(args):
 
     if rank == 0 and not args.no_batch:
         line["batch"] = batch_report(q, stream, learned=not args.no_learned)
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.no_node_form:
+        import oracle
+
+        oracle.set_threads(cpu_cores())
+        for key, base in oracle_stage_baselines(psi, ids, wnd, xyz, F).items():
+            if isinstance(line.get(key), dict):
+                line[key]["cpu_baseline"] = base
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
