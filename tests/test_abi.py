@@ -69,3 +69,29 @@ def test_sample_layout_is_32_bytes():
     assert ctypes.sizeof(qtv.Sample) == 32
     assert qtv.SAMPLE_DTYPE.itemsize == 32
     assert qtv.Sample.face_id.offset == 16 and qtv.Sample.winding.offset == 24
+
+
+def declared_prototypes():
+    """{name: parameter count} of every QTV_API function in the header."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"QTV_API\s+[^;(]*?\b(qtv_\w+)\s*\(([^)]*)\)\s*;", src, flags=re.S):
+        params = " ".join(m.group(2).split())
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_the_header(lib):
+    # every function the binding declares argtypes for takes as many
+    # arguments as its prototype (a mismatch would pass garbage through ctypes)
+    protos = declared_prototypes()
+    assert len(protos) == len(declared_functions())
+    checked = 0
+    for name, n in protos.items():
+        argtypes = getattr(lib, name).argtypes
+        if argtypes is None:
+            continue
+        assert len(argtypes) == n, (name, len(argtypes), n)
+        checked += 1
+    assert checked >= 30
