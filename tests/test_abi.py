@@ -95,3 +95,56 @@ def test_binding_argument_counts_match_the_header(lib):
         assert len(argtypes) == n, (name, len(argtypes), n)
         checked += 1
     assert checked >= 30
+
+
+def _header_kinds():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"QTV_API\s+[^;(]*?\b(qtv_\w+)\s*\(([^)]*)\)\s*;", src, flags=re.S):
+        params = " ".join(m.group(2).split())
+        if params in ("", "void"):
+            out[m.group(1)] = []
+            continue
+        kinds = []
+        for p in params.split(","):
+            p = p.strip()
+            if "*" in p or p.startswith("qtv_handle"):
+                kinds.append("ptr")
+            elif re.match(r"(const\s+)?u?int64_t\b", p):
+                kinds.append("i64")
+            elif re.match(r"(const\s+)?(int|u?int32_t)\b", p):
+                kinds.append("i32")
+            elif re.match(r"(const\s+)?float\b", p):
+                kinds.append("f32")
+            elif re.match(r"(const\s+)?double\b", p):
+                kinds.append("f64")
+            else:
+                kinds.append("?" + p)
+        out[m.group(1)] = kinds
+    return out
+
+
+def _ctypes_kind(t):
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or hasattr(t, "contents") or \
+            getattr(t, "_type_", None) is not None and isinstance(getattr(t, "_type_"), type):
+        return "ptr"
+    if t in (ctypes.c_uint64, ctypes.c_int64):
+        return "i64"
+    if t in (ctypes.c_int32, ctypes.c_uint32):
+        return "i32"
+    if t is ctypes.c_float:
+        return "f32"
+    if t is ctypes.c_double:
+        return "f64"
+    return "?" + repr(t)
+
+
+def test_binding_argument_kinds_match_the_header(lib):
+    # pointer, 64-bit, 32-bit and floating arguments in the same places
+    for name, kinds in _header_kinds().items():
+        argtypes = getattr(lib, name).argtypes
+        if argtypes is None:
+            continue
+        got = [_ctypes_kind(t) for t in argtypes]
+        assert got == kinds, (name, got, kinds)
