@@ -70,12 +70,13 @@ def parse():
     return p.parse_args()
 
 
-# ncu summary holding the DRAM bytes per node of the default (bit-sliced)
-# sweep, valid while the kernel sources hash to the value recorded with it
+# DRAM bytes per node of the default (bit-sliced) sweep from one ncu capture,
+# kept with the hash of the sweep sources it was taken on (profiles/, beside
+# the capture's summary); valid while the sources hash to that value
 SWEEP_SOURCES = ("paper_1911_12070_gb300/csrc/sweep_bits.cu",
                  "paper_1911_12070_gb300/csrc/sweep_common.cuh",
                  "paper_1911_12070_gb300/csrc/bits_layout.cuh")
-TRAFFIC_PROFILE = "profiles/sweep_bits_384_full.md"
+TRAFFIC_FILE = "profiles/sweep_bits_traffic.json"
 
 
 def sweep_sources_hash():
@@ -89,22 +90,19 @@ def sweep_sources_hash():
 
 
 def profiled_traffic(variant):
-    """(DRAM bytes per node, profile name) from the committed ncu summary of
-    the bit-sliced sweep, or (None, reason) when the sweep timed is another
-    kernel or has changed since the capture."""
+    """(DRAM bytes per node, capture summary) of the bit-sliced sweep, or
+    (None, reason) when the sweep timed is another kernel or has changed since
+    the capture."""
     if variant == 0:
         return None, "nibble sweep: no current capture"
-    path = os.path.join(ROOT, TRAFFIC_PROFILE)
+    path = os.path.join(ROOT, TRAFFIC_FILE)
     if not os.path.exists(path):
         return None, "no capture"
-    vals = {}
-    for line in open(path):
-        if ":" in line and line.strip().startswith(("traffic_bytes_per_node", "source_sha256")):
-            k, v = line.strip().split(":", 1)
-            vals[k.strip()] = v.strip()
+    with open(path) as fh:
+        vals = json.load(fh)
     if vals.get("source_sha256") != sweep_sources_hash():
         return None, "kernel changed since the capture"
-    return float(vals["traffic_bytes_per_node"]), TRAFFIC_PROFILE
+    return float(vals["traffic_bytes_per_node"]), vals.get("summary", TRAFFIC_FILE)
 
 
 def peaks():
@@ -243,7 +241,11 @@ def learned_report(q, psi, ids, wnd, F, stream, reps=20):
         "plain_ms": ms["plain"], "learned_ms": ms["tcgen05"],
         "learned_mma_sync_ms": ms["mma"],
         "learned_split_ms": split,
-        "learned_mlp_tflops": flop / (ms["tcgen05"] * 1e-3) / 1e12,
+        # network FLOPs over the network kernel's own time (the split), and
+        # over the whole learned localization (encode + network + head)
+        "learned_mlp_tflops": (flop / (split["network"] * 1e-3) / 1e12
+                               if split.get("network") else None),
+        "learned_localize_tflops": flop / (ms["tcgen05"] * 1e-3) / 1e12,
         "tensor_path": "tcgen05 (accumulators in tensor memory)",
         "accepted_frac": float(accepted.float().mean()),
         "rms_vs_plain_h": rms_all, "rms_vs_plain_accepted_h": rms_acc,
@@ -521,9 +523,9 @@ def batch_report(q, stream, reps=10, learned=False):
     return out
 
 
-def oracle_sample(psi_host_slab, planes):
+def oracle_sample(psi_host_slab, planes, want=False):
     """Oracle identify + localize on planes [0, planes) of a slab (with one halo
-    plane); returns (seconds, nodes, faces)."""
+    plane); returns (seconds, nodes, faces[, (windings, flags)])."""
     import oracle
 
     t0 = time.perf_counter()
@@ -532,7 +534,30 @@ def oracle_sample(psi_host_slab, planes):
     oracle.localize(psi_host_slab, ids, wind)
     dt = time.perf_counter() - t0
     nz, ny, nx = psi_host_slab.shape
+    if want:
+        return dt, planes * ny * nx, len(ids), (w, fl)
     return dt, planes * ny * nx, len(ids)
+
+
+def sample_parity(w_or, fl_or, gpu_ids, gpu_w, shape, planes):
+    """GPU windings against the oracle's on planes [0, planes): ambiguous faces
+    (an edge within 1e-4 rad of +-pi) and how many of them, and of the others,
+    differ."""
+    import oracle
+
+    nz, ny, nx = shape
+    ids = np.asarray(gpu_ids, dtype=np.uint64)
+    lin = (ids >> np.uint64(2)).astype(np.int64)
+    sel = lin < planes * nx * ny
+    g = np.zeros_like(w_or)
+    o = (ids[sel] & np.uint64(3)).astype(np.int64)
+    g[o, lin[sel] // (nx * ny), (lin[sel] // nx) % ny, lin[sel] % nx] = np.asarray(gpu_w)[sel]
+    amb = (fl_or & oracle.AMBIGUOUS) != 0
+    diff = g != w_or
+    return {"planes": planes, "oracle_pierced": int(np.count_nonzero(w_or)),
+            "oracle_ambiguous": int(amb.sum()),
+            "ambiguous_differing": int(np.count_nonzero(diff & amb)),
+            "unambiguous_differing": int(np.count_nonzero(diff & ~amb))}
 
 
 def oracle_stage_baselines(psi, ids, wnd, xyz, F, planes=32, nref=50000):
@@ -714,8 +739,9 @@ def run_qtv(args):
     nodes = n ** 3
     stream = torch.cuda.current_stream()
 
-    # size the outputs from one untimed call
-    ids0, w0, _ = q.identify(psi)
+    # size the outputs from one untimed call (with the statistics: ambiguous
+    # faces of this field, which every step identifies alike)
+    ids0, w0, id_stats = q.identify(psi, stats=True)
     F = ids0.numel()
     cap = int(F * 1.05) + 1024
     del ids0, w0
@@ -882,6 +908,10 @@ def run_qtv(args):
                 "h2d_bytes_per_step": 8 * nodes, "d2h_bytes_per_step": d2h // ke},
         "gpu_launches": launches,
         "clocks": clocks,
+        "ambiguous_faces": {"gpu": id_stats["ambiguous"], "pierced": id_stats["pierced"],
+                            "source": "qtv_stats of an untimed identification of the same "
+                                      "field (faces with an edge phase difference within "
+                                      "1e-4 rad of +-pi)"},
     }
 
     if rank == 0 and not args.no_node_form:
@@ -912,15 +942,23 @@ def run_qtv(args):
         oracle.set_threads(cpu_cores())
         # repeat the slab until about args.cpu_seconds of host work
         dt, nn, reps = 0.0, 0, 0
+        parity = None
         while reps < 1 or dt < args.cpu_seconds:
-            d, m, _ = oracle_sample(slab, planes)
+            if parity is None:
+                d, m, _, (w_or, fl_or) = oracle_sample(slab, planes, want=True)
+                nf = int(count.item())
+                parity = sample_parity(w_or, fl_or, ids[:nf].cpu().numpy().view(np.uint64),
+                                       wnd[:nf].cpu().numpy(), tuple(psi.shape), planes)
+            else:
+                d, m, _ = oracle_sample(slab, planes)
             dt += d
             nn += m
             reps += 1
         line["cpu_baseline"] = {
             "value": nn / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
             "sample": f"{planes} z-planes of the {n}^3 field ({nn // reps} nodes), FP64 identify "
-                      f"+ localize, {reps} passes, {dt:.1f} s"}
+                      f"+ localize, {reps} passes, {dt:.1f} s",
+            "parity_on_sample": parity}
     if rank == 0:
         print(json.dumps(line), flush=True)
     q.close()

@@ -326,6 +326,20 @@ QTV_API int qtv_configure_sweep(qtv_handle h, int variant, int warps_per_tile, i
                                 int ctas_per_sm);
 
 /*
+ * Failure injection for tests of the bounded device waits (no paper
+ * counterpart).  Every later identification of this handle runs its segment
+ * scan with look-back tile `hold_tile` never publishing its state (-1 = none),
+ * and with look-back waits that give up after `spin_cycles` SM cycles (0 = the
+ * default, about 2^32).  A wait that gives up ends its kernel normally, sets
+ * the reported face count to QTV_COUNT_TIMEOUT and leaves the CUDA context
+ * usable; the face list of that call is then meaningless (faces are still
+ * written only below capacity).  qtv_inject_scan_hold(h, -1, 0) restores
+ * normal operation.  Returns QTV_ERR_ARG for a NULL handle, hold_tile < -1 or
+ * a negative spin limit.
+ */
+QTV_API int qtv_inject_scan_hold(qtv_handle h, int64_t hold_tile, int64_t spin_cycles);
+
+/*
  * Batches of snapshots.  Identification (Sec. 2.2.2, Eq. 5) and localization
  * (Sec. 3.3.3, Eq. 6) of up to QTV_BATCH_MAX snapshots of different grid
  * sizes in one pass: persistent sweep launches whose CTAs take contiguous

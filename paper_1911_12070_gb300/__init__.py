@@ -146,6 +146,8 @@ def lib() -> ctypes.CDLL:
             getattr(L, name).restype = i32
         L.qtv_configure_sweep.argtypes = [P, i32, i32, i32, i32]
         L.qtv_configure_sweep.restype = i32
+        L.qtv_inject_scan_hold.argtypes = [P, ctypes.c_int64, ctypes.c_int64]
+        L.qtv_inject_scan_hold.restype = i32
         L.qtv_batch_plan.argtypes = [P, i32, ctypes.POINTER(Grid), ctypes.POINTER(P),
                                      ctypes.c_char_p, P]
         L.qtv_batch_info_get.argtypes = [P, ctypes.POINTER(BatchInfo)]
@@ -232,6 +234,12 @@ class Qtv:
         """Sweep shape of this handle's single-snapshot calls (qtv_configure_sweep)."""
         _check(lib().qtv_configure_sweep(self.h, int(variant), int(warps_per_tile), int(stages),
                                          int(ctas_per_sm)))
+
+    def inject_scan_hold(self, hold_tile: int = -1, spin_cycles: int = 0):
+        """Failure injection (qtv_inject_scan_hold): look-back tile hold_tile of
+        the segment scan never publishes, and look-back waits give up after
+        spin_cycles SM cycles (0 = default); (-1, 0) restores normal calls."""
+        _check(lib().qtv_inject_scan_hold(self.h, int(hold_tile), int(spin_cycles)))
 
     def reserve(self, shape, max_faces: int):
         g = Grid.of(shape)

@@ -103,6 +103,9 @@ int set_error(int code, const char* fmt, ...) {
 
 int check_cuda(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return QTV_OK;
+  // clear the runtime's last-error state (a failed non-launch call would
+  // otherwise be reported again by the next launch check)
+  (void)cudaGetLastError();
   return set_error(QTV_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
@@ -284,6 +287,16 @@ int qtv_configure_sweep(qtv_handle h, int variant, int warps_per_tile, int stage
   h->sweep_nwt = warps_per_tile;
   h->sweep_stages = stages;
   h->sweep_ctas = ctas_per_sm;
+  return QTV_OK;
+}
+
+int qtv_inject_scan_hold(qtv_handle h, int64_t hold_tile, int64_t spin_cycles) {
+  if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
+  if (hold_tile < -1 || spin_cycles < 0)
+    return set_error(QTV_ERR_ARG, "scan hold: tile %lld, spin limit %lld", (long long)hold_tile,
+                     (long long)spin_cycles);
+  h->scan_hold_tile = hold_tile;
+  h->scan_spin_limit = spin_cycles;
   return QTV_OK;
 }
 

@@ -141,6 +141,11 @@ struct qtv_handle_s {
   unsigned long long* refine_counter = nullptr;  // work counter of the refinement kernel
   // sweep shape of single-snapshot calls (qtv_configure_sweep); -1 / 0 = default
   int sweep_variant = -1, sweep_nwt = 0, sweep_stages = 0, sweep_ctas = 0;
+  // failure injection (qtv_inject_scan_hold): a look-back tile of the segment
+  // scan that never publishes its state (-1: none) and the spin limit, in SM
+  // cycles, of the look-back waits (0: the default of about 2^32)
+  long long scan_hold_tile = -1;
+  long long scan_spin_limit = 0;
 };
 
 namespace qtv {
@@ -205,6 +210,7 @@ struct SnapDesc {
                     // [t st, t st + st + 2), the last one [t st, nx)
   int hblock = 1;   // planes per z block
   int nwt = 1;      // warps per x tile (tile width 64 nwt columns)
+  int nstk = 0;     // bit-sliced sweep: columns of stacked last tiles (0: none)
   long long unit0 = 0, seg0 = 0, tab0 = 0;  // first unit / segment / table entry
 };
 constexpr int kMaxSnaps = QTV_BATCH_MAX;

@@ -38,6 +38,16 @@
 // k + 1.  Waits are bounded (about 2^32 SM cycles); a timeout sets a status
 // bit that turns the reported count into QTV_COUNT_TIMEOUT.
 //
+// Stacked last tiles.  A CTA's plane step costs about the same whatever the
+// tile width (the sweep is latency-bound per CTA), so a last tile of a row
+// that is narrower than one warp (16 columns at nx = 512) would cost a whole
+// CTA unit per band and plane.  Instead the last tiles of NW consecutive
+// bands share one unit: warp v takes band band0 + v as if it were warp 0 of
+// that band's last tile, in its own 32-column strip of the slot rows.  Strip
+// rows are too short for bulk copies to pay (each bulk copy has a fixed cost),
+// so each warp fills its own strip with 16-byte cp.async copies, one commit
+// group per plane, and the warps of a stacked unit run independently.
+//
 // Output and finalize.  Each lane with faces in a plane writes one 16-byte
 // record (L and H words of the three orientations, 16 rows each, and the lane)
 // into the fixed slot block of its (plane, band, tile, warp) step (32 records,
@@ -61,6 +71,7 @@ using namespace sweep;
 using namespace bits;
 
 constexpr int kMaxRun = 256;      // planes per run (bounds the shared face totals)
+constexpr int kTail = 8;          // padding elements after the ring (stacked strips)
 
 // acc' = (acc << 1) | sign bit of x
 __device__ __forceinline__ uint32_t push1(uint32_t acc, float x) {
@@ -128,9 +139,12 @@ __global__ void __launch_bounds__(NW * 32, MINB) sweep_bits_kernel(const __grid_
   const int w = tid >> 5;
   constexpr int W2 = BL * NW + 2;  // row pitch of a slot, in elements
   float2* ring = reinterpret_cast<float2*>(dsm);
-  uint64_t* full = reinterpret_cast<uint64_t*>(dsm + (size_t)STAGES * BRH * W2 * sizeof(float2));
+  uint64_t* full =
+      reinterpret_cast<uint64_t*>(dsm + ((size_t)STAGES * BRH * W2 + kTail) * sizeof(float2));
   uint64_t* empty = full + STAGES;
   unsigned int* s_faces = reinterpret_cast<unsigned int*>(empty + STAGES);  // [kMaxRun]
+  // per warp: first node of its band's rows in the tile
+  const float2** s_src = reinterpret_cast<const float2**>(s_faces + kMaxRun);
   const int xl = BL * w + lane;  // tile-local column of this lane
 
   if (tid == 0) {
@@ -145,6 +159,11 @@ __global__ void __launch_bounds__(NW * 32, MINB) sweep_bits_kernel(const __grid_
   uint32_t fill = 0, use = 0;  // planes issued (warp 0) / consumed, counted over the whole CTA
   bool timeout = false;
   int valid_w = W2, valid_r = BRH;  // padding bookkeeping, as in the nibble sweep
+  bool stk_padded = false;          // the ring holds padding outside the stacked strips
+  // padding past the last slot: the lanes of the last stacked strip read up to
+  // 32 NW - W2 elements beyond a slot row
+  for (int i = tid; i < kTail; i += blockDim.x)
+    ring[(size_t)STAGES * BRH * W2 + i] = make_float2(1.f, 1.f);
 
   const long long U = a.units;
   long long u = U * blockIdx.x / gridDim.x;
@@ -155,14 +174,23 @@ __global__ void __launch_bounds__(NW * 32, MINB) sweep_bits_kernel(const __grid_
     while (si + 1 < a.nsnap && a.s[si + 1].unit0 <= u) ++si;
     const SnapDesc& sd = a.s[si];
     const int nx = sd.nx, ny = sd.ny, nz = sd.nz, ntx = sd.ntx;
+    // columns: (band, tile) of the tiles before the last, then (with
+    // stacking) groups of NW bands whose narrow last tiles share a CTA, one
+    // band per warp, else (band, tile) of every tile
+    const int ntn = sd.nstk ? ntx - 1 : ntx;
+    const long long nnorm = (long long)sd.nbands * ntn;
     long long col;
     int kb, kblk;
-    unit_pos(u - sd.unit0, (long long)sd.nbands * ntx, nz, sd.hblock, col, kb, kblk);
-    const int band = (int)(col / ntx), tile = (int)(col % ntx);
+    unit_pos(u - sd.unit0, nnorm + sd.nstk, nz, sd.hblock, col, kb, kblk);
+    const bool stk = col >= nnorm;
+    const int band0 = stk ? (int)(col - nnorm) * NW : 0;  // first band of a stacked group
+    const int band = stk ? band0 + w : (int)(col / ntn);  // this warp's band
+    const int tile = stk ? ntx - 1 : (int)(col % ntn);
+    const bool wok = band < sd.nbands;  // a stacked group may hold fewer than NW bands
     const int ke = (int)min(min((long long)kblk, (long long)kb + (uend - u)), (long long)kb + kMaxRun);
     u += ke - kb;
     const int j0 = band * BR;
-    const int nrows = min(BRH, ny - j0);
+    const int nrows = wok ? min(BRH, ny - j0) : 0;
     const int klast = min(ke, nz - 1);
     const int nplanes = klast - kb + 1;
     const int nsteps = ke - kb;
@@ -171,26 +199,47 @@ __global__ void __launch_bounds__(NW * 32, MINB) sweep_bits_kernel(const __grid_
     const int tw = last_tile ? nx - xt0 : sd.st + 2;
     const int own_end = last_tile ? tw : sd.st;
     const uint32_t row_bytes = (uint32_t)tw * 8u;
-    const size_t plane = (size_t)nx * ny;
+    // first node of this warp's band (stacked) or the CTA's band in the tile,
+    // kept in shared memory (read once per plane by the copying lanes)
+    __syncwarp();
+    if (lane == 0) s_src[w] = sd.psi + (size_t)(wok ? band * BR : 0) * nx + xt0;
+    __syncwarp();
+    // tile-local column of this lane, and its column in a slot (a stacked
+    // group puts band band0 + v at slot columns 32 v ..)
+    const int xs = stk ? lane : xl;
+    const int xc = stk ? 32 * w + lane : xl;
 
-    if (tw < valid_w || nrows < valid_r) {
-      const int cw = valid_w - tw;
-      if (cw > 0)
-        for (int idx = tid; idx < STAGES * BRH * cw; idx += blockDim.x)
-          ring[(size_t)(idx / cw) * W2 + tw + idx % cw] = make_float2(1.f, 1.f);
-      const int rr = valid_r - nrows;
-      if (rr > 0) {
-        const int per = rr * W2;
-        for (int idx = tid; idx < STAGES * per; idx += blockDim.x) {
-          const int sl = idx / per, rem = idx % per;
-          ring[((size_t)sl * BRH + nrows + rem / W2) * W2 + rem % W2] = make_float2(1.f, 1.f);
-        }
+    if (stk) {
+      if (!stk_padded) {
+        for (int idx = tid; idx < STAGES * BRH * W2; idx += blockDim.x)
+          ring[idx] = make_float2(1.f, 1.f);
+        fence_proxy_async();
+        __syncthreads();
+        stk_padded = true;
       }
-      fence_proxy_async();
-      __syncthreads();
+      valid_w = W2;  // a later unstacked run re-pads what it needs
+      valid_r = BRH;
+    } else {
+      stk_padded = false;
+      if (tw < valid_w || nrows < valid_r) {
+        const int cw = valid_w - tw;
+        if (cw > 0)
+          for (int idx = tid; idx < STAGES * BRH * cw; idx += blockDim.x)
+            ring[(size_t)(idx / cw) * W2 + tw + idx % cw] = make_float2(1.f, 1.f);
+        const int rr = valid_r - nrows;
+        if (rr > 0) {
+          const int per = rr * W2;
+          for (int idx = tid; idx < STAGES * per; idx += blockDim.x) {
+            const int sl = idx / per, rem = idx % per;
+            ring[((size_t)sl * BRH + nrows + rem / W2) * W2 + rem % W2] = make_float2(1.f, 1.f);
+          }
+        }
+        fence_proxy_async();
+        __syncthreads();
+      }
+      valid_w = tw;
+      valid_r = nrows;
     }
-    valid_w = tw;
-    valid_r = nrows;
     for (int i = tid; i < nsteps; i += blockDim.x) s_faces[i] = 0u;
     __syncthreads();
 
@@ -206,38 +255,78 @@ __global__ void __launch_bounds__(NW * 32, MINB) sweep_bits_kernel(const __grid_
       __syncwarp();
       if (lane < nrows)
         bulk_g2s(ring + ((size_t)sl * BRH + lane) * W2,
-                 sd.psi + (size_t)m * plane + (size_t)(j0 + lane) * nx + xt0, row_bytes, &full[sl]);
+                 s_src[0] + (size_t)m * ((size_t)nx * ny) + (size_t)lane * nx, row_bytes, &full[sl]);
       ++fill;
     };
-    auto acquire = [&]() -> const float2* {
+    // Stacked group: each warp fills and reads only its own strip, so the
+    // warps run independently, with 16-byte cp.async copies (a strip row is
+    // too short for a bulk copy to pay) in one commit group per plane.  Lane
+    // chunks: (row, 16-byte column pair) = (r0, c0) + i (dr, dc), row-major.
+    // (plane m of a run sits in slot (m - kb) % STAGES)
+    auto sfill = [&](int m) {
+      if (m <= klast && wok) {
+        const int nch = (int)(row_bytes >> 4);  // 16-byte chunks of a strip row (tw is even)
+        const float2* src = s_src[w] + (size_t)m * ((size_t)nx * ny);
+        float2* dst = ring + (size_t)((m - kb) % STAGES) * BRH * W2 + 32 * w;
+        const int dr = 32 / nch, dc = 32 - dr * nch;
+        int r = lane / nch, c = lane - (lane / nch) * nch;
+        while (r < nrows) {
+          cp_async16(dst + r * W2 + 2 * c, src + (size_t)r * nx + 2 * c);
+          r += dr;
+          c += dc;
+          if (c >= nch) {
+            c -= nch;
+            ++r;
+          }
+        }
+      }
+      cp_async_commit();
+    };
+    auto acquire = [&](int m) -> const float2* {
+      if (stk) {
+        cp_async_wait<STAGES - 1>();
+        __syncwarp();
+        return ring + (size_t)((m - kb) % STAGES) * BRH * W2;
+      }
       const int sl = (int)(use % STAGES);
       if (!mbar_wait(&full[sl], (use / STAGES) & 1u)) timeout = true;
       return ring + (size_t)sl * BRH * W2;
     };
-    auto release = [&]() {
+    // done with plane m (a stacked warp refills its strip's slot at once)
+    auto release = [&](int m) {
       __syncwarp();
+      if (stk) {
+        sfill(m + STAGES);
+        return;
+      }
       if (lane == 0) mbar_arrive(&empty[use % STAGES]);
       ++use;
     };
 
     // masks of the faces this lane owns (rows 0..15 of the band)
-    const int avail = ny - j0;  // rows of the band that exist
+    const int avail = wok ? ny - j0 : 0;  // rows of the band that exist
     const uint32_t rv = avail >= BR ? kRows16 : ((1u << avail) - 1u);
     const uint32_t rv1 = avail - 1 >= BR ? kRows16 : (avail > 1 ? ((1u << (avail - 1)) - 1u) : 0u);
-    const bool own = lane < BL && xl < own_end;
-    const uint32_t m_xy = (own && xl + 1 < tw) ? rv1 : 0u;
-    const uint32_t m_yz = (own && xl < tw) ? rv1 : 0u;
-    const uint32_t m_zx = (own && xl + 1 < tw) ? rv : 0u;
+    const bool own = wok && lane < BL && xs < own_end;
+    const uint32_t m_xy = (own && xs + 1 < tw) ? rv1 : 0u;
+    const uint32_t m_yz = (own && xs < tw) ? rv1 : 0u;
+    const uint32_t m_zx = (own && xs + 1 < tw) ? rv : 0u;
     // table entries of this (band, tile, warp): one per plane, contiguous in k;
-    // records of entry e in the fixed slots 32 e .. 32 e + 31 (one per lane)
+    // records of entry e in the fixed slots 32 e .. 32 e + 31 (one per lane).
+    // A stacked warp is warp 0 of its band's last tile; that tile's other
+    // warps own no columns and get empty entries.
     const unsigned long long ebase =
-        (unsigned long long)sd.tab0 + (((unsigned long long)band * ntx + tile) * NW + w) * nz;
+        (unsigned long long)sd.tab0 +
+        (((unsigned long long)band * ntx + tile) * NW + (stk ? 0 : w)) * nz;
     uint2* const table = reinterpret_cast<uint2*>(a.table);
     uint4* const recs = reinterpret_cast<uint4*>(a.recs);
     uint2 tent = make_uint2(0u, 0u);  // entry of step t held by lane t % 32
 
-    if (w == 0)
+    if (stk) {
+      for (int i = 0; i < STAGES; ++i) sfill(kb + i);
+    } else if (w == 0) {
       for (int i = 0; i < min(STAGES, nplanes); ++i) produce(kb + i);
+    }
 
     // ---- prologue: plane kb (values into vA)
     float2 vA[BRH], vB[BRH];
@@ -245,22 +334,22 @@ __global__ void __launch_bounds__(NW * 32, MINB) sweep_bits_kernel(const __grid_
     Edge X0, Y0, Y0n;
     bool bad0;
     {
-      const float2* sp = acquire();
+      const float2* sp = acquire(kb);
       uint32_t SX = 0, SY = 0;
       unsigned long long prod = kProdOne;
       S0 = 0;
 #pragma unroll
       for (int r = BRH - 1; r >= 0; --r) {
-        const float2 v = sp[r * W2 + xl];
-        const float2 nb = sp[r * W2 + xl + 1];
+        const float2 v = sp[r * W2 + xc];
+        const float2 nb = sp[r * W2 + xc + 1];
         S0 = push1(S0, v.y);
         SX = push1(SX, cross_f(v.x, v.y, nb.x, nb.y));
         if (r < BR) SY = push1(SY, cross_f(v.x, v.y, vA[r + 1].x, vA[r + 1].y));
         prod = prod_step(prod, v);
         vA[r] = v;
       }
-      release();
-      if (w == 0 && kb + STAGES <= klast) produce(kb + STAGES);
+      release(kb);
+      if (w == 0 && !stk && kb + STAGES <= klast) produce(kb + STAGES);
       bad0 = __any_sync(0xffffffffu, prod_special(prod));
       if (bad0) {
 #pragma unroll
@@ -291,13 +380,13 @@ __global__ void __launch_bounds__(NW * 32, MINB) sweep_bits_kernel(const __grid_
       Edge X1{0, 0, 0}, Y1{0, 0, 0}, Y1n{0, 0, 0};
       bool bad1 = false;
       if (has_up) {
-        const float2* sp = acquire();
+        const float2* sp = acquire(k + 1);
         uint32_t SX = 0, SY = 0, SZ = 0;
         unsigned long long prod = kProdOne;
 #pragma unroll
         for (int r = BRH - 1; r >= 0; --r) {
-          const float2 v = sp[r * W2 + xl];
-          const float2 nb = sp[r * W2 + xl + 1];
+          const float2 v = sp[r * W2 + xc];
+          const float2 nb = sp[r * W2 + xc + 1];
           S1 = push1(S1, v.y);
           SX = push1(SX, cross_f(v.x, v.y, nb.x, nb.y));
           SZ = push1(SZ, cross_f(V0[r].x, V0[r].y, v.x, v.y));
@@ -305,8 +394,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) sweep_bits_kernel(const __grid_
           prod = prod_step(prod, v);
           V1[r] = v;
         }
-        release();
-        if (w == 0 && k + 1 + STAGES <= klast) produce(k + 1 + STAGES);
+        release(k + 1);
+        if (w == 0 && !stk && k + 1 + STAGES <= klast) produce(k + 1 + STAGES);
         bad1 = __any_sync(0xffffffffu, prod_special(prod));
         S1n = __shfl_down_sync(0xffffffffu, S1, 1);
         const uint32_t SYn = __shfl_down_sync(0xffffffffu, SY, 1);
@@ -365,10 +454,18 @@ __global__ void __launch_bounds__(NW * 32, MINB) sweep_bits_kernel(const __grid_
         recs[e * 32ull + lane] =
             make_uint4(Lxy | (Hxy << 16), Lyz | (Hyz << 16), Lzx | (Hzx << 16), (uint32_t)lane);
       if (lane == (t & 31)) tent = make_uint2(bal, faces_w);
-      if ((t & 31) == 31 || t == nsteps - 1) {
-        if (lane <= (t & 31)) table[ebase + (unsigned long long)(kb + (t & ~31) + lane)] = tent;
+      if (((t & 31) == 31 || t == nsteps - 1) && wok) {
+        if (lane <= (t & 31)) {
+          const unsigned long long ei = ebase + (unsigned long long)(kb + (t & ~31) + lane);
+          table[ei] = tent;
+          if (stk)
+            for (int v = 1; v < NW; ++v) table[ei + (unsigned long long)v * nz] = make_uint2(0u, 0u);
+        }
       }
-      if (lane == 0 && faces_w) atomicAdd(&s_faces[t], faces_w);
+      if (lane == 0 && faces_w) {
+        if (stk) atomicAdd(&a.segf[sd.seg0 + (size_t)k * sd.nbands + band], faces_w);
+        else atomicAdd(&s_faces[t], faces_w);
+      }
       // plane k + 1 becomes plane k
       S0 = S1;
       S0n = S1n;
@@ -386,6 +483,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) sweep_bits_kernel(const __grid_
       step(vA, vB, t);
       if (t + 1 < nsteps) step(vB, vA, t + 1);
     }
+    if (stk) cp_async_wait<0>();  // only empty groups are left
     __syncthreads();
     // face totals of the run's planes into the (plane, band) segments
     for (int i = tid; i < nsteps; i += blockDim.x)
@@ -415,8 +513,9 @@ int bits_fn_index(int nw, int stages) {
 }  // namespace
 
 size_t bits_smem_bytes(int nw, int stages) {
-  return (size_t)stages * BRH * (BL * nw + 2) * sizeof(float2) + 2 * stages * sizeof(uint64_t) +
-         kMaxRun * sizeof(unsigned int);
+  return ((size_t)stages * BRH * (BL * nw + 2) + kTail) * sizeof(float2) +
+         2 * stages * sizeof(uint64_t) + kMaxRun * sizeof(unsigned int) +
+         (size_t)nw * sizeof(const float2*);
 }
 
 int bits_variant_occupancy(int nw, int stages, int* ctas_per_sm, size_t* smem) {

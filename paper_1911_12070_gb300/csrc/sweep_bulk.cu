@@ -546,7 +546,7 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
 __global__ void __launch_bounds__(kScanThreads) v3_scan_kernel(
     const unsigned int* __restrict__ segf, long long nseg, unsigned long long* __restrict__ seg_off,
     uint64_t* count, unsigned long long* counters, unsigned long long* tiles, long long ntiles,
-    qtv_stats* stats, unsigned long long scanned) {
+    qtv_stats* stats, unsigned long long scanned, long long hold_tile, long long spin_limit) {
   __shared__ unsigned long long s_warp[kScanThreads / 32];
   __shared__ unsigned long long s_prefix;
   __shared__ long long s_tile;
@@ -587,10 +587,13 @@ __global__ void __launch_bounds__(kScanThreads) v3_scan_kernel(
       // ix: tile aggregate
       const unsigned long long agg = ix;
       unsigned long long prefix = 0;
+      // a held tile (failure injection) never publishes, so a later tile's
+      // look-back wait on it runs out
+      const bool publish = tile != hold_tile;
       if (tile == 0) {
-        atomicExch(&tiles[0], kFlagP | agg);
+        if (publish) atomicExch(&tiles[0], kFlagP | agg);
       } else {
-        atomicExch(&tiles[tile], kFlagA | agg);
+        if (publish) atomicExch(&tiles[tile], kFlagA | agg);
         long long p = tile - 1;
         while (p >= 0) {
           unsigned long long st = ld_volatile_u64(&tiles[p]);
@@ -598,7 +601,7 @@ __global__ void __launch_bounds__(kScanThreads) v3_scan_kernel(
             const long long t0 = clock64();
             while ((st >> 62) == 0) {
               st = ld_volatile_u64(&tiles[p]);
-              if (clock64() - t0 > (1ll << 32)) break;
+              if (clock64() - t0 > spin_limit) break;
             }
             if ((st >> 62) == 0) {
               atomicOr(reinterpret_cast<unsigned int*>(counters + 1), 4u);
@@ -609,7 +612,7 @@ __global__ void __launch_bounds__(kScanThreads) v3_scan_kernel(
           if ((st >> 62) == 2) break;
           --p;
         }
-        atomicExch(&tiles[tile], kFlagP | (prefix + agg));
+        if (publish) atomicExch(&tiles[tile], kFlagP | (prefix + agg));
       }
       s_prefix = prefix;
       if (tile == ntiles - 1) {
@@ -949,6 +952,13 @@ int batch_layout(int num_sms, int nsnap, const qtv_grid* grids, const float2* co
       d.nwt = tc.nwt > 0 ? tc.nwt : 4;
       d.st = 31 * d.nwt;
       d.ntx = (g.nx + d.st - 1) / d.st;
+      // A last tile narrower than one warp would cost a whole CTA step per
+      // plane and band for a few columns: the last tiles of nwt bands share
+      // one CTA instead (one band per warp, each in its own 32-column strip
+      // of the slot rows, which must fit the row pitch 31 nwt + 2).
+      const int tw_last = g.nx - (d.ntx - 1) * d.st;
+      d.nstk = (tw_last + 32 * (d.nwt - 1) <= 31 * d.nwt + 2) ? (d.nbands + d.nwt - 1) / d.nwt : 0;
+      // warps of the last tile that own columns (a warp owns 31)
     } else {
       d.nbands = (g.ny + R - 1) / R;
       d.nwt = tc.nwt > 0 ? tc.nwt : (g.nx + 63) / 64;
@@ -988,7 +998,8 @@ int batch_layout(int num_sms, int nsnap, const qtv_grid* grids, const float2* co
       if (B->group_of[i] != (int)gi) continue;
       SnapDesc d = fin.s[i];
       d.unit0 = units;
-      units += (long long)d.nbands * d.ntx * d.nz;
+      units += d.nstk ? ((long long)d.nbands * (d.ntx - 1) + d.nstk) * d.nz
+                      : (long long)d.nbands * d.ntx * d.nz;
       nodes += (double)d.nx * d.ny * d.nz;
       p.s[p.nsnap++] = d;
     }
@@ -1011,7 +1022,8 @@ int batch_layout(int num_sms, int nsnap, const qtv_grid* grids, const float2* co
     // are spread over its (band, tile) columns
     for (int j = 0; j < p.nsnap; ++j) {
       SnapDesc& d = p.s[j];
-      const long long cols = (long long)d.nbands * d.ntx;
+      const long long cols =
+          d.nstk ? (long long)d.nbands * (d.ntx - 1) + d.nstk : (long long)d.nbands * d.ntx;
       const double share = (double)grid * (double)(cols * d.nz) / (double)units;
       long long zblocks = (long long)(share / (double)cols + 0.5);
       if (zblocks < 1) zblocks = 1;
@@ -1111,7 +1123,9 @@ int batch_launch(qtv_handle h, BatchLayout& B, const IdentScratch& sc, uint64_t*
     TraceScope ts(h, K_SEG_SCAN, st);
     e = launch_dependent(v3_scan_kernel, dim3((unsigned)B.ntiles), dim3(kScanThreads), 0, st,
                          reinterpret_cast<const unsigned int*>(sc.seg), B.fin.nseg, sc.seg_off,
-                         count, sc.counters, sc.tiles, B.ntiles, stats, scanned);
+                         count, sc.counters, sc.tiles, B.ntiles, stats, scanned,
+                         h ? h->scan_hold_tile : -1ll,
+                         (h && h->scan_spin_limit > 0) ? h->scan_spin_limit : (1ll << 32));
   }
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return check_cuda(e, "v3_scan_kernel launch");
