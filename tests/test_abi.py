@@ -148,3 +148,7 @@ def test_binding_argument_kinds_match_the_header(lib):
             continue
         got = [_ctypes_kind(t) for t in argtypes]
         assert got == kinds, (name, got, kinds)
+
+
+def test_scan_hold_injection_is_validated_on_the_host(lib):
+    assert lib.qtv_inject_scan_hold(None, 0, 0) == qtv.ERR_ARG

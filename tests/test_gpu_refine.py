@@ -34,6 +34,11 @@ def q():
     h.close()
 
 
+# density agreement off the strict subset: relative to the oracle's density
+# there, plus an absolute floor relative to max |psi|^2 (FP32 evaluation of rho)
+RHO_REL, RHO_ABS = 1e-3, 1e-7
+
+
 def _face_centres(ids, shape):
     nz, ny, nx = shape
     o = (ids & np.uint64(3)).astype(np.int64)
@@ -48,15 +53,27 @@ def _host(out):
 
 
 def _compare(host, x0, g, r, min_sel=0.6):
+    """Every sample is checked.  Flags: no-tangent exactly; converged / step
+    limit equal except where both searches ended at a zero of rho (a search
+    that reaches a zero stops within a step or two of the step limit in FP32
+    and FP64 alike, so the limit may be hit on one side only).  Positions within
+    1e-4 h on the strict subset (both converged, away from the grid and box
+    boundaries, well-conditioned zero); on every other sample the two searches
+    must end at the same density, since rho is what the descent minimizes and
+    flat directions of rho leave the position itself loosely fixed."""
     m2 = float(np.max(np.abs(host.astype(np.complex128)) ** 2))
     nt_g = (g["flags"] & 2) != 0
     nt_o = (r["flags"] & oracle.R_NO_TANGENT) != 0
     assert np.array_equal(nt_g, nt_o)
     both = ~nt_o
     assert np.max(np.abs(g["t"][both] - r["t"][both]), initial=0.0) < 1e-3
+    at_zero = (g["rho"] < 1e-9 * m2) & (r["rho"] < 1e-9 * m2)
+    differ = both & (g["flags"] != r["flags"])
+    assert not np.any(differ & ~at_zero), np.nonzero(differ & ~at_zero)[0][:10]
+    assert differ.sum() <= max(2, 0.002 * both.sum()), int(differ.sum())
     hi = np.array(host.shape[::-1]) - 1
     dx = r["xyz"] - x0
-    sel = both & (r["flags"] == oracle.R_CONVERGED) & \
+    sel = both & (r["flags"] == oracle.R_CONVERGED) & (g["flags"] == oracle.R_CONVERGED) & \
         np.all((r["xyz"] > 1e-6) & (r["xyz"] < hi - 1e-6), axis=1) & \
         (np.max(np.abs(dx), axis=1) < 1 - 1e-6) & (np.abs(r["detj"]) >= 1e-3 * m2)
     assert sel.mean() >= min_sel, sel.mean()
@@ -65,6 +82,26 @@ def _compare(host, x0, g, r, min_sel=0.6):
     bad = sel & (err > tol)
     assert not bad.any(), (int(bad.sum()), float(err[sel].max()))
     assert np.max(g["rho"][sel]) < 1e-9 * m2
+    # off the strict subset, start points inside the grid: both searches end
+    # at the same density; start points on the grid boundary: a direction that
+    # leaves the grid is rejected, so an FP32 and an FP64 direction that differ
+    # by rounding may decide whether the search moves at all; there both only
+    # never increase rho
+    inner = np.all((x0 > 1e-6) & (x0 < hi - 1e-6), axis=1)
+    rest = both & ~sel & inner
+    edge = both & ~sel & ~inner
+    drho = np.abs(g["rho"].astype(np.float64) - r["rho"])
+    rho_tol = RHO_REL * r["rho"] + RHO_ABS * m2
+    print(f"strict {int(sel.sum())}, rest {int(rest.sum())}, boundary {int(edge.sum())}, "
+          f"flags differ {int(differ.sum())}, "
+          f"max |drho|/m2 on rest {np.max(drho[rest] / m2, initial=0.0):.2e}")
+    assert not np.any(rest & (drho > rho_tol)), (
+        int(np.sum(rest & (drho > rho_tol))), float(np.max((drho / rho_tol)[rest])))
+    rho0 = oracle.density(host, x0)
+    assert np.all(r["rho"][both] <= rho0[both] * (1 + 1e-12) + 1e-15 * m2)
+    assert np.all(g["rho"][both] <= rho0[both] * (1 + 1e-5) + 1e-9 * m2)
+    # the position never leaves the search box around x0 on either side
+    assert np.all(np.max(np.abs(g["xyz"][both] - x0[both]), axis=1) <= 1 + 1e-5)
     return int(sel.sum()), float(err[sel].max())
 
 
