@@ -166,6 +166,22 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": max(pw) if pw else None}
 
 
+def field_pin(psi, n):
+    """SHA-256 of the field's bytes and whether it equals the value pinned for
+    this environment in synth/pins.json (the 512^3 workload only)."""
+    from synth import make_pins
+
+    sha = make_pins.sha256_of(psi)
+    pinned = None
+    if n == 512:
+        try:
+            pinned = make_pins.load()["device"].get(make_pins.environment_key(), {}).get(
+                "512_waves_noise")
+        except Exception:
+            pinned = None
+    return {"sha256": sha, "matches_pin": (sha == pinned) if pinned else None}
+
+
 def make_field(n, device):
     import synth
 
@@ -737,6 +753,7 @@ def run_qtv(args):
     psi = make_field(n, dev)
     torch.cuda.synchronize()
     nodes = n ** 3
+    input_pin = field_pin(psi, n)
     stream = torch.cuda.current_stream()
 
     # size the outputs from one untimed call (with the statistics: ambiguous
@@ -891,6 +908,7 @@ def run_qtv(args):
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": [n, n, n], "pierced_faces": F,
+                   "input_sha256": input_pin,
                    "l2": "inputs larger than L2 (1 GiB field, 129 MB L2); no flush",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": "sweep", "achieved": achieved, "peak": peak,

@@ -248,7 +248,11 @@ QTV_API int qtv_identify_localize_host(qtv_handle h, const qtv_grid* grid, const
  * are rejected with QTV_ERR_ARG and a message naming the limit.
  * The first call on a device resolves the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before capturing any stream.  The call uses the current device.
+ * before capturing any stream.  The call uses the current device.  The
+ * address is kept for the life of the process: calls after cudaDeviceReset
+ * on that device are not supported.  Odd nx, or psi aligned to 8 but not 16
+ * bytes, runs the register sweep instead of the staged one, within the same
+ * limits.
  * Every call shares the one array, and the array keeps the last call's
  * contents (each call clears what must start at zero): calls that may
  * overlap on the GPU (different streams, or different host threads on the

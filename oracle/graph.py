@@ -41,6 +41,18 @@ Readings where the text leaves details open:
   per segment; open lines repeat their end points, loops wrap around;
 * Eq. 7: e = sum |rho(x_i)| / (mean rho over the field * N) over the spline
   points x_i, rho trilinearly interpolated;
+* lattice box reduction (`box_reduce`, an order-independent parallel reading
+  of Sec. 3.3.1-3.3.2): positions are held in fixed point, integers in units
+  of 2^-32 h (the FP32 sample positions convert exactly); pass p lays a
+  lattice of boxes of side D = round(d 2^32) over space, shifted by
+  floor(D / 2) in every axis on odd passes; the nodes of one box that are
+  connected through edges inside that box form one cluster, which collapses
+  to one node at the rounded mean floor((sum + c / 2) / c) of its members'
+  positions (each current node counted once), named by the lowest original
+  index it contains and carrying the union of its members' external edges;
+  passes repeat until two consecutive passes (one of each lattice) merge
+  nothing, at most 10 passes.  Unlike the sequential traversal of `reduce`,
+  its result does not depend on the numbering of the nodes;
 * arc-length thinning (`thin_piece`, a parallel reading of the box means of
   Sec. 3.3.2 on ordered pieces): consecutive samples of a piece are grouped by
   the box index floor(s / d) of their arc length s along the piece, each group
@@ -234,6 +246,85 @@ def reduce(g: Graph, d: float = 4.0, tol: float = 1e-3, max_passes: int = 10):
         if move < tol:
             break
     return g, passes
+
+
+FIX = 2 ** 32  # fixed-point units per grid spacing of box_reduce
+
+
+def _fixed(pos):
+    """Exact fixed-point integers (units of 2^-32 h) of positions that are
+    FP32 values (asserts exactness)."""
+    out = []
+    for p in np.asarray(pos, np.float64).reshape(-1, 3):
+        row = []
+        for x in p:
+            q = float(x) * FIX
+            assert q == int(q) and x >= 0.0, "positions must be non-negative FP32 values"
+            row.append(int(q))
+        out.append(tuple(row))
+    return out
+
+
+def box_reduce(g: Graph, d: float = 4.0, max_passes: int = 10):
+    """Lattice box reduction of a graph (the order-independent reading of Sec.
+    3.3.1-3.3.2 in the module header).  Returns (reduced graph, label of every
+    node of g = the lowest node index of its final cluster, fixed-point
+    positions of the reduced nodes, number of passes).  Reduced nodes are in
+    ascending order of their labels."""
+    D = int(round(d * FIX))
+    assert D > 0
+    # current graph: nodes named by their lowest original index
+    names = list(range(g.n))
+    qpos = dict(zip(names, _fixed(g.pos)))
+    dirs = {u: np.array(g.dirs[u], np.float64) for u in names}
+    adj = {u: set(g.adj[u]) for u in names}
+    label = list(range(g.n))
+    quiet = 0
+    passes = 0
+    while passes < max_passes and quiet < 2:
+        off = 0 if passes % 2 == 0 else D // 2
+        key = {u: tuple((c - off) // D for c in qpos[u]) for u in names}
+        seen, clusters = set(), []
+        for s in sorted(names):
+            if s in seen:
+                continue
+            seen.add(s)
+            members, stack = [s], [s]
+            while stack:
+                u = stack.pop()
+                for v in adj[u]:
+                    if v not in seen and key[v] == key[u]:
+                        seen.add(v)
+                        members.append(v)
+                        stack.append(v)
+            clusters.append(sorted(members))
+        new_of = {}
+        nq, nd, nadj = {}, {}, {}
+        for m in clusters:
+            rep = m[0]
+            c = len(m)
+            nq[rep] = tuple((sum(qpos[u][a] for u in m) + c // 2) // c for a in range(3))
+            nd[rep] = sum((dirs[u] for u in m), np.zeros(3))
+            for u in m:
+                new_of[u] = rep
+        for u in names:
+            a = new_of[u]
+            nadj.setdefault(a, set())
+            for v in adj[u]:
+                b = new_of[v]
+                if a != b:
+                    nadj[a].add(b)
+        merged = len(clusters) < len(names)
+        names = sorted(nq)
+        qpos, dirs, adj = nq, nd, nadj
+        label = [new_of[x] for x in label]
+        passes += 1
+        quiet = 0 if merged else quiet + 1
+    index = {u: a for a, u in enumerate(names)}
+    red = Graph(np.array([[c / FIX for c in qpos[u]] for u in names], np.float64).reshape(-1, 3),
+                np.array([dirs[u] for u in names], np.float64).reshape(-1, 3),
+                [set(index[v] for v in adj[u]) for u in names])
+    return red, np.array(label, np.int64), [qpos[u] for u in names], passes
 
 
 # ---------------------------------------------------------------------------

@@ -304,3 +304,65 @@ def test_learned_localize_fallback_is_plain(q, trained):
     d = torch.linalg.norm(xyz_l - xyz_p, dim=1).cpu().numpy()
     print(f"learned accepted {learned_mask.mean():.3f}, RMS vs plain {np.sqrt(np.mean(d**2)):.4f} h")
     assert np.sqrt(np.mean(d ** 2)) <= 0.05
+
+
+def test_learned_batch_against_oracle(q, trained):
+    """The uneven batch with the trained locator on (the batched workload runs
+    it): every face is accepted (LEARNED) or falls back (FALLBACK), never both;
+    fallback samples are the oracle's plain zeros within 1e-4 h (Sec. 3.3.3,
+    Eq. 6) on unambiguous, well-conditioned faces; an accepted sample lies in
+    its face, its reported residual is the oracle's interpolated density there
+    (linear interpolation, Sec. 5), that density meets the acceptance rule
+    against the oracle's neighbourhood RMS, and accepted samples are within
+    0.05 h RMS of the oracle's plain zeros."""
+    import paper_1911_12070_gb300 as qtv
+    from oracle import mlp
+    from qtv_testutil import compare_positions
+
+    shapes = [(40, 48, 130), (24, 64, 96), (33, 45, 66)]
+    hosts = [synth.multiplicative_noise(
+        synth.random_waves_numpy(s, synth.wave_spec(400 + i, 512)), 500 + i)
+        for i, s in enumerate(shapes)]
+    devs = [torch.from_numpy(h).cuda() for h in hosts]
+    q.batch_plan(devs)
+    out = q.batch_run(mode=qtv.LEARNED, fallback_resid=1e-3)
+    n_acc = n_all = 0
+    for host, d in zip(hosts, out):
+        ids = d["ids"].cpu().numpy().view(np.uint64)
+        w = d["w"].cpu().numpy()
+        xyz = d["xyz"].cpu().numpy()
+        resid = d["resid"].cpu().numpy()
+        fl = d["flags"].cpu().numpy()
+        acc = (fl & qtv.FLAG_LEARNED) != 0
+        fb = (fl & qtv.FLAG_FALLBACK) != 0
+        assert np.all(acc ^ fb)
+        ora = oracle.localize(host, ids, w)
+        _, ofl = oracle.identify(host)
+        o = (ids & np.uint64(3)).astype(np.int64)
+        lin = (ids >> np.uint64(2)).astype(np.int64)
+        f = ofl.reshape(3, -1)[o, lin]
+        ok = ((ora["flags"] & (oracle.L_ANOMALOUS | oracle.L_ILLCOND)) == 0) & \
+            ((f & (oracle.AMBIGUOUS | oracle.ZERO_NODE)) == 0)
+        bad, emax = compare_positions(xyz[fb], {"xyz": ora["xyz"][fb]}, ok[fb])
+        assert bad == 0, (bad, emax)
+        m2 = float(np.max(np.abs(host.astype(np.complex128)) ** 2))
+        _, okenc, rms = mlp.encode(host, ids[acc], w[acc])
+        assert okenc.all()
+        rho = oracle.density(host, xyz[acc].astype(np.float64))
+        # |F| at the FP32 sample against |F| at its FP32 grid coordinates: the
+        # coordinates round by |x| 2^-24, and |grad F| <= 4 max|psi| on a face
+        slack = 4 * np.sqrt(m2) * np.max(np.abs(xyz[acc]), axis=1) * 2.0 ** -23 + 1e-6 * np.sqrt(m2)
+        assert np.all(np.abs(np.sqrt(resid[acc]) - np.sqrt(rho)) <= slack)
+        assert np.all(np.sqrt(rho) <= np.sqrt(1e-3) * rms + slack)
+        corner = np.column_stack([lin % host.shape[2], (lin // host.shape[2]) % host.shape[1],
+                                  lin // (host.shape[2] * host.shape[1])])[acc]
+        normal = np.array([2, 0, 1])[o[acc]]  # the axis the face does not span
+        rel = xyz[acc] - corner
+        assert np.all(np.abs(rel[np.arange(len(rel)), normal]) == 0)
+        assert np.all((rel > -0.01 - 1e-5) & (rel < 1.01 + 1e-5))
+        dd = np.linalg.norm(xyz[acc] - ora["xyz"][acc], axis=1)
+        assert np.sqrt(np.mean(dd ** 2)) <= 0.05
+        n_acc += int(acc.sum())
+        n_all += len(ids)
+    print(f"learned batch: {n_acc} of {n_all} faces accepted")
+    assert n_acc > 0.8 * n_all

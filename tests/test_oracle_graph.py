@@ -237,3 +237,122 @@ def test_bridged_perpendicular_lines_are_type_III():
     assert len(out["lines"]) == 5 and all(l["piece"] == "I" for l in out["lines"])
     # the pieces cover the three segments: total length ~ 27 + 27 + 8
     assert 55 < sum(l["length"] for l in out["lines"]) < 66
+
+
+# ------------------------------------------- lattice box reduction (Sec. 3.3.2)
+def _f32(g):
+    """The graph with FP32 positions (as the GPU sample stream has them)."""
+    return graph.Graph(g.pos.astype(np.float32).astype(np.float64), g.dirs, g.adj)
+
+
+def _chain(xs, y=3.0, z=5.0):
+    xs = np.asarray(xs, np.float64)
+    pos = np.stack([xs, np.full_like(xs, y), np.full_like(xs, z)], 1)
+    return _path_graph(pos, [(a, a + 1) for a in range(len(xs) - 1)])
+
+
+@pytest.mark.parametrize("step", [1.0, 0.5, 0.25])
+def test_box_reduce_chain_closed_form(step):
+    # a straight chain with a spacing that divides the box: the first lattice
+    # groups the nodes x in [4 m, 4 m + 4) and each group becomes its mean,
+    # 4 m + 2 - step / 2, so the means are 4 apart; the shifted lattice then
+    # finds each mean alone in its box, and so does the first again: three
+    # passes
+    xs = np.arange(0.0, 20.0, step)
+    red, lab, q, passes = graph.box_reduce(_chain(xs), 4.0)
+    groups = [xs[(xs >= 4 * m) & (xs < 4 * m + 4)] for m in range(5)]
+    assert passes == 3
+    assert np.allclose(red.pos[:, 0], [g.mean() for g in groups], atol=1e-9)
+    assert np.all(red.pos[:, 1:] == [3.0, 5.0])
+    assert list(lab) == [int(np.flatnonzero(xs >= 4 * np.floor(x / 4))[0]) for x in xs]
+    assert [len(a) for a in red.adj] == [1, 2, 2, 2, 1]
+
+
+def test_box_reduce_merges_across_the_first_lattice():
+    # nodes at x = 3.5 and 4.5 sit in different boxes of the first lattice and
+    # in one box of the shifted lattice (side 4, shifted by 2)
+    red, lab, _, passes = graph.box_reduce(_chain([3.5, 4.5]), 4.0)
+    assert len(red.adj) == 1 and red.pos[0, 0] == 4.0 and list(lab) == [0, 0]
+    assert passes == 4  # merge on pass 2, then one quiet pass of each lattice
+
+
+def test_box_reduce_never_merges_unconnected_nodes():
+    pos = np.array([[1.0, 1.0, 1.0], [1.5, 1.0, 1.0], [2.0, 1.0, 1.0]])
+    red, lab, _, _ = graph.box_reduce(_path_graph(pos, [(0, 1)]), 4.0)
+    assert list(lab) == [0, 0, 2] and len(red.adj) == 2
+
+
+def test_box_reduce_rounds_means_in_fixed_point():
+    # mean of 0, 2^-32 and 2^-32 (in h) is 2/3 of a unit: rounded to 1 unit
+    u = 2.0 ** -32
+    red, _, q, _ = graph.box_reduce(_chain([0.0, u, u]), 4.0)
+    assert q[0][0] == 1 and red.pos[0, 0] == u
+
+
+def test_box_reduce_keeps_a_branch_point():
+    # three arms from a centre: the reduced graph is still a tree with one
+    # node of degree three (a reconnection point, Sec. 3.4)
+    c = np.array([10.0, 10.0, 10.0])
+    pos, edges = [c], []
+    for d in ((1, 0, 0), (0, 1, 0), (-1, 0, 0)):
+        prev = 0
+        for s in range(1, 9):
+            pos.append(c + s * np.array(d, np.float64))
+            edges.append((prev, len(pos) - 1))
+            prev = len(pos) - 1
+    red, _, _, _ = graph.box_reduce(_path_graph(pos, edges), 4.0)
+    deg = sorted(len(a) for a in red.adj)
+    assert deg.count(3) == 1 and deg.count(1) == 3 and set(deg) <= {1, 2, 3}
+    assert sum(deg) == 2 * (len(deg) - 1)  # a tree
+
+
+def test_box_reduce_does_not_depend_on_the_numbering():
+    g = _f32(_faces(synth.random_waves_numpy((24, 28, 32), synth.wave_spec(61, 256))))
+    red, lab, q, passes = graph.box_reduce(g, 4.0)
+    perm = np.random.default_rng(3).permutation(g.n)
+    inv = np.argsort(perm)
+    gp = graph.Graph(g.pos[perm], g.dirs[perm], [set(int(inv[v]) for v in g.adj[u]) for u in perm])
+    red2, lab2, q2, passes2 = graph.box_reduce(gp, 4.0)
+    assert passes2 == passes and sorted(q2) == sorted(q)
+    # the same partition of the original nodes
+    part = {frozenset(np.flatnonzero(lab == r)) for r in np.unique(lab)}
+    part2 = {frozenset(perm[np.flatnonzero(lab2 == r)]) for r in np.unique(lab2)}
+    assert part == part2
+
+
+def test_box_reduce_is_a_fixed_point():
+    g = _f32(_faces(synth.random_waves_numpy((24, 28, 32), synth.wave_spec(62, 256))))
+    red, _, q, passes = graph.box_reduce(g, 4.0)
+    assert 3 <= passes <= 10
+    again, lab, q2, p2 = graph.box_reduce(red, 4.0)
+    assert p2 == 2 and q2 == q and list(lab) == list(range(red.n))
+
+
+def test_box_reduce_of_the_straight_line_and_the_ring():
+    # config 0 line: one xy face per plane, z = k exactly: means at 4 m + 1.5
+    red, _, _, _ = graph.box_reduce(_f32(_faces(synth.analytic_line_ring(with_ring=False))), 4.0)
+    assert np.array_equal(red.pos[:, 2], 4.0 * np.arange(16) + 1.5)
+    assert np.all(np.abs(red.pos[:, 0] - 31.37) < 1) and np.all(np.abs(red.pos[:, 1] - 30.81) < 1)
+    # the ring stays one loop; its polygon length approaches 2 pi R
+    g = _f32(_faces(synth.analytic_line_ring(with_line=False)))
+    target = 2 * np.pi * 12
+    errs = []
+    for d in (6.0, 4.0, 3.0):
+        red, _, _, _ = graph.box_reduce(g, d)
+        assert all(len(a) == 2 for a in red.adj)
+        (nodes,) = graph.components(red)
+        _, path, closed = graph.ordered_lines(red, nodes)[0]
+        assert closed
+        errs.append(abs(graph.curve_length(red.pos[path], True) - target))
+    assert errs[-1] < 0.03 * target and errs[-1] < errs[0]
+
+
+def test_box_reduce_uneven_chain_by_hand():
+    # x = 0, 0.75, ..., 19.5: the first lattice gives means 1.875, 6, 9.75,
+    # 13.875, 18; on the shifted lattice (boxes [4 m + 2, 4 m + 6)) 6 and 9.75
+    # share box m = 1 and merge into 7.875; then neither lattice merges
+    # anything (keys 0, 1, 3, 4 and -1, 1, 2, 4): four passes
+    red, lab, _, passes = graph.box_reduce(_chain(np.arange(0.0, 20.0, 0.75)), 4.0)
+    assert passes == 4
+    assert list(red.pos[:, 0]) == [1.875, 7.875, 13.875, 18.0]
+    assert list(lab) == [0] * 6 + [6] * 10 + [16] * 6 + [22] * 5
