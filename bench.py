@@ -445,7 +445,29 @@ def lines_report(q, psi, ids, wnd, xyz, F, stream, reps=5):
     except qtv.QtvError as err:
         return {"error": str(err)}
     k2 = {k: v[1] / max(1, v[0]) for k, v in tr2.items()}
+    # the box-mean reduction of the whole face graph (lattice reading of Sec.
+    # 3.3.2: clusters across branch points, passes to a fixed point), then the
+    # refinement of its means and their Eq. 7 error
+    try:
+        for _ in range(2):
+            lab, reps_, rmeans, rpasses = q.box_reduce(nbr, deg, xyz[:F], box=4.0)
+        q.trace_enable(True, only="reduce")
+        q.trace_read(reset=True)
+        for _ in range(reps):
+            lab, reps_, rmeans, rpasses = q.box_reduce(nbr, deg, xyz[:F], box=4.0)
+        tr3 = q.trace_read(reset=True)
+        q.trace_enable(False)
+        rref = q.refine_samples(psi, xyz0=rmeans.float())
+        e_rmeans, _, _ = q.density_error(psi, rmeans.float())
+        e_rref, _, _ = q.density_error(psi, rref["xyz"])
+        reduced = {"box_h": 4.0, "means": int(reps_.numel()), "passes": rpasses,
+                   "ms": tr3["reduce"][1] / max(1, tr3["reduce"][0]),
+                   "refined_converged_fraction": (rref["flags"] == 1).float().mean().item(),
+                   "eq7_error_means": e_rmeans, "eq7_error_refined": e_rref}
+    except qtv.QtvError as err:
+        reduced = {"error": str(err)}
     return {"ms": kms, "pieces": int(len(P)), "closed_pieces": int(P["closed"].sum()),
+            "box_reduced": reduced,
             "pieces_in_type_I_II_III": [int(types[1]), int(types[2]), int(types[3])],
             "reversed_pieces": int(P["reversed"].sum()), "curve_points": int(curve.shape[0]),
             "total_length_h": float(length.double().sum().item()),

@@ -649,6 +649,47 @@ QTV_API int qtv_thin_pieces(qtv_handle h, const float* xyz, const uint32_t* node
                             uint64_t* total, void* stream);
 
 /*
+ * Box-mean reduction of a sample graph (Sec. 3.3.1-3.3.2), data-parallel:
+ * the paper collapses, box by box along each line, the samples a box of side
+ * d reaches into their mean, keeping the edges that leave the box, and
+ * repeats whole passes until the samples settle.  Here each pass lays a
+ * lattice of boxes of side `box` over space (shifted by box / 2 in every axis
+ * on odd passes); the samples of one box that are connected through edges
+ * inside it form a cluster, which becomes one node at the mean of its
+ * members' positions with every edge leaving it.  Passes repeat until one pass
+ * of each lattice merges nothing (a fixed point), at most max_passes.  The
+ * result does not depend on the numbering of the samples: positions are held
+ * in fixed point (integers in units of 2^-32 of the length unit: x 2^32
+ * rounded to the nearest integer, ties to even), a mean is
+ * floor((sum + floor(c / 2)) / c) over
+ * the c members, and a cluster is named by the lowest input index it contains.
+ *
+ *   n, n_dev     host bound on the node count (< 2^32 - 1) and an optional
+ *                device uint64 limiting it to min(n, *n_dev).
+ *   nbr, deg     device uint32[n][stride] neighbour table (ascending, then
+ *                0xFFFFFFFF) and uint8[n] degrees, as from qtv_face_graph
+ *                (stride 10) or qtv_node_graph (stride 6).
+ *   xyz          device float[n][3]: positions below 4096 in magnitude, in
+ *                the unit of box (e.g. grid units); larger or non-finite
+ *                values give unspecified clusters (memory stays in bounds).
+ *   box          box side, 0 < box <= 32 (the paper takes d = k h, k in
+ *                [3, 8]); max_passes in [1, 64] (the paper needs 2 to 5).
+ *   label        device uint32[n]: the cluster of every node (its lowest
+ *                node index), written.
+ *   out_xyz      device double[n][3]: at every index r with label[r] == r
+ *                the cluster's mean position (exact); other entries are
+ *                scratch and unspecified.
+ *   counts       device uint64[2]: clusters and passes made
+ *                (QTV_COUNT_TIMEOUT as clusters if a bounded union-find
+ *                retry loop gave up).
+ * Asynchronous, capture-safe once the handle's workspace has reached n.
+ */
+QTV_API int qtv_box_reduce(qtv_handle h, uint64_t n, const uint64_t* n_dev, const uint32_t* nbr,
+                           const uint8_t* deg, int stride, const float* xyz, float box,
+                           int max_passes, uint32_t* label, double* out_xyz, uint64_t* counts,
+                           void* stream);
+
+/*
  * Kernel timing trace.  While enabled, the handle records a pair of CUDA
  * events on the launching stream around each of its kernel launches (names:
  * "sweep", "seg_scan", "scatter", "stats", "localize", "emit_pack", "batch"
@@ -656,7 +697,8 @@ QTV_API int qtv_thin_pieces(qtv_handle h, const float* xyz, const uint32_t* node
  * parts of learned localization, "node_form", "node_scan", "node_scatter"
  * for the node form, "density" for the density error, "refine" for
  * sample refinement, "graph" for the face graph and its components, "lines"
- * and "curves" for line pieces and their curves, "thin" for their thinning).
+ * and "curves" for line pieces and their curves, "thin" for their thinning,
+ * "reduce" for the box-mean reduction).
  * qtv_trace_read waits for the recorded events, writes up to max_entries
  * per-kernel totals (launch count and summed device time) and, if reset is
  * nonzero, clears the record.  Tracing adds host work per launch and a gap

@@ -43,11 +43,13 @@ Readings where the text leaves details open:
   points x_i, rho trilinearly interpolated;
 * lattice box reduction (`box_reduce`, an order-independent parallel reading
   of Sec. 3.3.1-3.3.2): positions are held in fixed point, integers in units
-  of 2^-32 h (the FP32 sample positions convert exactly); pass p lays a
+  of 2^-32 h (a position times 2^32, rounded to the nearest integer, ties to
+  even; a sample may lie slightly outside the grid, so positions may be
+  negative); pass p lays a
   lattice of boxes of side D = round(d 2^32) over space, shifted by
   floor(D / 2) in every axis on odd passes; the nodes of one box that are
   connected through edges inside that box form one cluster, which collapses
-  to one node at the rounded mean floor((sum + c / 2) / c) of its members'
+  to one node at the rounded mean floor((sum + floor(c / 2)) / c) of its members'
   positions (each current node counted once), named by the lowest original
   index it contains and carrying the union of its members' external edges;
   passes repeat until two consecutive passes (one of each lattice) merge
@@ -252,15 +254,15 @@ FIX = 2 ** 32  # fixed-point units per grid spacing of box_reduce
 
 
 def _fixed(pos):
-    """Exact fixed-point integers (units of 2^-32 h) of positions that are
-    FP32 values (asserts exactness)."""
+    """Fixed-point integers (units of 2^-32 h) of positions below 2^31 in
+    magnitude: x 2^32 (exact in FP64 for an FP32 x) rounded to the nearest
+    integer, ties to even."""
     out = []
     for p in np.asarray(pos, np.float64).reshape(-1, 3):
         row = []
         for x in p:
-            q = float(x) * FIX
-            assert q == int(q) and x >= 0.0, "positions must be non-negative FP32 values"
-            row.append(int(q))
+            assert abs(x) < 2.0 ** 31, "positions must be below 2^31 in magnitude"
+            row.append(round(float(x) * FIX))
         out.append(tuple(row))
     return out
 

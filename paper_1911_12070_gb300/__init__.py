@@ -164,6 +164,8 @@ def lib() -> ctypes.CDLL:
         L.qtv_identify_localize_host.argtypes = [P, ctypes.POINTER(Grid), P, u64, P, P, P]
         L.qtv_thin_pieces.argtypes = [P, P, P, P, u64, u64, f32, P, u64, P, P, P]
         L.qtv_node_graph.argtypes = [P, ctypes.POINTER(Grid), P, u64, P, P, P, P, P, P]
+        L.qtv_box_reduce.argtypes = [P, u64, P, P, P, i32, P, f32, i32, P, P, P, P]
+        L.qtv_box_reduce.restype = i32
         for name in ("qtv_node_circulation", "qtv_density_error", "qtv_refine_samples",
                      "qtv_face_graph", "qtv_line_pieces", "qtv_piece_curves",
                      "qtv_identify_localize_host", "qtv_thin_pieces", "qtv_node_graph"):
@@ -603,6 +605,33 @@ class Qtv:
         if k < 0:
             raise QtvError(ERR_TIMEOUT, "a bounded union-find retry loop gave up")
         return nbr[:n], deg[:n], comp[:n], k
+
+    def box_reduce(self, nbr, deg, xyz, box: float = 4.0, max_passes: int = 10, n_dev=None,
+                   stream=None):
+        """Box-mean reduction of a sample graph (qtv_box_reduce): nbr / deg as
+        from face_graph or node_graph, xyz float32 [n, 3] non-negative positions.
+
+        Returns (label int32 [n] = lowest node index of each node's cluster,
+        reps int64 [c] = the cluster labels in ascending order, xyz float64
+        [c, 3] = their mean positions, passes)."""
+        import torch
+
+        n = xyz.shape[0]
+        dev = xyz.device
+        label = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        out = torch.empty((max(n, 1), 3), dtype=torch.float64, device=dev)
+        counts = torch.zeros(2, dtype=torch.int64, device=dev)
+        _check(lib().qtv_box_reduce(self.h, n, _ptr(n_dev), _ptr(nbr), _ptr(deg),
+                                    int(nbr.shape[1]) if n else 10, _ptr(xyz), float(box),
+                                    int(max_passes), _ptr(label), _ptr(out), _ptr(counts),
+                                    _stream_ptr(stream)))
+        c = counts.cpu()
+        if int(c[0]) < 0:
+            raise QtvError(ERR_TIMEOUT, "a bounded union-find retry loop gave up")
+        label = label[:n]
+        reps = torch.nonzero(label == torch.arange(n, device=dev, dtype=torch.int32))[:, 0]
+        assert reps.numel() == int(c[0])
+        return label, reps, out[reps], int(c[1])
 
     def node_graph(self, shape, node_ids, n_dev=None, grid=None, stream=None):
         """Graph of vortex nodes (6-connectivity) and its components: (nbr int32

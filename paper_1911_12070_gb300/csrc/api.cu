@@ -124,7 +124,7 @@ const char* kKernelNames[K_COUNT] = {"sweep",     "seg_scan",  "scatter",      "
                                      "localize",  "emit_pack", "batch",        "encode",
                                      "network",   "head",      "node_form",    "node_scan",
                                      "node_scatter", "density",   "refine",       "graph",
-                                     "lines",     "curves",    "thin"};
+                                     "lines",     "curves",    "thin",      "reduce"};
 }  // namespace
 
 // Inside a stream capture the records become event-record nodes of the graph
@@ -262,6 +262,7 @@ int qtv_destroy(qtv_handle h) {
   node_work_free(h->node);
   graph_work_free(h->graph);
   line_work_free(h->lines);
+  reduce_work_free(h->reduce);
   host_pipe_free(h->pipe);
   cudaFree(h->refine_counter);
   for (auto& r : h->trace) {
@@ -695,6 +696,24 @@ int qtv_thin_pieces(qtv_handle h, const float* xyz, const uint32_t* nodes, const
   }
   return thin_pieces_launch(h, xyz, nodes, pieces, npieces, nnodes, box, out_xyz, out_cap,
                             out_pieces, total, st);
+}
+
+int qtv_box_reduce(qtv_handle h, uint64_t n, const uint64_t* n_dev, const uint32_t* nbr,
+                   const uint8_t* deg, int stride, const float* xyz, float box, int max_passes,
+                   uint32_t* label, double* out_xyz, uint64_t* counts, void* stream) {
+  if (!h) return set_error(QTV_ERR_ARG, "handle is NULL");
+  if (!counts) return set_error(QTV_ERR_ARG, "counts is NULL");
+  if (n > 0 && (!nbr || !deg || !xyz || !label || !out_xyz))
+    return set_error(QTV_ERR_ARG, "a required pointer is NULL");
+  if (n >= 0xFFFFFFFFull) return set_error(QTV_ERR_ARG, "too many nodes (%llu)", (unsigned long long)n);
+  if (stride < 1 || stride > 64) return set_error(QTV_ERR_ARG, "neighbour stride %d (1 to 64)", stride);
+  if (!(box > 0.f && box <= 32.f)) return set_error(QTV_ERR_ARG, "box must be in (0, 32]");
+  if (max_passes < 1 || max_passes > 64)
+    return set_error(QTV_ERR_ARG, "max_passes %d (1 to 64)", max_passes);
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return set_error(QTV_ERR_CUDA, "cudaSetDevice failed");
+  return box_reduce_launch(h, n, n_dev, nbr, deg, stride, xyz, box, max_passes, label, out_xyz,
+                           counts, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int qtv_node_graph(qtv_handle h, const qtv_grid* grid, const uint64_t* node_ids, uint64_t n,

@@ -106,7 +106,7 @@ struct Locator;  // learned locator state (locator.cu)
 void locator_free(Locator* L);
 enum KernelId {
   K_SWEEP = 0, K_SEG_SCAN, K_SCATTER, K_STATS, K_LOCALIZE, K_EMIT_PACK, K_BATCH,
-  K_ENCODE, K_NETWORK, K_HEAD, K_NODE_FORM, K_NODE_SCAN, K_NODE_SCATTER, K_DENSITY, K_REFINE, K_GRAPH, K_LINES, K_CURVES, K_THIN, K_COUNT
+  K_ENCODE, K_NETWORK, K_HEAD, K_NODE_FORM, K_NODE_SCAN, K_NODE_SCATTER, K_DENSITY, K_REFINE, K_GRAPH, K_LINES, K_CURVES, K_THIN, K_REDUCE, K_COUNT
 };
 struct BatchPlan;  // batched snapshots (batch.cu)
 void batch_free(BatchPlan* b);
@@ -116,6 +116,8 @@ struct GraphWork;  // face-graph workspace (graph.cu)
 void graph_work_free(GraphWork* w);
 struct LineWork;   // line-extraction workspace (lines.cu)
 void line_work_free(LineWork* w);
+struct ReduceWork;  // box-reduction workspace (reduce.cu)
+void reduce_work_free(ReduceWork* w);
 struct HostPipe;   // double-buffered device copies for calls from host memory (api.cu)
 void host_pipe_free(HostPipe* p);
 struct TraceRec {
@@ -137,6 +139,7 @@ struct qtv_handle_s {
   qtv::NodeWork* node = nullptr;         // node-form / density-error workspace
   qtv::GraphWork* graph = nullptr;       // face-graph workspace
   qtv::LineWork* lines = nullptr;        // line-extraction workspace
+  qtv::ReduceWork* reduce = nullptr;     // box-reduction workspace
   qtv::HostPipe* pipe = nullptr;         // calls from host memory
   unsigned long long* refine_counter = nullptr;  // work counter of the refinement kernel
   // sweep shape of single-snapshot calls (qtv_configure_sweep); -1 / 0 = default
@@ -357,6 +360,11 @@ int bulk_identify(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* 
                   int8_t* winding, uint64_t capacity, uint64_t* count, qtv_stats* stats,
                   cudaStream_t st, const IdentScratch& sc, uint64_t max_warps,
                   float* xyz = nullptr, float* resid = nullptr, uint8_t* flags = nullptr);
+
+// Box-mean reduction of a sample graph (reduce.cu)
+int box_reduce_launch(qtv_handle h, uint64_t n, const uint64_t* n_dev, const uint32_t* nbr,
+                      const uint8_t* deg, int stride, const float* xyz, float box, int max_passes,
+                      uint32_t* label, double* out_xyz, uint64_t* counts, cudaStream_t st);
 
 // Localization launch (localize.cu)
 int localize_launch(qtv_handle h, const qtv_grid& g, const float2* psi, const uint64_t* face_ids,

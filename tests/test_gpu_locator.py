@@ -348,18 +348,24 @@ def test_learned_batch_against_oracle(q, trained):
         m2 = float(np.max(np.abs(host.astype(np.complex128)) ** 2))
         _, okenc, rms = mlp.encode(host, ids[acc], w[acc])
         assert okenc.all()
-        rho = oracle.density(host, xyz[acc].astype(np.float64))
-        # |F| at the FP32 sample against |F| at its FP32 grid coordinates: the
-        # coordinates round by |x| 2^-24, and |grad F| <= 4 max|psi| on a face
-        slack = 4 * np.sqrt(m2) * np.max(np.abs(xyz[acc]), axis=1) * 2.0 ** -23 + 1e-6 * np.sqrt(m2)
-        assert np.all(np.abs(np.sqrt(resid[acc]) - np.sqrt(rho)) <= slack)
-        assert np.all(np.sqrt(rho) <= np.sqrt(1e-3) * rms + slack)
         corner = np.column_stack([lin % host.shape[2], (lin // host.shape[2]) % host.shape[1],
                                   lin // (host.shape[2] * host.shape[1])])[acc]
         normal = np.array([2, 0, 1])[o[acc]]  # the axis the face does not span
         rel = xyz[acc] - corner
         assert np.all(np.abs(rel[np.arange(len(rel)), normal]) == 0)
         assert np.all((rel > -0.01 - 1e-5) & (rel < 1.01 + 1e-5))
+        # inside the face the trilinear interpolant the oracle evaluates is the
+        # face's bilinear one (a sample up to 0.01 beyond an edge is in the
+        # neighbouring face's territory, where the two differ)
+        inside = np.all((rel >= 0) & (rel <= 1), axis=1)
+        rho = oracle.density(host, xyz[acc][inside].astype(np.float64))
+        # |F| at the FP32 sample against |F| at its FP32 grid coordinates: the
+        # coordinates round by |x| 2^-24, and |grad F| <= 4 max|psi| on a face
+        slack = (4 * np.sqrt(m2) * np.max(np.abs(xyz[acc][inside]), axis=1) * 2.0 ** -23 +
+                 1e-6 * np.sqrt(m2))
+        assert np.all(np.abs(np.sqrt(resid[acc][inside]) - np.sqrt(rho)) <= slack)
+        assert np.all(np.sqrt(rho) <= np.sqrt(1e-3) * rms[inside] + slack)
+        assert inside.mean() > 0.9
         dd = np.linalg.norm(xyz[acc] - ora["xyz"][acc], axis=1)
         assert np.sqrt(np.mean(dd ** 2)) <= 0.05
         n_acc += int(acc.sum())
