@@ -308,12 +308,14 @@ QTV_API int qtv_locator_gradients(qtv_handle h, const uint16_t* x, const float* 
 QTV_API int qtv_locator_train_step(qtv_handle h, const uint16_t* x, const float* targets,
                                    uint64_t n, float lr, float* loss, void* stream);
 QTV_API int qtv_locator_save(qtv_handle h, const char* path);
-/* Tensor-core path of inference forward passes (qtv_locator_forward and
- * learned localization): 0 = mma.sync layer kernels, 1 = one tcgen05 kernel
- * for the whole network (accumulators and the hidden activations in tensor
- * memory; the default).  Both use BF16 operands with FP32 accumulation;
- * results agree to accumulation order.  Training always uses the layer
- * kernels. */
+/* Tensor-core path of the network: 0 = mma.sync layer kernels, 1 = tcgen05
+ * (the default): inference (qtv_locator_forward and learned localization) in
+ * one kernel for the whole network (accumulators and the hidden activations
+ * in tensor memory), training (qtv_locator_gradients, qtv_locator_train_step)
+ * with every dense contraction - forward, data gradient and weight gradients
+ * - as tcgen05 GEMMs with accumulators in tensor memory (weight gradients
+ * split along the batch and summed in a fixed order).  Both paths use BF16
+ * operands with FP32 accumulation; results agree to accumulation order. */
 QTV_API int qtv_locator_set_tensor_path(qtv_handle h, int path);
 QTV_API int qtv_locator_load(qtv_handle h, const char* path);
 

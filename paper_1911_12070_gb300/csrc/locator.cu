@@ -310,9 +310,16 @@ __global__ void out_layer_kernel(const uint16_t* __restrict__ A2, const float* _
       dy[3 * m + 2] = sc * d2;
     }
   }
-  if (t) {
+  if (t) {  // per-block loss into loss[blockIdx.x] (summed in block order later)
+    __shared__ float ws[32];
     for (int d = 16; d; d >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, d);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, lsum / (float)n);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = lsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float b = 0.f;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) b += ws[i];
+      loss[blockIdx.x] = b / (float)n;
+    }
   }
 }
 
@@ -332,11 +339,15 @@ __global__ void out_back_kernel(const float* __restrict__ dy, const float* __res
 }
 
 constexpr int kRowChunk = 64;  // rows per block of the reductions below
+constexpr int kSplits = 16;    // most K splits of a weight-gradient GEMM on tcgen05
+constexpr int kLossBlocks = 1024;                     // most blocks of the loss
+constexpr int kPartW3 = kOut * kH + kOut;             // W3 and b3 partials per chunk
 
-// dW3[o][k] += sum_m dY[m][o] A2[m][k] and db3[o] += sum_m dY[m][o] over one
-// chunk of rows per block (thread k = 0..kH, k == kH the bias); G zeroed first
+// partial dW3[o][k] = sum_m dY[m][o] A2[m][k] and db3[o] = sum_m dY[m][o] over
+// one chunk of rows per block (thread k = 0..kH, k == kH the bias), into
+// part[block][kOut kH + kOut] (the layout of W3 and b3 in the parameters)
 __global__ void out_wgrad_kernel(const float* __restrict__ dy, const uint16_t* __restrict__ A2,
-                                 unsigned long long n, float* __restrict__ G) {
+                                 unsigned long long n, float* __restrict__ part) {
   const int k = threadIdx.x;
   const unsigned long long m0 = (unsigned long long)blockIdx.x * kRowChunk;
   const unsigned long long m1 = m0 + kRowChunk < n ? m0 + kRowChunk : n;
@@ -347,33 +358,46 @@ __global__ void out_wgrad_kernel(const float* __restrict__ dy, const uint16_t* _
     s1 = fmaf(dy[3 * m + 1], a, s1);
     s2 = fmaf(dy[3 * m + 2], a, s2);
   }
+  float* out = part + (size_t)blockIdx.x * (kOut * kH + kOut);
   if (k < kH) {
-    atomicAdd(&G[kOffW3 + k], s0);
-    atomicAdd(&G[kOffW3 + kH + k], s1);
-    atomicAdd(&G[kOffW3 + 2 * kH + k], s2);
+    out[k] = s0;
+    out[kH + k] = s1;
+    out[2 * kH + k] = s2;
   } else if (k == kH) {
-    atomicAdd(&G[kOffB3], s0);
-    atomicAdd(&G[kOffB3 + 1], s1);
-    atomicAdd(&G[kOffB3 + 2], s2);
+    out[kOut * kH] = s0;
+    out[kOut * kH + 1] = s1;
+    out[kOut * kH + 2] = s2;
   }
 }
 
-// out[k] += column sums of a BF16 [n x kH] matrix over one chunk of rows
+// part[block][k] = column sums of a BF16 [n x kH] matrix over one chunk of rows
 __global__ void colsum_kernel(const uint16_t* __restrict__ D, unsigned long long n,
-                              float* __restrict__ out) {
+                              float* __restrict__ part) {
   const int k = threadIdx.x;
   const unsigned long long m0 = (unsigned long long)blockIdx.x * kRowChunk;
   const unsigned long long m1 = m0 + kRowChunk < n ? m0 + kRowChunk : n;
   float s = 0.f;
   for (unsigned long long m = m0; m < m1; ++m) s += bf2f(D[m * kH + k]);
-  atomicAdd(&out[k], s);
+  part[(size_t)blockIdx.x * kH + k] = s;
+}
+
+// out[i] = sum over blocks b = 0, 1, ... of part[b][i], in that order (the
+// reductions over the batch give the same result on every run)
+__global__ void sum_parts_kernel(const float* __restrict__ part, int nb, int width,
+                                 float* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < width; i += gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int b = 0; b < nb; ++b) acc += part[(size_t)b * width + i];
+    out[i] = acc;
+  }
 }
 
 // Adam (Kingma & Ba), bias-corrected; refreshes the BF16 copies of W1, W2
 __global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G,
                             float* __restrict__ Mo, float* __restrict__ Vo, int n, float lr,
                             float b1, float b2, float eps, float c1, float c2,
-                            uint16_t* __restrict__ w1b, uint16_t* __restrict__ w2b) {
+                            uint16_t* __restrict__ w1b, uint16_t* __restrict__ w2b,
+                            uint16_t* __restrict__ w2tb) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const float g = G[i];
     const float m = b1 * Mo[i] + (1.f - b1) * g;
@@ -382,17 +406,45 @@ __global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G,
     Vo[i] = v;
     const float p = P[i] - lr * (m / c1) / (sqrtf(v / c2) + eps);
     P[i] = p;
-    if (i < (int)kOffB1) w1b[i - kOffW1] = f2bf(p);
-    else if (i >= (int)kOffW2 && i < (int)kOffB2) w2b[i - kOffW2] = f2bf(p);
+    if (i < (int)kOffB1) {
+      w1b[i - kOffW1] = f2bf(p);
+    } else if (i >= (int)kOffW2 && i < (int)kOffB2) {
+      const int j = i - (int)kOffW2;  // W2[o][k], j = o kH + k
+      w2b[j] = f2bf(p);
+      w2tb[(j % kH) * kH + j / kH] = f2bf(p);
+    }
   }
 }
 
 __global__ void refresh_bf16_kernel(const float* __restrict__ P, uint16_t* __restrict__ w1b,
-                                    uint16_t* __restrict__ w2b) {
+                                    uint16_t* __restrict__ w2b, uint16_t* __restrict__ w2tb) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kH * kIn + kH * kH;
        i += gridDim.x * blockDim.x) {
-    if (i < kH * kIn) w1b[i] = f2bf(P[kOffW1 + i]);
-    else w2b[i - kH * kIn] = f2bf(P[kOffW2 + i - kH * kIn]);
+    if (i < kH * kIn) {
+      w1b[i] = f2bf(P[kOffW1 + i]);
+    } else {
+      const int j = i - kH * kIn;
+      const uint16_t b = f2bf(P[kOffW2 + j]);
+      w2b[j] = b;
+      w2tb[(j % kH) * kH + j / kH] = b;
+    }
+  }
+}
+
+// dst[c][m] = src[m][c] for m < n, zero for n <= m < ldT (BF16, 32 x 32 tiles)
+__global__ void transpose_bf16_kernel(const uint16_t* __restrict__ src, unsigned long long n,
+                                      int C, uint16_t* __restrict__ dst, unsigned long long ldT) {
+  __shared__ uint16_t t[32][34];
+  const unsigned long long m0 = (unsigned long long)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const unsigned long long m = m0 + r;
+    t[r][threadIdx.x] = m < n ? src[m * C + c0 + threadIdx.x] : (uint16_t)0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const unsigned long long m = m0 + threadIdx.x;
+    if (m < ldT) dst[(unsigned long long)(c0 + r) * ldT + m] = t[threadIdx.x][r];
   }
 }
 
@@ -509,6 +561,7 @@ struct Locator {
   float* V = nullptr;      // Adam second moment
   uint16_t* w1b = nullptr; // BF16 W1 [256][128]
   uint16_t* w2b = nullptr; // BF16 W2 [256][256]
+  uint16_t* w2tb = nullptr; // BF16 W2^T [256 in][256 out] (backward on tcgen05)
   unsigned long long step = 0;
   bool ready = false;
   // activations for up to `cap` rows; rows_gen counts their reallocations
@@ -519,6 +572,16 @@ struct Locator {
   int num_sms = 0;
   unsigned int* status = nullptr;  // timeout flag of the tcgen05 kernel
   uint16_t *A1 = nullptr, *A2 = nullptr, *D1 = nullptr, *D2 = nullptr, *X = nullptr;
+  // transposed copies for the weight gradients on tcgen05 ([features][ldT],
+  // columns past the batch zero) and the split-K partials
+  uint16_t *A1T = nullptr, *D1T = nullptr, *D2T = nullptr, *XT = nullptr;
+  unsigned long long ldT = 0;
+  float* part = nullptr;
+  // per-block partials of the reductions over the batch: loss [1024], then
+  // per 64-row chunk W3 and b3 (kOut kH + kOut), b2 and b1 (kH each)
+  float* lpart = nullptr;
+  float* gpart = nullptr;
+  unsigned long long gpart_cap = 0;  // chunks
   float *Y = nullptr, *DY = nullptr, *rms = nullptr;
   uint8_t* ok = nullptr;
 };
@@ -531,6 +594,14 @@ void locator_free(Locator* L) {
   cudaFree(L->V);
   cudaFree(L->w1b);
   cudaFree(L->w2b);
+  cudaFree(L->w2tb);
+  cudaFree(L->A1T);
+  cudaFree(L->D1T);
+  cudaFree(L->D2T);
+  cudaFree(L->XT);
+  cudaFree(L->part);
+  cudaFree(L->lpart);
+  cudaFree(L->gpart);
   cudaFree(L->A1);
   cudaFree(L->A2);
   cudaFree(L->D1);
@@ -556,6 +627,9 @@ static int locator_alloc(qtv_handle h) {
   if (e == cudaSuccess) e = cudaMalloc(&L->V, pb);
   if (e == cudaSuccess) e = cudaMalloc(&L->w1b, (size_t)kH * kIn * 2);
   if (e == cudaSuccess) e = cudaMalloc(&L->w2b, (size_t)kH * kH * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&L->w2tb, (size_t)kH * kH * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&L->part, (size_t)kSplits * kH * kH * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&L->lpart, (size_t)kLossBlocks * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&L->status, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(L->status, 0, sizeof(unsigned int));
   if (e != cudaSuccess) {
@@ -582,6 +656,11 @@ static int locator_rows(qtv_handle h, unsigned long long n, cudaStream_t st) {
   cudaFree(L->DY);
   cudaFree(L->rms);
   cudaFree(L->ok);
+  cudaFree(L->A1T);
+  cudaFree(L->D1T);
+  cudaFree(L->D2T);
+  cudaFree(L->XT);
+  L->A1T = L->D1T = L->D2T = L->XT = nullptr;
   L->A1 = L->A2 = L->D1 = L->D2 = L->X = nullptr;
   L->Y = L->DY = L->rms = nullptr;
   L->ok = nullptr;
@@ -595,7 +674,13 @@ static int locator_rows(qtv_handle h, unsigned long long n, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMalloc(&L->DY, n * kOut * 4);
   if (e == cudaSuccess) e = cudaMalloc(&L->rms, n * 4);
   if (e == cudaSuccess) e = cudaMalloc(&L->ok, n);
+  const unsigned long long ldT = (n + 63) / 64 * 64;
+  if (e == cudaSuccess) e = cudaMalloc(&L->A1T, ldT * kH * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&L->D1T, ldT * kH * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&L->D2T, ldT * kH * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&L->XT, ldT * kIn * 2);
   if (e != cudaSuccess) return check_cuda(e, "cudaMalloc(locator rows)");
+  L->ldT = ldT;
   L->cap = n;
   ++L->rows_gen;
   return QTV_OK;
@@ -622,20 +707,113 @@ static int forward_y(Locator* L, const uint16_t* X, unsigned long long n, float*
   return check_cuda(cudaGetLastError(), "out_layer_kernel launch");
 }
 
+// the partial buffers of the batch reductions for n rows
+static int grad_parts(Locator* L, unsigned long long n, cudaStream_t st) {
+  const unsigned long long chunks = (n + kRowChunk - 1) / kRowChunk;
+  if (chunks <= L->gpart_cap) return QTV_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+    return set_error(QTV_ERR_STATE, "locator buffers must grow during stream capture");
+  cudaFree(L->gpart);
+  L->gpart = nullptr;
+  L->gpart_cap = 0;
+  const cudaError_t e = cudaMalloc(&L->gpart, chunks * (kPartW3 + 2 * kH) * sizeof(float));
+  if (e != cudaSuccess) return check_cuda(e, "cudaMalloc(gradient partials)");
+  L->gpart_cap = chunks;
+  return QTV_OK;
+}
+
+// output layer with loss and dY, its weight gradients, and the loss summed in
+// block order (the first half of the backward pass, both tensor paths)
+static int output_backward(Locator* L, const float* T, unsigned long long n, float* loss,
+                           cudaStream_t st) {
+  const int nbl = blocks_for(n, 256, kLossBlocks);
+  out_layer_kernel<<<nbl, 256, 0, st>>>(L->A2, L->P, n, L->Y, T, L->DY, L->lpart);
+  sum_parts_kernel<<<1, 32, 0, st>>>(L->lpart, nbl, 1, loss);
+  out_back_kernel<<<blocks_for(n * kH, 256, 4096), 256, 0, st>>>(L->DY, L->P, L->A2, n, L->D2);
+  const unsigned chunks = (unsigned)((n + kRowChunk - 1) / kRowChunk);
+  float* p3 = L->gpart;
+  out_wgrad_kernel<<<chunks, kH + 32, 0, st>>>(L->DY, L->A2, n, p3);
+  sum_parts_kernel<<<4, 256, 0, st>>>(p3, (int)chunks, kPartW3, L->G + kOffW3);
+  return check_cuda(cudaGetLastError(), "locator output backward");
+}
+
+// bias gradient of a layer: column sums of dH (BF16 [n][kH]) in block order
+static int bias_grad(Locator* L, const uint16_t* D, unsigned long long n, int which, float* out,
+                     cudaStream_t st) {
+  const unsigned chunks = (unsigned)((n + kRowChunk - 1) / kRowChunk);
+  float* p = L->gpart + (size_t)L->gpart_cap * kPartW3 + (size_t)which * L->gpart_cap * kH;
+  colsum_kernel<<<chunks, kH, 0, st>>>(D, n, p);
+  sum_parts_kernel<<<1, kH, 0, st>>>(p, (int)chunks, kH, out);
+  return check_cuda(cudaGetLastError(), "locator bias gradient");
+}
+
+// splits of a K range of k64 chunks of 64: the largest divisor up to kSplits
+static int splits_for(unsigned long long k64) {
+  int s = kSplits;
+  while (s > 1 && k64 % (unsigned long long)s) --s;
+  return s;
+}
+
+// forward + backward into L->G on tcgen05 (L->tensor_path == 1): the dense
+// layers and the data-gradient GEMM take the row-major activations, the
+// weight-gradient GEMMs the transposed copies (K = the padded batch, split
+// into parts summed in a fixed order)
+static int forward_backward_tc(Locator* L, const uint16_t* X, const float* T, unsigned long long n,
+                               float* loss, cudaStream_t st) {
+  const unsigned long long ldT = (n + 63) / 64 * 64;
+  const dim3 tb(32, 8);
+  transpose_bf16_kernel<<<dim3((unsigned)(ldT / 32), kIn / 32), tb, 0, st>>>(X, n, kIn, L->XT, ldT);
+  // A1 = relu(X W1^T + b1), and A1^T
+  cudaError_t e = cudaSuccess;
+  if (ldT > n) {  // the GEMM epilogues write columns below n only
+    e = cudaMemset2DAsync(L->A1T + n, ldT * 2, 0, (ldT - n) * 2, kH, st);
+    if (e == cudaSuccess) e = cudaMemset2DAsync(L->D1T + n, ldT * 2, 0, (ldT - n) * 2, kH, st);
+    if (e != cudaSuccess) return check_cuda(e, "memset(transposed padding)");
+  }
+  int rc = tc_gemm(X, kIn, L->w1b, kIn, (long long)n, kH, kIn, 1, 1, nullptr, 0, nullptr, L->A1, kH,
+                   L->A1T, (long long)ldT, L->P + kOffB1, nullptr, 0, L->status, st);
+  if (rc) return rc;
+  // A2 = relu(A1 W2^T + b2)
+  rc = tc_gemm(L->A1, kH, L->w2b, kH, (long long)n, kH, kH, 1, 1, nullptr, 0, nullptr, L->A2, kH,
+               nullptr, 0, L->P + kOffB2, nullptr, 0, L->status, st);
+  if (rc) return rc;
+  rc = output_backward(L, T, n, loss, st);
+  if (rc) return rc;
+  transpose_bf16_kernel<<<dim3((unsigned)(ldT / 32), kH / 32), tb, 0, st>>>(L->D2, n, kH, L->D2T, ldT);
+  rc = bias_grad(L, L->D2, n, 0, L->G + kOffB2, st);
+  if (rc) return rc;
+  const int sp = splits_for(ldT / 64);
+  // dW2[o][k] = sum_m dH2[m][o] A1[m][k]
+  rc = tc_gemm(L->D2T, (long long)ldT, L->A1T, (long long)ldT, kH, kH, (long long)ldT, sp, 0,
+               L->G + kOffW2, kH, L->part, nullptr, 0, nullptr, 0, nullptr, nullptr, 0, L->status, st);
+  if (rc) return rc;
+  // dH1[m][k] = (sum_o dH2[m][o] W2[o][k]) * (A1[m][k] > 0), and its transpose
+  rc = tc_gemm(L->D2, kH, L->w2tb, kH, (long long)n, kH, kH, 1, 2, nullptr, 0, nullptr, L->D1, kH,
+               L->D1T, (long long)ldT, nullptr, L->A1, kH, L->status, st);
+  if (rc) return rc;
+  rc = bias_grad(L, L->D1, n, 1, L->G + kOffB1, st);
+  if (rc) return rc;
+  // dW1[o][i] = sum_m dH1[m][o] X[m][i]
+  rc = tc_gemm(L->D1T, (long long)ldT, L->XT, (long long)ldT, kH, kIn, (long long)ldT, sp, 0,
+               L->G + kOffW1, kIn, L->part, nullptr, 0, nullptr, 0, nullptr, nullptr, 0, L->status,
+               st);
+  if (rc) return rc;
+  return check_cuda(cudaGetLastError(), "locator backward (tcgen05)");
+}
+
 // forward + backward into L->G; loss (device float) accumulated
 static int forward_backward(Locator* L, const uint16_t* X, const float* T, unsigned long long n,
                             float* loss, cudaStream_t st) {
-  int rc = forward_hidden(L, X, n, st);
+  int rc = grad_parts(L, n, st);
   if (rc) return rc;
-  out_layer_kernel<<<blocks_for(n, 256, 1024), 256, 0, st>>>(L->A2, L->P, n, L->Y, T, L->DY, loss);
-  out_back_kernel<<<blocks_for(n * kH, 256, 4096), 256, 0, st>>>(L->DY, L->P, L->A2, n, L->D2);
-  const unsigned chunks = (unsigned)((n + kRowChunk - 1) / kRowChunk);
-  cudaError_t e = cudaMemsetAsync(L->G + kOffB1, 0, kH * sizeof(float), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(L->G + kOffB2, 0, kH * sizeof(float), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(L->G + kOffW3, 0, (kOut * kH + kOut) * sizeof(float), st);
-  if (e != cudaSuccess) return check_cuda(e, "memset(grads)");
-  out_wgrad_kernel<<<chunks, kH + 32, 0, st>>>(L->DY, L->A2, n, L->G);
-  colsum_kernel<<<chunks, kH, 0, st>>>(L->D2, n, L->G + kOffB2);
+  if (L->tensor_path == 1) return forward_backward_tc(L, X, T, n, loss, st);
+  rc = forward_hidden(L, X, n, st);
+  if (rc) return rc;
+  rc = output_backward(L, T, n, loss, st);
+  if (rc) return rc;
+  rc = bias_grad(L, L->D2, n, 0, L->G + kOffB2, st);
+  if (rc) return rc;
   // dW2[n][k] = sum_m dH2[m][n] A1[m][k]
   rc = gemm<true, true, EPI_STORE_F32>(kH, kH, (int)n, L->D2, kH, L->A1, kH, L->G + kOffW2, kH,
                                        nullptr, nullptr, st);
@@ -644,7 +822,8 @@ static int forward_backward(Locator* L, const uint16_t* X, const float* T, unsig
   rc = gemm<false, true, EPI_RELU_MASK_BF16>((int)n, kH, kH, L->D2, kH, L->w2b, kH, L->D1, kH,
                                              nullptr, L->A1, st);
   if (rc) return rc;
-  colsum_kernel<<<chunks, kH, 0, st>>>(L->D1, n, L->G + kOffB1);
+  rc = bias_grad(L, L->D1, n, 1, L->G + kOffB1, st);
+  if (rc) return rc;
   // dW1[n][k] = sum_m dH1[m][n] X[m][k]
   rc = gemm<true, true, EPI_STORE_F32>(kH, kIn, (int)n, L->D1, kH, X, kIn, L->G + kOffW1, kIn,
                                        nullptr, nullptr, st);
@@ -704,7 +883,7 @@ int qtv_locator_init(qtv_handle h, uint64_t seed) {
   init_kernel<<<64, 256>>>(L->P, seed);
   cudaMemset(L->M, 0, kNumParams * 4);
   cudaMemset(L->V, 0, kNumParams * 4);
-  refresh_bf16_kernel<<<64, 256>>>(L->P, L->w1b, L->w2b);
+  refresh_bf16_kernel<<<64, 256>>>(L->P, L->w1b, L->w2b, L->w2tb);
   L->step = 0;
   L->ready = true;
   return check_cuda(cudaDeviceSynchronize(), "qtv_locator_init");
@@ -747,7 +926,7 @@ int qtv_locator_set(qtv_handle h, const float* params, const float* adam, uint64
     }
   }
   if (e != cudaSuccess) return check_cuda(e, "qtv_locator_set");
-  refresh_bf16_kernel<<<64, 256>>>(L->P, L->w1b, L->w2b);
+  refresh_bf16_kernel<<<64, 256>>>(L->P, L->w1b, L->w2b, L->w2tb);
   L->step = step;
   L->ready = true;
   return check_cuda(cudaDeviceSynchronize(), "qtv_locator_set");
@@ -805,7 +984,7 @@ int qtv_locator_train_step(qtv_handle h, const uint16_t* x, const float* targets
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.f - powf(b1, (float)L->step), c2 = 1.f - powf(b2, (float)L->step);
   adam_kernel<<<128, 256, 0, st>>>(L->P, L->G, L->M, L->V, (int)kNumParams, lr, b1, b2, 1e-8f, c1,
-                                   c2, L->w1b, L->w2b);
+                                   c2, L->w1b, L->w2b, L->w2tb);
   return check_cuda(cudaGetLastError(), "adam_kernel launch");
 }
 

@@ -423,7 +423,239 @@ __global__ void __launch_bounds__(kMlpThreads, 1) tc_mlp_kernel(
                  : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// General training GEMM on the tensor cores: C[M][N] = A[M][K] B[N][K]^T, A
+// and B BF16 and K-major (row pitch lda / ldb elements), N = 128 or 256, FP32
+// accumulation in tensor memory.  One CTA of 4 warps per (128-row tile, K
+// split): K chunks of 64 are staged by cp.async into two shared-memory
+// stages in the canonical no-swizzle layout, one elected thread issues four
+// M = 128, N, K = 16 MMAs per chunk and commits them to the stage's mbarrier,
+// and the next chunk's copies overlap the current chunk's MMAs.  Epilogues:
+//   kEpiF32       C[(split M + row) ldc + col] = acc (per-split partials when
+//                 the K range is split; tc_split_sum adds them in split order)
+//   kEpiBiasRelu  v = relu(acc + bias[col]) as BF16 into O[row][col] and,
+//                 if OT, OT[col][row]
+//   kEpiMask      v = acc where mask[row][col] > 0, else 0, into O and OT
+// Rows of A at or beyond M are read as zero; K must be a multiple of 64 per
+// split (the callers pad with zero columns).
+// ---------------------------------------------------------------------------
+enum { kEpiF32 = 0, kEpiBiasRelu = 1, kEpiMask = 2 };
+constexpr int kGemmKc = 64;  // K per chunk
+
+template <int N>
+constexpr uint32_t idesc_n() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+// rows [r0, r0 + R) x columns [0, 64) of a K-major BF16 matrix (row pitch ld,
+// columns already offset) into the canonical layout; rows at or beyond nrows
+// are zero
+__device__ __forceinline__ void load_chunk_async(unsigned char* dst, const uint16_t* __restrict__ src,
+                                                 long long ld, long long r0, int R, long long nrows) {
+  constexpr int kc8 = kGemmKc / 8;
+  const int chunks = R * kc8;
+  for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+    const int rr = c & 7, kc = (c >> 3) % kc8, rg = (c >> 3) / kc8;
+    const long long r = r0 + rg * 8 + rr;
+    const bool in = r < nrows;
+    const uint16_t* g = src + (in ? r : 0) * ld + kc * 8;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst + (size_t)c * 16)),
+                 "l"(g), "r"(in ? 16 : 0)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(
+    const uint16_t* __restrict__ A, long long lda, const uint16_t* __restrict__ B, long long ldb,
+    long long M, int ksplit, int epi, float* __restrict__ C, long long ldc,
+    uint16_t* __restrict__ O, long long ldo, uint16_t* __restrict__ OT, long long ldot,
+    const float* __restrict__ bias, const uint16_t* __restrict__ mask, long long ldm,
+    unsigned int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  constexpr uint32_t kA = TM * kGemmKc * 2, kB = N * kGemmKc * 2;  // bytes of one stage
+  // stage s: A at dsm + s (kA + kB), B right after it
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(dsm + 2 * (kA + kB));  // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const long long r0 = (long long)blockIdx.x * TM;
+  const long long k0 = (long long)blockIdx.y * ksplit;
+  const int nch = ksplit / kGemmKc;
+
+  if (w == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"((uint32_t)N)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1u);
+    mbar_init(&mbar[1], 1u);
+    fence_mbar_init();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t lbo = 128u, sbo = (uint32_t)(kGemmKc / 8) * 128u;
+  bool timeout = false;
+
+  for (int i = 0; i < nch; ++i) {
+    const int s = i & 1;
+    // the MMAs of chunk i - 2 read this stage: wait for their commit
+    if (i >= 2 && !mbar_wait(&mbar[s], (uint32_t)((i / 2 - 1) & 1))) timeout = true;
+    const long long kk = k0 + (long long)i * kGemmKc;
+    unsigned char* const sA = dsm + (size_t)s * (kA + kB);
+    unsigned char* const sB = sA + kA;
+    load_chunk_async(sA, A + kk, lda, r0, TM, M);
+    load_chunk_async(sB, B + kk, ldb, 0, N, N);
+    cp_async_wait_all();
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint64_t ad = smem_desc(smem_u32(sA), lbo, sbo);
+      const uint64_t bd = smem_desc(smem_u32(sB), lbo, sbo);
+#pragma unroll
+      for (int kb = 0; kb < kGemmKc / 16; ++kb) {
+        const uint64_t adv = (uint64_t)((kb * 256) >> 4);
+        const uint32_t acc = (i > 0 || kb > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad + adv), "l"(bd + adv), "r"(idesc_n<N>()), "r"(acc)
+            : "memory");
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&mbar[s]))
+          : "memory");
+    }
+  }
+  // the last commit covers every MMA issued before it
+  if (nch > 0 && !mbar_wait(&mbar[(nch - 1) & 1], (uint32_t)(((nch - 1) / 2) & 1))) timeout = true;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+  // epilogue: warp w owns TMEM lanes (rows) 32 w .. 32 w + 31
+  const long long row = r0 + 32 * w + lane;
+  const bool live = row < M && nch > 0;
+#pragma unroll 1
+  for (int c0 = 0; c0 < N; c0 += 32) {
+    uint32_t v[32];
+    tmem_ld32(tmem + ((uint32_t)(32 * w) << 16) + (uint32_t)c0, v);
+    if (epi == kEpiF32) {
+      if (live) {
+        float4* dst = reinterpret_cast<float4*>(C + ((long long)blockIdx.y * M + row) * ldc + c0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          dst[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                               __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+      }
+      continue;
+    }
+    float f[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      float x = __uint_as_float(v[j]);
+      if (epi == kEpiBiasRelu) {
+        x = fmaxf(x + bias[c0 + j], 0.f);
+      } else if (live) {
+        const uint16_t mk = mask[row * ldm + c0 + j];
+        if (!(__uint_as_float((uint32_t)mk << 16) > 0.f)) x = 0.f;
+      }
+      f[j] = x;
+    }
+    if (live) {
+      uint32_t pk[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) pk[j] = bf16x2_bits(f[2 * j], f[2 * j + 1]);
+      uint4* dst = reinterpret_cast<uint4*>(O + row * ldo + c0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+      if (OT) {
+        // column c0 + j of the 32 rows of this warp: 64 contiguous bytes
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const __nv_bfloat16 b = __float2bfloat16_rn(f[j]);
+          OT[(long long)(c0 + j) * ldot + row] = *reinterpret_cast<const uint16_t*>(&b);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  if (timeout) atomicOr(status, 1u);
+  __syncthreads();
+  if (w == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)N)
+                 : "memory");
+}
+
+// G[i] = sum over splits s = 0, 1, ... of P[s][i], in that order
+__global__ void tc_split_sum_kernel(const float* __restrict__ P, long long n, int splits,
+                                    float* __restrict__ G) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int s = 0; s < splits; ++s) acc += P[(long long)s * n + i];
+    G[i] = acc;
+  }
+}
+
 }  // namespace
+
+size_t tc_gemm_smem(int N) { return (size_t)2 * (TM + N) * kGemmKc * 2 + 16 + 16; }
+
+// C[M][N] = A[M][K] B[N][K]^T on the tensor cores (see tc_gemm_kernel).
+// epi 0: FP32 into C (row pitch ldc); with splits > 1 the K range is cut in
+// `splits` parts whose partials go to `part` ([splits][M][N]) and are summed
+// into C (pitch N) in split order, so the result does not depend on timing.
+// epi 1 / 2: BF16 into O (and OT transposed, if not null).
+int tc_gemm(const uint16_t* A, long long lda, const uint16_t* B, long long ldb, long long M, int N,
+            long long K, int splits, int epi, float* C, long long ldc, float* part, uint16_t* O,
+            long long ldo, uint16_t* OT, long long ldot, const float* bias, const uint16_t* mask,
+            long long ldm, unsigned int* status, cudaStream_t st) {
+  if (M <= 0) return QTV_OK;
+  if (N != 128 && N != 256) return set_error(QTV_ERR_ARG, "tc_gemm: N = %d (128 or 256)", N);
+  if (splits < 1 || K % ((long long)splits * kGemmKc) != 0)
+    return set_error(QTV_ERR_ARG, "tc_gemm: K = %lld not a multiple of %d splits x %d", K, splits,
+                     kGemmKc);
+  if (splits > 1 && (epi != kEpiF32 || !part))
+    return set_error(QTV_ERR_ARG, "tc_gemm: split K needs the FP32 epilogue and partials");
+  static bool attr[2] = {false, false};
+  const int which = N == 256 ? 1 : 0;
+  const size_t smem = tc_gemm_smem(N);
+  if (!attr[which]) {
+    cudaError_t e = N == 256 ? cudaFuncSetAttribute(tc_gemm_kernel<256>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                             : cudaFuncSetAttribute(tc_gemm_kernel<128>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return check_cuda(e, "cudaFuncSetAttribute(tc_gemm)");
+    attr[which] = true;
+  }
+  const dim3 grid((unsigned)((M + TM - 1) / TM), (unsigned)splits);
+  const int ksplit = (int)(K / splits);
+  float* Cout = splits > 1 ? part : C;
+  const long long ldcc = splits > 1 ? N : ldc;
+  if (N == 256)
+    tc_gemm_kernel<256><<<grid, 128, smem, st>>>(A, lda, B, ldb, M, ksplit, epi, Cout, ldcc, O, ldo,
+                                                 OT, ldot, bias, mask, ldm, status);
+  else
+    tc_gemm_kernel<128><<<grid, 128, smem, st>>>(A, lda, B, ldb, M, ksplit, epi, Cout, ldcc, O, ldo,
+                                                 OT, ldot, bias, mask, ldm, status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return check_cuda(e, "tc_gemm_kernel launch");
+  if (splits > 1) {
+    const long long n = M * N;
+    tc_split_sum_kernel<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(
+        part, n, splits, C);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return check_cuda(e, "tc_split_sum_kernel launch");
+  }
+  return QTV_OK;
+}
 
 size_t tc_dense_smem(int K) {
   return (size_t)(TN + TM) * K * 2 + 8 + 16 + TN * sizeof(float);

@@ -177,6 +177,48 @@ def test_gradients_match_oracle(q, small_faces):
         assert cos > 0.999 and rel < 2e-2, (key, cos, rel)
 
 
+@pytest.fixture(scope="module")
+def more_faces(q):
+    host = synth.random_waves_numpy((64, 96, 128), synth.wave_spec(14, 512))
+    psi = torch.from_numpy(host).cuda()
+    ids, w, _ = q.identify(psi)
+    return host, psi, ids, w
+
+
+@pytest.mark.parametrize("n", [64, 192, 4096])
+def test_tcgen05_training_gradients_match_oracle(q, more_faces, n):
+    """Training on tcgen05 (the default path): forward, data-gradient and
+    weight-gradient GEMMs with accumulators in tensor memory, batches of 1, 3
+    and 64 K chunks of 64 rows (the weight gradients split along the batch
+    into 1, 3 and 16 parts summed in a fixed order), against the FP64 oracle;
+    and against the mma.sync layer kernels (the same BF16 operands, another
+    accumulation order)."""
+    q.locator_init(21)
+    xb, t = _batch(q, more_faces, n=n)
+    q.locator_set_tensor_path(1)
+    g1, loss1 = q.locator_gradients(xb, t)
+    q.locator_set_tensor_path(0)
+    try:
+        g0, loss0 = q.locator_gradients(xb, t)
+    finally:
+        q.locator_set_tensor_path(1)
+    _, d = _oracle_with_bf16_weights(q)
+    lo, go = mlp.loss_and_grads(d, bf16_to_f64(xb), t.cpu().numpy().astype(np.float64))
+    assert abs(float(loss1.item()) - lo) < 1e-2 * lo
+    gg1 = params_to_dict(g1.cpu().numpy())
+    gg0 = params_to_dict(g0.cpu().numpy())
+    for key in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        a, b = gg1[key].reshape(-1), go[key].reshape(-1)
+        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert cos > 0.999 and rel < 2e-2, (key, cos, rel)
+        c = gg0[key].reshape(-1)
+        assert np.linalg.norm(a - c) / np.linalg.norm(c) < 1e-2, key
+    # deterministic: the same gradients bit for bit on a second call
+    g2, _ = q.locator_gradients(xb, t)
+    assert torch.equal(g1, g2)
+
+
 def test_adam_step_matches_oracle(q, small_faces):
     q.locator_init(13)
     xb, t = _batch(q, small_faces)
