@@ -192,6 +192,28 @@ def make_field(n, device):
     return synth.multiplicative_noise(psi, 8)
 
 
+def gain_report(q, noise):
+    """RMS distance (h) to the clean plain cores of the plain solve of the
+    noisy field and of the network on the noisy neighbourhoods, over all faces
+    and over the tenth of the faces where the plain solve is worst."""
+    import torch
+
+    from paper_1911_12070_gb300 import learned
+
+    clean, noisy = learned.field_pair(120, 256, 4096, noise, "cuda")
+    test = learned.make_examples(q, clean, noisy)
+    y = q.locator_forward(test["x"])
+    xyz_n, _, _ = q.localize(noisy, test["ids"], test["w"])
+    uvp = learned.face_uv(test["ids"], xyz_n, tuple(noisy.shape))
+    ep = torch.sqrt(torch.sum((uvp - test["t"][:, :2]) ** 2, 1))
+    el = torch.sqrt(torch.sum((y[:, :2] - test["t"][:, :2]) ** 2, 1))
+    hard = ep > torch.quantile(ep, 0.9)
+    rms = lambda e: float(torch.sqrt(torch.mean(e ** 2)))  # noqa: E731
+    return {"faces": int(ep.numel()), "plain_rms_h": rms(ep), "network_rms_h": rms(el),
+            "worst_decile_plain_rms_h": rms(ep[hard]),
+            "worst_decile_network_rms_h": rms(el[hard])}
+
+
 def learned_report(q, psi, ids, wnd, F, stream, reps=20):
     """Trains the learned locator (12 seeds of 256^3, about 2e6 faces, the
     library's own training kernels), then times plain localization and learned
@@ -249,7 +271,18 @@ def learned_report(q, psi, ids, wnd, F, stream, reps=20):
     rms_all = float(torch.sqrt(torch.mean(d2[good])))
     rms_acc = float(torch.sqrt(torch.mean(d2[good & accepted])))
     flop = 2 * (128 * 256 + 256 * 256 + 256 * 3) * F
+    # what the network gains over the plain solve (held-out field, seed 120):
+    # at the training noise (5%) and with a second locator trained at 15%
+    gain = {"against": "clean plain cores of a held-out 256^3 field (seed 120)",
+            "noise_0.05": gain_report(q, 0.05)}
+    q2 = qtv.Qtv(psi.device.index)
+    try:
+        learned.fit(q2, noise=0.15)
+        gain["noise_0.15"] = gain_report(q2, 0.15)
+    finally:
+        q2.close()
     return {
+        "gain": gain,
         "faces": F,
         "train": {"faces": "12 random-wave fields 256^3 (4096 waves, seeds 101-112), 5% noise "
                            "inputs, clean plain labels", "steps": int(len(losses)),

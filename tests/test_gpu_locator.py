@@ -288,22 +288,55 @@ def test_training_reduces_loss_and_meets_accuracy(q, trained):
     assert rms_learned <= 0.05
 
 
-def test_gain_over_plain_on_noisy_field(q, trained):
-    """What the network adds, measured: on the 5%-noise field the plain zero
-    moves with the noise; the network sees 64 nodes.  Both are compared with
-    the clean plain cores.  The network does not beat the plain solve here
-    (about 0.019 h against 0.015 h), so the test records both numbers and
-    holds each to the 0.05 h target."""
+def _gain(q, noise):
+    """(plain RMS, network RMS, worst-decile plain RMS, network RMS there) in h
+    against the clean plain cores of the held-out field (seed 120) with the
+    given multiplicative noise: plain solves the noisy field, the network
+    sees the noisy 4 x 4 x 4 neighbourhoods."""
     from paper_1911_12070_gb300 import learned
 
-    _, test, clean, noisy = trained
+    clean, noisy = learned.field_pair(120, 256, 4096, noise, "cuda")
+    test = learned.make_examples(q, clean, noisy)
     y = q.locator_forward(test["x"])
-    rms_learned = learned.rms_h(y[:, :2], test["t"][:, :2])
     xyz_n, _, _ = q.localize(noisy, test["ids"], test["w"])
-    uv_plain_noisy = learned.face_uv(test["ids"], xyz_n, tuple(noisy.shape))
-    rms_plain = learned.rms_h(uv_plain_noisy, test["t"][:, :2])
-    print(f"noisy field vs clean cores: plain {rms_plain:.4f} h, learned {rms_learned:.4f} h")
-    assert rms_plain <= 0.05 and rms_learned <= 0.05
+    uvp = learned.face_uv(test["ids"], xyz_n, tuple(noisy.shape))
+    ep = torch.sqrt(torch.sum((uvp - test["t"][:, :2]) ** 2, 1))
+    el = torch.sqrt(torch.sum((y[:, :2] - test["t"][:, :2]) ** 2, 1))
+    hard = ep > torch.quantile(ep, 0.9)
+    rms = lambda e: float(torch.sqrt(torch.mean(e ** 2)))  # noqa: E731
+    return rms(ep), rms(el), rms(ep[hard]), rms(el[hard])
+
+
+def test_gain_over_plain_on_noisy_field(q, trained):
+    """What the network adds, measured against the clean plain cores.  At 5%
+    noise the plain zero of the noisy field is 0.015 h away and the network
+    0.019 h: no gain on average, but on the tenth of the faces where the plain
+    solve is worst (a noisy corner moves the zero most) the network, which
+    sees 64 nodes, is closer (about 0.021 against 0.030 h)."""
+    p, n, ph, nh = _gain(q, 0.05)
+    print(f"5% noise vs clean cores: plain {p:.4f} h, network {n:.4f} h; "
+          f"worst-decile plain faces: plain {ph:.4f} h, network {nh:.4f} h")
+    assert p <= 0.05 and n <= 0.05
+    assert nh < 0.85 * ph
+
+
+def test_gain_at_higher_noise():
+    """A locator trained and tested at 15% noise: the network's 64-node
+    receptive field averages the noise the 4-corner solve cannot (measured
+    about 0.026 h against 0.046 h for plain), so it gains over the method
+    without it on all faces."""
+    import paper_1911_12070_gb300 as qtv
+    from paper_1911_12070_gb300 import learned
+
+    q2 = qtv.Qtv(0)
+    try:
+        learned.fit(q2, noise=0.15)
+        p, n, ph, nh = _gain(q2, 0.15)
+    finally:
+        q2.close()
+    print(f"15% noise vs clean cores: plain {p:.4f} h, network {n:.4f} h; "
+          f"worst-decile plain faces: plain {ph:.4f} h, network {nh:.4f} h")
+    assert n <= 0.05 and n < 0.75 * p and nh < 0.5 * ph
 
 
 def test_learned_localize_tcgen05_path(q, trained):
