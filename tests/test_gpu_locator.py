@@ -137,6 +137,28 @@ def test_tcgen05_forward_matches_oracle(q, small_faces):
     assert np.max(np.abs(y - yo)) < 2e-2 * scale
 
 
+@pytest.mark.parametrize("n", [1, 64, 129, 128 * 151 + 1])
+def test_tcgen05_forward_small_and_ragged(q, n):
+    """Row counts below one tile, one row past a tile, and one row past one
+    tile per SM (the grid smaller than, or one tile past, the SM count): the
+    tensor copies read the rows past the end as zeros and the first and last
+    rows match the oracle."""
+    q.locator_init(11)
+    g = torch.Generator(device="cpu").manual_seed(n)
+    xf = torch.randn((n, 128), generator=g) * 0.7
+    x = xf.to(torch.bfloat16).view(torch.int16).cuda()
+    y = q.locator_forward(x)
+    _, d = _oracle_with_bf16_weights(q)
+    rows = np.unique(np.r_[0:min(n, 3), max(0, n - 3):n])
+    yo, _ = mlp.forward(d, bf16_to_f64(x[torch.from_numpy(rows).cuda()]))
+    # the output scale of this network on 256 rows of the same distribution
+    xs = (torch.randn((256, 128), generator=g) * 0.7).to(torch.bfloat16).view(torch.int16)
+    ys, _ = mlp.forward(d, bf16_to_f64(xs))
+    scale = float(np.sqrt(np.mean(ys ** 2)))
+    assert y.shape == (n, 3) and bool(torch.isfinite(y).all())
+    assert np.max(np.abs(y[torch.from_numpy(rows).cuda()].cpu().numpy() - yo)) < 2e-2 * scale
+
+
 def test_tcgen05_matches_mma_path_on_many_tiles(q):
     """Ragged row count over many 128-row tiles (more tiles than SMs, so every
     persistent CTA loops and prefetches): the two tensor paths agree to
