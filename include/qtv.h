@@ -315,7 +315,9 @@ QTV_API int qtv_locator_save(qtv_handle h, const char* path);
  * with every dense contraction - forward, data gradient and weight gradients
  * - as tcgen05 GEMMs with accumulators in tensor memory (weight gradients
  * split along the batch and summed in a fixed order).  Both paths use BF16
- * operands with FP32 accumulation; results agree to accumulation order. */
+ * operands with FP32 accumulation; results agree to accumulation order.
+ * On path 1, qtv_locator_forward reads x by tensor copies: x must be 16-byte
+ * aligned and n below 2^31 (else QTV_ERR_ARG). */
 QTV_API int qtv_locator_set_tensor_path(qtv_handle h, int path);
 QTV_API int qtv_locator_load(qtv_handle h, const char* path);
 
