@@ -1,23 +1,18 @@
 // locator_tc.cu -- the learned locator's network on the 5th-generation tensor
-// cores (tcgen05, accumulators in tensor memory): a dense layer
-// out[M][256] = relu(A[M][K] W[256][K]^T + b) in BF16 (K = 128 or 256), the
-// training GEMM (tc_gemm_kernel) and the whole 128-256-256-3 network fused
-// per 128-row tile (tc_mlp_kernel, warp-specialised; its design is described
-// at its definition).
+// cores (tcgen05, accumulators in tensor memory): the training GEMM
+// (tc_gemm_kernel) and the whole 128-256-256-3 network fused per 128-row tile
+// (tc_mlp_kernel, warp-specialised; its design is described at its
+// definition).
 //
-// The dense layer: a persistent CTA of 4 warps keeps W in shared memory for
-// all its 128-row tiles of A.  Operands are stored in the canonical K-major
-// layout without swizzle: 8 x 8 core matrices of 128 contiguous bytes (8 rows
-// of 16 bytes), core matrix (r / 8, k / 8) at ((r / 8) (K / 8) + k / 8) 128
-// bytes, so the leading-dimension offset (next core matrix along K) is 128
-// bytes and the stride offset (next 8-row group) is 16 K bytes.  One elected
-// thread issues K / 16 tcgen05.mma instructions of M = 128, N = 256, K = 16
-// into a 256-column FP32 accumulator in tensor memory and commits them to an
-// mbarrier; then each warp reads its 32 rows back with tcgen05.ld (32 columns
-// at a time), adds the bias, applies ReLU, rounds to BF16 and stores 64
-// contiguous bytes per row.  The accumulator columns are allocated once per
-// CTA and freed before exit; the mbarrier wait is bounded and sets a status
-// flag on timeout.
+// Operands staged by threads are stored in the canonical K-major layout
+// without swizzle: 8 x 8 core matrices of 128 contiguous bytes (8 rows of 16
+// bytes), core matrix (r / 8, k / 8) at ((r / 8) (K / 8) + k / 8) 128 bytes,
+// so the leading-dimension offset (next core matrix along K) is 128 bytes and
+// the stride offset (next 8-row group) is 16 K bytes.  One elected thread
+// issues the tcgen05.mma instructions and commits them to mbarriers; warps
+// read their 32 TMEM lanes back with tcgen05.ld.  Accumulator columns are
+// allocated once per CTA and freed before exit; every mbarrier wait is
+// bounded and sets a status flag on timeout.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -31,7 +26,6 @@ namespace {
 using namespace sweep;
 
 constexpr int TM = 128;   // rows per tile (M of one instruction, TMEM lanes)
-constexpr int TN = 256;   // outputs (N of one instruction, TMEM columns)
 
 __device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -47,10 +41,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
   d |= (uint64_t)1 << 46;  // descriptor version of the 5th-generation tensor cores
   return d;                // base offset 0, swizzle none
 }
-
-// instruction descriptor of kind::f16: D F32, A and B BF16, both K-major
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
-                            ((uint32_t)(TM >> 4) << 24);
 
 // rows [r0, r0 + R) of a row-major BF16 matrix (K columns, row pitch K) into
 // the canonical layout at dst; rows at or beyond nrows become zero.  Piece c
@@ -72,116 +62,6 @@ __device__ __forceinline__ void load_canon(unsigned char* dst, const uint16_t* _
 
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
-}
-
-__global__ void __launch_bounds__(128, 1) tc_dense_kernel(const uint16_t* __restrict__ A,
-                                                          long long M, int K,
-                                                          const uint16_t* __restrict__ W,
-                                                          const float* __restrict__ bias,
-                                                          uint16_t* __restrict__ out,
-                                                          unsigned int* __restrict__ status) {
-  extern __shared__ __align__(1024) unsigned char dsm[];
-  unsigned char* sW = dsm;                                 // TN x K
-  unsigned char* sA = dsm + (size_t)TN * K * 2;            // TM x K
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sA + (size_t)TM * K * 2);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
-  float* sb = reinterpret_cast<float*>(tslot + 4);         // bias [TN]
-  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-
-  if (w == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tslot)),
-                 "r"((uint32_t)TN)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  if (tid == 0) {
-    mbar_init(mbar, 1u);
-    fence_mbar_init();
-  }
-  for (int i = tid; i < TN; i += blockDim.x) sb[i] = bias[i];
-  load_canon(sW, W, 0, TN, TN, K);
-  fence_proxy_async();
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *tslot;
-  const uint32_t lbo = 128u, sbo = (uint32_t)(K / 8) * 128u;
-  const uint64_t adesc0 = smem_desc(smem_u32(sA), lbo, sbo);
-  const uint64_t bdesc0 = smem_desc(smem_u32(sW), lbo, sbo);
-  bool timeout = false;
-  uint32_t phase = 0;
-
-  const long long ntiles = (M + TM - 1) / TM;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long r0 = tile * TM;
-    load_canon(sA, A, r0, TM, M, K);
-    fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      for (int kb = 0; kb < K / 16; ++kb) {
-        // advance both start addresses by two core matrices (256 bytes) per K step
-        const uint64_t adv = (uint64_t)((kb * 256) >> 4);
-        const uint32_t acc = kb > 0 ? 1u : 0u;
-        asm volatile(
-            "{\n"
-            " .reg .pred p;\n"
-            " setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
-            "}\n" ::"r"(tmem),
-            "l"(adesc0 + adv), "l"(bdesc0 + adv), "r"(kIdesc), "r"(acc)
-            : "memory");
-      }
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_u32(mbar))
-          : "memory");
-    }
-    if (!mbar_wait(mbar, phase)) timeout = true;
-    phase ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: warp w owns TMEM lanes (rows) 32 w .. 32 w + 31
-    const long long row = r0 + 32 * w + lane;
-#pragma unroll 1
-    for (int c0 = 0; c0 < TN; c0 += 32) {
-      uint32_t v[32];
-      const uint32_t taddr = tmem + ((uint32_t)(32 * w) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-          "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
-          "%28, %29, %30, %31}, [%32];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-            "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
-            "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-            "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
-            "=r"(v[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < M) {
-        uint32_t pk[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const float lo = fmaxf(__uint_as_float(v[2 * j]) + sb[c0 + 2 * j], 0.f);
-          const float hi = fmaxf(__uint_as_float(v[2 * j + 1]) + sb[c0 + 2 * j + 1], 0.f);
-          pk[j] = bf16x2_bits(lo, hi);
-        }
-        uint4* dst = reinterpret_cast<uint4*>(out + row * TN + c0);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
-      }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-  }
-  if (timeout) atomicOr(status, 1u);
-  __syncthreads();
-  if (w == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"((uint32_t)TN)
-                 : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -875,29 +755,6 @@ int tc_gemm(const uint16_t* A, long long lda, const uint16_t* B, long long ldb, 
     if (e != cudaSuccess) return check_cuda(e, "tc_split_sum_kernel launch");
   }
   return QTV_OK;
-}
-
-size_t tc_dense_smem(int K) {
-  return (size_t)(TN + TM) * K * 2 + 8 + 16 + TN * sizeof(float);
-}
-
-// out[M][256] = relu(A W^T + b) (BF16, row-major); A [M][K], W [256][K] BF16.
-int tc_dense_relu(const uint16_t* A, long long M, int K, const uint16_t* W, const float* bias,
-                  uint16_t* out, unsigned int* status, int num_sms, cudaStream_t st) {
-  if (K != 128 && K != 256) return set_error(QTV_ERR_ARG, "tc_dense: K = %d (128 or 256)", K);
-  if (M <= 0) return QTV_OK;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(tc_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             227 * 1024);
-    if (e != cudaSuccess) return check_cuda(e, "cudaFuncSetAttribute(tc_dense)");
-    attr = true;
-  }
-  const long long ntiles = (M + TM - 1) / TM;
-  const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
-  tc_dense_kernel<<<grid, 128, tc_dense_smem(K), st>>>(A, M, K, W, bias, out, status);
-  return check_cuda(cudaGetLastError(), "tc_dense_kernel launch");
 }
 
 // Y[M][3] of the whole network on the tensor cores (see tc_mlp_kernel).

@@ -382,18 +382,14 @@ int locator_localize(qtv_handle h, const FaceGeo& geo, const uint64_t* face_ids,
 // locator is loaded.
 int locator_prepare(qtv_handle h, uint64_t n, uint64_t* generation);
 
-// Dense layer on the 5th-generation tensor cores (locator_tc.cu):
-// out[M][256] = relu(A[M][K] W[256][K]^T + b) in BF16, K = 128 or 256.
-int tc_dense_relu(const uint16_t* A, long long M, int K, const uint16_t* W, const float* bias,
-                  uint16_t* out, unsigned int* status, int num_sms, cudaStream_t st);
-// The whole network, fused: Y[M][3] from X[M][128] (W1, W2 BF16; biases and
-// W3 FP32).
 // C[M][N] = A[M][K] B[N][K]^T on tcgen05 (locator_tc.cu); epi 0 FP32 (split K
 // summed in order), 1 relu(. + bias) BF16, 2 masked by mask > 0 BF16
 int tc_gemm(const uint16_t* A, long long lda, const uint16_t* B, long long ldb, long long M, int N,
             long long K, int splits, int epi, float* C, long long ldc, float* part, uint16_t* O,
             long long ldo, uint16_t* OT, long long ldot, const float* bias, const uint16_t* mask,
             long long ldm, unsigned int* status, cudaStream_t st);
+// The whole network, fused (locator_tc.cu): Y[M][3] from X[M][128] (W1, W2
+// BF16; biases and W3 FP32); X 16-byte aligned, M below 2^31.
 int tc_mlp_forward(const uint16_t* X, long long M, const uint16_t* W1, const uint16_t* W2,
                    const float* b1, const float* b2, const float* w3, const float* b3, float* Y,
                    unsigned int* status, int num_sms, cudaStream_t st);
