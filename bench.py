@@ -352,6 +352,36 @@ def node_form_report(q, psi, xyz, count, stream, reps=20):
                   "components": ncomp, "edges": int(ndeg.long().sum().item()) // 2}
     except QtvError as err:
         ngraph = {"error": str(err)}
+    # the same node form from the identification's face list (a ring's
+    # circulation is the sum of its four plaquettes' windings)
+    try:
+        fids, fw, _ = q.identify(psi)
+        fcap = cap
+        f_ids = torch.empty(fcap, dtype=torch.int64, device=dev)
+        f_circ = torch.empty((fcap, 3), dtype=torch.int8, device=dev)
+        f_cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        f_tie = torch.zeros(1, dtype=torch.int32, device=dev)
+        shape = tuple(psi.shape)
+        for _ in range(3):
+            q.node_circulation_faces_into(shape, fids, fw, f_ids, f_circ, f_cnt, f_tie)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(reps):
+            q.node_circulation_faces_into(shape, fids, fw, f_ids, f_circ, f_cnt, f_tie)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fn = int(f_cnt.item())
+        from_faces = {
+            "ms_per_call": f0.elapsed_time(f1) / reps,
+            "faces": int(fids.numel()),
+            "tie": bool(int(f_tie.item())),
+            "equal_to_psi_form": bool(fn == nv and torch.equal(f_ids[:fn], ids[:nv])
+                                      and torch.equal(f_circ[:fn], circ[:nv])),
+        }
+    except QtvError as err:
+        from_faces = {"error": str(err)}
     peak, peak_kind = peaks()
     kms = {k: v[1] / max(1, v[0]) for k, v in tr.items()}
     nf_ms = kms.get("node_form", 0.0)
@@ -369,6 +399,7 @@ def node_form_report(q, psi, xyz, count, stream, reps=20):
                      "unit": "GB/s", "frac": ach / peak, "peak_source": peak_kind,
                      "algorithmic_bytes": alg},
         "vortex_node_graph": ngraph,
+        "from_faces": from_faces,
         "density_error": {"e": e, "mean_abs_rho": mean_rho, "rho_bar": rho_bar,
                           "ms": d_ms[1] / max(1, d_ms[0]),
                           "points": "plain samples of the timed step"},

@@ -442,6 +442,37 @@ QTV_API int qtv_node_circulation(qtv_handle h, const qtv_grid* grid, const void*
                                  uint64_t* count, int8_t* dense, void* stream);
 
 /*
+ * The same node form (Sec. 2.2.2) from the pierced-face list of
+ * qtv_identify instead of from psi: the ring of a node in a plane encloses
+ * the four plaquettes of that plane at the node, its interior edges cancel,
+ * so S is the sum of their windings.  Per node row one warp adds the
+ * windings of the faces of the four neighbouring face rows and stages the
+ * row's vortex nodes; a scan over the rows and a scatter list them.  Work is
+ * per face, not per node.
+ *
+ *   face_ids, winding, n, n_dev  the ascending output of qtv_identify for
+ *             this grid (n entries, or min(n, *n_dev) if n_dev is given).
+ *   node_ids, circ, capacity, count  as qtv_node_circulation.
+ *   tie       device uint32: non-zero when the outputs are not valid: 1 when
+ *             a face has winding 2 (W mod 4 = 2: four exact +-pi ties), whose
+ *             sign the face list does not carry (call qtv_node_circulation);
+ *             2 if the staging buffer (sized for four nodes per face) ran
+ *             out, which the sizing excludes.
+ * Equal to qtv_node_circulation node for node when psi is finite (the
+ * identification reported qtv_stats.nonfinite == 0: rings through a
+ * non-finite node count 0 there, while the identification drops the faces
+ * touching it) and tie stays 0.  Rows up to 6000 nodes; fewer than 2^32
+ * faces; the handle keeps row tables of ny * nz entries and a staging buffer
+ * of 4 n entries plus 8192 per resident warp.  QTV_ERR_STATE if they must
+ * grow during stream capture.
+ */
+QTV_API int qtv_node_circulation_faces(qtv_handle h, const qtv_grid* grid,
+                                       const uint64_t* face_ids, const int8_t* winding,
+                                       uint64_t n, const uint64_t* n_dev, uint64_t* node_ids,
+                                       int8_t* circ, uint64_t capacity, uint64_t* count,
+                                       uint32_t* tie, void* stream);
+
+/*
  * Density error of the sample points (Eq. 7, Sec. 5):
  *   e = (sum over the n points of |rho(p)|) / (n * rho_bar),
  * rho = |psi|^2 of the trilinearly interpolated field at p (Sec. 5: psi is

@@ -166,6 +166,9 @@ def lib() -> ctypes.CDLL:
         L.qtv_node_graph.argtypes = [P, ctypes.POINTER(Grid), P, u64, P, P, P, P, P, P]
         L.qtv_box_reduce.argtypes = [P, u64, P, P, P, i32, P, f32, i32, P, P, P, P]
         L.qtv_box_reduce.restype = i32
+        L.qtv_node_circulation_faces.argtypes = [P, ctypes.POINTER(Grid), P, P, u64, P, P, P, u64,
+                                                 P, P, P]
+        L.qtv_node_circulation_faces.restype = i32
         for name in ("qtv_node_circulation", "qtv_density_error", "qtv_refine_samples",
                      "qtv_face_graph", "qtv_line_pieces", "qtv_piece_curves",
                      "qtv_identify_localize_host", "qtv_thin_pieces", "qtv_node_graph"):
@@ -538,6 +541,39 @@ class Qtv:
                 break
             capacity = n
         return ids[:n], circ[:n], d
+
+    def node_circulation_faces_into(self, shape, face_ids, winding, node_ids, circ, count, tie,
+                                    n_dev=None, grid=None, stream=None):
+        """Raw call: preallocated device outputs (count: uint64[1], tie: int32[1])."""
+        g = grid or Grid.of(tuple(shape))
+        cap = 0 if node_ids is None else node_ids.numel()
+        _check(lib().qtv_node_circulation_faces(
+            self.h, ctypes.byref(g), _ptr(face_ids), _ptr(winding), face_ids.numel(), _ptr(n_dev),
+            _ptr(node_ids), _ptr(circ), cap, _ptr(count), _ptr(tie), _stream_ptr(stream)))
+
+    def node_circulation_faces(self, shape, face_ids, winding, capacity: int | None = None,
+                               n_dev=None, stream=None):
+        """The node form from the face list of identify (same grid shape
+        (nz, ny, nx)): (node_ids int64 [n] ascending, circ int8 [n, 3], tie);
+        tie true means a face of winding 2 was met and the lists are not
+        valid (use node_circulation)."""
+        import torch
+
+        dev = face_ids.device
+        if capacity is None:
+            capacity = max(1024, 3 * face_ids.numel())
+        count = torch.zeros(1, dtype=torch.int64, device=dev)
+        tie = torch.zeros(1, dtype=torch.int32, device=dev)
+        for _ in range(2):
+            ids = torch.empty(capacity, dtype=torch.int64, device=dev)
+            circ = torch.empty((capacity, 3), dtype=torch.int8, device=dev)
+            self.node_circulation_faces_into(shape, face_ids, winding, ids, circ, count, tie,
+                                             n_dev=n_dev, stream=stream)
+            n = int(count.item())
+            if n <= capacity:
+                break
+            capacity = n
+        return ids[:n], circ[:n], bool(int(tie.item()))
 
     def density_error(self, psi, xyz, n_dev=None, want_rho: bool = False, grid=None,
                       stream=None):

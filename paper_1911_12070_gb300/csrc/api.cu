@@ -124,7 +124,8 @@ const char* kKernelNames[K_COUNT] = {"sweep",     "seg_scan",  "scatter",      "
                                      "localize",  "emit_pack", "batch",        "encode",
                                      "network",   "head",      "node_form",    "node_scan",
                                      "node_scatter", "density",   "refine",       "graph",
-                                     "lines",     "curves",    "thin",      "reduce"};
+                                     "lines",     "curves",    "thin",      "reduce",
+                                     "node_faces"};
 }  // namespace
 
 // Inside a stream capture the records become event-record nodes of the graph
@@ -263,6 +264,7 @@ int qtv_destroy(qtv_handle h) {
   graph_work_free(h->graph);
   line_work_free(h->lines);
   reduce_work_free(h->reduce);
+  node_faces_work_free(h->nodef);
   host_pipe_free(h->pipe);
   cudaFree(h->refine_counter);
   for (auto& r : h->trace) {

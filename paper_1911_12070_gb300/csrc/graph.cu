@@ -77,6 +77,20 @@ __global__ void row_table_kernel(const uint64_t* __restrict__ ids, unsigned long
   }
 }
 
+}  // namespace
+
+cudaError_t row_table_launch(const uint64_t* ids, unsigned long long n, const uint64_t* n_dev,
+                             int nx, long long R, int shift, uint32_t* rows, int num_sms,
+                             cudaStream_t st) {
+  long long blocks = (R + 1 + GT - 1) / GT;
+  if (blocks > (long long)num_sms * 16) blocks = (long long)num_sms * 16;
+  if (blocks < 1) blocks = 1;
+  row_table_kernel<<<(int)blocks, GT, 0, st>>>(ids, n, n_dev, nx, R, shift, rows);
+  return cudaGetLastError();
+}
+
+namespace {
+
 struct GraphArgs {
   const uint64_t* ids;
   unsigned long long n;

@@ -106,7 +106,7 @@ struct Locator;  // learned locator state (locator.cu)
 void locator_free(Locator* L);
 enum KernelId {
   K_SWEEP = 0, K_SEG_SCAN, K_SCATTER, K_STATS, K_LOCALIZE, K_EMIT_PACK, K_BATCH,
-  K_ENCODE, K_NETWORK, K_HEAD, K_NODE_FORM, K_NODE_SCAN, K_NODE_SCATTER, K_DENSITY, K_REFINE, K_GRAPH, K_LINES, K_CURVES, K_THIN, K_REDUCE, K_COUNT
+  K_ENCODE, K_NETWORK, K_HEAD, K_NODE_FORM, K_NODE_SCAN, K_NODE_SCATTER, K_DENSITY, K_REFINE, K_GRAPH, K_LINES, K_CURVES, K_THIN, K_REDUCE, K_NODE_FACES, K_COUNT
 };
 struct BatchPlan;  // batched snapshots (batch.cu)
 void batch_free(BatchPlan* b);
@@ -118,6 +118,8 @@ struct LineWork;   // line-extraction workspace (lines.cu)
 void line_work_free(LineWork* w);
 struct ReduceWork;  // box-reduction workspace (reduce.cu)
 void reduce_work_free(ReduceWork* w);
+struct NodeFacesWork;  // node form from a face list (node_faces.cu)
+void node_faces_work_free(NodeFacesWork* w);
 struct HostPipe;   // double-buffered device copies for calls from host memory (api.cu)
 void host_pipe_free(HostPipe* p);
 struct TraceRec {
@@ -140,6 +142,7 @@ struct qtv_handle_s {
   qtv::GraphWork* graph = nullptr;       // face-graph workspace
   qtv::LineWork* lines = nullptr;        // line-extraction workspace
   qtv::ReduceWork* reduce = nullptr;     // box-reduction workspace
+  qtv::NodeFacesWork* nodef = nullptr;   // node form from a face list
   qtv::HostPipe* pipe = nullptr;         // calls from host memory
   unsigned long long* refine_counter = nullptr;  // work counter of the refinement kernel
   // sweep shape of single-snapshot calls (qtv_configure_sweep); -1 / 0 = default
@@ -394,6 +397,11 @@ int tc_mlp_forward(const uint16_t* X, long long M, const uint16_t* W1, const uin
                    const float* b1, const float* b2, const float* w3, const float* b3, float* Y,
                    unsigned int* status, int num_sms, cudaStream_t st);
 
+// rows[r] = first index a with ids[a] >= (r nx) << shift, r in [0, R]
+// (graph.cu); ids ascending, n or *n_dev of them
+cudaError_t row_table_launch(const uint64_t* ids, unsigned long long n, const uint64_t* n_dev,
+                             int nx, long long R, int shift, uint32_t* rows, int num_sms,
+                             cudaStream_t st);
 // Node form of the circulation: vortex nodes in ascending order with their
 // three ring windings, optional dense field (node_form.cu)
 int node_circulation_launch(qtv_handle h, const qtv_grid& g, const float2* psi,
