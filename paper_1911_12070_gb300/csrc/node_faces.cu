@@ -243,24 +243,51 @@ __global__ void __launch_bounds__(kNfWarps * 32) node_faces_kernel(const __grid_
   }
 }
 
-// The staged rows at their places in the ascending list: a warp per node row,
-// lane i copying the row's entry i.
+// The staged rows at their places in the ascending list.  A warp takes 32
+// consecutive node rows (lane = row for their counts, staging blocks and
+// offsets); their outputs are one contiguous range, which the lanes fill in
+// order, each finding the row of its entry among the 32 by a binary search
+// over the rows' exclusive counts.
 __global__ void __launch_bounds__(256) node_faces_scatter(const __grid_constant__ NfArgs a) {
   const int lane = threadIdx.x & 31;
   const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < a.R; r += warps) {
-    const uint32_t cnt = a.rowcnt[r];
-    if (cnt == 0) continue;
-    const unsigned long long base = a.rowbase[r];
-    const unsigned long long dst0 = a.boff[r / kScanRows] + a.rowoff[r];
-    for (uint32_t q = (uint32_t)lane; q < cnt; q += 32) {
-      const unsigned long long dst = dst0 + q;
-      if (dst >= a.capacity) break;
-      const unsigned long long e = a.stage[base + q];
-      a.node_ids[dst] = (unsigned long long)r * (unsigned long long)a.nx + (e >> 32);
-      a.circ[3 * dst] = (int8_t)((int)(e & 0xFFu) - 8);
-      a.circ[3 * dst + 1] = (int8_t)((int)((e >> 8) & 0xFFu) - 8);
-      a.circ[3 * dst + 2] = (int8_t)((int)((e >> 16) & 0xFFu) - 8);
+  for (long long r0 = 32 * (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5); r0 < a.R;
+       r0 += 32 * warps) {
+    const long long r = r0 + lane;
+    uint32_t cnt = 0;
+    unsigned long long base = 0;
+    if (r < a.R) {
+      cnt = a.rowcnt[r];
+      if (cnt) base = a.rowbase[r];
+    }
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t u = __shfl_up_sync(FULL, incl, d);
+      if (lane >= d) incl += u;
+    }
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    if (total == 0) continue;
+    const uint32_t excl = incl - cnt;
+    // the first output of row r0 (the rows' outputs follow it contiguously)
+    const unsigned long long dst0 = a.boff[r0 / kScanRows] + a.rowoff[r0];
+    for (uint32_t e0 = 0; e0 < total; e0 += 32) {  // uniform trip count: shuffles below
+      const uint32_t e = e0 + (uint32_t)lane;
+      int m = 0;  // the last row whose exclusive count is <= e
+#pragma unroll
+      for (int stp = 16; stp >= 1; stp >>= 1) {
+        const uint32_t xv = __shfl_sync(FULL, excl, (m + stp) & 31);
+        if (m + stp < 32 && xv <= e) m += stp;
+      }
+      const uint32_t em = __shfl_sync(FULL, excl, m);
+      const unsigned long long bm = __shfl_sync(FULL, base, m);
+      const unsigned long long dst = dst0 + e;
+      if (e >= total || dst >= a.capacity) continue;
+      const unsigned long long v = a.stage[bm + (e - em)];
+      a.node_ids[dst] = (unsigned long long)(r0 + m) * (unsigned long long)a.nx + (v >> 32);
+      a.circ[3 * dst] = (int8_t)((int)(v & 0xFFu) - 8);
+      a.circ[3 * dst + 1] = (int8_t)((int)((v >> 8) & 0xFFu) - 8);
+      a.circ[3 * dst + 2] = (int8_t)((int)((v >> 16) & 0xFFu) - 8);
     }
   }
 }
@@ -453,7 +480,7 @@ QTV_API int qtv_node_circulation_faces(qtv_handle h, const qtv_grid* grid, const
   nf_scan_rows<<<(int)nb, kScanThreads, 0, st>>>(w->rowcnt, R, w->rowoff, w->boff);
   nf_scan_blocks<<<1, kScanThreads, 0, st>>>(w->boff, nb, count);
   if (capacity > 0) {
-    long long sblocks = (R + 7) / 8;
+    long long sblocks = (R + 255) / 256;  // 32 rows per warp
     if (sblocks > (long long)h->num_sms * 16) sblocks = (long long)h->num_sms * 16;
     node_faces_scatter<<<(int)sblocks, 256, 0, st>>>(a);
   }
