@@ -95,7 +95,7 @@ struct NfArgs {
 // S + 8 in three bytes) and a bit mask of the columns that received a face
 // (nx / 32 words): only those are read, listed and reset, so a row costs its
 // faces, not its nx nodes.
-__global__ void __launch_bounds__(kNfWarps * 32) node_faces_kernel(const __grid_constant__ NfArgs a) {
+__global__ void __launch_bounds__(kNfWarps * 32, 8) node_faces_kernel(const __grid_constant__ NfArgs a) {
   extern __shared__ uint32_t nf_acc[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kNfWarps * 32) node_faces_kernel(const __grid_
   __syncwarp();
   const long long warps = (long long)gridDim.x * kNfWarps;
   for (long long r = (long long)blockIdx.x * kNfWarps + wib; r < a.R; r += warps) {
-    const int j = (int)(r % ny), k = (int)(r / ny);
+    const int k = (int)((uint32_t)r / (uint32_t)ny), j = (int)r - k * ny;  // R < 2^31
     // face rows q = (j + dj, k + dk), dj = (q & 1) - 1, dk = (q >> 1) - 1:
     // xy faces of plane k, yz faces of all four, zx faces of row j.  Their
     // bounds come from six row-table entries read at once (lanes 0-5), and
@@ -180,11 +180,14 @@ __global__ void __launch_bounds__(kNfWarps * 32) node_faces_kernel(const __grid_
       }
       return mine;
     };
-    // the row's total first (its staging block is reserved before writing)
-    uint32_t cnt = 0;
+    // the row's total first (its staging block is reserved before writing);
+    // rows of up to 1024 nodes keep each lane's count for the listing below
+    uint32_t cnt = 0, mine0 = 0;
     for (int w0 = 0; w0 < nwords; w0 += 32) {
       const int wi = w0 + lane;
-      cnt += __reduce_add_sync(FULL, lane_count(wi < nwords ? touched[wi] : 0u, wi));
+      const uint32_t m = lane_count(wi < nwords ? touched[wi] : 0u, wi);
+      if (w0 == 0) mine0 = m;
+      cnt += __reduce_add_sync(FULL, m);
     }
     unsigned long long off = 0;
     bool store = false;
@@ -214,7 +217,7 @@ __global__ void __launch_bounds__(kNfWarps * 32) node_faces_kernel(const __grid_
     for (int w0 = 0; w0 < nwords; w0 += 32) {
       const int wi = w0 + lane;
       const uint32_t bits = wi < nwords ? touched[wi] : 0u;
-      const uint32_t mine = cnt ? lane_count(bits, wi) : 0u;
+      const uint32_t mine = w0 == 0 ? mine0 : (cnt ? lane_count(bits, wi) : 0u);
       uint32_t incl = mine;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
@@ -399,6 +402,7 @@ QTV_API int qtv_node_circulation_faces(qtv_handle h, const qtv_grid* grid, const
   if (smem > 200 * 1024)
     return set_error(QTV_ERR_ARG, "rows of %d nodes are too wide for the face-derived node form", nx);
   const long long R = (long long)ny * nz;
+  if (R >= (1ll << 31)) return set_error(QTV_ERR_ARG, "ny * nz of 2^31 or more node rows");
   const long long nb = (R + kScanRows - 1) / kScanRows;
   long long blocks = (R + kNfWarps - 1) / kNfWarps;
   const long long maxb = (long long)h->num_sms * 8;
@@ -447,6 +451,11 @@ QTV_API int qtv_node_circulation_faces(qtv_handle h, const qtv_grid* grid, const
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                 200 * 1024);
     if (e0 != cudaSuccess) return check_cuda(e0, "cudaFuncSetAttribute(node_faces)");
+    // all of the unified L1 / shared memory as shared memory: eight CTAs of
+    // 8 warps fit on an SM for rows up to 1000 nodes
+    const cudaError_t e1 = cudaFuncSetAttribute(node_faces_kernel,
+                                                cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e1 != cudaSuccess) return check_cuda(e1, "cudaFuncSetAttribute(node_faces carveout)");
     attr = true;
   }
   TraceScope ts(h, K_NODE_FACES, st);
