@@ -461,7 +461,7 @@ QTV_API int qtv_node_circulation(qtv_handle h, const qtv_grid* grid, const void*
  * Equal to qtv_node_circulation node for node when psi is finite (the
  * identification reported qtv_stats.nonfinite == 0: rings through a
  * non-finite node count 0 there, while the identification drops the faces
- * touching it) and tie stays 0.  Rows up to 6000 nodes; fewer than 2^32
+ * touching it) and tie stays 0.  Rows up to 4000 nodes; fewer than 2^32
  * faces; the handle keeps row tables of ny * nz entries and a staging buffer
  * of 4 n entries plus 8192 per resident warp.  QTV_ERR_STATE if they must
  * grow during stream capture.

@@ -100,8 +100,10 @@ __global__ void __launch_bounds__(kNfWarps * 32, 8) node_faces_kernel(const __gr
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const int nwords = (nx + 31) >> 5;
-  uint32_t* acc = nf_acc + (size_t)wib * (size_t)(nx + nwords);
+  const int wstride = nx + nwords + (nx + 1) / 2;  // words per warp
+  uint32_t* acc = nf_acc + (size_t)wib * (size_t)wstride;
   uint32_t* touched = acc + nx;
+  uint16_t* cols = reinterpret_cast<uint16_t*>(touched + nwords);  // touched columns of a row
   unsigned long long chunk_at = 0;  // this warp's staging block (lane 0)
   uint32_t chunk_left = 0;
   for (int i = lane; i < nx; i += 32) acc[i] = kBias;
@@ -160,34 +162,60 @@ __global__ void __launch_bounds__(kNfWarps * 32, 8) node_faces_kernel(const __gr
       }
     }
     __syncwarp();
-    // the touched columns with a non-zero S (rings leaving the grid count 0),
-    // lane l taking mask word l of each group of 32 (ascending x in lane
-    // order); each column is reset after it is read
+    // The touched columns, compacted in ascending order into the warp's column
+    // list (lane l owns mask word l of each group of 32), then read one column
+    // per lane: S of the three planes (rings leaving the grid count 0), the
+    // vortex nodes ranked by a ballot, staged, and every column reset.
     const bool jin = j >= 1 && j <= ny - 2, kin = k >= 1 && k <= nz - 2;
-    auto node_s = [&](int i, int& s0, int& s1, int& s2) {
-      const uint32_t v = acc[i];
-      const bool iin = i >= 1 && i <= nx - 2;
-      s0 = (iin && jin) ? (int)(v & 0xFFu) - 8 : 0;
-      s1 = (jin && kin) ? (int)((v >> 8) & 0xFFu) - 8 : 0;
-      s2 = (kin && iin) ? (int)((v >> 16) & 0xFFu) - 8 : 0;
-    };
-    auto lane_count = [&](uint32_t bits, int wi) {
-      uint32_t mine = 0;
-      for (uint32_t b = bits; b; b &= b - 1u) {
-        int s0, s1, s2;
-        node_s(32 * wi + __ffs(b) - 1, s0, s1, s2);
-        mine += (s0 | s1 | s2) != 0;
-      }
-      return mine;
-    };
-    // the row's total first (its staging block is reserved before writing);
-    // rows of up to 1024 nodes keep each lane's count for the listing below
-    uint32_t cnt = 0, mine0 = 0;
+    uint32_t ntouched = 0;
     for (int w0 = 0; w0 < nwords; w0 += 32) {
       const int wi = w0 + lane;
-      const uint32_t m = lane_count(wi < nwords ? touched[wi] : 0u, wi);
-      if (w0 == 0) mine0 = m;
-      cnt += __reduce_add_sync(FULL, m);
+      uint32_t bits = 0;
+      if (wi < nwords) {
+        bits = touched[wi];
+        touched[wi] = 0u;
+      }
+      const uint32_t pc = (uint32_t)__popc(bits);
+      uint32_t incl = pc;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t u = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += u;
+      }
+      uint32_t pos = ntouched + incl - pc;
+      for (uint32_t b = bits; b; b &= b - 1u) cols[pos++] = (uint16_t)(32 * wi + __ffs(b) - 1);
+      ntouched += __shfl_sync(FULL, incl, 31);
+    }
+    __syncwarp();
+    auto col_s = [&](uint32_t t, int& i, uint32_t& packed) -> bool {
+      i = cols[t];
+      const uint32_t v = acc[i];
+      acc[i] = kBias;
+      const bool iin = i >= 1 && i <= nx - 2;
+      const int s0 = (iin && jin) ? (int)(v & 0xFFu) - 8 : 0;
+      const int s1 = (jin && kin) ? (int)((v >> 8) & 0xFFu) - 8 : 0;
+      const int s2 = (kin && iin) ? (int)((v >> 16) & 0xFFu) - 8 : 0;
+      packed = (uint32_t)((s0 + 8) | ((s1 + 8) << 8) | ((s2 + 8) << 16));
+      return (s0 | s1 | s2) != 0;
+    };
+    // the first 32 columns are read once and held; the row's total is known
+    // before its staging block is reserved
+    int i0 = 0;
+    uint32_t p0 = 0;
+    const bool v0 = (uint32_t)lane < ntouched && col_s((uint32_t)lane, i0, p0);
+    const uint32_t bal0 = __ballot_sync(FULL, v0);
+    uint32_t cnt = (uint32_t)__popc(bal0);
+    for (uint32_t t0 = 32; t0 < ntouched; t0 += 32) {  // wide rows: count only
+      const uint32_t t = t0 + (uint32_t)lane;
+      bool v = false;
+      if (t < ntouched) {
+        const int ii = cols[t];
+        const uint32_t vv = acc[ii];
+        const bool iin = ii >= 1 && ii <= nx - 2;
+        v = ((iin && jin) && (vv & 0xFFu) != 8u) || ((jin && kin) && ((vv >> 8) & 0xFFu) != 8u) ||
+            ((kin && iin) && ((vv >> 16) & 0xFFu) != 8u);
+      }
+      cnt += (uint32_t)__popc(__ballot_sync(FULL, v));
     }
     unsigned long long off = 0;
     bool store = false;
@@ -214,33 +242,20 @@ __global__ void __launch_bounds__(kNfWarps * 32, 8) node_faces_kernel(const __gr
       store = off + cnt <= a.stage_cap;
     }
     if (lane == 0) a.rowcnt[r] = cnt;
-    for (int w0 = 0; w0 < nwords; w0 += 32) {
-      const int wi = w0 + lane;
-      const uint32_t bits = wi < nwords ? touched[wi] : 0u;
-      const uint32_t mine = w0 == 0 ? mine0 : (cnt ? lane_count(bits, wi) : 0u);
-      uint32_t incl = mine;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t u = __shfl_up_sync(FULL, incl, d);
-        if (lane >= d) incl += u;
-      }
-      const uint32_t tot = __shfl_sync(FULL, incl, 31);
-      unsigned long long dst = off + (incl - mine);
-      for (uint32_t b = bits; b; b &= b - 1u) {
-        const int i = 32 * wi + __ffs(b) - 1;
-        int s0, s1, s2;
-        node_s(i, s0, s1, s2);
-        if ((s0 | s1 | s2) != 0) {
-          // staged: x and the three S + 8
-          if (store)
-            a.stage[dst] = ((unsigned long long)(unsigned)i << 32) |
-                           (unsigned)((s0 + 8) | ((s1 + 8) << 8) | ((s2 + 8) << 16));
-          ++dst;
-        }
-        acc[i] = kBias;
-      }
-      if (wi < nwords) touched[wi] = 0u;
-      off += tot;
+    if (store && v0)
+      a.stage[off + (unsigned)__popc(bal0 & ((1u << lane) - 1u))] =
+          ((unsigned long long)(unsigned)i0 << 32) | p0;
+    off += (unsigned)__popc(bal0);
+    for (uint32_t t0 = 32; t0 < ntouched; t0 += 32) {
+      const uint32_t t = t0 + (uint32_t)lane;
+      int ii = 0;
+      uint32_t pp = 0;
+      const bool v = t < ntouched && col_s(t, ii, pp);
+      const uint32_t bal = __ballot_sync(FULL, v);
+      if (store && v)
+        a.stage[off + (unsigned)__popc(bal & ((1u << lane) - 1u))] =
+            ((unsigned long long)(unsigned)ii << 32) | pp;
+      off += (unsigned)__popc(bal);
     }
     __syncwarp();  // the row is reset before the next one adds into it
   }
@@ -398,7 +413,8 @@ QTV_API int qtv_node_circulation_faces(qtv_handle h, const qtv_grid* grid, const
   if (capacity > 0 && (!node_ids || !circ)) return set_error(QTV_ERR_ARG, "output lists are NULL");
   if (n >= (1ull << 32)) return set_error(QTV_ERR_ARG, "more than 2^32 - 1 faces");
   const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
-  const size_t smem = (size_t)kNfWarps * (size_t)(nx + (nx + 31) / 32) * sizeof(uint32_t);
+  const size_t smem =
+      (size_t)kNfWarps * (size_t)(nx + (nx + 31) / 32 + (nx + 1) / 2) * sizeof(uint32_t);
   if (smem > 200 * 1024)
     return set_error(QTV_ERR_ARG, "rows of %d nodes are too wide for the face-derived node form", nx);
   const long long R = (long long)ny * nz;
