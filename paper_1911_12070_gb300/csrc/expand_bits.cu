@@ -134,11 +134,13 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kBitsExpandCtasPerSm) expan
         racc[2 * q + 1] += (tot[q] >> 8) & 0x00FF00FFu;
       }
     };
-    // pass 1: faces per row over the segment's records
+    // pass 1: faces per row over the segment's records (byte sums over the
+    // lanes: at most 3 x 32 per byte, no carry between bytes)
     auto tally = [&](const uint4& rec) {
-      uint32_t cw[4], ex[4], tot[4];
+      uint32_t cw[4], tot[4];
       counts(rec, cw);
-      scan4(cw, ex, tot);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) tot[q] = __reduce_add_sync(0xffffffffu, cw[q]);
       add_tot(tot);
     };
     const unsigned long long lin0 = ((unsigned long long)k * ny + (unsigned long long)j0) * nx;
