@@ -964,6 +964,20 @@ def run_qtv(args):
     ms_e2e = e0.elapsed_time(e1)
     if ws > 1:
         ms_e2e = slowest_ms(ms_e2e, dev)
+    # the host link alone (outside every timed region): plain copies of the
+    # pinned field to the device, the bound of the end-to-end rate
+    link_dst = torch.empty_like(psi)
+    with torch.cuda.stream(stream):
+        link_dst.copy_(host_psi, non_blocking=True)
+        l0 = torch.cuda.Event(enable_timing=True)
+        l1 = torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        for _ in range(5):
+            link_dst.copy_(host_psi, non_blocking=True)
+        l1.record(stream)
+    torch.cuda.synchronize()
+    link_gbs = 5 * 8 * nodes / (l0.elapsed_time(l1) * 1e-3) / 1e9
+    del link_dst
     clk.stop()
 
     # ---- roofline of the dominant kernel (the sweep)
@@ -1010,6 +1024,10 @@ def run_qtv(args):
                          "K eager steps (sweeps bracketed by events)"),
         "e2e": {"value": job_value(ws, nodes, ke, ms_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * nodes, "d2h_bytes_per_step": d2h // ke},
+        "host_link": {"h2d_gbs": link_gbs,
+                      "e2e_bound": link_gbs * 1e9 / 8 * ws,
+                      "note": "pinned host-to-device copies of the field alone; the "
+                              "end-to-end rate cannot exceed e2e_bound (grid points/s)"},
         "gpu_launches": launches,
         "clocks": clocks,
         "ambiguous_faces": {"gpu": id_stats["ambiguous"], "pierced": id_stats["pierced"],
