@@ -65,6 +65,8 @@ def parse():
                    help="skip the 16-snapshot batch against per-snapshot launches")
     p.add_argument("--no-learned", action="store_true",
                    help="skip training the learned locator and its report against plain")
+    p.add_argument("--no-paper-size", action="store_true",
+                   help="skip the identification + localization of a 2048^3 field")
     p.add_argument("--no-node-form", action="store_true",
                    help="skip the node-form, density-error, refinement, face-graph and line reports")
     return p.parse_args()
@@ -300,6 +302,79 @@ def learned_report(q, psi, ids, wnd, F, stream, reps=20):
         "rms_vs_plain_h": rms_all, "rms_vs_plain_accepted_h": rms_acc,
         "fallback_resid": 1e-3,
     }
+
+
+def paper_size_report(peak, n=2048, waves=1024, reps=5):
+    """Identification + plain localization of one field at the paper's own
+    resolution, n^3 complex64 (2048^3: 64 GiB, the size of the paper's NLKG
+    snapshots), on one GPU: CUDA-event time of `reps` steps after two warm-up
+    steps, with a traced pass for the per-kernel times (the sweep against the
+    HBM peak)."""
+    import torch
+
+    import paper_1911_12070_gb300 as qtv
+    import synth
+
+    nodes = n ** 3
+    free, _ = torch.cuda.mem_get_info()
+    need = 8 * nodes + 24 * 2 ** 30
+    if free < need:
+        return {"skipped": f"needs {need / 2 ** 30:.0f} GiB free, {free / 2 ** 30:.0f} GiB free"}
+    t0 = time.time()
+    psi = synth.random_waves((n, n, n), synth.wave_spec(2048, waves), device="cuda")
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    torch.cuda.empty_cache()  # the generator's temporaries
+    h = qtv.Qtv(0)
+    try:
+        dev = psi.device
+        cap = int(0.02 * nodes)
+        h.reserve((n, n, n), cap)
+        ids = torch.empty(cap, dtype=torch.int64, device=dev)
+        wnd = torch.empty(cap, dtype=torch.int8, device=dev)
+        count = torch.zeros(1, dtype=torch.int64, device=dev)
+        xyz = torch.empty((cap, 3), dtype=torch.float32, device=dev)
+        resid = torch.empty(cap, dtype=torch.float32, device=dev)
+        flags = torch.empty(cap, dtype=torch.uint8, device=dev)
+
+        def step():
+            h.identify_localize_into(psi, ids, wnd, count, xyz, resid, flags)
+
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        F = int(count.item())
+        if F < 0 or F > cap:
+            return {"error": f"count {F} (capacity {cap})"}
+        h.trace_enable(True)
+        h.trace_read(reset=True)
+        step()
+        torch.cuda.synchronize()
+        h.trace_enable(False)
+        per_kernel = {k: v[1] / max(1, v[0]) for k, v in h.trace_read(reset=True).items()}
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        step_bytes = 8 * nodes + 9 * F + F * (9 + 32 + 17)
+        sweep_ms = per_kernel.get("sweep")
+        out = {"grid": [n, n, n], "waves": waves, "field_gib": 8 * nodes / 2 ** 30,
+               "pierced_faces": F, "ms_per_step": ms, "grid_points_per_s": nodes / (ms * 1e-3),
+               "step_hbm_gbs": step_bytes / (ms * 1e-3) / 1e9,
+               "kernels_ms": per_kernel, "generate_s": gen_s,
+               "timing": f"CUDA events over {reps} eager steps after 2 warm-up steps; "
+                         "kernels_ms from one traced step"}
+        if sweep_ms:
+            out["sweep_hbm_frac"] = 8 * nodes / (sweep_ms * 1e-3) / 1e9 / peak
+        return out
+    finally:
+        h.close()
+        del psi
+        torch.cuda.empty_cache()
 
 
 def node_form_report(q, psi, xyz, count, stream, reps=20):
@@ -1047,6 +1122,9 @@ def run_qtv(args):
 
     if rank == 0 and not args.no_batch:
         line["batch"] = batch_report(q, stream, learned=not args.no_learned)
+
+    if rank == 0 and not args.no_paper_size:
+        line["paper_resolution"] = paper_size_report(peak)
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.no_node_form:
         import oracle

@@ -359,7 +359,8 @@ QTV_API int qtv_inject_scan_hold(qtv_handle h, int64_t hold_tile, int64_t spin_c
  * replayed by later calls with the same outputs and mode.
  *
  * qtv_batch_plan: grids[i] / psis[i] (device, complex64, x fastest, 16-byte
- * aligned, even nx <= 1024, periodic = 0) must stay valid and unchanged in
+ * aligned, even nx <= 2048, periodic = 0; rows wider than 1024 columns only
+ * with the bit-sliced sweep) must stay valid and unchanged in
  * place until the next plan or qtv_destroy (new data may be written into the
  * same buffers between runs).  The call runs a counting pass, then picks the
  * sweep shape (warps per x tile, resident CTAs per SM, z-block height) by

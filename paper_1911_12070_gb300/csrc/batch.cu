@@ -333,9 +333,9 @@ int qtv_batch_plan(qtv_handle h, int n, const qtv_grid* grids, const void* const
   if (!grids || !psis) return set_error(QTV_ERR_ARG, "grids or psis is NULL");
   for (int i = 0; i < n; ++i) {
     const qtv_grid& g = grids[i];
-    if (g.nx < 2 || g.ny < 1 || g.nz < 1 || (g.nx & 1) || g.nx > 1024)
-      return set_error(QTV_ERR_ARG, "snapshot %d: grid %d x %d x %d (even nx in [2, 1024], "
-                       "ny, nz >= 1 required)", i, g.nx, g.ny, g.nz);
+    if (g.nx < 2 || g.ny < 1 || g.nz < 1 || (g.nx & 1) || g.nx > 64 * kMaxWarpsX)
+      return set_error(QTV_ERR_ARG, "snapshot %d: grid %d x %d x %d (even nx in [2, %d], "
+                       "ny, nz >= 1 required)", i, g.nx, g.ny, g.nz, 64 * kMaxWarpsX);
     if (g.periodic != 0) return set_error(QTV_ERR_ARG, "snapshot %d: periodic grids are not supported", i);
     if (!(g.h > 0.f)) return set_error(QTV_ERR_ARG, "snapshot %d: grid spacing must be positive", i);
     if (!psis[i] || (reinterpret_cast<uintptr_t>(psis[i]) & 15u))
@@ -380,10 +380,16 @@ int qtv_batch_plan(qtv_handle h, int n, const qtv_grid* grids, const void* const
       }
     }
   }
-  // counting pass with the default shape: the face total sizes the staging of
-  // the candidates (face totals do not depend on the staging size)
+  // counting pass with the default shape (the bit-sliced sweep where a grid
+  // is wider than the nibble sweep takes): the face total sizes the staging
+  // of the candidates (face totals do not depend on the staging size)
   BatchLayout L0;
-  int rc = batch_layout(h->num_sms, n, b->grids.data(), b->psis.data(), TileConfig(), 0, 0, &L0);
+  TileConfig t0;
+  int rc = batch_layout(h->num_sms, n, b->grids.data(), b->psis.data(), t0, 0, 0, &L0);
+  if (rc == QTV_ERR_ARG) {
+    t0.variant = 1;
+    rc = batch_layout(h->num_sms, n, b->grids.data(), b->psis.data(), t0, 0, 0, &L0);
+  }
   if (rc) return rc;
   rc = ensure_scratch(b, L0);
   if (rc) return rc;

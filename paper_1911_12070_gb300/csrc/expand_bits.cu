@@ -14,10 +14,14 @@ using namespace bits;
 // ---------------------------------------------------------------------------
 // Expand: one warp per (snapshot, plane, band) segment writes its faces in
 // ascending face-id order: row by row, within a row by x (tile, warp, lane
-// order of the records), within a node by orientation.
+// order of the records), within a node by orientation.  A band row has up to
+// kBitsBandWarps (tile, warp) steps (nx up to 2048 and more); lane l holds
+// the table entries l E .. l E + E - 1, E = ceil(steps / 32).
 // ---------------------------------------------------------------------------
 constexpr int kExpandWarps = 8;
 constexpr int kHeld = 3;  // record chunks (of 32) a warp keeps in registers
+constexpr int kMaxE = (kBitsBandWarps + 31) / 32;  // table entries per lane
+static_assert(kMaxE == 3, "the entry selection below handles three entries per lane");
 
 // bits 4q..4q+3 of m spread to the low bit of bytes 0..3
 __device__ __forceinline__ uint32_t spread4(uint32_t m, int q) {
@@ -28,7 +32,8 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kBitsExpandCtasPerSm) expan
     const __grid_constant__ BulkParams a, const unsigned long long* __restrict__ seg_off,
     uint64_t* __restrict__ face_ids, int8_t* __restrict__ winding, unsigned long long capacity,
     uint64_t* __restrict__ offsets) {
-  __shared__ uint32_t s_rowbase[kExpandWarps][BR / 2];
+  __shared__ uint32_t s_rowbase[kExpandWarps][BR / 2];  // running offsets within rows
+  __shared__ uint32_t s_base[kExpandWarps][BR];          // first face of each row
   pdl_wait();  // segment offsets and counts of the scan
   pdl_trigger();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -54,22 +59,29 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kBitsExpandCtasPerSm) expan
     const int nbands = sd.nbands;
     const long long k = local / nbands;
     const long long band = local % nbands;
-    // entry of (tile, warp) i = lane: ((band ntx + tile) nwt + warp) nz + k
-    uint2 e = make_uint2(0u, 0u);
-    unsigned long long eidx = 0;
-    if (lane < NW) {
-      eidx = (unsigned long long)sd.tab0 + ((unsigned long long)band * NW + lane) * sd.nz + k;
-      e = table[eidx];
+    // entry of (tile, warp) step i: ((band ntx + tile) nwt + warp) nz + k =
+    // ebase + i nz; lane l holds steps l E + j (their record lane masks)
+    const int E = (NW + 31) >> 5;
+    const int NL = (NW + E - 1) / E;  // lanes holding steps
+    const unsigned long long nzl = (unsigned long long)sd.nz;
+    const unsigned long long ebase =
+        (unsigned long long)sd.tab0 + (unsigned long long)band * (unsigned long long)NW * nzl +
+        (unsigned long long)k;
+    uint32_t em[kMaxE];
+#pragma unroll
+    for (int j = 0; j < kMaxE; ++j) {
+      const int i = lane * E + j;
+      em[j] = (j < E && i < NW) ? table[ebase + (unsigned long long)i * nzl].x : 0u;
     }
     const unsigned long long fbase = seg_off[s];  // loaded alongside the entries
-    const uint32_t n = __popc(e.x);
+    const uint32_t n = __popc(em[0]) + __popc(em[1]) + __popc(em[2]);
     uint32_t incl = n;
 #pragma unroll
     for (int dd = 1; dd < 32; dd <<= 1) {
       const uint32_t x = __shfl_up_sync(0xffffffffu, incl, dd);
       if (lane >= dd) incl += x;
     }
-    const uint32_t start = lane < NW ? incl - n : 0xFFFFFFFFu;
+    const uint32_t start = lane < NL ? incl - n : 0xFFFFFFFFu;
     const uint32_t rtot = __shfl_sync(0xffffffffu, incl, 31);
     if (rtot == 0) continue;
     const unsigned long long nx = (unsigned)sd.nx, ny = (unsigned)sd.ny;
@@ -77,7 +89,9 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kBitsExpandCtasPerSm) expan
     const int nwt = sd.nwt;
     const uint32_t nchunks = (rtot + 31) / 32;
 
-    // record of flattened index g = g0 + lane (zero past the end); ww = its warp
+    // record of flattened index g = g0 + lane (zero past the end); ww = its
+    // (tile, warp) step: the lane holding the step (the last lane whose first
+    // record is at or before g), then the step among that lane's E
     auto load = [&](uint32_t g0, uint4& rec, int& ww) {
       const uint32_t g = g0 + lane;
       int lo = 0;
@@ -85,15 +99,31 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kBitsExpandCtasPerSm) expan
       for (int stp = 16; stp >= 1; stp >>= 1) {
         const int cand = lo + stp;
         const uint32_t sv = __shfl_sync(0xffffffffu, start, cand & 31);
-        if (cand < NW && sv <= g) lo = cand;
+        if (cand < NL && sv <= g) lo = cand;
       }
-      ww = lo;
-      const uint32_t qi = g - __shfl_sync(0xffffffffu, start, lo);
-      const uint32_t mask = __shfl_sync(0xffffffffu, e.x, lo);
-      const unsigned long long ei = __shfl_sync(0xffffffffu, eidx, lo);
+      uint32_t qi = g - __shfl_sync(0xffffffffu, start, lo);
+      uint32_t mask = __shfl_sync(0xffffffffu, em[0], lo);
+      int j = 0;
+      if (E > 1) {  // warp-uniform
+        const uint32_t m1 = __shfl_sync(0xffffffffu, em[1], lo);
+        const uint32_t m2 = __shfl_sync(0xffffffffu, em[2], lo);
+        const uint32_t c0 = __popc(mask), c1 = __popc(m1);
+        if (qi >= c0) {
+          qi -= c0;
+          j = 1;
+          mask = m1;
+          if (qi >= c1) {
+            qi -= c1;
+            j = 2;
+            mask = m2;
+          }
+        }
+      }
+      ww = lo * E + j;
       rec = make_uint4(0u, 0u, 0u, 0u);
       if (g < rtot) {
-        const unsigned long long idx = ei * 32ull + (unsigned)(__fns(mask, 0, (int)qi + 1));
+        const unsigned long long idx = (ebase + (unsigned long long)ww * nzl) * 32ull +
+                                       (unsigned)(__fns(mask, 0, (int)qi + 1));
         if (idx < recs_cap) rec = recs[idx];
       }
     };
@@ -119,11 +149,11 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kBitsExpandCtasPerSm) expan
       }
     };
 
-    // faces per row (pass 1), then in place the running base of each row (pass 2)
-    // Faces per row, then each row's running base, as 16-bit halves: row r in
-    // word 2 (r >> 2) + (r & 1), half (r >> 1) & 1 (the layout of the byte
-    // counts' even and odd bytes).  A segment holds at most 3 x 16 x 992 faces
-    // (32 warps of 31 columns), below 2^16.
+    // Faces per row (pass 1), then the running offset of each row within it
+    // (pass 2), as 16-bit halves: row r in word 2 (r >> 2) + (r & 1), half
+    // (r >> 1) & 1 (the layout of the byte counts' even and odd bytes).  A row
+    // holds at most 3 nx faces, below 2^16; the rows' first faces (up to
+    // 3 x 16 nx in a segment) are kept as 32-bit words in s_base.
     uint32_t racc[BR / 2];
 #pragma unroll
     for (int q = 0; q < BR / 2; ++q) racc[q] = 0;
@@ -168,7 +198,8 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kBitsExpandCtasPerSm) expan
           const int q = r >> 2;
           const uint32_t exq = q == 0 ? ex[0] : (q == 1 ? ex[1] : (q == 2 ? ex[2] : ex[3]));
           const uint32_t rb =
-              (s_rowbase[wib][2 * q + (r & 1)] >> (16 * ((r >> 1) & 1))) & 0xFFFFu;
+              s_base[wib][r] +
+              ((s_rowbase[wib][2 * q + (r & 1)] >> (16 * ((r >> 1) & 1))) & 0xFFFFu);
           unsigned long long pos = fbase + rb + ((exq >> (8 * (r & 3))) & 0xFFu);
           const unsigned long long lin = lin0 + (unsigned long long)((uint32_t)r * (uint32_t)nx + x);
           const uint32_t Ls[3] = {rec.x, rec.y, rec.z};
@@ -187,20 +218,19 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kBitsExpandCtasPerSm) expan
       }
       add_tot(tot);
     };
-    // row totals -> exclusive row bases, in place
+    // row totals -> each row's first face (32-bit, shared with the lanes);
+    // the running offsets within rows start at zero
     auto bases = [&]() {
-      uint32_t acc = 0, out[BR / 2];
-#pragma unroll
-      for (int q = 0; q < BR / 2; ++q) out[q] = 0;
+      uint32_t acc = 0;
 #pragma unroll
       for (int r = 0; r < BR; ++r) {
         const int wi = 2 * (r >> 2) + (r & 1), sh = 16 * ((r >> 1) & 1);
-        const uint32_t t = (racc[wi] >> sh) & 0xFFFFu;
-        out[wi] |= acc << sh;
-        acc += t;
+        if (lane == r) s_base[wib][r] = acc;
+        acc += (racc[wi] >> sh) & 0xFFFFu;
       }
 #pragma unroll
-      for (int q = 0; q < BR / 2; ++q) racc[q] = out[q];
+      for (int q = 0; q < BR / 2; ++q) racc[q] = 0;
+      __syncwarp();
     };
 
     if (nchunks <= (uint32_t)kHeld) {

@@ -588,7 +588,7 @@ int identify_needs(qtv_handle h, int num_sms, const qtv_grid& g, uint64_t capaci
   *n = IdentNeeds();
   const uint64_t nbands = (uint64_t)(g.ny + R - 1) / R;
   const uint64_t nseg = nbands * (uint64_t)g.nz;
-  if (sweep_bulk_supported(g.nx, g.ny, g.nz, psi)) {
+  if (staged_variant(h, g.nx, g.ny, g.nz, psi) >= 0) {
     BulkNeeds b;
     const int rc = bulk_needs(h, num_sms, g, capacity, max_warps, &b);
     if (rc) return rc;
@@ -609,7 +609,7 @@ int identify_launch(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t
                     int8_t* winding, uint64_t capacity, uint64_t* count, qtv_stats* stats,
                     cudaStream_t st, const IdentScratch& sc, uint64_t max_warps, float* xyz,
                     float* resid, uint8_t* flags) {
-  if (sweep_bulk_supported(g.nx, g.ny, g.nz, psi)) {
+  if (staged_variant(h, g.nx, g.ny, g.nz, psi) >= 0) {
     const int rc = bulk_identify(h, g, psi, face_ids, winding, capacity, count, stats, st, sc,
                                  max_warps, xyz, resid, flags);
     if (rc) return rc;

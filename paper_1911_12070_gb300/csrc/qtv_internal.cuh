@@ -345,6 +345,10 @@ void bits_sweep_launch(const BulkParams& p, int grid, int nw, int stages, size_t
                        cudaStream_t st);
 // resident CTAs per SM of the bit-sliced expand kernel (its launch bound)
 constexpr int kBitsExpandCtasPerSm = 3;
+// (tile, warp) steps per band row the bit-sliced expand handles (31 columns
+// each: nx up to 2976); the nibble sweep's expand handles 32
+constexpr int kBitsBandWarps = 96;
+constexpr int kNibbleBandWarps = 32;
 cudaError_t bits_expand_launch(const BulkParams& p, int blocks, const unsigned long long* seg_off,
                                uint64_t* face_ids, int8_t* winding, unsigned long long capacity,
                                uint64_t* offsets, cudaStream_t st);
@@ -356,7 +360,12 @@ int batch_launch(qtv_handle h, BatchLayout& B, const IdentScratch& sc, uint64_t*
                  const SweepBranches* br);
 int batch_sweep_only(qtv_handle h, BatchLayout& B, const IdentScratch& sc, cudaStream_t st,
                      const SweepBranches* br);
-bool sweep_bulk_supported(int nx, int ny, int nz, const void* psi);
+// whether a staged sweep (variant 1: bit-sliced, 0: nibble) can take a grid
+bool sweep_bulk_supported(int variant, int nx, int ny, int nz, const void* psi);
+// the staged sweep a single-snapshot call of handle h takes for a grid: the
+// handle's variant when it can, else the nibble sweep when that can, else -1
+// (the register sweep of identify.cu)
+int staged_variant(const qtv_handle_s* h, int nx, int ny, int nz, const void* psi);
 int bulk_needs(qtv_handle h, int num_sms, const qtv_grid& g, uint64_t capacity,
                uint64_t max_warps, BulkNeeds* n);
 int bulk_identify(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t* face_ids,

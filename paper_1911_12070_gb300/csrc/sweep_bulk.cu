@@ -909,9 +909,13 @@ int bulk_variant_occupancy(int nw, int* ctas_per_sm, size_t* smem) {
   return QTV_OK;
 }
 
-bool sweep_bulk_supported(int nx, int ny, int nz, const void* psi) {
-  if (nx < 2 || ny < 1 || nz < 1 || (nx & 1) || nx > 1024) return false;
+bool sweep_bulk_supported(int variant, int nx, int ny, int nz, const void* psi) {
+  if (nx < 2 || ny < 1 || nz < 1 || (nx & 1)) return false;
   if (reinterpret_cast<uintptr_t>(psi) & 15u) return false;
+  // bit-sliced: tiles of 31 nwt columns for any nwt, at most kBitsBandWarps
+  // (tile, warp) steps per band row at nwt = 4 (tiles of 124 columns)
+  if (variant == 1) return (nx + 123) / 124 * 4 <= kBitsBandWarps;
+  if (nx > 1024) return false;
   return bulk_smem_for_warps((nx + 63) / 64) <= 227u * 1024u;
 }
 
@@ -938,9 +942,10 @@ int batch_layout(int num_sms, int nsnap, const qtv_grid* grids, const float2* co
   long long nseg = 0, tab = 0;
   for (int i = 0; i < nsnap; ++i) {
     const qtv_grid& g = grids[i];
-    if (!sweep_bulk_supported(g.nx, g.ny, g.nz, psis[i]))
+    if (!sweep_bulk_supported(tc.variant, g.nx, g.ny, g.nz, psis[i]))
       return set_error(QTV_ERR_ARG, "snapshot %d (%d x %d x %d): the staged sweep needs even nx "
-                       "<= 1024 and a 16-byte aligned field", i, g.nx, g.ny, g.nz);
+                       "(<= 1024 for the nibble sweep) and a 16-byte aligned field", i, g.nx,
+                       g.ny, g.nz);
     SnapDesc& d = fin.s[i];
     d.psi = psis[i];
     d.nx = g.nx;
@@ -965,9 +970,10 @@ int batch_layout(int num_sms, int nsnap, const qtv_grid* grids, const float2* co
       int rc = snap_tiles(g.nx, d.nwt, &d.ntx, &d.st);
       if (rc) return rc;
     }
-    if (d.ntx * d.nwt > 32)
-      return set_error(QTV_ERR_ARG, "snapshot %d: %d tiles of %d warps exceed 32 warps per row",
-                       i, d.ntx, d.nwt);
+    const int max_row_warps = bits ? kBitsBandWarps : kNibbleBandWarps;
+    if (d.ntx * d.nwt > max_row_warps)
+      return set_error(QTV_ERR_ARG, "snapshot %d: %d tiles of %d warps exceed %d warps per row",
+                       i, d.ntx, d.nwt, max_row_warps);
     d.seg0 = nseg;
     d.tab0 = tab;
     nseg += (long long)d.nbands * g.nz;
@@ -1179,14 +1185,22 @@ TileConfig handle_sweep_config(const qtv_handle_s* h) {
   return tc;
 }
 
+int staged_variant(const qtv_handle_s* h, int nx, int ny, int nz, const void* psi) {
+  const int v = handle_sweep_config(h).variant;
+  if (sweep_bulk_supported(v, nx, ny, nz, psi)) return v;
+  if (v != 0 && sweep_bulk_supported(0, nx, ny, nz, psi)) return 0;
+  return -1;
+}
+
 namespace {
 // Layout of a single snapshot in the handle's shape; a grid the bit-sliced
-// sweep cannot tile (more than 32 warps per row) takes the nibble sweep.
+// sweep cannot tile (too many warps per row for the handle's tile width)
+// takes the nibble sweep where that can.
 int single_layout(qtv_handle h, int num_sms, const qtv_grid& g, const float2* psi,
                   uint64_t capacity, uint64_t max_warps, BatchLayout* B) {
   TileConfig tc = handle_sweep_config(h);
   int rc = batch_layout(num_sms, 1, &g, &psi, tc, capacity, max_warps, B);
-  if (rc && tc.variant == 1) {
+  if (rc && tc.variant == 1 && sweep_bulk_supported(0, g.nx, g.ny, g.nz, psi)) {
     TileConfig t0;
     rc = batch_layout(num_sms, 1, &g, &psi, t0, capacity, max_warps, B);
   }

@@ -6,7 +6,8 @@ launch, one finalize pass and one localization pass, replayed as a CUDA graph.
   bit on unambiguous faces (windings) and within 1e-4 h (positions), for each
   sweep shape (nibble sweep: one tile width of 64 to 1024 columns for all
   snapshots, or one sweep per row-width group, serial or concurrent;
-  bit-sliced sweep: tiles of 62, 124 or 248 columns, 2 or 3 ring stages;
+  bit-sliced sweep: tiles of 62, 124 or 248 columns, 2 or 3 ring stages,
+  rows up to 2048 columns;
   various CTAs per SM and z-block heights), shapes pinned through a
   tune-cache line with the key "*";
 * the slices equal the single-snapshot calls bit for bit (ids, windings, plain
@@ -33,9 +34,11 @@ torch = pytest.importorskip("torch")
 
 SMALL = [(20, 40, 130), (13, 29, 64), (9, 15, 1024), (7, 33, 200), (16, 16, 2), (1, 5, 6),
          (25, 31, 384), (3, 8, 66)]
-# the bit-sliced sweep tiles rows of at most 32 warps x 31 columns = 992
+# the bit-sliced sweep also takes rows wider than the nibble sweep's 1024
+# columns (up to 96 tile warps of 31 columns per band row)
 SMALL_BITS = [(20, 40, 130), (13, 33, 64), (9, 15, 992), (7, 34, 200), (16, 16, 2), (1, 5, 6),
-              (25, 31, 384), (3, 8, 66), (6, 17, 124), (5, 18, 126)]
+              (25, 31, 384), (3, 8, 66), (6, 17, 124), (5, 18, 126), (4, 20, 2048),
+              (3, 18, 1986)]
 
 
 @pytest.fixture(scope="module")
@@ -120,6 +123,20 @@ def test_small_batch_bit_sliced_sweep_matches_oracle(q, small_batch_bits, shape)
     assert info["source"] == 1 and info["variant"] == 1 and info["warps_per_tile"] == nwt
     out = q.batch_run()
     _check_slices(hosts, out)
+
+
+def test_wide_snapshots_autotuned(q):
+    # snapshots wider than the nibble sweep's 1024 columns: the counting pass
+    # and every candidate the autotuner keeps use the bit-sliced sweep
+    hosts, devs = _fields([(4, 20, 2048), (6, 24, 130), (3, 17, 1538)], 370)
+    with tempfile.TemporaryDirectory() as d:
+        info = q.batch_plan(devs, tune_cache=os.path.join(d, "tune.txt"))
+    assert info["source"] == 2 and info["variant"] == 1
+    out = q.batch_run()
+    _check_slices(hosts, out)
+    for dev, d in zip(devs, out):
+        ids, w, _ = q.identify(dev)
+        assert torch.equal(ids, d["ids"]) and torch.equal(w, d["w"])
 
 
 def test_batch_equals_single_calls(q, small_batch):

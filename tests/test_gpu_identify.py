@@ -4,7 +4,8 @@ The CUDA winding field must equal the FP64 oracle bit for bit on every face
 whose edge phase differences lie at least 1e-4 rad from +-pi; the remaining
 faces are counted and reported.  Sizes span several CTA bands and warps,
 ragged tails in x, y and z, odd nx (scalar-load path), nx above 512 (wider
-CTAs), degenerate grids, non-finite input, capacity overflow, and the full
+CTAs) and up to 2048 (more than 32 tile warps per band row), a field with
+every face pierced, degenerate grids, non-finite input, capacity overflow, and the full
 512^3 workload that the benchmark times (checked on sampled planes), each
 with the nibble sweep and with the bit-sliced sweep.
 """
@@ -23,8 +24,8 @@ torch = pytest.importorskip("torch")
 @pytest.fixture(scope="module", params=[0, 1], ids=["nibble", "bits"])
 def q(request):
     """A handle whose single-snapshot calls use the nibble sweep or the
-    bit-sliced sweep (rows wider than 992 columns fall back to the nibble
-    sweep); every test runs with both."""
+    bit-sliced sweep (rows wider than 1024 columns take the register sweep
+    with the nibble setting); every test runs with both."""
     import paper_1911_12070_gb300 as qtv
 
     qtv.build()
@@ -65,7 +66,8 @@ def test_config0_analytic_bit_exact(q):
 @pytest.mark.parametrize("shape", [(33, 45, 67), (40, 50, 130), (20, 29, 200), (9, 15, 1024),
                                    (6, 8, 1999), (7, 14, 64), (17, 7, 128), (12, 13, 2),
                                    (11, 33, 248), (5, 16, 126), (8, 17, 992), (6, 31, 124),
-                                   (4, 48, 250), (13, 3, 62)])
+                                   (4, 48, 250), (13, 3, 62), (4, 20, 1026), (5, 33, 1538),
+                                   (3, 18, 1986), (4, 17, 1996), (3, 40, 2048)])
 def test_ragged_random_waves_bit_exact(q, shape):
     psi = _waves(shape, seed=sum(shape))
     n, namb, damb = _check_full(q, psi)
@@ -80,6 +82,27 @@ def test_dense_tangles_bit_exact(q, shape, kmin, kmax):
     psi = synth.random_waves_numpy(shape, synth.wave_spec(sum(shape), 512, kmin=kmin, kmax=kmax))
     n, namb, damb = _check_full(q, psi)
     assert n > 0.03 * psi.size
+
+
+def _all_pierced(shape):
+    """A field whose every plaquette of all three orientations is pierced:
+    phases 2 pi f / 5 with f a fixed pattern of period 2 in x, y and z (edge
+    differences 0, +-2 pi / 5, +-4 pi / 5, none near +-pi), unit modulus."""
+    f = np.array([0, 0, 1, 3, 3, 2, 1, 4])  # f[x % 2 + 2 (y % 2) + 4 (z % 2)]
+    z, y, x = np.indices(shape)
+    th = 2 * np.pi * f[x % 2 + 2 * (y % 2) + 4 * (z % 2)] / 5
+    return np.exp(1j * th).astype(np.complex64)
+
+
+@pytest.mark.parametrize("shape", [(3, 17, 2048), (3, 35, 1000), (4, 20, 66)])
+def test_every_face_pierced(q, shape):
+    # a 16-row band of a 2048-column plane then holds 3 x 16 x 2047 faces,
+    # above 2^16: the expand pass's row offsets must not wrap
+    psi = _all_pierced(shape)
+    nz, ny, nx = shape
+    full = (nx - 1) * (ny - 1) * nz + nx * (ny - 1) * (nz - 1) + (nx - 1) * ny * (nz - 1)
+    n, namb, damb = _check_full(q, psi)
+    assert n == full and namb == 0
 
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (2, 2, 2), (1, 5, 6), (3, 1, 7), (4, 6, 1),
