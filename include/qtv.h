@@ -79,7 +79,11 @@ extern "C" {
 typedef struct qtv_handle_s* qtv_handle;
 
 /* Grid geometry.  h and origin only scale and shift output positions:
- * node (i,j,k) sits at origin + h*(i,j,k).  periodic must be 0. */
+ * node (i,j,k) sits at origin + h*(i,j,k).  periodic must be 0.  Sizes: nx up
+ * to 2048, any ny and nz (node indices are 64-bit, so grids beyond 2^32
+ * nodes such as 2048^3 work).  Even nx with a 16-byte aligned field takes the
+ * staged sweeps (the bit-sliced default up to 2048 columns, the nibble sweep
+ * up to 1024); odd nx or an 8-byte aligned field takes the register sweep. */
 typedef struct {
   int32_t nx, ny, nz;
   float h;
