@@ -776,6 +776,10 @@ int node_circulation_launch(qtv_handle h, const qtv_grid& g, const float2* psi,
   const long long launch_warps = (long long)launch_blocks(w, nitems) * NODE_WARPS;
   const uint64_t recs_need = capacity + capacity / 7 + 1 + (uint64_t)launch_warps * kChunk;
   static_assert(NB * NCOL * 8 <= (int)kChunk, "chunk slack bound");
+  // table entries keep 32-bit staging offsets
+  if (recs_need > 0xFFFFFFFFull)
+    return set_error(QTV_ERR_ARG, "node form: %llu staging records (capacity %llu) exceed 2^32",
+                     (unsigned long long)recs_need, (unsigned long long)capacity);
   rc = grow(w->recs, w->recs_cap, recs_need, st, "cudaMalloc(node records)");
   if (!rc) rc = grow(w->table, w->table_cap, ntab, st, "cudaMalloc(node table)");
   if (!rc) rc = grow(w->segtot, w->segtot_cap, (uint64_t)nseg, st, "cudaMalloc(node totals)");

@@ -9,7 +9,8 @@ grid has none, and every well-conditioned position is within 1e-4 h (plus
 half an FP32 ulp of the absolute coordinate, about 1.2e-4 h at z = 2047).
 The list is strictly ascending over the whole field.  Both the bit-sliced
 sweep (the default) and, with the nibble setting, the register sweep (rows
-wider than the nibble sweep's 1024 columns) are checked.
+wider than the nibble sweep's 1024 columns) are checked.  The node form from
+psi and from the face list give the same vortex nodes and circulations there.
 """
 import numpy as np
 import pytest
@@ -87,3 +88,16 @@ def test_paper_resolution_face_by_face(q, field):
         checked += int(ok.sum())
     print(f"2048^3: {n} pierced faces; {checked} positions checked on {len(PLANES)} planes")
     assert checked > 50_000
+
+
+def test_paper_resolution_node_form(q, field):
+    """The node form (Sec. 2.2.2) at 2048^3, from psi and from the face list:
+    the same vortex nodes and ring circulations, node for node."""
+    ids, w, _ = q.identify(field)
+    a_ids, a_circ, _ = q.node_circulation(field)
+    b_ids, b_circ, tie = q.node_circulation_faces(tuple(field.shape), ids, w)
+    del ids, w
+    assert not tie
+    assert a_ids.numel() > 10_000_000
+    assert bool(torch.all(a_ids[1:] > a_ids[:-1]))
+    assert torch.equal(a_ids, b_ids) and torch.equal(a_circ, b_circ)
