@@ -317,7 +317,7 @@ def paper_size_report(peak, n=2048, waves=1024, reps=5):
 
     nodes = n ** 3
     free, _ = torch.cuda.mem_get_info()
-    need = 8 * nodes + 24 * 2 ** 30
+    need = 8 * nodes + 48 * 2 ** 30
     if free < need:
         return {"skipped": f"needs {need / 2 ** 30:.0f} GiB free, {free / 2 ** 30:.0f} GiB free"}
     t0 = time.time()
@@ -370,11 +370,58 @@ def paper_size_report(peak, n=2048, waves=1024, reps=5):
                          "kernels_ms from one traced step"}
         if sweep_ms:
             out["sweep_hbm_frac"] = 8 * nodes / (sweep_ms * 1e-3) / 1e9 / peak
+        out["node_form"] = paper_size_node_form(h, psi, ids[:F], wnd[:F], peak)
         return out
     finally:
         h.close()
         del psi
         torch.cuda.empty_cache()
+
+
+def paper_size_node_form(h, psi, fids, fw, peak, reps=3):
+    """The node form (Sec. 2.2.2) of the paper-resolution field, from psi and
+    from the face list: CUDA-event time per call after one warm-up call, and
+    whether the two lists are equal."""
+    import torch
+
+    from paper_1911_12070_gb300 import QtvError
+
+    dev = psi.device
+    shape = tuple(psi.shape)
+    nodes = psi.numel()
+    try:
+        cap = int(0.06 * nodes)
+        n_ids = torch.empty(cap, dtype=torch.int64, device=dev)
+        n_circ = torch.empty((cap, 3), dtype=torch.int8, device=dev)
+        n_cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        f_ids = torch.empty(cap, dtype=torch.int64, device=dev)
+        f_circ = torch.empty((cap, 3), dtype=torch.int8, device=dev)
+        f_cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        f_tie = torch.zeros(1, dtype=torch.int32, device=dev)
+        times = {}
+        for name, call in (("from_psi", lambda: h.node_circulation_into(psi, n_ids, n_circ, n_cnt)),
+                           ("from_faces", lambda: h.node_circulation_faces_into(
+                               shape, fids, fw, f_ids, f_circ, f_cnt, f_tie))):
+            call()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                call()
+            e1.record()
+            torch.cuda.synchronize()
+            times[name] = e0.elapsed_time(e1) / reps
+        nv, fn = int(n_cnt.item()), int(f_cnt.item())
+        if nv > cap or fn > cap:
+            return {"error": f"vortex nodes {max(nv, fn)} above capacity {cap}"}
+        return {"vortex_nodes": nv, "ms_from_psi": times["from_psi"],
+                "ms_from_faces": times["from_faces"], "tie": bool(int(f_tie.item())),
+                "equal": bool(fn == nv and torch.equal(f_ids[:fn], n_ids[:nv])
+                              and torch.equal(f_circ[:fn], n_circ[:nv])),
+                "from_psi_hbm_frac": (8 * nodes + 11 * nv) / (times["from_psi"] * 1e-3) / 1e9 / peak}
+    except QtvError as err:
+        return {"error": str(err)}
 
 
 def node_form_report(q, psi, xyz, count, stream, reps=20):
