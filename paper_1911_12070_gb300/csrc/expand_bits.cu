@@ -28,6 +28,9 @@ __device__ __forceinline__ uint32_t spread4(uint32_t m, int q) {
   return (((m >> (4 * q)) & 0xFu) * 0x00204081u) & 0x01010101u;
 }
 
+// MAXE: table entries a lane may hold (1 when every band row has at most 32
+// (tile, warp) steps, the common case, compiled without the wider selection)
+template <int MAXE>
 __global__ void __launch_bounds__(32 * kExpandWarps, kBitsExpandCtasPerSm) expand_bits_kernel(
     const __grid_constant__ BulkParams a, const unsigned long long* __restrict__ seg_off,
     uint64_t* __restrict__ face_ids, int8_t* __restrict__ winding, unsigned long long capacity,
@@ -61,20 +64,22 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kBitsExpandCtasPerSm) expan
     const long long band = local % nbands;
     // entry of (tile, warp) step i: ((band ntx + tile) nwt + warp) nz + k =
     // ebase + i nz; lane l holds steps l E + j (their record lane masks)
-    const int E = (NW + 31) >> 5;
+    const int E = MAXE == 1 ? 1 : (NW + 31) >> 5;
     const int NL = (NW + E - 1) / E;  // lanes holding steps
     const unsigned long long nzl = (unsigned long long)sd.nz;
     const unsigned long long ebase =
         (unsigned long long)sd.tab0 + (unsigned long long)band * (unsigned long long)NW * nzl +
         (unsigned long long)k;
-    uint32_t em[kMaxE];
+    uint32_t em[MAXE];
 #pragma unroll
-    for (int j = 0; j < kMaxE; ++j) {
+    for (int j = 0; j < MAXE; ++j) {
       const int i = lane * E + j;
       em[j] = (j < E && i < NW) ? table[ebase + (unsigned long long)i * nzl].x : 0u;
     }
     const unsigned long long fbase = seg_off[s];  // loaded alongside the entries
-    const uint32_t n = __popc(em[0]) + __popc(em[1]) + __popc(em[2]);
+    uint32_t n = 0;
+#pragma unroll
+    for (int j = 0; j < MAXE; ++j) n += __popc(em[j]);
     uint32_t incl = n;
 #pragma unroll
     for (int dd = 1; dd < 32; dd <<= 1) {
@@ -104,9 +109,9 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kBitsExpandCtasPerSm) expan
       uint32_t qi = g - __shfl_sync(0xffffffffu, start, lo);
       uint32_t mask = __shfl_sync(0xffffffffu, em[0], lo);
       int j = 0;
-      if (E > 1) {  // warp-uniform
-        const uint32_t m1 = __shfl_sync(0xffffffffu, em[1], lo);
-        const uint32_t m2 = __shfl_sync(0xffffffffu, em[2], lo);
+      if constexpr (MAXE > 1) if (E > 1) {  // warp-uniform
+        const uint32_t m1 = __shfl_sync(0xffffffffu, em[1 % MAXE], lo);
+        const uint32_t m2 = __shfl_sync(0xffffffffu, em[2 % MAXE], lo);
         const uint32_t c0 = __popc(mask), c1 = __popc(m1);
         if (qi >= c0) {
           qi -= c0;
@@ -152,8 +157,10 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kBitsExpandCtasPerSm) expan
     // Faces per row (pass 1), then the running offset of each row within it
     // (pass 2), as 16-bit halves: row r in word 2 (r >> 2) + (r & 1), half
     // (r >> 1) & 1 (the layout of the byte counts' even and odd bytes).  A row
-    // holds at most 3 nx faces, below 2^16; the rows' first faces (up to
-    // 3 x 16 nx in a segment) are kept as 32-bit words in s_base.
+    // holds at most 3 nx faces, below 2^16.  With at most 32 (tile, warp)
+    // steps a row (nx <= 992) a whole segment holds fewer than 3 x 16 x 992 <
+    // 2^16 faces and the halves carry the running row bases themselves;
+    // otherwise the rows' first faces are kept as 32-bit words in s_base.
     uint32_t racc[BR / 2];
 #pragma unroll
     for (int q = 0; q < BR / 2; ++q) racc[q] = 0;
@@ -197,9 +204,8 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kBitsExpandCtasPerSm) expan
           rm &= rm - 1u;
           const int q = r >> 2;
           const uint32_t exq = q == 0 ? ex[0] : (q == 1 ? ex[1] : (q == 2 ? ex[2] : ex[3]));
-          const uint32_t rb =
-              s_base[wib][r] +
-              ((s_rowbase[wib][2 * q + (r & 1)] >> (16 * ((r >> 1) & 1))) & 0xFFFFu);
+          uint32_t rb = (s_rowbase[wib][2 * q + (r & 1)] >> (16 * ((r >> 1) & 1))) & 0xFFFFu;
+          if constexpr (MAXE > 1) rb += s_base[wib][r];
           unsigned long long pos = fbase + rb + ((exq >> (8 * (r & 3))) & 0xFFu);
           const unsigned long long lin = lin0 + (unsigned long long)((uint32_t)r * (uint32_t)nx + x);
           const uint32_t Ls[3] = {rec.x, rec.y, rec.z};
@@ -218,19 +224,34 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kBitsExpandCtasPerSm) expan
       }
       add_tot(tot);
     };
-    // row totals -> each row's first face (32-bit, shared with the lanes);
-    // the running offsets within rows start at zero
+    // row totals -> each row's first face: 32-bit words shared with the lanes
+    // (the running offsets within rows then start at zero), or for narrow
+    // rows the 16-bit halves themselves
     auto bases = [&]() {
       uint32_t acc = 0;
+      if constexpr (MAXE > 1) {
 #pragma unroll
-      for (int r = 0; r < BR; ++r) {
-        const int wi = 2 * (r >> 2) + (r & 1), sh = 16 * ((r >> 1) & 1);
-        if (lane == r) s_base[wib][r] = acc;
-        acc += (racc[wi] >> sh) & 0xFFFFu;
+        for (int r = 0; r < BR; ++r) {
+          const int wi = 2 * (r >> 2) + (r & 1), sh = 16 * ((r >> 1) & 1);
+          if (lane == r) s_base[wib][r] = acc;
+          acc += (racc[wi] >> sh) & 0xFFFFu;
+        }
+#pragma unroll
+        for (int q = 0; q < BR / 2; ++q) racc[q] = 0;
+        __syncwarp();
+      } else {
+        uint32_t out[BR / 2];
+#pragma unroll
+        for (int q = 0; q < BR / 2; ++q) out[q] = 0;
+#pragma unroll
+        for (int r = 0; r < BR; ++r) {
+          const int wi = 2 * (r >> 2) + (r & 1), sh = 16 * ((r >> 1) & 1);
+          out[wi] |= acc << sh;
+          acc += (racc[wi] >> sh) & 0xFFFFu;
+        }
+#pragma unroll
+        for (int q = 0; q < BR / 2; ++q) racc[q] = out[q];
       }
-#pragma unroll
-      for (int q = 0; q < BR / 2; ++q) racc[q] = 0;
-      __syncwarp();
     };
 
     if (nchunks <= (uint32_t)kHeld) {
@@ -271,7 +292,12 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kBitsExpandCtasPerSm) expan
 cudaError_t bits_expand_launch(const BulkParams& p, int blocks, const unsigned long long* seg_off,
                                uint64_t* face_ids, int8_t* winding, unsigned long long capacity,
                                uint64_t* offsets, cudaStream_t st) {
-  return launch_dependent(expand_bits_kernel, dim3(blocks), dim3(32 * kExpandWarps), 0, st, p,
+  bool wide = false;
+  for (int i = 0; i < p.nsnap; ++i) wide |= p.s[i].ntx * p.s[i].nwt > 32;
+  if (wide)
+    return launch_dependent(expand_bits_kernel<kMaxE>, dim3(blocks), dim3(32 * kExpandWarps), 0,
+                            st, p, seg_off, face_ids, winding, capacity, offsets);
+  return launch_dependent(expand_bits_kernel<1>, dim3(blocks), dim3(32 * kExpandWarps), 0, st, p,
                           seg_off, face_ids, winding, capacity, offsets);
 }
 
