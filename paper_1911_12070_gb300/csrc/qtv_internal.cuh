@@ -197,8 +197,9 @@ int identify_launch(qtv_handle h, const qtv_grid& g, const float2* psi, uint64_t
                     cudaStream_t st, const IdentScratch& sc, uint64_t max_warps,
                     float* xyz = nullptr, float* resid = nullptr, uint8_t* flags = nullptr);
 
-// Bulk-copy staged sweep with per-warp compaction (sweep_bulk.cu): even
-// nx <= 1024, 16-byte aligned psi.
+// Bulk-copy staged sweeps (sweep_bulk.cu, sweep_bits.cu): even nx and a
+// 16-byte aligned psi; nx <= 1024 for the nibble sweep, <= 2048 for the
+// bit-sliced one.
 struct BulkNeeds {
   uint64_t recs = 0, table = 0, seg_off = 0, tiles = 0, segf = 0;
 };
