@@ -1077,8 +1077,10 @@ def run_qtv(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    c0 = time.perf_counter()
     for i in range(ke):
         e2e_step(i)
+    enqueue_ms = (time.perf_counter() - c0) * 1e3 / ke
     e1.record(stream)
     torch.cuda.synchronize()
     assert all(int(c[0]) == F for c in host_cnts), "end-to-end sample count differs"
@@ -1100,6 +1102,23 @@ def run_qtv(args):
     torch.cuda.synchronize()
     link_gbs = 5 * 8 * nodes / (l0.elapsed_time(l1) * 1e-3) / 1e9
     del link_dst
+    # and device-to-host copies of one step's packed samples alone (a
+    # diagnostic: a failure here is reported, not raised)
+    try:
+        d2h_src = torch.empty(cap * 32, dtype=torch.uint8, device=psi.device)
+        with torch.cuda.stream(stream):
+            host_outs[0].copy_(d2h_src, non_blocking=True)
+            d0 = torch.cuda.Event(enable_timing=True)
+            d1 = torch.cuda.Event(enable_timing=True)
+            d0.record(stream)
+            for _ in range(5):
+                host_outs[0].copy_(d2h_src, non_blocking=True)
+            d1.record(stream)
+        torch.cuda.synchronize()
+        d2h_gbs = 5 * cap * 32 / (d0.elapsed_time(d1) * 1e-3) / 1e9
+        del d2h_src
+    except Exception as err:
+        d2h_gbs = f"unmeasured: {err}"
     clk.stop()
 
     # ---- roofline of the dominant kernel (the sweep)
@@ -1147,9 +1166,13 @@ def run_qtv(args):
         "e2e": {"value": job_value(ws, nodes, ke, ms_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * nodes, "d2h_bytes_per_step": d2h // ke},
         "host_link": {"h2d_gbs": link_gbs,
+                      "e2e_enqueue_ms_per_step": enqueue_ms,
+                      "d2h_gbs": d2h_gbs,
                       "e2e_bound": link_gbs * 1e9 / 8 * ws,
                       "note": "pinned host-to-device copies of the field alone; the "
-                              "end-to-end rate cannot exceed e2e_bound (grid points/s)"},
+                              "end-to-end rate cannot exceed e2e_bound (grid points/s); "
+                              "e2e_enqueue_ms_per_step is the host time to issue one "
+                              "end-to-end step"},
         "gpu_launches": launches,
         "clocks": clocks,
         "ambiguous_faces": {"gpu": id_stats["ambiguous"], "pierced": id_stats["pierced"],
